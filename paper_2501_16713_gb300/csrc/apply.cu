@@ -1,0 +1,190 @@
+// Operator application: the process diagrams of the paper as sequences of
+// cuFFT calls and the library's kernels, all on the caller's stream.
+//
+//  T_j   (image-space gridding, forward):  F_N -> K1 (1/C*, Z) -> F_G^H -> K2 (B_j^(i))
+//        The first three steps do not depend on j and run once for all phases.
+//  T^H   (adjoint, summed over phases):    K3 (P_j^(i), all phases into one
+//        grid) -> F_G -> K4 (Z^H, 1/C) -> F_N^H
+//  G_j S (per phase):                       K5 (S, 1/c*, Z) -> F_G (C coils
+//        batched) -> K6 (B^(k))
+//  S^H G_j^H (per phase):                   K7 (P^(k)) -> F_G^H (batched) ->
+//        K8 (Z^H, 1/c, S^H)
+#include "plan_internal.h"
+
+using namespace nrs;
+
+namespace {
+
+#define NRS_TRY(expr)                  \
+  do {                                 \
+    nrsense_status _st = (expr);       \
+    if (_st != NRSENSE_OK) return _st; \
+  } while (0)
+
+nrsense_status fft(cufftHandle h, cudaStream_t s, nrsense_c64* in, nrsense_c64* out, int dir) {
+  if (cufftSetStream(h, s) != CUFFT_SUCCESS) return NRSENSE_ERR_CUFFT;
+  if (cufftExecC2C(h, reinterpret_cast<cufftComplex*>(in), reinterpret_cast<cufftComplex*>(out),
+                   dir) != CUFFT_SUCCESS)
+    return NRSENSE_ERR_CUFFT;
+  return NRSENSE_OK;
+}
+
+nrsense_status launched() {
+  return cudaGetLastError() == cudaSuccess ? NRSENSE_OK : NRSENSE_ERR_CUDA;
+}
+
+// m (P x nvox) = T_j x for all phases
+nrsense_status warp_forward(nrsense_plan_s* p, const nrsense_c64* x, nrsense_c64* m,
+                            cudaStream_t s) {
+  const Geo& g = p->geo;
+  if (p->identity_warp) {
+    launch_copy_phases(g, p->P, x, m, s);
+    return launched();
+  }
+  NRS_TRY(fft(p->fft_n, s, const_cast<nrsense_c64*>(x), p->b_xhat, CUFFT_FORWARD));
+  launch_deapod_pad(g, p->deapod, p->b_xhat, p->b_upad, s);
+  NRS_TRY(launched());
+  NRS_TRY(fft(p->fft_g, s, p->b_upad, p->b_ugrid, CUFFT_INVERSE));
+  launch_interp_image(g, p->W, p->kc, p->P, p->disp, p->b_ugrid, m, s);
+  return launched();
+}
+
+// x = sum_j T_j^H m_j
+nrsense_status warp_adjoint(nrsense_plan_s* p, const nrsense_c64* m, nrsense_c64* x,
+                            cudaStream_t s) {
+  const Geo& g = p->geo;
+  if (p->identity_warp) {
+    launch_sum_phases(g, p->P, m, x, s);
+    return launched();
+  }
+  launch_spread(g, p->W, p->kc, 1, p->tiles, p->ipts, m, p->b_ugrid, p->b_scratch, p->d_status, s);
+  NRS_TRY(launched());
+  NRS_TRY(fft(p->fft_g, s, p->b_ugrid, p->b_ugrid, CUFFT_FORWARD));
+  launch_crop_deapod(g, p->deapod, p->b_ugrid, x, s);
+  NRS_TRY(launched());
+  return fft(p->fft_n, s, x, x, CUFFT_INVERSE);
+}
+
+// y_j (M_j x C) = G_j S m_j
+nrsense_status sense_phase_forward(nrsense_plan_s* p, int j, const nrsense_c64* mj,
+                                   nrsense_c64* yj, cudaStream_t s) {
+  const Geo& g = p->geo;
+  launch_coil_fanout_pad(g, p->C, p->deapod, p->smaps, mj, p->b_xpad, s);
+  NRS_TRY(launched());
+  NRS_TRY(fft(p->fft_gc, s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
+  launch_interp_kspace(g, p->W, p->kc, p->C, p->kpts[j], p->b_xwork, yj, s);
+  return launched();
+}
+
+// w_j (nvox) = S^H G_j^H y_j
+nrsense_status sense_phase_adjoint(nrsense_plan_s* p, int j, const nrsense_c64* yj,
+                                   nrsense_c64* wj, cudaStream_t s) {
+  const Geo& g = p->geo;
+  launch_spread(g, p->W, p->kc, p->C, p->tiles, p->kpts[j], yj, p->b_xwork, p->b_scratch,
+                p->d_status, s);
+  NRS_TRY(launched());
+  NRS_TRY(fft(p->fft_gc, s, p->b_xwork, p->b_xwork, CUFFT_INVERSE));
+  launch_crop_coilsum(g, p->C, p->deapod, p->smaps, p->b_xwork, wj, s);
+  return launched();
+}
+
+}  // namespace
+
+extern "C" {
+
+nrsense_status nrsense_warp_forward(nrsense_plan_t p, const nrsense_c64* x, nrsense_c64* m,
+                                    void* stream) {
+  if (p == nullptr || x == nullptr || m == nullptr) return NRSENSE_ERR_ARG;
+  return warp_forward(p, x, m, static_cast<cudaStream_t>(stream));
+}
+
+nrsense_status nrsense_warp_adjoint(nrsense_plan_t p, const nrsense_c64* m, nrsense_c64* x,
+                                    void* stream) {
+  if (p == nullptr || x == nullptr || m == nullptr) return NRSENSE_ERR_ARG;
+  return warp_adjoint(p, m, x, static_cast<cudaStream_t>(stream));
+}
+
+nrsense_status nrsense_kspace_forward(nrsense_plan_t p, int32_t phase, const nrsense_c64* v,
+                                      nrsense_c64* y, void* stream) {
+  if (p == nullptr || v == nullptr || y == nullptr) return NRSENSE_ERR_ARG;
+  if (p->C == 0) return NRSENSE_ERR_STATE;
+  if (phase < 0 || phase >= p->P) return NRSENSE_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  launch_image_to_padded(p->geo, p->C, p->deapod, v, p->b_xpad, s);
+  NRS_TRY(launched());
+  NRS_TRY(fft(p->fft_gc, s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
+  launch_interp_kspace(p->geo, p->W, p->kc, p->C, p->kpts[phase], p->b_xwork, y, s);
+  return launched();
+}
+
+nrsense_status nrsense_kspace_adjoint(nrsense_plan_t p, int32_t phase, const nrsense_c64* y,
+                                      nrsense_c64* v, void* stream) {
+  if (p == nullptr || v == nullptr || y == nullptr) return NRSENSE_ERR_ARG;
+  if (p->C == 0) return NRSENSE_ERR_STATE;
+  if (phase < 0 || phase >= p->P) return NRSENSE_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  launch_spread(p->geo, p->W, p->kc, p->C, p->tiles, p->kpts[phase], y, p->b_xwork, p->b_scratch,
+                p->d_status, s);
+  NRS_TRY(launched());
+  NRS_TRY(fft(p->fft_gc, s, p->b_xwork, p->b_xwork, CUFFT_INVERSE));
+  launch_crop_to_coils(p->geo, p->C, p->deapod, p->b_xwork, v, s);
+  return launched();
+}
+
+nrsense_status nrsense_apply_forward(nrsense_plan_t p, const nrsense_c64* x, nrsense_c64* y,
+                                     void* stream) {
+  if (p == nullptr || x == nullptr || y == nullptr) return NRSENSE_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->C == 0) return warp_forward(p, x, y, s);
+  NRS_TRY(warp_forward(p, x, p->b_m, s));
+  for (int j = 0; j < p->P; ++j) {
+    if (p->M[j] == 0) continue;
+    NRS_TRY(sense_phase_forward(p, j, p->b_m + (long long)j * p->geo.nvox, y + p->off[j] * p->C, s));
+  }
+  return NRSENSE_OK;
+}
+
+nrsense_status nrsense_apply_adjoint(nrsense_plan_t p, const nrsense_c64* y, nrsense_c64* x,
+                                     void* stream) {
+  if (p == nullptr || x == nullptr || y == nullptr) return NRSENSE_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->C == 0) return warp_adjoint(p, y, x, s);
+  for (int j = 0; j < p->P; ++j) {
+    nrsense_c64* wj = p->b_m + (long long)j * p->geo.nvox;
+    if (p->M[j] == 0) {
+      if (cudaMemsetAsync(wj, 0, size_t(p->geo.nvox) * sizeof(nrsense_c64), s) != cudaSuccess)
+        return NRSENSE_ERR_CUDA;
+      continue;
+    }
+    NRS_TRY(sense_phase_adjoint(p, j, y + p->off[j] * p->C, wj, s));
+  }
+  return warp_adjoint(p, p->b_m, x, s);
+}
+
+nrsense_status nrsense_apply_normal(nrsense_plan_t p, const nrsense_c64* x, double lambda,
+                                    nrsense_c64* out, void* stream) {
+  if (p == nullptr || x == nullptr || out == nullptr || x == out) return NRSENSE_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  NRS_TRY(warp_forward(p, x, p->b_m, s));
+  if (p->C > 0) {
+    for (int j = 0; j < p->P; ++j) {
+      nrsense_c64* mj = p->b_m + (long long)j * p->geo.nvox;
+      if (p->M[j] == 0) {
+        if (cudaMemsetAsync(mj, 0, size_t(p->geo.nvox) * sizeof(nrsense_c64), s) != cudaSuccess)
+          return NRSENSE_ERR_CUDA;
+        continue;
+      }
+      nrsense_c64* yj = p->b_y + p->off[j] * p->C;
+      NRS_TRY(sense_phase_forward(p, j, mj, yj, s));
+      NRS_TRY(sense_phase_adjoint(p, j, yj, mj, s));
+    }
+  }
+  NRS_TRY(warp_adjoint(p, p->b_m, out, s));
+  if (lambda != 0.0) {
+    launch_axpby(p->geo.nvox, x, float(lambda), out, 1.0f, s);
+    NRS_TRY(launched());
+  }
+  return NRSENSE_OK;
+}
+
+}  // extern "C"

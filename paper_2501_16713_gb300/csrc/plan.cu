@@ -1,0 +1,505 @@
+// Plan construction for the nonrigid SENSE operator (host, plan time).
+//
+// nrsense_plan_create validates the problem statement (stacked SENSE
+// equation: P motion states sharing one image, C coils, M_j samples per
+// state), evaluates the kernel polynomials and deapodization tables in FP64,
+// decomposes every k-space sample position q = omega G / (2 pi) and every
+// displaced voxel position q = sigma (n + d_j[n]) into first tap and fraction,
+// sorts the points into 8^3 grid tiles, builds the per-tile halo lists and
+// work items of the output-stationary spreading kernels, and creates the cuFFT
+// plans and work buffers.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "kb_host.h"
+#include "plan_internal.h"
+
+using namespace nrs;
+
+namespace {
+
+// Host-side fault injection for the error paths (NRSENSE_FAULT=alloc|cufft|upload).
+bool fault_requested(const char* what) {
+  const char* f = std::getenv("NRSENSE_FAULT");
+  return f != nullptr && std::strcmp(f, what) == 0;
+}
+
+nrsense_status dev_alloc(nrsense_plan_s* p, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) return NRSENSE_OK;
+  if (fault_requested("alloc")) return NRSENSE_ERR_OOM;
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return NRSENSE_ERR_OOM;
+  }
+  p->allocations.push_back(*ptr);
+  p->device_bytes += (long long)bytes;
+  return NRSENSE_OK;
+}
+
+template <typename T>
+nrsense_status dev_alloc_n(nrsense_plan_s* p, T** ptr, long long n) {
+  return dev_alloc(p, reinterpret_cast<void**>(ptr), size_t(n) * sizeof(T));
+}
+
+template <typename T>
+nrsense_status upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
+  if (src.empty()) return NRSENSE_OK;
+  if (fault_requested("upload")) return NRSENSE_ERR_CUDA;
+  if (cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
+    return NRSENSE_ERR_CUDA;
+  // host vectors are freed by the caller after return: wait here
+  if (cudaStreamSynchronize(s) != cudaSuccess) return NRSENSE_ERR_CUDA;
+  return NRSENSE_OK;
+}
+
+#define NRS_TRY(expr)                          \
+  do {                                         \
+    nrsense_status _st = (expr);               \
+    if (_st != NRSENSE_OK) return _st;         \
+  } while (0)
+
+// (C, nvox) -> (nvox, C) transpose of the coil maps
+__global__ void transpose_maps_kernel(long long nvox, int C, const float2* __restrict__ in,
+                                      float2* __restrict__ out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nvox * C) return;
+  const long long v = t / C;
+  const int c = int(t - v * C);
+  out[t] = in[(long long)c * nvox + v];
+}
+
+struct HostPoint {
+  float f[3];
+  int b[3];
+  int32_t row;
+};
+
+// Decompose a position on the periodic grid: first tap index (mod G) and the
+// fractional offset f = q - floor(q) of the kernel's centre cell.
+inline void decompose(double q, int G, int W, int* base, float* frac) {
+  const double fl = std::floor(q);
+  long long b = (long long)fl - (W / 2 - 1);
+  b %= G;
+  if (b < 0) b += G;
+  *base = int(b);
+  *frac = float(q - fl);
+}
+
+inline int tile_of(int idx, int tile) { return idx / tile; }
+
+// Sort points into tiles, build halo lists and work items, upload.
+nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, PointSet* ps,
+                              cudaStream_t s) {
+  const Geo& g = p->geo;
+  const TilePlan& tp = p->tiles;
+  const int W = p->W;
+  const long long npts = (long long)pts.size();
+  ps->npts = npts;
+  if (npts == 0) return NRSENSE_OK;
+  if (npts >= (1ll << 31)) return NRSENSE_ERR_ARG;
+
+  // primary key: tile of the first tap; secondary: cell inside the tile
+  std::vector<int64_t> key(npts);
+  for (long long i = 0; i < npts; ++i) {
+    const HostPoint& h = pts[i];
+    const long long t = ((long long)tile_of(h.b[0], tp.t0) * tp.nt1 + tile_of(h.b[1], tp.t1)) *
+                            tp.nt2 + tile_of(h.b[2], tp.t2);
+    const int cell = ((h.b[0] % tp.t0) * tp.t1 + (h.b[1] % tp.t1)) * tp.t2 + (h.b[2] % tp.t2);
+    key[i] = t * 4096 + cell;
+  }
+  std::vector<int32_t> order(npts);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  key.clear();
+  key.shrink_to_fit();
+
+  std::vector<float4> qs(npts);
+  std::vector<int32_t> perm(npts);
+  for (long long s_i = 0; s_i < npts; ++s_i) {
+    const HostPoint& h = pts[order[s_i]];
+    const uint32_t packed = pack_base(h.b[0], h.b[1], h.b[2]);
+    float w;
+    std::memcpy(&w, &packed, sizeof(w));
+    qs[s_i] = make_float4(h.f[0], h.f[1], h.f[2], w);
+    perm[s_i] = h.row;
+  }
+
+  // halo lists: every tile touched by a point's W^3 footprint
+  const int gsz[3] = {g.g0, g.g1, g.g2};
+  const int tsz[3] = {tp.t0, tp.t1, tp.t2};
+  const int ntz[3] = {tp.nt0, tp.nt1, tp.nt2};
+  auto touched = [&](const HostPoint& h, int a, int* out) {
+    int n = 0;
+    for (int t = 0; t < W; ++t) {
+      int gi = h.b[a] + t;
+      if (gi >= gsz[a]) gi -= gsz[a];
+      const int ti = gi / tsz[a];
+      bool seen = false;
+      for (int k = 0; k < n; ++k) seen |= (out[k] == ti);
+      if (!seen) out[n++] = ti;
+    }
+    (void)ntz;
+    return n;
+  };
+  std::vector<int64_t> counts(tp.ntiles + 1, 0);
+  for (long long s_i = 0; s_i < npts; ++s_i) {
+    const HostPoint& h = pts[order[s_i]];
+    int t0[8], t1[8], t2[8];
+    const int n0 = touched(h, 0, t0), n1 = touched(h, 1, t1), n2 = touched(h, 2, t2);
+    for (int a = 0; a < n0; ++a)
+      for (int b = 0; b < n1; ++b)
+        for (int c = 0; c < n2; ++c)
+          counts[((long long)t0[a] * tp.nt1 + t1[b]) * tp.nt2 + t2[c] + 1]++;
+  }
+  for (long long t = 0; t < tp.ntiles; ++t) counts[t + 1] += counts[t];
+  const long long list_len = counts[tp.ntiles];
+  if (list_len >= (1ll << 31)) return NRSENSE_ERR_ARG;
+  std::vector<int32_t> list(list_len);
+  std::vector<int64_t> fill(counts.begin(), counts.end() - 1);
+  for (long long s_i = 0; s_i < npts; ++s_i) {
+    const HostPoint& h = pts[order[s_i]];
+    int t0[8], t1[8], t2[8];
+    const int n0 = touched(h, 0, t0), n1 = touched(h, 1, t1), n2 = touched(h, 2, t2);
+    for (int a = 0; a < n0; ++a)
+      for (int b = 0; b < n1; ++b)
+        for (int c = 0; c < n2; ++c)
+          list[fill[((long long)t0[a] * tp.nt1 + t1[b]) * tp.nt2 + t2[c]]++] = int32_t(s_i);
+  }
+  ps->list_len = list_len;
+
+  // work items: every tile (empty tiles write zeros); heavy tiles split
+  std::vector<SpreadItem> items;
+  std::vector<ReduceItem> reds;
+  int slots = 0, occupied = 0;
+  for (long long t = 0; t < tp.ntiles; ++t) {
+    const long long b = counts[t], e = counts[t + 1];
+    const long long L = e - b;
+    if (L > 0) occupied++;
+    if (L <= kSpreadMaxItem) {
+      items.push_back({int32_t(t), int32_t(b), int32_t(e), -1});
+    } else {
+      const int nchunk = int((L + kSpreadMaxItem - 1) / kSpreadMaxItem);
+      const long long step = (L + nchunk - 1) / nchunk;
+      ReduceItem r{int32_t(t), slots, nchunk, 0};
+      for (int k = 0; k < nchunk; ++k) {
+        const long long cb = b + k * step, ce = std::min(e, cb + step);
+        items.push_back({int32_t(t), int32_t(cb), int32_t(ce), slots + k});
+      }
+      slots += nchunk;
+      reds.push_back(r);
+    }
+  }
+  // heaviest first for load balance
+  std::stable_sort(items.begin(), items.end(), [](const SpreadItem& a, const SpreadItem& b) {
+    return (a.end - a.begin) > (b.end - b.begin);
+  });
+  ps->n_items = int(items.size());
+  ps->n_reduces = int(reds.size());
+  ps->n_slots = slots;
+  ps->n_occupied = occupied;
+
+  NRS_TRY(dev_alloc_n(p, &ps->qs, npts));
+  NRS_TRY(dev_alloc_n(p, &ps->perm, npts));
+  NRS_TRY(dev_alloc_n(p, &ps->list, std::max<long long>(list_len, 1)));
+  NRS_TRY(dev_alloc_n(p, &ps->items, (long long)items.size()));
+  NRS_TRY(dev_alloc_n(p, &ps->reduces, std::max<long long>((long long)reds.size(), 1)));
+  NRS_TRY(upload(ps->qs, qs, s));
+  NRS_TRY(upload(ps->perm, perm, s));
+  NRS_TRY(upload(ps->list, list, s));
+  NRS_TRY(upload(ps->items, items, s));
+  NRS_TRY(upload(ps->reduces, reds, s));
+  return NRSENSE_OK;
+}
+
+nrsense_status cufft_check(cufftResult r) {
+  return r == CUFFT_SUCCESS ? NRSENSE_OK : NRSENSE_ERR_CUFFT;
+}
+
+nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const int64_t* n_samples,
+                           const float* coords, const float* disp, const nrsense_c64* smaps,
+                           cudaStream_t s) {
+  const nrsense_desc& d = *desc;
+  for (int a = 0; a < 3; ++a)
+    if (d.n[a] < 4 || (d.n[a] & 1)) return NRSENSE_ERR_ARG;
+  if (d.osf < 2 || d.osf > 4) return NRSENSE_ERR_ARG;
+  if (d.kb_width != 4 && d.kb_width != 6) return NRSENSE_ERR_ARG;
+  if (d.n_phases < 1 || d.n_coils < 0) return NRSENSE_ERR_ARG;
+  if (d.precision != NRSENSE_FP32) return NRSENSE_ERR_ARG;
+  if (!(d.kb_beta >= 0.0) || !std::isfinite(d.kb_beta)) return NRSENSE_ERR_ARG;
+  p->desc = d;
+  p->identity_warp = (d.flags & NRSENSE_IDENTITY_WARP) != 0;
+  p->P = d.n_phases;
+  p->C = d.n_coils;
+  p->W = d.kb_width;
+  Geo& g = p->geo;
+  g.n0 = d.n[0]; g.n1 = d.n[1]; g.n2 = d.n[2];
+  g.osf = d.osf;
+  g.g0 = d.osf * d.n[0]; g.g1 = d.osf * d.n[1]; g.g2 = d.osf * d.n[2];
+  if (g.g0 > 1024 || g.g1 > 1024 || g.g2 > 1024) return NRSENSE_ERR_ARG;  // 10-bit packed taps
+  g.nvox = (long long)g.n0 * g.n1 * g.n2;
+  g.ngrid = (long long)g.g0 * g.g1 * g.g2;
+  if ((long long)p->P * g.nvox >= (1ll << 31)) return NRSENSE_ERR_ARG;
+  if (!p->identity_warp && disp == nullptr) return NRSENSE_ERR_ARG;
+  if (p->C > 0 && (coords == nullptr || smaps == nullptr || n_samples == nullptr))
+    return NRSENSE_ERR_ARG;
+  p->beta = d.kb_beta > 0 ? d.kb_beta : beatty_beta(p->W, double(d.osf));
+  if (!(p->beta > 0)) return NRSENSE_ERR_ARG;
+  p->poly_err = fit_kernel_polys(p->W, p->beta, &p->kc);
+
+  TilePlan& tp = p->tiles;
+  tp.t0 = tp.t1 = tp.t2 = kSpreadTile;
+  tp.nt0 = (g.g0 + tp.t0 - 1) / tp.t0;
+  tp.nt1 = (g.g1 + tp.t1 - 1) / tp.t1;
+  tp.nt2 = (g.g2 + tp.t2 - 1) / tp.t2;
+  tp.ntiles = (long long)tp.nt0 * tp.nt1 * tp.nt2;
+
+  // deapodization: 1/C(m/G) for m in [-N/2, N/2), per axis
+  {
+    std::vector<float> tab;
+    const int ns[3] = {g.n0, g.n1, g.n2}, gs[3] = {g.g0, g.g1, g.g2};
+    for (int a = 0; a < 3; ++a)
+      for (int m = -ns[a] / 2; m < ns[a] / 2; ++m)
+        tab.push_back(float(1.0 / kb_kernel_ft(double(m) / gs[a], p->W, p->beta)));
+    NRS_TRY(dev_alloc_n(p, &p->deapod, (long long)tab.size()));
+    NRS_TRY(upload(p->deapod, tab, s));
+  }
+  NRS_TRY(dev_alloc_n(p, &p->d_status, 1));
+  if (cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), s) != cudaSuccess) return NRSENSE_ERR_CUDA;
+
+  // displacements: copy, validate, and build the image-space point set
+  if (!p->identity_warp) {
+    const long long nd = (long long)p->P * 3 * g.nvox;
+    NRS_TRY(dev_alloc_n(p, &p->disp, nd));
+    if (cudaMemcpyAsync(p->disp, disp, size_t(nd) * sizeof(float), cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+      return NRSENSE_ERR_CUDA;
+    std::vector<float> hd(nd);
+    if (cudaMemcpyAsync(hd.data(), disp, size_t(nd) * sizeof(float), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return NRSENSE_ERR_CUDA;
+    for (long long i = 0; i < nd; ++i)
+      if (!std::isfinite(hd[i]) || std::fabs(hd[i]) > 1e6f) return NRSENSE_ERR_ARG;
+    std::vector<HostPoint> pts((size_t)(p->P * g.nvox));
+    const int gs[3] = {g.g0, g.g1, g.g2};
+    for (int j = 0; j < p->P; ++j) {
+      const float* dj = hd.data() + (long long)j * 3 * g.nvox;
+      for (long long v = 0; v < g.nvox; ++v) {
+        const int i2 = int(v % g.n2);
+        const int i1 = int((v / g.n2) % g.n1);
+        const int i0 = int(v / ((long long)g.n1 * g.n2));
+        const int ii[3] = {i0, i1, i2};
+        HostPoint& h = pts[(size_t)(j * g.nvox + v)];
+        for (int a = 0; a < 3; ++a) {
+          // q = sigma * (n + d) = sigma*n + sigma*d, exact in FP64
+          const double q = double(d.osf) * double(ii[a]) + double(d.osf) * double(dj[a * g.nvox + v]);
+          decompose(q, gs[a], p->W, &h.b[a], &h.f[a]);
+        }
+        h.row = int32_t(j * g.nvox + v);
+      }
+    }
+    NRS_TRY(build_pointset(p, pts, &p->ipts, s));
+  }
+
+  // coils and k-space
+  if (p->C > 0) {
+    p->M.assign(n_samples, n_samples + p->P);
+    p->off.resize(p->P);
+    long long tot = 0;
+    for (int j = 0; j < p->P; ++j) {
+      if (p->M[j] < 0 || p->M[j] >= (1ll << 31)) return NRSENSE_ERR_ARG;
+      p->off[j] = tot;
+      tot += p->M[j];
+    }
+    p->Mtot = tot;
+    const long long nm = g.nvox * p->C;
+    NRS_TRY(dev_alloc_n(p, &p->smaps, nm));
+    transpose_maps_kernel<<<unsigned((nm + 255) / 256), 256, 0, s>>>(
+        g.nvox, p->C, reinterpret_cast<const float2*>(smaps), reinterpret_cast<float2*>(p->smaps));
+    if (cudaGetLastError() != cudaSuccess) return NRSENSE_ERR_CUDA;
+
+    std::vector<float> hc(size_t(3 * tot));
+    if (tot > 0) {
+      if (cudaMemcpyAsync(hc.data(), coords, size_t(3 * tot) * sizeof(float),
+                          cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return NRSENSE_ERR_CUDA;
+    }
+    p->kpts.resize(p->P);
+    const int gs[3] = {g.g0, g.g1, g.g2};
+    for (int j = 0; j < p->P; ++j) {
+      std::vector<HostPoint> pts((size_t)p->M[j]);
+      for (long long i = 0; i < p->M[j]; ++i) {
+        HostPoint& h = pts[(size_t)i];
+        for (int a = 0; a < 3; ++a) {
+          const float om = hc[size_t(3 * (p->off[j] + i) + a)];
+          if (!std::isfinite(om)) return NRSENSE_ERR_ARG;
+          // q = omega G / (2 pi) in FP64; periodic, so any finite omega wraps
+          const double q = double(om) * double(gs[a]) / (2.0 * M_PI);
+          decompose(q, gs[a], p->W, &h.b[a], &h.f[a]);
+        }
+        h.row = int32_t(i);
+      }
+      NRS_TRY(build_pointset(p, pts, &p->kpts[j], s));
+    }
+  }
+
+  // cuFFT plans
+  if (fault_requested("cufft")) return NRSENSE_ERR_CUFFT;
+  if (!p->identity_warp) {
+    NRS_TRY(cufft_check(cufftPlan3d(&p->fft_n, g.n0, g.n1, g.n2, CUFFT_C2C)));
+    p->have_fft_n = true;
+    NRS_TRY(cufft_check(cufftPlan3d(&p->fft_g, g.g0, g.g1, g.g2, CUFFT_C2C)));
+    p->have_fft_g = true;
+  }
+  if (p->C > 0) {
+    int n[3] = {g.g0, g.g1, g.g2};
+    NRS_TRY(cufft_check(cufftPlanMany(&p->fft_gc, 3, n, n, p->C, 1, n, p->C, 1, CUFFT_C2C, p->C)));
+    p->have_fft_gc = true;
+  }
+
+  // work buffers
+  NRS_TRY(dev_alloc_n(p, &p->b_m, (long long)p->P * g.nvox));
+  NRS_TRY(dev_alloc_n(p, &p->b_tmp, g.nvox));
+  if (!p->identity_warp) {
+    NRS_TRY(dev_alloc_n(p, &p->b_xhat, g.nvox));
+    NRS_TRY(dev_alloc_n(p, &p->b_upad, g.ngrid));
+    NRS_TRY(dev_alloc_n(p, &p->b_ugrid, g.ngrid));
+    if (cudaMemsetAsync(p->b_upad, 0, size_t(g.ngrid) * sizeof(nrsense_c64), s) != cudaSuccess)
+      return NRSENSE_ERR_CUDA;
+  }
+  if (p->C > 0) {
+    NRS_TRY(dev_alloc_n(p, &p->b_xpad, g.ngrid * p->C));
+    NRS_TRY(dev_alloc_n(p, &p->b_xwork, g.ngrid * p->C));
+    NRS_TRY(dev_alloc_n(p, &p->b_y, std::max<long long>(p->Mtot * p->C, 1)));
+    if (cudaMemsetAsync(p->b_xpad, 0, size_t(g.ngrid * p->C) * sizeof(nrsense_c64), s) !=
+        cudaSuccess)
+      return NRSENSE_ERR_CUDA;
+  }
+  // scratch for split tiles: slots x coil chunks x tile x chunk coils
+  long long need = 0;
+  const long long tile_pts = (long long)kSpreadTile * kSpreadTile * kSpreadTile;
+  if (!p->identity_warp) need = std::max(need, (long long)p->ipts.n_slots * tile_pts);
+  if (p->C > 0) {
+    const int cc = spread_coil_chunk(p->C);
+    const int chunks = (p->C + cc - 1) / cc;
+    for (const auto& k : p->kpts)
+      need = std::max(need, (long long)k.n_slots * chunks * tile_pts * cc);
+  }
+  p->scratch_elems = need;
+  if (need > 0) NRS_TRY(dev_alloc_n(p, &p->b_scratch, need));
+  if (cudaStreamSynchronize(s) != cudaSuccess) return NRSENSE_ERR_CUDA;
+  return NRSENSE_OK;
+}
+
+void release(nrsense_plan_s* p) {
+  if (p->have_fft_n) cufftDestroy(p->fft_n);
+  if (p->have_fft_g) cufftDestroy(p->fft_g);
+  if (p->have_fft_gc) cufftDestroy(p->fft_gc);
+  for (void* a : p->allocations) cudaFree(a);
+  p->allocations.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+nrsense_status nrsense_plan_create(const nrsense_desc* desc, const int64_t* n_samples_host,
+                                   const float* coords_dev, const float* disp_dev,
+                                   const nrsense_c64* smaps_dev, void* stream,
+                                   nrsense_plan_t* out) {
+  if (desc == nullptr || out == nullptr) return NRSENSE_ERR_ARG;
+  *out = nullptr;
+  auto* p = new (std::nothrow) nrsense_plan_s();
+  if (p == nullptr) return NRSENSE_ERR_OOM;
+  nrsense_status st;
+  try {
+    st = create_impl(p, desc, n_samples_host, coords_dev, disp_dev, smaps_dev,
+                     static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    st = NRSENSE_ERR_OOM;
+  }
+  if (st != NRSENSE_OK) {
+    cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    release(p);
+    delete p;
+    return st;
+  }
+  *out = p;
+  return NRSENSE_OK;
+}
+
+nrsense_status nrsense_plan_destroy(nrsense_plan_t plan) {
+  if (plan == nullptr) return NRSENSE_OK;
+  cudaDeviceSynchronize();
+  release(plan);
+  delete plan;
+  return NRSENSE_OK;
+}
+
+nrsense_status nrsense_plan_info(nrsense_plan_t p, nrsense_info* out) {
+  if (p == nullptr || out == nullptr) return NRSENSE_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->grid[0] = p->geo.g0;
+  out->grid[1] = p->geo.g1;
+  out->grid[2] = p->geo.g2;
+  out->kb_beta = p->beta;
+  out->kernel_poly_err = p->poly_err;
+  out->total_samples = p->Mtot;
+  out->tile[0] = p->tiles.t0;
+  out->tile[1] = p->tiles.t1;
+  out->tile[2] = p->tiles.t2;
+  out->n_tiles = p->tiles.ntiles;
+  long long occ = 0, items = 0, split = 0;
+  for (const auto& k : p->kpts) {
+    occ += k.n_occupied;
+    items += k.n_items;
+    split += k.n_reduces;
+  }
+  out->occupied_fraction =
+      p->kpts.empty() ? 0.0 : double(occ) / (double(p->tiles.ntiles) * double(p->kpts.size()));
+  out->spread_items = items;
+  out->split_tiles = split;
+  out->device_bytes = p->device_bytes;
+  return NRSENSE_OK;
+}
+
+const char* nrsense_status_string(nrsense_status s) {
+  switch (s) {
+    case NRSENSE_OK: return "ok";
+    case NRSENSE_ERR_ARG: return "invalid argument";
+    case NRSENSE_ERR_OOM: return "out of memory";
+    case NRSENSE_ERR_CUFFT: return "cuFFT failure";
+    case NRSENSE_ERR_CUDA: return "CUDA runtime failure";
+    case NRSENSE_ERR_BREAKDOWN: return "CG breakdown";
+    case NRSENSE_ERR_NOT_CONVERGED: return "CG not converged";
+    case NRSENSE_ERR_TIMEOUT: return "device wait timed out";
+    case NRSENSE_ERR_BOUNDS: return "device bounds check fired";
+    case NRSENSE_ERR_STATE: return "call not valid for this plan";
+    default: return "unknown status";
+  }
+}
+
+nrsense_status nrsense_device_status(nrsense_plan_t p, int32_t clear, int32_t* out_host,
+                                     void* stream) {
+  if (p == nullptr || out_host == nullptr) return NRSENSE_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(out_host, p->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    return NRSENSE_ERR_CUDA;
+  if (clear && cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), s) != cudaSuccess)
+    return NRSENSE_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return NRSENSE_ERR_CUDA;
+  return NRSENSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// Host-side plan structure and kernel launchers (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace nrs {
+
+// Sorted points of one spreading problem (one k-space phase, or all displaced
+// voxels of all phases for the image-space adjoint).
+struct PointSet {
+  long long npts = 0;
+  float4* qs = nullptr;        // sorted: (f0, f1, f2, packed base bits)
+  int32_t* perm = nullptr;     // sorted index -> value row
+  int32_t* list = nullptr;     // per-tile halo lists (sorted indices)
+  SpreadItem* items = nullptr; // spreading work, heaviest first
+  int n_items = 0;
+  ReduceItem* reduces = nullptr;
+  int n_reduces = 0;
+  int n_slots = 0;             // partial tiles needed in scratch
+  int n_occupied = 0;          // tiles with at least one point
+  long long list_len = 0;
+};
+
+struct TilePlan {
+  int t0, t1, t2;       // tile size (grid points per axis)
+  int nt0, nt1, nt2;    // tiles per axis (last tile may be ragged)
+  long long ntiles;
+};
+
+}  // namespace nrs
+
+struct nrsense_plan_s {
+  nrsense_desc desc{};
+  nrs::Geo geo{};
+  int P = 0, C = 0, W = 0;
+  double beta = 0.0;
+  nrs::KernelCoefs kc{};
+  double poly_err = 0.0;
+  bool identity_warp = false;
+
+  // tables
+  float* deapod = nullptr;       // 1/C(m/G) for m in [-N/2, N/2), per axis, offsets 0, n0, n0+n1
+  float* disp = nullptr;         // (P, 3, nvox)
+  nrsense_c64* smaps = nullptr;  // (nvox, C) interleaved
+
+  // k-space
+  std::vector<long long> M, off;
+  long long Mtot = 0;
+  std::vector<nrs::PointSet> kpts;  // per phase
+  nrs::PointSet ipts;               // displaced voxels of all phases
+  nrs::TilePlan tiles{};
+
+  // work buffers
+  nrsense_c64* b_xhat = nullptr;   // N^3
+  nrsense_c64* b_upad = nullptr;   // G^3, zero outside the K_N block
+  nrsense_c64* b_ugrid = nullptr;  // G^3
+  nrsense_c64* b_m = nullptr;      // P * N^3
+  nrsense_c64* b_xpad = nullptr;   // G^3 * C, zero outside the centred N^3 block
+  nrsense_c64* b_xwork = nullptr;  // G^3 * C
+  nrsense_c64* b_y = nullptr;      // Mtot * C
+  nrsense_c64* b_tmp = nullptr;    // N^3 (normal operator scratch)
+  nrsense_c64* b_scratch = nullptr;  // partial tiles
+  long long scratch_elems = 0;
+  int32_t* d_status = nullptr;
+
+  cufftHandle fft_n = 0, fft_g = 0, fft_gc = 0;
+  bool have_fft_n = false, have_fft_g = false, have_fft_gc = false;
+
+  long long device_bytes = 0;
+  std::vector<void*> allocations;
+};
+
+namespace nrs {
+
+// ---- launchers (kernels_*.cu) -------------------------------------------
+// image space
+void launch_deapod_pad(const Geo& g, const float* deapod, const nrsense_c64* xhat,
+                       nrsense_c64* upad, cudaStream_t s);
+void launch_crop_deapod(const Geo& g, const float* deapod, const nrsense_c64* ufreq,
+                        nrsense_c64* xhat, cudaStream_t s);
+void launch_interp_image(const Geo& g, int W, const KernelCoefs& kc, int P,
+                         const float* disp, const nrsense_c64* u, nrsense_c64* m,
+                         cudaStream_t s);
+void launch_axpby(long long n, const nrsense_c64* x, float a, nrsense_c64* y, float b,
+                  cudaStream_t s);
+void launch_copy_phases(const Geo& g, int P, const nrsense_c64* x, nrsense_c64* m,
+                        cudaStream_t s);
+void launch_sum_phases(const Geo& g, int P, const nrsense_c64* m, nrsense_c64* x,
+                       cudaStream_t s);
+
+// k space
+void launch_coil_fanout_pad(const Geo& g, int C, const float* deapod,
+                            const nrsense_c64* smaps, const nrsense_c64* m,
+                            nrsense_c64* xpad, cudaStream_t s);
+void launch_image_to_padded(const Geo& g, int C, const float* deapod,
+                            const nrsense_c64* v, nrsense_c64* xpad, cudaStream_t s);
+void launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C,
+                          const PointSet& ps, const nrsense_c64* grid, nrsense_c64* y,
+                          cudaStream_t s);
+void launch_crop_coilsum(const Geo& g, int C, const float* deapod,
+                         const nrsense_c64* smaps, const nrsense_c64* xg,
+                         nrsense_c64* w, cudaStream_t s);
+void launch_crop_to_coils(const Geo& g, int C, const float* deapod,
+                          const nrsense_c64* xg, nrsense_c64* v, cudaStream_t s);
+
+// spreading (both domains)
+void launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
+                   const PointSet& ps, const nrsense_c64* vals, nrsense_c64* grid,
+                   nrsense_c64* scratch, int32_t* status, cudaStream_t s);
+// coils handled by one spreading CTA, and the tile edge used by the kernels
+int spread_coil_chunk(int C);
+constexpr int kSpreadTile = 8;
+// largest number of list entries one spreading CTA processes
+constexpr int kSpreadMaxItem = 1024;
+
+}  // namespace nrs

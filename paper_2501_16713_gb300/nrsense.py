@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libnrsense (include/nrsense.h).
+
+Argument marshalling only: every step of the operator runs in the library's
+CUDA kernels and cuFFT.  PyTorch provides device memory and streams.  If the
+library is missing this module raises at load time: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libnrsense.so")
+
+OK = 0
+STATUS = {
+    0: "ok", -1: "invalid argument", -2: "out of memory", -3: "cuFFT failure",
+    -4: "CUDA runtime failure", -5: "CG breakdown", -6: "CG not converged",
+    -7: "device wait timed out", -8: "device bounds check fired",
+    -9: "call not valid for this plan",
+}
+FP32 = 0
+IDENTITY_WARP = 1
+
+
+class NrsenseError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {STATUS.get(code, 'unknown')} ({code})")
+        self.code = code
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("osf", ctypes.c_int32),
+                ("kb_width", ctypes.c_int32), ("kb_beta", ctypes.c_double),
+                ("n_phases", ctypes.c_int32), ("n_coils", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32 * 3), ("kb_beta", ctypes.c_double),
+                ("kernel_poly_err", ctypes.c_double), ("total_samples", ctypes.c_int64),
+                ("tile", ctypes.c_int32 * 3), ("n_tiles", ctypes.c_int64),
+                ("occupied_fraction", ctypes.c_double), ("spread_items", ctypes.c_int64),
+                ("split_tiles", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "nrsense_plan_create": [ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_int64), _VP, _VP, _VP,
+                            _VP, ctypes.POINTER(_VP)],
+    "nrsense_plan_destroy": [_VP],
+    "nrsense_plan_info": [_VP, ctypes.POINTER(Info)],
+    "nrsense_apply_forward": [_VP, _VP, _VP, _VP],
+    "nrsense_apply_adjoint": [_VP, _VP, _VP, _VP],
+    "nrsense_apply_normal": [_VP, _VP, ctypes.c_double, _VP, _VP],
+    "nrsense_warp_forward": [_VP, _VP, _VP, _VP],
+    "nrsense_warp_adjoint": [_VP, _VP, _VP, _VP],
+    "nrsense_kspace_forward": [_VP, ctypes.c_int32, _VP, _VP, _VP],
+    "nrsense_kspace_adjoint": [_VP, ctypes.c_int32, _VP, _VP, _VP],
+    "nrsense_device_status": [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _VP],
+    "nrsense_status_string": [ctypes.c_int32],
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libnrsense.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libnrsense.so not built ({p}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "nrsense_status_string" else ctypes.c_int32
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _check(code, where):
+    if code != OK:
+        raise NrsenseError(code, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class Plan:
+    """Nonrigid SENSE operator A_j = G_j S T_j over P motion states.
+
+    shape   image size (n0, n1, n2), each even
+    disp    (P, 3, n0, n1, n2) float32 CUDA tensor (voxels), or None with
+            identity_warp=True
+    coords  list of P (M_j, 3) float32 CUDA tensors (radians), or None (no coils)
+    smaps   (C, n0, n1, n2) complex64 CUDA tensor, or None (image-space only)
+    """
+
+    def __init__(self, shape, disp=None, coords=None, smaps=None, n_phases=None, osf=2,
+                 width=4, beta=0.0, identity_warp=False, stream=None):
+        import torch
+        self.lib = load()
+        self.shape = tuple(int(s) for s in shape)
+        if smaps is not None:
+            _need(smaps, torch.complex64, None, "smaps")
+            self.n_coils = int(smaps.shape[0])
+        else:
+            self.n_coils = 0
+        if n_phases is None:
+            n_phases = int(disp.shape[0]) if disp is not None else len(coords)
+        self.n_phases = int(n_phases)
+        if disp is not None:
+            _need(disp, torch.float32, (self.n_phases, 3) + self.shape, "disp")
+        d = Desc()
+        d.n[:] = self.shape
+        d.osf, d.kb_width, d.kb_beta = int(osf), int(width), float(beta)
+        d.n_phases, d.n_coils = self.n_phases, self.n_coils
+        d.precision = FP32
+        d.flags = IDENTITY_WARP if identity_warp else 0
+        self.counts = [0] * self.n_phases
+        cat = None
+        if self.n_coils > 0:
+            if coords is None or len(coords) != self.n_phases:
+                raise ValueError("coords must list one (M_j, 3) tensor per phase")
+            for c in coords:
+                _need(c, torch.float32, None, "coords[j]")
+            self.counts = [int(c.shape[0]) for c in coords]
+            cat = torch.cat([c.reshape(-1, 3) for c in coords]).contiguous()
+        self.offsets = np.concatenate([[0], np.cumsum(self.counts)]).astype(np.int64)
+        counts = (ctypes.c_int64 * self.n_phases)(*self.counts)
+        h = ctypes.c_void_p()
+        st = self.lib.nrsense_plan_create(ctypes.byref(d), counts, _ptr(cat), _ptr(disp),
+                                          _ptr(smaps), _stream(stream), ctypes.byref(h))
+        _check(st, "nrsense_plan_create")
+        self._h = h
+        self.total_samples = int(self.offsets[-1])
+
+    # -- lifetime --------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.nrsense_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        inf = Info()
+        _check(self.lib.nrsense_plan_info(self._h, ctypes.byref(inf)), "nrsense_plan_info")
+        return {f: (list(getattr(inf, f)) if f in ("grid", "tile") else getattr(inf, f))
+                for f, _ in Info._fields_}
+
+    # -- operators -------------------------------------------------------
+    def _img(self):
+        import torch
+        return torch.empty(self.shape, dtype=torch.complex64, device="cuda")
+
+    def forward_shape(self):
+        if self.n_coils == 0:
+            return (self.n_phases,) + self.shape
+        return (self.total_samples, self.n_coils)
+
+    def forward(self, x, out=None, stream=None):
+        import torch
+        _need(x, torch.complex64, self.shape, "x")
+        if out is None:
+            out = torch.empty(self.forward_shape(), dtype=torch.complex64, device="cuda")
+        _need(out, torch.complex64, self.forward_shape(), "out")
+        _check(self.lib.nrsense_apply_forward(self._h, _ptr(x), _ptr(out), _stream(stream)),
+               "nrsense_apply_forward")
+        return out
+
+    def adjoint(self, y, out=None, stream=None):
+        import torch
+        _need(y, torch.complex64, self.forward_shape(), "y")
+        out = self._img() if out is None else out
+        _need(out, torch.complex64, self.shape, "out")
+        _check(self.lib.nrsense_apply_adjoint(self._h, _ptr(y), _ptr(out), _stream(stream)),
+               "nrsense_apply_adjoint")
+        return out
+
+    def normal(self, x, lam=0.0, out=None, stream=None):
+        import torch
+        _need(x, torch.complex64, self.shape, "x")
+        out = self._img() if out is None else out
+        _need(out, torch.complex64, self.shape, "out")
+        _check(self.lib.nrsense_apply_normal(self._h, _ptr(x), float(lam), _ptr(out),
+                                             _stream(stream)), "nrsense_apply_normal")
+        return out
+
+    def warp_forward(self, x, out=None, stream=None):
+        import torch
+        _need(x, torch.complex64, self.shape, "x")
+        if out is None:
+            out = torch.empty((self.n_phases,) + self.shape, dtype=torch.complex64, device="cuda")
+        _check(self.lib.nrsense_warp_forward(self._h, _ptr(x), _ptr(out), _stream(stream)),
+               "nrsense_warp_forward")
+        return out
+
+    def warp_adjoint(self, m, out=None, stream=None):
+        import torch
+        _need(m, torch.complex64, (self.n_phases,) + self.shape, "m")
+        out = self._img() if out is None else out
+        _check(self.lib.nrsense_warp_adjoint(self._h, _ptr(m), _ptr(out), _stream(stream)),
+               "nrsense_warp_adjoint")
+        return out
+
+    def kspace_forward(self, phase, v, out=None, stream=None):
+        import torch
+        _need(v, torch.complex64, (self.n_coils,) + self.shape, "v")
+        if out is None:
+            out = torch.empty((self.counts[phase], self.n_coils), dtype=torch.complex64,
+                              device="cuda")
+        _check(self.lib.nrsense_kspace_forward(self._h, int(phase), _ptr(v), _ptr(out),
+                                               _stream(stream)), "nrsense_kspace_forward")
+        return out
+
+    def kspace_adjoint(self, phase, y, out=None, stream=None):
+        import torch
+        _need(y, torch.complex64, (self.counts[phase], self.n_coils), "y")
+        if out is None:
+            out = torch.empty((self.n_coils,) + self.shape, dtype=torch.complex64, device="cuda")
+        _check(self.lib.nrsense_kspace_adjoint(self._h, int(phase), _ptr(y), _ptr(out),
+                                               _stream(stream)), "nrsense_kspace_adjoint")
+        return out
+
+    def device_status(self, clear=True, stream=None):
+        v = ctypes.c_int32()
+        _check(self.lib.nrsense_device_status(self._h, int(bool(clear)), ctypes.byref(v),
+                                              _stream(stream)), "nrsense_device_status")
+        return v.value
+
+    def phase_slice(self, y, j):
+        """Rows of phase j in a stacked (sum M_j, C) k-space array."""
+        return y[int(self.offsets[j]):int(self.offsets[j + 1])]

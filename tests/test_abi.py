@@ -1,0 +1,83 @@
+"""C ABI checks that need no GPU: the library builds and loads, exports every
+entry point include/nrsense.h declares, and the ctypes structures match the C
+layout (checked with a small C program compiled by gcc against the header)."""
+
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nrsense.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(nrsense_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2501_16713_gb300 import nrsense
+    return nrsense.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "nrsense_plan_create" in names and "nrsense_apply_normal" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_header():
+    from paper_2501_16713_gb300 import nrsense
+    assert set(_declared()) == set(nrsense.exported_symbols())
+
+
+def test_status_strings(lib):
+    lib.nrsense_status_string.restype = ctypes.c_char_p
+    assert lib.nrsense_status_string(0) == b"ok"
+    assert lib.nrsense_status_string(-1) == b"invalid argument"
+    assert lib.nrsense_status_string(-123) == b"unknown status"
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    # argument validation happens before any CUDA call
+    h = ctypes.c_void_p()
+    assert lib.nrsense_plan_create(None, None, None, None, None, None, ctypes.byref(h)) == -1
+    assert lib.nrsense_apply_forward(None, None, None, None) == -1
+    assert lib.nrsense_plan_destroy(None) == 0
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc not available")
+def test_struct_layout_matches_header(tmp_path):
+    from paper_2501_16713_gb300 import nrsense
+    src = tmp_path / "layout.c"
+    src.write_text(f"""
+#include <stdio.h>
+#include <stddef.h>
+#include "{HEADER}"
+int main(void) {{
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(nrsense_desc), offsetof(nrsense_desc, kb_beta),
+         offsetof(nrsense_desc, n_phases), offsetof(nrsense_desc, flags), sizeof(nrsense_c64));
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(nrsense_info), offsetof(nrsense_info, kb_beta),
+         offsetof(nrsense_info, tile), offsetof(nrsense_info, n_tiles),
+         offsetof(nrsense_info, device_bytes));
+  return 0;
+}}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    d = [int(v) for v in out[0].split()]
+    i = [int(v) for v in out[1].split()]
+    D, I = nrsense.Desc, nrsense.Info
+    assert d == [ctypes.sizeof(D), D.kb_beta.offset, D.n_phases.offset, D.flags.offset, 8]
+    assert i == [ctypes.sizeof(I), I.kb_beta.offset, I.tile.offset, I.n_tiles.offset,
+                 I.device_bytes.offset]

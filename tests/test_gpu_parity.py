@@ -1,0 +1,226 @@
+"""GPU (sm_103a) parity of the nonrigid SENSE operator against the FP64 oracle.
+
+Every comparison feeds both sides the same seeded inputs (rounded to the FP32
+/ complex64 types the library takes) and compares element by element in
+relative L2 at the FP32 tolerance.  Sizes span several 8^3 spreading tiles,
+ragged last tiles (grids not divisible by 8) and non-cubic images.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from helpers import TOL_ADJ, TOL_FP32, c64, crandn, make_plan, rel_l2, to_dev
+from oracle import operators as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _d64(case):
+    return [d.astype(np.float64) for d in case["disp"]]
+
+
+# ----------------------------------------------------- image-space T_j ----
+
+@pytest.mark.parametrize("shape,P", [((16, 16, 16), 1), ((10, 12, 14), 2), ((32, 24, 20), 3)])
+def test_warp_forward_adjoint_vs_oracle(shape, P):
+    case = synth.small_case(shape, 0, P, 0, seed=21 + P, max_disp=3.0, rigid=1.5)
+    plan = make_plan(case, shape)
+    geo = O.Geometry(shape)
+    x = case["x"]
+    m = plan.warp_forward(to_dev(x)).cpu().numpy()
+    for j in range(P):
+        ref = O.warp_forward(geo, x, case["disp"][j].astype(np.float64))
+        assert rel_l2(m[j], ref) < TOL_FP32, j
+    rng = np.random.default_rng(5)
+    w = crandn(rng, (P,) + shape)
+    xa = plan.warp_adjoint(to_dev(w)).cpu().numpy()
+    ref = sum(O.warp_adjoint(geo, w[j], case["disp"][j].astype(np.float64)) for j in range(P))
+    assert rel_l2(xa, ref) < TOL_FP32
+    plan.close()
+
+
+def test_warp_full_size_32cube():
+    # the 32^3 image-space warp workload, in full, against the oracle
+    w = synth.workload("warp32")
+    shape = w["spec"].shape
+    plan = make_plan({"disp": w["disp"]}, shape)
+    geo = O.Geometry(shape)
+    m = plan.warp_forward(to_dev(w["x"])).cpu().numpy()[0]
+    ref = O.warp_forward(geo, w["x"], w["disp"][0].astype(np.float64))
+    assert rel_l2(m, ref) < TOL_FP32
+    xa = plan.warp_adjoint(to_dev(c64(ref)[None])).cpu().numpy()
+    refa = O.warp_adjoint(geo, c64(ref), w["disp"][0].astype(np.float64))
+    assert rel_l2(xa, refa) < TOL_FP32
+    plan.close()
+
+
+def test_warp_integer_displacement_is_shift():
+    # integer displacement: T(d) x = roll(T(0) x, -d); checked on the GPU alone
+    shape = (16, 16, 16)
+    rng = np.random.default_rng(3)
+    x = crandn(rng, shape)
+    dz = np.zeros((2, 3) + shape, np.float32)
+    dz[1] = np.array([2, -3, 5], np.float32)[:, None, None, None]
+    plan = make_plan({"disp": list(dz)}, shape)
+    m = plan.warp_forward(to_dev(x)).cpu().numpy()
+    assert rel_l2(m[1], np.roll(m[0], (-2, 3, -5), axis=(0, 1, 2))) < 1e-6
+    plan.close()
+
+
+# ----------------------------------------------------- k-space G_j --------
+
+@pytest.mark.parametrize("shape,C,M", [((16, 16, 16), 4, 3000), ((10, 12, 14), 3, 1500),
+                                       ((24, 16, 20), 8, 5000)])
+def test_kspace_forward_adjoint_vs_oracle(shape, C, M):
+    rng = np.random.default_rng(C)
+    case = synth.small_case(shape, C, 1, [M], seed=30 + C, uniform_coords=(C == 3))
+    plan = make_plan(case, shape)
+    geo = O.Geometry(shape)
+    v = crandn(rng, (C,) + shape)
+    y = plan.kspace_forward(0, to_dev(v)).cpu().numpy()
+    ref = O.kspace_forward(geo, v, case["coords"][0])
+    assert rel_l2(y, ref) < TOL_FP32
+    yin = crandn(rng, (M, C))
+    va = plan.kspace_adjoint(0, to_dev(yin)).cpu().numpy()
+    refa = O.kspace_adjoint(geo, yin, case["coords"][0])
+    assert rel_l2(va, refa) < TOL_FP32
+    plan.close()
+
+
+def test_kspace_heavy_tiles_are_split():
+    # all samples in a few cells at the k-space centre: spreading work items
+    # are split and reduced; results still match the oracle
+    shape = (16, 16, 16)
+    rng = np.random.default_rng(9)
+    M, C = 6000, 2
+    om = rng.normal(0, 0.05, (M, 3)).astype(np.float32)
+    case = {"coords": [om], "smaps": synth.coil_maps(shape, C, 4),
+            "disp": [np.zeros((3,) + shape, np.float32)]}
+    plan = make_plan(case, shape)
+    assert plan.info()["split_tiles"] > 0
+    geo = O.Geometry(shape)
+    yin = crandn(rng, (M, C))
+    va = plan.kspace_adjoint(0, to_dev(yin)).cpu().numpy()
+    assert rel_l2(va, O.kspace_adjoint(geo, yin, om)) < TOL_FP32
+    plan.close()
+
+
+# ----------------------------------------------------- full A_j ------------
+
+@pytest.mark.parametrize("shape,C,Ms", [((16, 16, 16), 3, [1200, 900]),
+                                        ((12, 16, 10), 5, [800, 0, 1]),
+                                        ((20, 20, 20), 8, [2500])])
+def test_sense_forward_adjoint_normal_vs_oracle(shape, C, Ms):
+    P = len(Ms)
+    case = synth.small_case(shape, C, P, Ms, seed=40 + C, max_disp=2.5, rigid=1.0)
+    plan = make_plan(case, shape)
+    geo = O.Geometry(shape)
+    x = case["x"]
+    d64 = _d64(case)
+    ys = O.stacked_forward(geo, x, d64, case["smaps"], case["coords"])
+    y = plan.forward(to_dev(x)).cpu().numpy()
+    for j in range(P):
+        if Ms[j]:
+            assert rel_l2(plan.phase_slice(y, j), ys[j]) < TOL_FP32, j
+    # adjoint of the oracle's own data (rounded to complex64)
+    yin = c64(np.concatenate(ys)) if sum(Ms) else np.zeros((0, C), np.complex64)
+    yin_list = [plan.phase_slice(yin, j).astype(np.complex128) for j in range(P)]
+    xa = plan.adjoint(to_dev(yin)).cpu().numpy()
+    ref = O.stacked_adjoint(geo, yin_list, d64, case["smaps"], case["coords"])
+    assert rel_l2(xa, ref) < TOL_FP32
+    lam = 0.37
+    xn = plan.normal(to_dev(x), lam).cpu().numpy()
+    refn = O.normal(geo, x, d64, case["smaps"], case["coords"], lam)
+    assert rel_l2(xn, refn) < TOL_FP32
+    plan.close()
+
+
+def test_identity_warp_is_plain_sense():
+    shape = (16, 12, 16)
+    case = synth.small_case(shape, 4, 2, [1000, 1300], seed=50)
+    plan = make_plan(case, shape, identity_warp=True)
+    geo = O.Geometry(shape)
+    y = plan.forward(to_dev(case["x"])).cpu().numpy()
+    for j in range(2):
+        ref = O.sense_forward(geo, case["x"], None, case["smaps"], case["coords"][j])
+        assert rel_l2(plan.phase_slice(y, j), ref) < TOL_FP32
+    plan.close()
+
+
+def test_coordinates_wrap_periodically():
+    # omega and omega + 2 pi k are the same sample of a periodic grid
+    shape = (12, 12, 12)
+    rng = np.random.default_rng(1)
+    case = synth.small_case(shape, 2, 1, [700], seed=52, uniform_coords=True)
+    plan = make_plan(case, shape)
+    shifted = dict(case)
+    shifted["coords"] = [(case["coords"][0].astype(np.float64) +
+                          2 * np.pi * rng.integers(-2, 3, (700, 3))).astype(np.float32)]
+    plan2 = make_plan(shifted, shape)
+    x = to_dev(case["x"])
+    y1 = plan.forward(x).cpu().numpy()
+    y2 = plan2.forward(x).cpu().numpy()
+    assert rel_l2(y2, y1) < 1e-5
+    plan.close()
+    plan2.close()
+
+
+def test_gpu_adjointness_and_determinism():
+    shape = (24, 24, 24)
+    case = synth.small_case(shape, 6, 3, [3000, 2000, 2500], seed=60, max_disp=3.0)
+    plan = make_plan(case, shape)
+    rng = np.random.default_rng(0)
+    x = to_dev(crandn(rng, shape))
+    y = to_dev(crandn(rng, (7500, 6)))
+    Ax = plan.forward(x)
+    Ahy = plan.adjoint(y)
+    import torch
+    lhs = torch.vdot(y.flatten().to(torch.complex128), Ax.flatten().to(torch.complex128))
+    rhs = torch.vdot(Ahy.flatten().to(torch.complex128), x.flatten().to(torch.complex128))
+    scale = torch.linalg.norm(Ax.to(torch.complex128)) * torch.linalg.norm(y.to(torch.complex128))
+    assert abs(complex(lhs - rhs)) / float(scale) < TOL_ADJ
+    # bitwise determinism of every output
+    assert torch.equal(plan.forward(x), Ax)
+    assert torch.equal(plan.adjoint(y), Ahy)
+    n1 = plan.normal(x, 0.1)
+    assert torch.equal(plan.normal(x, 0.1), n1)
+    plan.close()
+
+
+def test_inputs_are_not_modified():
+    import torch
+    shape = (16, 16, 16)
+    case = synth.small_case(shape, 3, 2, [500, 600], seed=61)
+    plan = make_plan(case, shape)
+    x = to_dev(case["x"])
+    x0 = x.clone()
+    y = plan.forward(x)
+    y0 = y.clone()
+    plan.adjoint(y)
+    plan.normal(x, 0.5)
+    assert torch.equal(x, x0) and torch.equal(y, y0)
+    assert plan.device_status() == 0
+    plan.close()
+
+
+def test_invalid_arguments_raise():
+    import torch
+    from paper_2501_16713_gb300 import NrsenseError, Plan
+    shape = (15, 16, 16)  # odd size
+    with pytest.raises(NrsenseError):
+        Plan(shape, disp=torch.zeros((1, 3) + shape, device="cuda"))
+    shape = (16, 16, 16)
+    bad = torch.zeros((1, 3) + shape, device="cuda")
+    bad[0, 0, 1, 2, 3] = float("nan")
+    with pytest.raises(NrsenseError):
+        Plan(shape, disp=bad)
