@@ -1,0 +1,425 @@
+"""Benchmark of the nonrigid SENSE normal operator E = sum_j A_j^H A_j.
+
+Workload (default): 128^3 complex64 image, 8 coils, 4 respiratory phases,
+~1.5M cone-like k-space samples per phase (synthetic, seeded), sigma 2, W 4.
+One step = one application of E (all phases, all coils): the operator a CG
+iteration applies.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on a bounded sample of the same workload and reports the same metric.
+Under torchrun each rank runs an independent replica (weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "nonrigid-SENSE A^H.A applies/s"
+UNIT = "applies/s"
+
+# stage -> algorithmic bytes per step
+STAGE_KERNEL_SOURCE = {
+    "interp_kspace": "kernels_kspace.cu", "spread_kspace": "kernels_spread.cu",
+    "interp_image": "kernels_image.cu", "spread_image": "kernels_spread.cu",
+    "coil_fanout_pad": "kernels_kspace.cu", "crop_coilsum": "kernels_kspace.cu",
+    "deapod_pad": "kernels_image.cu", "crop_deapod": "kernels_image.cu",
+    "vector": "kernels_image.cu",
+}
+FFT_STAGES = ("fft_n", "fft_g", "fft_gc")
+
+
+def stage_bytes(info, shape, C, P, M):
+    """Compulsory HBM bytes per E apply, per stage.
+
+    Grids count occupied tiles only (rho = fraction of (phase, tile) pairs with
+    samples); coordinates count 12 B per point (3 x f32); complex values 8 B."""
+    N3 = float(shape[0] * shape[1] * shape[2])
+    G3 = float(info["grid"][0] * info["grid"][1] * info["grid"][2])
+    rho = info["occupied_fraction"]
+    Ms = float(sum(M))
+    k = 8.0 * C * rho * G3 * P + (12.0 + 8.0 * C) * Ms
+    img = 8.0 * G3 + (12.0 + 8.0) * P * N3
+    return {
+        "interp_kspace": k, "spread_kspace": k,
+        "interp_image": img, "spread_image": img,
+        "deapod_pad": 16.0 * N3, "crop_deapod": 16.0 * N3,
+        "coil_fanout_pad": P * 8.0 * (1 + 2 * C) * N3,
+        "crop_coilsum": P * 8.0 * (1 + 2 * C) * N3,
+    }
+
+
+def source_hash(name):
+    path = os.path.join(ROOT, "paper_2501_16713_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(stage, workload):
+    """DRAM bytes per launch of `stage` from the committed ncu summary, if it
+    was taken on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    r = rec.get(workload, {}).get(stage)
+    if not r or r.get("source_sha") != source_hash(STAGE_KERNEL_SOURCE[stage]):
+        return None
+    return r.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle leg (bounded sample)
+# --------------------------------------------------------------------------
+
+def oracle_cost(w, frac=1.0 / 32, seed=0):
+    """Time the FP64 oracle's own steps on a bounded sample of the workload and
+    return the modelled wall time of one E apply (seconds) and a description.
+
+    The oracle computes E phase by phase and coil by coil: per phase one
+    T_j/T_j^H pair (two N^3 FFTs, two G^3 FFTs, interpolation and spreading of
+    the N^3 displaced voxels) and per coil one G_j/G_j^H pair (two G^3 FFTs,
+    interpolation and spreading of the M_j samples).  The FFTs are timed in
+    full; interpolation and spreading are timed on a random `frac` of phase
+    0's points and scaled by the point counts."""
+    import numpy as np
+    from oracle import operators as O
+
+    spec = w["spec"]
+    shape = spec.shape
+    geo = O.Geometry(shape)
+    rng = np.random.default_rng(seed)
+    P, C = len(w["disp"]), spec.n_coils
+    M = [c.shape[0] for c in w["coords"]]
+
+    def timed(fn):
+        t = time.perf_counter()
+        fn()
+        return time.perf_counter() - t
+
+    xN = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    xG = (rng.standard_normal(geo.grid) + 1j * rng.standard_normal(geo.grid))
+    t_fft_n = timed(lambda: O.sfft.fftn(xN, workers=O.FFT_WORKERS))
+    t_fft_g = timed(lambda: O.sfft.fftn(xG, workers=O.FFT_WORKERS))
+    nv = int(np.prod(shape))
+    # contiguous blocks keep the access pattern of the full pass
+    nsel = max(1, int(nv * frac))
+    st = int(rng.integers(0, nv - nsel + 1))
+    sel = np.arange(st, st + nsel)
+    q = O.warp_positions(geo, w["disp"][0].astype(np.float64))[:, sel]
+    vals = rng.standard_normal(sel.size) + 1j * rng.standard_normal(sel.size)
+    t_ti = timed(lambda: O.backprojection_core(xG, q, geo.width, geo.beta)) * nv / sel.size
+    t_ts = timed(lambda: O.projection_core(vals, q, geo.grid, geo.width, geo.beta)) * nv / sel.size
+    nk = max(1, int(M[0] * frac))
+    stk = int(rng.integers(0, M[0] - nk + 1))
+    selk = np.arange(stk, stk + nk)
+    qk = O.kspace_positions(geo, w["coords"][0][selk])
+    valk = rng.standard_normal(selk.size) + 1j * rng.standard_normal(selk.size)
+    t_gi = timed(lambda: O.backprojection_core(xG, qk, geo.width, geo.beta)) / selk.size
+    t_gs = timed(lambda: O.projection_core(valk, qk, geo.grid, geo.width, geo.beta)) / selk.size
+    e = P * (2 * t_fft_n + 2 * t_fft_g + t_ti + t_ts)
+    e += sum(C * (2 * t_fft_g + (t_gi + t_gs) * m) for m in M)
+    cpu_s = 2 * t_fft_n + 2 * t_fft_g + (t_ti + t_ts) * frac + (t_gi + t_gs) * selk.size
+    desc = (f"FP64 numpy oracle, single thread; FFTs of N^3 and G^3 timed in full, "
+            f"interpolation+spreading timed on a contiguous {frac:.4g} of phase 0's voxels and samples; "
+            f"E modelled as P x T-pair + sum_j C x G-pair ({cpu_s:.1f} s of CPU work)")
+    if os.environ.get("NRSENSE_BENCH_DEBUG"):
+        print(dict(t_fft_n=t_fft_n, t_fft_g=t_fft_g, t_ti=t_ti, t_ts=t_ts,
+                   t_gi_full=t_gi * M[0], t_gs_full=t_gs * M[0]), file=sys.stderr)
+    desc += "; elementwise steps (deapodization, padding, coil products) not timed"
+    return e, desc
+
+
+# --------------------------------------------------------------------------
+# GPU leg
+# --------------------------------------------------------------------------
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2501_16713_gb300 import Plan, build
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    build()
+    w = synth.workload(args.workload)
+    spec = w["spec"]
+    shape = spec.shape
+    disp = torch.from_numpy(np.stack(w["disp"])).to(dev)
+    smaps = torch.from_numpy(w["smaps"]).to(dev)
+    coords = [torch.from_numpy(c).to(dev) for c in w["coords"]]
+    plan = Plan(shape, disp=disp, coords=coords, smaps=smaps)
+    del disp, smaps, coords
+    info = plan.info()
+    x = torch.from_numpy(w["x"]).to(dev)
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.normal(x, args.lam, out)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(vis.split(",")[local_rank] if vis else str(local_rank))
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    plan.profile_start(max_launches=args.steps * 64 + 64)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.normal(x, args.lam, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    stages, own = plan.profile_stop()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    # forward / adjoint split (untimed region; context only)
+    y = plan.forward(x)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        plan.forward(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1) / 3
+    e0.record(stream)
+    for _ in range(3):
+        plan.adjoint(y, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_adj = e0.elapsed_time(e1) / 3
+    del y
+
+    # end to end through the public API with host buffers
+    xh = torch.from_numpy(w["x"]).pin_memory()
+    oh = torch.empty(shape, dtype=torch.complex64).pin_memory()
+    xd = torch.empty_like(x)
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        plan.normal(xd, args.lam, out)
+        oh.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    te = time.perf_counter()
+    ke = max(3, args.steps // 2)
+    for _ in range(ke):
+        xd.copy_(xh, non_blocking=True)
+        plan.normal(xd, args.lam, out)
+        oh.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - te) * 1000.0 / ke
+    te_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(te_t.item())
+
+    M = plan.counts
+    sb = stage_bytes(info, shape, spec.n_coils, len(M), M)
+    own_stages = {k: v for k, v in stages.items() if k not in FFT_STAGES and v[1] > 0}
+    dom = max(own_stages, key=lambda k: own_stages[k][0])
+    dom_ms, dom_n = own_stages[dom]
+    per_step_launches = dom_n / args.steps
+    bytes_per_launch = sb.get(dom, 0.0) / per_step_launches
+    achieved = bytes_per_launch / (dom_ms / dom_n * 1e-3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    traffic = ncu_traffic(dom, args.workload)
+    fft_ms = sum(stages[k][0] for k in FFT_STAGES) / args.steps
+    breakdown = {k: {"ms_per_step": round(v[0] / args.steps, 4),
+                     "launches_per_step": v[1] / args.steps,
+                     "gbs": (round(sb[k] / (v[0] / args.steps * 1e-3) / 1e9, 1)
+                             if k in sb and v[0] > 0 else None)}
+                 for k, v in stages.items() if v[1] > 0}
+    result = {
+        "metric": METRIC, "value": world * 1000.0 / ms_max, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64/f32 (FP32 arithmetic)",
+        "data": "synthetic (seeded phantom, Gaussian-bump displacements, Gaussian coil "
+                "maps, cone-like trajectory); no trained weights",
+        "config": {"workload": args.workload, "image": list(shape), "coils": spec.n_coils,
+                   "phases": len(M), "samples_per_phase": M, "osf": 2, "kb_width": 4,
+                   "lambda": args.lam, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: per-phase coil grids 1.07 GB, "
+                         "E touches ~12 GB per step; no flush"},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "alg_bytes_per_launch": bytes_per_launch,
+                     "ms_per_launch": dom_ms / dom_n,
+                     "traffic": traffic},
+        "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT,
+                "h2d_bytes_per_step": int(xh.numel() * 8),
+                "d2h_bytes_per_step": int(oh.numel() * 8)},
+        "gpu_launches": int(own),
+        "fft_ms_per_step": round(fft_ms, 3),
+        "forward_ms": round(ms_fwd, 3), "adjoint_ms": round(ms_adj, 3),
+        "breakdown": breakdown,
+        "clocks": clk,
+    }
+    plan.close()
+    return result, w
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sense128")
+    ap.add_argument("--lam", type=float, default=0.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        # the oracle on the host cores; rank 0 only
+        if rank != 0:
+            return
+        import synth
+        w = synth.workload(args.workload)
+        for _ in range(min(args.warmup, 1)):
+            oracle_cost(w, seed=99)
+        vals = []
+        desc = ""
+        for k in range(args.steps):
+            e, desc = oracle_cost(w, seed=k)
+            vals.append(e)
+        e_s = statistics.mean(vals)
+        v = 1.0 / e_s
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": e_s * 1000.0, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": desc},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    result, w = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            e, desc = oracle_cost(w, frac=1.0 / 8)
+            result["cpu_baseline"] = {"value": 1.0 / e, "unit": UNIT, "cores": 1,
+                                      "kind": "oracle", "sample": desc}
+        else:
+            result["cpu_baseline"] = None
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -182,6 +182,34 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t plan, int32_t phase,
 nrsense_status nrsense_device_status(nrsense_plan_t plan, int32_t clear, int32_t* out_host,
                                      void* stream);
 
+/*
+ * Stage profiling.  Between nrsense_profile_start and nrsense_profile_stop the
+ * plan records a CUDA event pair around every stage it launches (on the
+ * launching stream), for at most max_launches stages.  nrsense_profile_stop
+ * synchronises the device and writes, per stage s < NRSENSE_NUM_STAGES, the
+ * summed device time ms_host[s] and the number of recorded launches
+ * count_host[s]; *own_kernels_host receives the number of the library's own
+ * CUDA kernels launched in the window (cuFFT kernels excluded).
+ */
+#define NRSENSE_NUM_STAGES 13
+#define NRSENSE_STAGE_FFT_N          0  /* cuFFT, N^3 */
+#define NRSENSE_STAGE_FFT_G          1  /* cuFFT, G^3 single grid */
+#define NRSENSE_STAGE_FFT_GC         2  /* cuFFT, G^3 x C batched */
+#define NRSENSE_STAGE_DEAPOD_PAD     3  /* K1 */
+#define NRSENSE_STAGE_INTERP_IMAGE   4  /* K2 */
+#define NRSENSE_STAGE_SPREAD_IMAGE   5  /* K3 (+ partial-tile reduction) */
+#define NRSENSE_STAGE_CROP_DEAPOD    6  /* K4 */
+#define NRSENSE_STAGE_COIL_FANOUT    7  /* K5 */
+#define NRSENSE_STAGE_INTERP_KSPACE  8  /* K6 */
+#define NRSENSE_STAGE_SPREAD_KSPACE  9  /* K7 (+ partial-tile reduction) */
+#define NRSENSE_STAGE_CROP_COILSUM  10  /* K8 */
+#define NRSENSE_STAGE_VECTOR        11  /* elementwise vector kernels */
+#define NRSENSE_STAGE_SOLVER        12  /* CG reductions and updates */
+nrsense_status nrsense_profile_start(nrsense_plan_t plan, int32_t max_launches);
+nrsense_status nrsense_profile_stop(nrsense_plan_t plan, double* ms_host, int64_t* count_host,
+                                    int64_t* own_kernels_host);
+const char* nrsense_stage_name(int32_t stage);
+
 /* Static description of a status code. */
 const char* nrsense_status_string(nrsense_status status);
 

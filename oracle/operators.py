@@ -118,15 +118,13 @@ def backprojection_core(grid, q, width, beta):
 
 def projection_core(vals, q, grid_shape, width, beta):
     """P: grid[g] = sum_p c3(q_p - g) vals[p] (spreading), the exact transpose
-    of backprojection_core.  vals: (M,) or (M, C)."""
+    of backprojection_core.  vals: (M,) or (M, C).  Scatter-add by np.add.at,
+    one call per tap."""
     gs = tuple(grid_shape)
     idx, wts = zip(*[_axis_taps(q[a], gs[a], width, beta) for a in range(3)])
     ntap = wts[0].shape[1]
     vals = np.asarray(vals, dtype=np.complex128)
-    two_d = vals.ndim == 2
-    ncoil = vals.shape[1] if two_d else 1
-    size = gs[0] * gs[1] * gs[2]
-    out = np.zeros((ncoil, size), dtype=np.complex128)
+    out = np.zeros((gs[0] * gs[1] * gs[2],) + vals.shape[1:], dtype=np.complex128)
     for t0 in range(ntap):
         for t1 in range(ntap):
             w01 = wts[0][:, t0] * wts[1][:, t1]
@@ -134,15 +132,8 @@ def projection_core(vals, q, grid_shape, width, beta):
             for t2 in range(ntap):
                 w = w01 * wts[2][:, t2]
                 lin = lin01 * gs[2] + idx[2][:, t2]
-                for c in range(ncoil):
-                    v = vals[:, c] if two_d else vals
-                    wv = w * v
-                    out[c] += np.bincount(lin, weights=wv.real, minlength=size)
-                    out[c] += 1j * np.bincount(lin, weights=wv.imag, minlength=size)
-    out = out.reshape((ncoil,) + gs)
-    if two_d:
-        return np.moveaxis(out, 0, -1)
-    return out[0]
+                np.add.at(out, lin, (w[:, None] * vals) if vals.ndim == 2 else w * vals)
+    return out.reshape(gs + vals.shape[1:])
 
 
 # --------------------------------------------------------------------------

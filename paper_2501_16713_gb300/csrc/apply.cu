@@ -21,7 +21,9 @@ namespace {
     if (_st != NRSENSE_OK) return _st; \
   } while (0)
 
-nrsense_status fft(cufftHandle h, cudaStream_t s, nrsense_c64* in, nrsense_c64* out, int dir) {
+nrsense_status fft(nrsense_plan_s* p, int stage, cufftHandle h, cudaStream_t s, nrsense_c64* in,
+                   nrsense_c64* out, int dir) {
+  StageMark mark(p, stage, s);
   if (cufftSetStream(h, s) != CUFFT_SUCCESS) return NRSENSE_ERR_CUFFT;
   if (cufftExecC2C(h, reinterpret_cast<cufftComplex*>(in), reinterpret_cast<cufftComplex*>(out),
                    dir) != CUFFT_SUCCESS)
@@ -33,19 +35,27 @@ nrsense_status launched() {
   return cudaGetLastError() == cudaSuccess ? NRSENSE_OK : NRSENSE_ERR_CUDA;
 }
 
+// Launch one stage of the library's kernels: event marks when profiling, and
+// the launch count.
+#define STAGE(stage, call)                          \
+  do {                                              \
+    StageMark _mark(p, NRSENSE_STAGE_##stage, s);   \
+    p->launches += (call);                          \
+  } while (0)
+
 // m (P x nvox) = T_j x for all phases
 nrsense_status warp_forward(nrsense_plan_s* p, const nrsense_c64* x, nrsense_c64* m,
                             cudaStream_t s) {
   const Geo& g = p->geo;
   if (p->identity_warp) {
-    launch_copy_phases(g, p->P, x, m, s);
+    STAGE(VECTOR, launch_copy_phases(g, p->P, x, m, s));
     return launched();
   }
-  NRS_TRY(fft(p->fft_n, s, const_cast<nrsense_c64*>(x), p->b_xhat, CUFFT_FORWARD));
-  launch_deapod_pad(g, p->deapod, p->b_xhat, p->b_upad, s);
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_N, p->fft_n, s, const_cast<nrsense_c64*>(x), p->b_xhat, CUFFT_FORWARD));
+  STAGE(DEAPOD_PAD, launch_deapod_pad(g, p->deapod, p->b_xhat, p->b_upad, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p->fft_g, s, p->b_upad, p->b_ugrid, CUFFT_INVERSE));
-  launch_interp_image(g, p->W, p->kc, p->P, p->disp, p->b_ugrid, m, s);
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_upad, p->b_ugrid, CUFFT_INVERSE));
+  STAGE(INTERP_IMAGE, launch_interp_image(g, p->W, p->kc, p->P, p->disp, p->b_ugrid, m, s));
   return launched();
 }
 
@@ -54,25 +64,26 @@ nrsense_status warp_adjoint(nrsense_plan_s* p, const nrsense_c64* m, nrsense_c64
                             cudaStream_t s) {
   const Geo& g = p->geo;
   if (p->identity_warp) {
-    launch_sum_phases(g, p->P, m, x, s);
+    STAGE(VECTOR, launch_sum_phases(g, p->P, m, x, s));
     return launched();
   }
-  launch_spread(g, p->W, p->kc, 1, p->tiles, p->ipts, m, p->b_ugrid, p->b_scratch, p->d_status, s);
+  STAGE(SPREAD_IMAGE, launch_spread(g, p->W, p->kc, 1, p->tiles, p->ipts, m, p->b_ugrid,
+                                     p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p->fft_g, s, p->b_ugrid, p->b_ugrid, CUFFT_FORWARD));
-  launch_crop_deapod(g, p->deapod, p->b_ugrid, x, s);
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_ugrid, p->b_ugrid, CUFFT_FORWARD));
+  STAGE(CROP_DEAPOD, launch_crop_deapod(g, p->deapod, p->b_ugrid, x, s));
   NRS_TRY(launched());
-  return fft(p->fft_n, s, x, x, CUFFT_INVERSE);
+  return fft(p, NRSENSE_STAGE_FFT_N, p->fft_n, s, x, x, CUFFT_INVERSE);
 }
 
 // y_j (M_j x C) = G_j S m_j
 nrsense_status sense_phase_forward(nrsense_plan_s* p, int j, const nrsense_c64* mj,
                                    nrsense_c64* yj, cudaStream_t s) {
   const Geo& g = p->geo;
-  launch_coil_fanout_pad(g, p->C, p->deapod, p->smaps, mj, p->b_xpad, s);
+  STAGE(COIL_FANOUT, launch_coil_fanout_pad(g, p->C, p->deapod, p->smaps, mj, p->b_xpad, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p->fft_gc, s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
-  launch_interp_kspace(g, p->W, p->kc, p->C, p->kpts[j], p->b_xwork, yj, s);
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, p->fft_gc, s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
+  STAGE(INTERP_KSPACE, launch_interp_kspace(g, p->W, p->kc, p->C, p->kpts[j], p->b_xwork, yj, s));
   return launched();
 }
 
@@ -80,11 +91,11 @@ nrsense_status sense_phase_forward(nrsense_plan_s* p, int j, const nrsense_c64* 
 nrsense_status sense_phase_adjoint(nrsense_plan_s* p, int j, const nrsense_c64* yj,
                                    nrsense_c64* wj, cudaStream_t s) {
   const Geo& g = p->geo;
-  launch_spread(g, p->W, p->kc, p->C, p->tiles, p->kpts[j], yj, p->b_xwork, p->b_scratch,
-                p->d_status, s);
+  STAGE(SPREAD_KSPACE, launch_spread(g, p->W, p->kc, p->C, p->tiles, p->kpts[j], yj, p->b_xwork,
+                                     p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p->fft_gc, s, p->b_xwork, p->b_xwork, CUFFT_INVERSE));
-  launch_crop_coilsum(g, p->C, p->deapod, p->smaps, p->b_xwork, wj, s);
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, p->fft_gc, s, p->b_xwork, p->b_xwork, CUFFT_INVERSE));
+  STAGE(CROP_COILSUM, launch_crop_coilsum(g, p->C, p->deapod, p->smaps, p->b_xwork, wj, s));
   return launched();
 }
 
@@ -110,10 +121,10 @@ nrsense_status nrsense_kspace_forward(nrsense_plan_t p, int32_t phase, const nrs
   if (p->C == 0) return NRSENSE_ERR_STATE;
   if (phase < 0 || phase >= p->P) return NRSENSE_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  launch_image_to_padded(p->geo, p->C, p->deapod, v, p->b_xpad, s);
+  STAGE(COIL_FANOUT, launch_image_to_padded(p->geo, p->C, p->deapod, v, p->b_xpad, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p->fft_gc, s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
-  launch_interp_kspace(p->geo, p->W, p->kc, p->C, p->kpts[phase], p->b_xwork, y, s);
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, p->fft_gc, s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
+  STAGE(INTERP_KSPACE, launch_interp_kspace(p->geo, p->W, p->kc, p->C, p->kpts[phase], p->b_xwork, y, s));
   return launched();
 }
 
@@ -123,11 +134,11 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t p, int32_t phase, const nrs
   if (p->C == 0) return NRSENSE_ERR_STATE;
   if (phase < 0 || phase >= p->P) return NRSENSE_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  launch_spread(p->geo, p->W, p->kc, p->C, p->tiles, p->kpts[phase], y, p->b_xwork, p->b_scratch,
-                p->d_status, s);
+  STAGE(SPREAD_KSPACE, launch_spread(p->geo, p->W, p->kc, p->C, p->tiles, p->kpts[phase], y,
+                                     p->b_xwork, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p->fft_gc, s, p->b_xwork, p->b_xwork, CUFFT_INVERSE));
-  launch_crop_to_coils(p->geo, p->C, p->deapod, p->b_xwork, v, s);
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, p->fft_gc, s, p->b_xwork, p->b_xwork, CUFFT_INVERSE));
+  STAGE(CROP_COILSUM, launch_crop_to_coils(p->geo, p->C, p->deapod, p->b_xwork, v, s));
   return launched();
 }
 
@@ -181,7 +192,7 @@ nrsense_status nrsense_apply_normal(nrsense_plan_t p, const nrsense_c64* x, doub
   }
   NRS_TRY(warp_adjoint(p, p->b_m, out, s));
   if (lambda != 0.0) {
-    launch_axpby(p->geo.nvox, x, float(lambda), out, 1.0f, s);
+    STAGE(VECTOR, launch_axpby(p->geo.nvox, x, float(lambda), out, 1.0f, s));
     NRS_TRY(launched());
   }
   return NRSENSE_OK;

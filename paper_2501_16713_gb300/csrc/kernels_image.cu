@@ -145,21 +145,23 @@ inline unsigned blocks_for(long long n, int threads) {
 
 }  // namespace
 
-void launch_deapod_pad(const Geo& g, const float* deapod, const nrsense_c64* xhat,
+int launch_deapod_pad(const Geo& g, const float* deapod, const nrsense_c64* xhat,
                        nrsense_c64* upad, cudaStream_t s) {
   deapod_pad_kernel<<<blocks_for(g.nvox, 256), 256, 0, s>>>(
       g, deapod, reinterpret_cast<const float2*>(xhat), reinterpret_cast<float2*>(upad),
       float(1.0 / double(g.nvox)));
+  return 1;
 }
 
-void launch_crop_deapod(const Geo& g, const float* deapod, const nrsense_c64* ufreq,
+int launch_crop_deapod(const Geo& g, const float* deapod, const nrsense_c64* ufreq,
                         nrsense_c64* xhat, cudaStream_t s) {
   crop_deapod_kernel<<<blocks_for(g.nvox, 256), 256, 0, s>>>(
       g, deapod, reinterpret_cast<const float2*>(ufreq), reinterpret_cast<float2*>(xhat),
       float(1.0 / double(g.nvox)));
+  return 1;
 }
 
-void launch_interp_image(const Geo& g, int W, const KernelCoefs& kc, int P,
+int launch_interp_image(const Geo& g, int W, const KernelCoefs& kc, int P,
                          const float* disp, const nrsense_c64* u, nrsense_c64* m,
                          cudaStream_t s) {
   const auto* up = reinterpret_cast<const float2*>(u);
@@ -168,24 +170,28 @@ void launch_interp_image(const Geo& g, int W, const KernelCoefs& kc, int P,
     interp_image_kernel<4><<<blocks_for(g.nvox, 256), 256, 0, s>>>(g, kc, P, disp, up, mp);
   else
     interp_image_kernel<6><<<blocks_for(g.nvox, 256), 256, 0, s>>>(g, kc, P, disp, up, mp);
+  return 1;
 }
 
-void launch_axpby(long long n, const nrsense_c64* x, float a, nrsense_c64* y, float b,
+int launch_axpby(long long n, const nrsense_c64* x, float a, nrsense_c64* y, float b,
                   cudaStream_t s) {
   axpby_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, reinterpret_cast<const float2*>(x), a,
                                                   reinterpret_cast<float2*>(y), b);
+  return 1;
 }
 
-void launch_copy_phases(const Geo& g, int P, const nrsense_c64* x, nrsense_c64* m,
+int launch_copy_phases(const Geo& g, int P, const nrsense_c64* x, nrsense_c64* m,
                         cudaStream_t s) {
   copy_phases_kernel<<<blocks_for(g.nvox, 256), 256, 0, s>>>(
       g.nvox, P, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(m));
+  return 1;
 }
 
-void launch_sum_phases(const Geo& g, int P, const nrsense_c64* m, nrsense_c64* x,
+int launch_sum_phases(const Geo& g, int P, const nrsense_c64* m, nrsense_c64* x,
                        cudaStream_t s) {
   sum_phases_kernel<<<blocks_for(g.nvox, 256), 256, 0, s>>>(
       g.nvox, P, reinterpret_cast<const float2*>(m), reinterpret_cast<float2*>(x));
+  return 1;
 }
 
 }  // namespace nrs

@@ -174,9 +174,9 @@ inline unsigned blocks_for(long long n, int threads) {
 }
 
 template <int W>
-void interp_dispatch(const Geo& g, const KernelCoefs& kc, int C, const PointSet& ps,
+int interp_dispatch(const Geo& g, const KernelCoefs& kc, int C, const PointSet& ps,
                      const float2* grid, float2* y, cudaStream_t s) {
-  if (ps.npts == 0) return;
+  if (ps.npts == 0) return 0;
   if (C % 4 == 0) {
     const long long n = ps.npts * (C / 4);
     interp_kspace_kernel<W, 4><<<blocks_for(n, 256), 256, 0, s>>>(g, kc, C, ps.npts, ps.qs,
@@ -190,47 +190,50 @@ void interp_dispatch(const Geo& g, const KernelCoefs& kc, int C, const PointSet&
     interp_kspace_kernel<W, 1><<<blocks_for(n, 256), 256, 0, s>>>(g, kc, C, ps.npts, ps.qs,
                                                                    ps.perm, grid, y);
   }
+  return 1;
 }
 
 }  // namespace
 
-void launch_coil_fanout_pad(const Geo& g, int C, const float* deapod,
+int launch_coil_fanout_pad(const Geo& g, int C, const float* deapod,
                             const nrsense_c64* smaps, const nrsense_c64* m,
                             nrsense_c64* xpad, cudaStream_t s) {
   coil_fanout_pad_kernel<<<blocks_for(g.nvox * C, 256), 256, 0, s>>>(
       g, C, deapod, reinterpret_cast<const float2*>(smaps), reinterpret_cast<const float2*>(m),
       reinterpret_cast<float2*>(xpad));
+  return 1;
 }
 
-void launch_image_to_padded(const Geo& g, int C, const float* deapod,
+int launch_image_to_padded(const Geo& g, int C, const float* deapod,
                             const nrsense_c64* v, nrsense_c64* xpad, cudaStream_t s) {
   image_to_padded_kernel<<<blocks_for(g.nvox * C, 256), 256, 0, s>>>(
       g, C, deapod, reinterpret_cast<const float2*>(v), reinterpret_cast<float2*>(xpad));
+  return 1;
 }
 
-void launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C,
+int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C,
                           const PointSet& ps, const nrsense_c64* grid, nrsense_c64* y,
                           cudaStream_t s) {
   const auto* gp = reinterpret_cast<const float2*>(grid);
   auto* yp = reinterpret_cast<float2*>(y);
-  if (W == 4)
-    interp_dispatch<4>(g, kc, C, ps, gp, yp, s);
-  else
-    interp_dispatch<6>(g, kc, C, ps, gp, yp, s);
+  return W == 4 ? interp_dispatch<4>(g, kc, C, ps, gp, yp, s)
+                : interp_dispatch<6>(g, kc, C, ps, gp, yp, s);
 }
 
-void launch_crop_coilsum(const Geo& g, int C, const float* deapod,
+int launch_crop_coilsum(const Geo& g, int C, const float* deapod,
                          const nrsense_c64* smaps, const nrsense_c64* xg,
                          nrsense_c64* w, cudaStream_t s) {
   crop_coilsum_kernel<<<blocks_for(g.nvox, 256), 256, 0, s>>>(
       g, C, deapod, reinterpret_cast<const float2*>(smaps), reinterpret_cast<const float2*>(xg),
       reinterpret_cast<float2*>(w));
+  return 1;
 }
 
-void launch_crop_to_coils(const Geo& g, int C, const float* deapod,
+int launch_crop_to_coils(const Geo& g, int C, const float* deapod,
                           const nrsense_c64* xg, nrsense_c64* v, cudaStream_t s) {
   crop_to_coils_kernel<<<blocks_for(g.nvox * C, 256), 256, 0, s>>>(
       g, C, deapod, reinterpret_cast<const float2*>(xg), reinterpret_cast<float2*>(v));
+  return 1;
 }
 
 }  // namespace nrs

@@ -155,7 +155,7 @@ __global__ void reduce_kernel(Geo g, int C, TilePlan tp, const ReduceItem* __res
 }
 
 template <int W, int CC>
-void spread_dispatch(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& tp,
+int spread_dispatch(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& tp,
                      const PointSet& ps, const float2* vals, float2* grid, float2* scratch,
                      cudaStream_t s) {
   const int coil_chunks = (C + CC - 1) / CC;
@@ -166,29 +166,31 @@ void spread_dispatch(const Geo& g, const KernelCoefs& kc, int C, const TilePlan&
   if (ps.n_reduces > 0) {
     dim3 rd(ps.n_reduces, coil_chunks);
     reduce_kernel<CC><<<rd, 256, 0, s>>>(g, C, tp, ps.reduces, scratch, grid);
+    return 2;
   }
+  return 1;
 }
 
 }  // namespace
 
-void launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
+int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                    const PointSet& ps, const nrsense_c64* vals, nrsense_c64* grid,
                    nrsense_c64* scratch, int32_t* status, cudaStream_t s) {
   (void)status;
-  if (ps.n_items == 0) return;
+  if (ps.n_items == 0) return 0;
   const auto* v = reinterpret_cast<const float2*>(vals);
   auto* gr = reinterpret_cast<float2*>(grid);
   auto* sc = reinterpret_cast<float2*>(scratch);
   if (W == 4) {
-    if (C == 1) spread_dispatch<4, 1>(g, kc, C, tp, ps, v, gr, sc, s);
-    else if (C <= 2) spread_dispatch<4, 2>(g, kc, C, tp, ps, v, gr, sc, s);
-    else if (C <= 4) spread_dispatch<4, 4>(g, kc, C, tp, ps, v, gr, sc, s);
-    else spread_dispatch<4, 8>(g, kc, C, tp, ps, v, gr, sc, s);
+    if (C == 1) return spread_dispatch<4, 1>(g, kc, C, tp, ps, v, gr, sc, s);
+    else if (C <= 2) return spread_dispatch<4, 2>(g, kc, C, tp, ps, v, gr, sc, s);
+    else if (C <= 4) return spread_dispatch<4, 4>(g, kc, C, tp, ps, v, gr, sc, s);
+    else return spread_dispatch<4, 8>(g, kc, C, tp, ps, v, gr, sc, s);
   } else {
-    if (C == 1) spread_dispatch<6, 1>(g, kc, C, tp, ps, v, gr, sc, s);
-    else if (C <= 2) spread_dispatch<6, 2>(g, kc, C, tp, ps, v, gr, sc, s);
-    else if (C <= 4) spread_dispatch<6, 4>(g, kc, C, tp, ps, v, gr, sc, s);
-    else spread_dispatch<6, 8>(g, kc, C, tp, ps, v, gr, sc, s);
+    if (C == 1) return spread_dispatch<6, 1>(g, kc, C, tp, ps, v, gr, sc, s);
+    else if (C <= 2) return spread_dispatch<6, 2>(g, kc, C, tp, ps, v, gr, sc, s);
+    else if (C <= 4) return spread_dispatch<6, 4>(g, kc, C, tp, ps, v, gr, sc, s);
+    else return spread_dispatch<6, 8>(g, kc, C, tp, ps, v, gr, sc, s);
   }
 }
 

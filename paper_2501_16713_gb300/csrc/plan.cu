@@ -191,7 +191,7 @@ nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, Po
       const long long step = (L + nchunk - 1) / nchunk;
       ReduceItem r{int32_t(t), slots, nchunk, 0};
       for (int k = 0; k < nchunk; ++k) {
-        const long long cb = b + k * step, ce = std::min(e, cb + step);
+        const long long cb = std::min(e, b + k * step), ce = std::min(e, cb + step);
         items.push_back({int32_t(t), int32_t(cb), int32_t(ce), slots + k});
       }
       slots += nchunk;
@@ -402,6 +402,8 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
 }
 
 void release(nrsense_plan_s* p) {
+  for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
+  p->prof_events.clear();
   if (p->have_fft_n) cufftDestroy(p->fft_n);
   if (p->have_fft_g) cufftDestroy(p->fft_g);
   if (p->have_fft_gc) cufftDestroy(p->fft_gc);
@@ -471,6 +473,46 @@ nrsense_status nrsense_plan_info(nrsense_plan_t p, nrsense_info* out) {
   out->split_tiles = split;
   out->device_bytes = p->device_bytes;
   return NRSENSE_OK;
+}
+
+nrsense_status nrsense_profile_start(nrsense_plan_t p, int32_t max_launches) {
+  if (p == nullptr || max_launches < 0 || max_launches > (1 << 20)) return NRSENSE_ERR_ARG;
+  while (p->prof_events.size() < size_t(2 * max_launches)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return NRSENSE_ERR_CUDA;
+    p->prof_events.push_back(e);
+  }
+  p->prof_stage.clear();
+  p->prof_on = true;
+  p->launches_at_start = p->launches;
+  return NRSENSE_OK;
+}
+
+nrsense_status nrsense_profile_stop(nrsense_plan_t p, double* ms, int64_t* count,
+                                    int64_t* own_kernels) {
+  if (p == nullptr) return NRSENSE_ERR_ARG;
+  p->prof_on = false;
+  if (cudaDeviceSynchronize() != cudaSuccess) return NRSENSE_ERR_CUDA;
+  if (ms) for (int i = 0; i < NRSENSE_NUM_STAGES; ++i) ms[i] = 0.0;
+  if (count) for (int i = 0; i < NRSENSE_NUM_STAGES; ++i) count[i] = 0;
+  for (size_t k = 0; k < p->prof_stage.size(); ++k) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p->prof_events[2 * k], p->prof_events[2 * k + 1]) != cudaSuccess)
+      return NRSENSE_ERR_CUDA;
+    const int st = p->prof_stage[k];
+    if (ms) ms[st] += double(t);
+    if (count) count[st] += 1;
+  }
+  if (own_kernels) *own_kernels = p->launches - p->launches_at_start;
+  p->prof_stage.clear();
+  return NRSENSE_OK;
+}
+
+const char* nrsense_stage_name(int32_t st) {
+  static const char* names[NRSENSE_NUM_STAGES] = {
+      "fft_n", "fft_g", "fft_gc", "deapod_pad", "interp_image", "spread_image", "crop_deapod",
+      "coil_fanout_pad", "interp_kspace", "spread_kspace", "crop_coilsum", "vector", "solver"};
+  return (st >= 0 && st < NRSENSE_NUM_STAGES) ? names[st] : "unknown";
 }
 
 const char* nrsense_status_string(nrsense_status s) {

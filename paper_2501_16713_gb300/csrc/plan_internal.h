@@ -74,43 +74,69 @@ struct nrsense_plan_s {
 
   long long device_bytes = 0;
   std::vector<void*> allocations;
+
+  // stage profiling (nrsense_profile_start/stop)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_events;  // pairs
+  std::vector<int> prof_stage;           // stage of each recorded pair
+  long long launches = 0;                // own kernels launched (always counted)
+  long long launches_at_start = 0;
 };
+
+namespace nrs {
+// RAII stage marker: records an event pair around a stage when profiling.
+struct StageMark {
+  nrsense_plan_s* p;
+  cudaStream_t s;
+  int pair = -1;
+  StageMark(nrsense_plan_s* plan, int stage, cudaStream_t stream) : p(plan), s(stream) {
+    if (p->prof_on && p->prof_stage.size() * 2 + 2 <= p->prof_events.size()) {
+      pair = int(p->prof_stage.size());
+      p->prof_stage.push_back(stage);
+      cudaEventRecord(p->prof_events[2 * pair], s);
+    }
+  }
+  ~StageMark() {
+    if (pair >= 0) cudaEventRecord(p->prof_events[2 * pair + 1], s);
+  }
+};
+}  // namespace nrs
 
 namespace nrs {
 
 // ---- launchers (kernels_*.cu) -------------------------------------------
 // image space
-void launch_deapod_pad(const Geo& g, const float* deapod, const nrsense_c64* xhat,
+int launch_deapod_pad(const Geo& g, const float* deapod, const nrsense_c64* xhat,
                        nrsense_c64* upad, cudaStream_t s);
-void launch_crop_deapod(const Geo& g, const float* deapod, const nrsense_c64* ufreq,
+int launch_crop_deapod(const Geo& g, const float* deapod, const nrsense_c64* ufreq,
                         nrsense_c64* xhat, cudaStream_t s);
-void launch_interp_image(const Geo& g, int W, const KernelCoefs& kc, int P,
+int launch_interp_image(const Geo& g, int W, const KernelCoefs& kc, int P,
                          const float* disp, const nrsense_c64* u, nrsense_c64* m,
                          cudaStream_t s);
-void launch_axpby(long long n, const nrsense_c64* x, float a, nrsense_c64* y, float b,
+int launch_axpby(long long n, const nrsense_c64* x, float a, nrsense_c64* y, float b,
                   cudaStream_t s);
-void launch_copy_phases(const Geo& g, int P, const nrsense_c64* x, nrsense_c64* m,
+int launch_copy_phases(const Geo& g, int P, const nrsense_c64* x, nrsense_c64* m,
                         cudaStream_t s);
-void launch_sum_phases(const Geo& g, int P, const nrsense_c64* m, nrsense_c64* x,
+int launch_sum_phases(const Geo& g, int P, const nrsense_c64* m, nrsense_c64* x,
                        cudaStream_t s);
 
 // k space
-void launch_coil_fanout_pad(const Geo& g, int C, const float* deapod,
+int launch_coil_fanout_pad(const Geo& g, int C, const float* deapod,
                             const nrsense_c64* smaps, const nrsense_c64* m,
                             nrsense_c64* xpad, cudaStream_t s);
-void launch_image_to_padded(const Geo& g, int C, const float* deapod,
+int launch_image_to_padded(const Geo& g, int C, const float* deapod,
                             const nrsense_c64* v, nrsense_c64* xpad, cudaStream_t s);
-void launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C,
+int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C,
                           const PointSet& ps, const nrsense_c64* grid, nrsense_c64* y,
                           cudaStream_t s);
-void launch_crop_coilsum(const Geo& g, int C, const float* deapod,
+int launch_crop_coilsum(const Geo& g, int C, const float* deapod,
                          const nrsense_c64* smaps, const nrsense_c64* xg,
                          nrsense_c64* w, cudaStream_t s);
-void launch_crop_to_coils(const Geo& g, int C, const float* deapod,
+int launch_crop_to_coils(const Geo& g, int C, const float* deapod,
                           const nrsense_c64* xg, nrsense_c64* v, cudaStream_t s);
 
 // spreading (both domains)
-void launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
+int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                    const PointSet& ps, const nrsense_c64* vals, nrsense_c64* grid,
                    nrsense_c64* scratch, int32_t* status, cudaStream_t s);
 // coils handled by one spreading CTA, and the tile edge used by the kernels

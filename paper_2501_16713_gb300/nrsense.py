@@ -62,7 +62,13 @@ _SIGS = {
     "nrsense_kspace_adjoint": [_VP, ctypes.c_int32, _VP, _VP, _VP],
     "nrsense_device_status": [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _VP],
     "nrsense_status_string": [ctypes.c_int32],
+    "nrsense_profile_start": [_VP, ctypes.c_int32],
+    "nrsense_profile_stop": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                             ctypes.POINTER(ctypes.c_int64)],
+    "nrsense_stage_name": [ctypes.c_int32],
 }
+NUM_STAGES = 13
+_STRING_RESULT = ("nrsense_status_string", "nrsense_stage_name")
 
 _lib = None
 
@@ -79,7 +85,7 @@ def load(path: str | None = None):
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name == "nrsense_status_string" else ctypes.c_int32
+        fn.restype = ctypes.c_char_p if name in _STRING_RESULT else ctypes.c_int32
     if path is None:
         _lib = lib
     return lib
@@ -263,6 +269,19 @@ class Plan:
         _check(self.lib.nrsense_device_status(self._h, int(bool(clear)), ctypes.byref(v),
                                               _stream(stream)), "nrsense_device_status")
         return v.value
+
+    def profile_start(self, max_launches=65536):
+        _check(self.lib.nrsense_profile_start(self._h, int(max_launches)), "nrsense_profile_start")
+
+    def profile_stop(self):
+        """Synchronise and return ({stage: (ms, launches)}, own kernel launches)."""
+        ms = (ctypes.c_double * NUM_STAGES)()
+        cnt = (ctypes.c_int64 * NUM_STAGES)()
+        own = ctypes.c_int64()
+        _check(self.lib.nrsense_profile_stop(self._h, ms, cnt, ctypes.byref(own)),
+               "nrsense_profile_stop")
+        names = [self.lib.nrsense_stage_name(i).decode() for i in range(NUM_STAGES)]
+        return {n: (ms[i], cnt[i]) for i, n in enumerate(names)}, own.value
 
     def phase_slice(self, y, j):
         """Rows of phase j in a stacked (sum M_j, C) k-space array."""
