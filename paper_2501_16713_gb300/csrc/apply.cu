@@ -7,7 +7,8 @@
 //        grid) -> F_G -> K4 (Z^H, 1/C) -> F_N^H
 //  G_j S (per phase):                       K5 (S, 1/c*, Z) -> F_G (C coils
 //        batched) -> K6 (B^(k))
-//  S^H G_j^H (per phase):                   K7 (P^(k)) -> F_G^H (batched) ->
+//  S^H G_j^H (per phase):                   K7 (P^(k), into a buffer whose
+//        empty tiles stay zero) -> F_G^H (batched, out of place) ->
 //        K8 (Z^H, 1/c, S^H)
 #include "plan_internal.h"
 
@@ -67,7 +68,7 @@ nrsense_status warp_adjoint(nrsense_plan_s* p, const nrsense_c64* m, nrsense_c64
     STAGE(VECTOR, launch_sum_phases(g, p->P, m, x, s));
     return launched();
   }
-  STAGE(SPREAD_IMAGE, launch_spread(g, p->W, p->kc, 1, p->tiles, p->ipts, m, p->b_ugrid,
+  STAGE(SPREAD_IMAGE, launch_spread(g, p->W, p->kc, 1, p->ipts, m, p->b_ugrid,
                                      p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_ugrid, p->b_ugrid, CUFFT_FORWARD));
@@ -91,10 +92,10 @@ nrsense_status sense_phase_forward(nrsense_plan_s* p, int j, const nrsense_c64* 
 nrsense_status sense_phase_adjoint(nrsense_plan_s* p, int j, const nrsense_c64* yj,
                                    nrsense_c64* wj, cudaStream_t s) {
   const Geo& g = p->geo;
-  STAGE(SPREAD_KSPACE, launch_spread(g, p->W, p->kc, p->C, p->tiles, p->kpts[j], yj, p->b_xwork,
-                                     p->b_scratch, p->d_status, s));
+  STAGE(SPREAD_KSPACE, launch_spread(g, p->W, p->kc, p->C, p->kpts[j], yj,
+                                     p->b_xspread, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, p->fft_gc, s, p->b_xwork, p->b_xwork, CUFFT_INVERSE));
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, p->fft_gc, s, p->b_xspread, p->b_xwork, CUFFT_INVERSE));
   STAGE(CROP_COILSUM, launch_crop_coilsum(g, p->C, p->deapod, p->smaps, p->b_xwork, wj, s));
   return launched();
 }
@@ -134,10 +135,10 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t p, int32_t phase, const nrs
   if (p->C == 0) return NRSENSE_ERR_STATE;
   if (phase < 0 || phase >= p->P) return NRSENSE_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  STAGE(SPREAD_KSPACE, launch_spread(p->geo, p->W, p->kc, p->C, p->tiles, p->kpts[phase], y,
-                                     p->b_xwork, p->b_scratch, p->d_status, s));
+  STAGE(SPREAD_KSPACE, launch_spread(p->geo, p->W, p->kc, p->C, p->kpts[phase], y,
+                                     p->b_xspread, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, p->fft_gc, s, p->b_xwork, p->b_xwork, CUFFT_INVERSE));
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, p->fft_gc, s, p->b_xspread, p->b_xwork, CUFFT_INVERSE));
   STAGE(CROP_COILSUM, launch_crop_to_coils(p->geo, p->C, p->deapod, p->b_xwork, v, s));
   return launched();
 }

@@ -43,12 +43,18 @@ __host__ __device__ inline void unpack_base(uint32_t p, int& b0, int& b1, int& b
 // list[begin, end) are spread into grid tile `tile`; slot < 0 writes the tile
 // to the grid directly, slot >= 0 writes a partial tile to scratch slot
 // `slot` (heavy tiles are split into several items and reduced afterwards).
+// The same record describes interpolation work (sorted point range of a tile).
 struct SpreadItem {
   int32_t tile;
   int32_t begin;
   int32_t end;
   int32_t slot;
 };
+
+// Offsets (relative to the item's begin) of the list entries of each
+// first-tap plane offset r0 in (-W, T), stored per spreading item:
+// bins[b] = first entry with r0 + W - 1 >= b, b = 0 .. W + T - 1.
+constexpr int kMaxBins = kMaxWidth + 16;
 
 // A split tile: partial tiles in scratch slots [first, first + count).
 struct ReduceItem {
@@ -69,6 +75,27 @@ __device__ __forceinline__ void kernel_weights(float f, const KernelCoefs& kc, f
     for (int k = kNumCoef - 2; k >= 0; --k) acc = fmaf(acc, s, kc.c[t][k]);
     w[t] = acc;
   }
+}
+
+// Select w[t] for a runtime t in [0, W) without dynamic register indexing.
+template <int W>
+__device__ __forceinline__ float select_tap(const float (&w)[W], int t) {
+  float r = 0.f;
+#pragma unroll
+  for (int k = 0; k < W; ++k) r = (t == k) ? w[k] : r;
+  return r;
+}
+
+// cp.async helpers (sm_80+): 8-byte global -> shared copy, zero-filled when
+// `valid` is false.
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem, bool valid) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int src_size = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem),
+               "r"(src_size));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 __device__ __forceinline__ int wrap_once(int i, int g) {

@@ -1,9 +1,9 @@
 // k-space half of the nonrigid SENSE operator: coil sensitivities S and
 // inverse k-space gridding G_j (section "k-space Gridding", inverse gridding
 // diagram 1/c* -> Z -> F -> B^(k)) and the elementwise ends of k-space
-// gridding G_j^H (F^H -> Z^H -> 1/c, then S^H).  Grids hold all C coils
-// interleaved ([G^3][C], coil fastest) so that one tap of one sample is one
-// contiguous C*8-byte read.
+// gridding G_j^H (F^H -> Z^H -> 1/c, then S^H).  Coil grids are coil-major
+// ([C][G^3]) so that cuFFT transforms contiguous batches; coil maps keep the
+// caller's (C, N^3) layout.
 #include "plan_internal.h"
 
 namespace nrs {
@@ -16,139 +16,214 @@ __device__ __forceinline__ int centred_pos(int i, int N, int G) {
   return c < 0 ? c + G : c;
 }
 
-// K5: v_{j,c}[n'] = S_c[n] m_j[n] / C3(n'/G) written into the centred N^3 block
-// of the zero-padded coil grids (steps S, 1/c* and Z).
-__global__ void coil_fanout_pad_kernel(Geo g, int C, const float* __restrict__ dtab,
-                                       const float2* __restrict__ smaps,  // [nvox][C]
-                                       const float2* __restrict__ m,
-                                       float2* __restrict__ xpad) {         // [G^3][C]
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= g.nvox * C) return;
-  const long long idx = t / C;
-  const int c = int(t - idx * C);
+struct VoxelPos {
+  long long grid;  // linear index of the centred voxel on the G grid
+  float deapod;    // 1/C3(n'/G)
+};
+
+__device__ __forceinline__ VoxelPos voxel_pos(const Geo& g, const float* __restrict__ dtab,
+                                              long long idx) {
   const int i2 = int(idx % g.n2);
   const long long r = idx / g.n2;
   const int i1 = int(r % g.n1);
   const int i0 = int(r / g.n1);
-  const float w = dtab[i0] * dtab[g.n0 + i1] * dtab[g.n0 + g.n1 + i2];
-  const float2 mv = m[idx];
-  const float2 sv = smaps[t];
-  const float2 v = make_float2((sv.x * mv.x - sv.y * mv.y) * w, (sv.x * mv.y + sv.y * mv.x) * w);
-  const long long p = ((long long)centred_pos(i0, g.n0, g.g0) * g.g1 + centred_pos(i1, g.n1, g.g1)) *
-                          g.g2 + centred_pos(i2, g.n2, g.g2);
-  xpad[p * C + c] = v;
+  VoxelPos v;
+  v.deapod = __ldg(dtab + i0) * __ldg(dtab + g.n0 + i1) * __ldg(dtab + g.n0 + g.n1 + i2);
+  v.grid = ((long long)centred_pos(i0, g.n0, g.g0) * g.g1 + centred_pos(i1, g.n1, g.g1)) * g.g2 +
+           centred_pos(i2, g.n2, g.g2);
+  return v;
+}
+
+// K5: v_{j,c}[n'] = S_c[n] m_j[n] / C3(n'/G) written into the centred N^3 block
+// of the zero-padded coil grids (steps S, 1/c* and Z).  Thread = (coil, voxel).
+__global__ void coil_fanout_pad_kernel(Geo g, int C, const float* __restrict__ dtab,
+                                       const float2* __restrict__ smaps,  // [C][nvox]
+                                       const float2* __restrict__ m,
+                                       float2* __restrict__ xpad) {         // [C][G^3]
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= g.nvox * C) return;
+  const int c = int(t / g.nvox);
+  const long long idx = t - (long long)c * g.nvox;
+  const VoxelPos vp = voxel_pos(g, dtab, idx);
+  const float2 mv = __ldg(m + idx);
+  const float2 sv = __ldg(smaps + t);
+  const float w = vp.deapod;
+  xpad[(long long)c * g.ngrid + vp.grid] =
+      make_float2((sv.x * mv.x - sv.y * mv.y) * w, (sv.x * mv.y + sv.y * mv.x) * w);
 }
 
 // Stage variant of K5 without S: coil images v (C, N^3) -> padded grids.
 __global__ void image_to_padded_kernel(Geo g, int C, const float* __restrict__ dtab,
-                                       const float2* __restrict__ v,  // [C][nvox]
-                                       float2* __restrict__ xpad) {
+                                       const float2* __restrict__ v, float2* __restrict__ xpad) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.nvox * C) return;
-  const long long idx = t / C;
-  const int c = int(t - idx * C);
-  const int i2 = int(idx % g.n2);
-  const long long r = idx / g.n2;
-  const int i1 = int(r % g.n1);
-  const int i0 = int(r / g.n1);
-  const float w = dtab[i0] * dtab[g.n0 + i1] * dtab[g.n0 + g.n1 + i2];
-  const float2 vv = v[(long long)c * g.nvox + idx];
-  const long long p = ((long long)centred_pos(i0, g.n0, g.g0) * g.g1 + centred_pos(i1, g.n1, g.g1)) *
-                          g.g2 + centred_pos(i2, g.n2, g.g2);
-  xpad[p * C + c] = make_float2(vv.x * w, vv.y * w);
+  const int c = int(t / g.nvox);
+  const long long idx = t - (long long)c * g.nvox;
+  const VoxelPos vp = voxel_pos(g, dtab, idx);
+  const float2 vv = __ldg(v + t);
+  xpad[(long long)c * g.ngrid + vp.grid] = make_float2(vv.x * vp.deapod, vv.y * vp.deapod);
 }
 
 // K6: y_{j,s,c} = sum_taps c3(q_s - g) X_{j,c}[g] (Backprojection Core B^(k)).
-// Thread = (sorted sample, group of CPT coils); coordinates are read once per
-// thread and all CPT coils of a tap come from one contiguous load.
-template <int W, int CPT>
-__global__ void __launch_bounds__(256) interp_kspace_kernel(
-    Geo g, KernelCoefs kc, int C, long long M, const float4* __restrict__ qs,
-    const int32_t* __restrict__ perm, const float2* __restrict__ grid, float2* __restrict__ y) {
-  const int tps = C / CPT;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= M * tps) return;
-  const long long s = t / tps;
-  const int cg = int(t - s * tps);
-  const float4 q = __ldg(qs + s);
-  int b0, b1, b2;
-  unpack_base(__float_as_uint(q.w), b0, b1, b2);
-  float w0[W], w1[W], w2[W];
-  kernel_weights<W>(q.x, kc, w0);
-  kernel_weights<W>(q.y, kc, w1);
-  kernel_weights<W>(q.z, kc, w2);
-  int x2[W];
+// CTA = one 8^3 tile and the sorted samples whose first tap lies in it: the
+// tile plus its (W-1)-point upper halo of CC coil grids is staged once into
+// shared memory with asynchronous copies, coil-interleaved ([z][y][x][c]).
+// A group of W*CC/2 lanes serves one sample: lane = (tap x, coil pair), so a
+// quarter-warp reads 128 contiguous bytes of one tap row (no bank
+// conflicts); each lane evaluates only its own tap's weights (coefficients
+// in shared memory), gets the other axes' by shuffles, and the tap-x partial
+// sums are reduced by shuffles at the end.
+template <int W, int CC>
+__global__ void __launch_bounds__(256) interp_tile_kernel(
+    Geo g, KernelCoefs kc, int C, TilePlan tp, const SpreadItem* __restrict__ items,
+    const float4* __restrict__ qs, const int32_t* __restrict__ perm,
+    const float2* __restrict__ grid, float2* __restrict__ y) {
+  constexpr int T = 8, H = T + W - 1, H3 = H * H * H;
+  constexpr int NQ = CC / 2, LPS = W * NQ, SPW = 32 / LPS;  // lanes/sample, samples/warp
+  extern __shared__ float4 smem_raw[];
+  float2* halo = reinterpret_cast<float2*>(smem_raw);  // [H][H][H][CC]
+  __shared__ float s_coef[W][kNumCoef];
+  const SpreadItem it = items[blockIdx.x];
+  const int coil0 = blockIdx.y * CC;
+  const int tz = it.tile / (tp.nt1 * tp.nt2);
+  const int rem = it.tile - tz * (tp.nt1 * tp.nt2);
+  const int ty = rem / tp.nt2;
+  const int tx = rem - ty * tp.nt2;
+  const int o0 = tz * T, o1 = ty * T, o2 = tx * T;
+  if (threadIdx.x < W * kNumCoef) s_coef[threadIdx.x / kNumCoef][threadIdx.x % kNumCoef] =
+      kc.c[threadIdx.x / kNumCoef][threadIdx.x % kNumCoef];
+  // stage: consecutive threads walk x, so global reads coalesce along rows
+  for (int i = threadIdx.x; i < CC * H3; i += blockDim.x) {
+    const int c = i / H3;
+    const int r = i - c * H3;
+    const int z = r / (H * H), yy = (r / H) % H, x = r % H;
+    const int gz = wrap_once(o0 + z, g.g0), gy = wrap_once(o1 + yy, g.g1),
+              gx = wrap_once(o2 + x, g.g2);
+    const bool valid = coil0 + c < C;
+    const float2* src =
+        grid + (valid ? (long long)(coil0 + c) * g.ngrid + ((long long)gz * g.g1 + gy) * g.g2 + gx
+                      : 0);
+    cp_async_8(halo + r * CC + c, src, valid);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPS;                 // sample slot in the warp
+  const int gl = lane - grp * LPS;            // lane in the group
+  const int q = gl % NQ, txl = gl / NQ;       // coil pair, tap x
+  const int gbase = grp * LPS;
+  const bool active_lane = grp < SPW;
+  const int nwarps = blockDim.x >> 5;
+  for (int s0 = it.begin + warp * SPW; s0 < it.end; s0 += nwarps * SPW) {
+    const int s = s0 + grp;
+    const bool live = active_lane && s < it.end;
+    float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
+    int l0 = 0, l1 = 0, l2 = 0;
+    if (live) {
+      qv = __ldg(qs + s);
+      int b0, b1, b2;
+      unpack_base(__float_as_uint(qv.w), b0, b1, b2);
+      l0 = min(max(b0 - o0, 0), T - 1);  // in range for a well-formed plan
+      l1 = min(max(b1 - o1, 0), T - 1);
+      l2 = min(max(b2 - o2, 0), T - 1);
+    }
+    // this lane's tap txl on each axis
+    float w0t = 0.f, w1t = 0.f, w2t = 0.f;
+    {
+      const float s0f = fmaf(2.f, qv.x, -1.f), s1f = fmaf(2.f, qv.y, -1.f),
+                  s2f = fmaf(2.f, qv.z, -1.f);
+      float a0 = s_coef[txl][kNumCoef - 1], a1 = a0, a2 = a0;
 #pragma unroll
-  for (int k = 0; k < W; ++k) x2[k] = wrap_once(b2 + k, g.g2);
-  float acc[2 * CPT];
+      for (int k = kNumCoef - 2; k >= 0; --k) {
+        const float ck = s_coef[txl][k];
+        a0 = fmaf(a0, s0f, ck);
+        a1 = fmaf(a1, s1f, ck);
+        a2 = fmaf(a2, s2f, ck);
+      }
+      w0t = a0;
+      w1t = a1;
+      w2t = a2;
+    }
+    float w0[W], w1[W];
 #pragma unroll
-  for (int i = 0; i < 2 * CPT; ++i) acc[i] = 0.f;
-  const float2* gbase = grid + cg * CPT;
+    for (int t = 0; t < W; ++t) {
+      w0[t] = __shfl_sync(0xffffffffu, w0t, gbase + t * NQ);
+      w1[t] = __shfl_sync(0xffffffffu, w1t, gbase + t * NQ);
+    }
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+      const float4* base4 = reinterpret_cast<const float4*>(halo + ((l0 * H + l1) * H + l2 + txl) * CC) + q;
 #pragma unroll
-  for (int t0 = 0; t0 < W; ++t0) {
-    const long long row0 = (long long)wrap_once(b0 + t0, g.g0) * g.g1;
+      for (int t0 = 0; t0 < W; ++t0) {
 #pragma unroll
-    for (int t1 = 0; t1 < W; ++t1) {
-      const float w01 = w0[t0] * w1[t1];
-      const long long row = (row0 + wrap_once(b1 + t1, g.g1)) * g.g2;
-#pragma unroll
-      for (int t2 = 0; t2 < W; ++t2) {
-        const float w = w01 * w2[t2];
-        const float2* p = gbase + (row + x2[t2]) * C;
-        if constexpr (CPT == 4) {
-          const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-          const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
-          acc[0] = fmaf(w, a.x, acc[0]); acc[1] = fmaf(w, a.y, acc[1]);
-          acc[2] = fmaf(w, a.z, acc[2]); acc[3] = fmaf(w, a.w, acc[3]);
-          acc[4] = fmaf(w, b.x, acc[4]); acc[5] = fmaf(w, b.y, acc[5]);
-          acc[6] = fmaf(w, b.z, acc[6]); acc[7] = fmaf(w, b.w, acc[7]);
-        } else if constexpr (CPT == 2) {
-          const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-          acc[0] = fmaf(w, a.x, acc[0]); acc[1] = fmaf(w, a.y, acc[1]);
-          acc[2] = fmaf(w, a.z, acc[2]); acc[3] = fmaf(w, a.w, acc[3]);
-        } else {
-          const float2 a = __ldg(p);
-          acc[0] = fmaf(w, a.x, acc[0]); acc[1] = fmaf(w, a.y, acc[1]);
+        for (int t1 = 0; t1 < W; ++t1) {
+          const float w = w0[t0] * w1[t1] * w2t;
+          const float4 v = base4[((t0 * H + t1) * H) * (CC / 2)];
+          acc.x = fmaf(w, v.x, acc.x);
+          acc.y = fmaf(w, v.y, acc.y);
+          acc.z = fmaf(w, v.z, acc.z);
+          acc.w = fmaf(w, v.w, acc.w);
         }
       }
     }
-  }
-  float2* out = y + (long long)__ldg(perm + s) * C + cg * CPT;
-  if constexpr (CPT == 4) {
-    reinterpret_cast<float4*>(out)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    reinterpret_cast<float4*>(out)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-  } else if constexpr (CPT == 2) {
-    reinterpret_cast<float4*>(out)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-  } else {
-    out[0] = make_float2(acc[0], acc[1]);
+    // reduce over tap x (lanes NQ apart within the group)
+#pragma unroll
+    for (int off = NQ; off < LPS; off <<= 1) {
+      if ((W & (W - 1)) == 0) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off);
+        acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off);
+      }
+    }
+    if constexpr ((W & (W - 1)) != 0) {
+      // W not a power of two: gather the tap-x partials explicitly
+      float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int t = 0; t < W; ++t) {
+        sum.x += __shfl_sync(0xffffffffu, acc.x, gbase + t * NQ + q);
+        sum.y += __shfl_sync(0xffffffffu, acc.y, gbase + t * NQ + q);
+        sum.z += __shfl_sync(0xffffffffu, acc.z, gbase + t * NQ + q);
+        sum.w += __shfl_sync(0xffffffffu, acc.w, gbase + t * NQ + q);
+      }
+      acc = sum;
+    }
+    if (live && txl == 0) {
+      const int c0 = coil0 + 2 * q;
+      float2* out = y + (long long)__ldg(perm + s) * C + c0;
+      if ((C & 1) == 0 && c0 + 1 < C) {
+        reinterpret_cast<float4*>(out)[0] = acc;
+      } else {
+        if (c0 < C) out[0] = make_float2(acc.x, acc.y);
+        if (c0 + 1 < C) out[1] = make_float2(acc.z, acc.w);
+      }
+    }
   }
 }
 
+template <int W, int CC>
+constexpr size_t interp_smem() {
+  return size_t(8 + W - 1) * (8 + W - 1) * (8 + W - 1) * CC * sizeof(float2);
+}
+
 // K8: w_j[n] = sum_c conj(S_c[n]) Xt_c[n' mod G] / C3(n'/G) (steps Z^H, 1/c of
-// k-space gridding, then S^H).
+// k-space gridding, then S^H).  Thread = voxel.
 __global__ void crop_coilsum_kernel(Geo g, int C, const float* __restrict__ dtab,
-                                    const float2* __restrict__ smaps,  // [nvox][C]
-                                    const float2* __restrict__ xg,     // [G^3][C]
+                                    const float2* __restrict__ smaps,  // [C][nvox]
+                                    const float2* __restrict__ xg,     // [C][G^3]
                                     float2* __restrict__ w) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= g.nvox) return;
-  const int i2 = int(idx % g.n2);
-  const long long r = idx / g.n2;
-  const int i1 = int(r % g.n1);
-  const int i0 = int(r / g.n1);
-  const float dk = dtab[i0] * dtab[g.n0 + i1] * dtab[g.n0 + g.n1 + i2];
-  const long long p = ((long long)centred_pos(i0, g.n0, g.g0) * g.g1 + centred_pos(i1, g.n1, g.g1)) *
-                          g.g2 + centred_pos(i2, g.n2, g.g2);
-  const float2* xs = xg + p * C;
-  const float2* ss = smaps + idx * C;
+  const VoxelPos vp = voxel_pos(g, dtab, idx);
   float ar = 0.f, ai = 0.f;
   for (int c = 0; c < C; ++c) {
-    const float2 s = __ldg(ss + c);
-    const float2 v = __ldg(xs + c);
+    const float2 s = __ldg(smaps + (long long)c * g.nvox + idx);
+    const float2 v = __ldg(xg + (long long)c * g.ngrid + vp.grid);
     ar = fmaf(s.x, v.x, fmaf(s.y, v.y, ar));
     ai = fmaf(s.x, v.y, fmaf(-s.y, v.x, ai));
   }
-  w[idx] = make_float2(ar * dk, ai * dk);
+  w[idx] = make_float2(ar * vp.deapod, ai * vp.deapod);
 }
 
 // Stage variant of K8 without S^H: padded grids -> coil images (C, N^3).
@@ -156,81 +231,80 @@ __global__ void crop_to_coils_kernel(Geo g, int C, const float* __restrict__ dta
                                      const float2* __restrict__ xg, float2* __restrict__ v) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.nvox * C) return;
-  const long long idx = t / C;
-  const int c = int(t - idx * C);
-  const int i2 = int(idx % g.n2);
-  const long long r = idx / g.n2;
-  const int i1 = int(r % g.n1);
-  const int i0 = int(r / g.n1);
-  const float dk = dtab[i0] * dtab[g.n0 + i1] * dtab[g.n0 + g.n1 + i2];
-  const long long p = ((long long)centred_pos(i0, g.n0, g.g0) * g.g1 + centred_pos(i1, g.n1, g.g1)) *
-                          g.g2 + centred_pos(i2, g.n2, g.g2);
-  const float2 x = xg[p * C + c];
-  v[(long long)c * g.nvox + idx] = make_float2(x.x * dk, x.y * dk);
+  const int c = int(t / g.nvox);
+  const long long idx = t - (long long)c * g.nvox;
+  const VoxelPos vp = voxel_pos(g, dtab, idx);
+  const float2 x = __ldg(xg + (long long)c * g.ngrid + vp.grid);
+  v[t] = make_float2(x.x * vp.deapod, x.y * vp.deapod);
 }
 
 inline unsigned blocks_for(long long n, int threads) {
   return unsigned((n + threads - 1) / threads);
 }
 
-template <int W>
-int interp_dispatch(const Geo& g, const KernelCoefs& kc, int C, const PointSet& ps,
-                     const float2* grid, float2* y, cudaStream_t s) {
-  if (ps.npts == 0) return 0;
-  if (C % 4 == 0) {
-    const long long n = ps.npts * (C / 4);
-    interp_kspace_kernel<W, 4><<<blocks_for(n, 256), 256, 0, s>>>(g, kc, C, ps.npts, ps.qs,
-                                                                   ps.perm, grid, y);
-  } else if (C % 2 == 0) {
-    const long long n = ps.npts * (C / 2);
-    interp_kspace_kernel<W, 2><<<blocks_for(n, 256), 256, 0, s>>>(g, kc, C, ps.npts, ps.qs,
-                                                                   ps.perm, grid, y);
-  } else {
-    const long long n = ps.npts * C;
-    interp_kspace_kernel<W, 1><<<blocks_for(n, 256), 256, 0, s>>>(g, kc, C, ps.npts, ps.qs,
-                                                                   ps.perm, grid, y);
-  }
-  return 1;
-}
-
 }  // namespace
 
-int launch_coil_fanout_pad(const Geo& g, int C, const float* deapod,
-                            const nrsense_c64* smaps, const nrsense_c64* m,
-                            nrsense_c64* xpad, cudaStream_t s) {
+int launch_coil_fanout_pad(const Geo& g, int C, const float* deapod, const nrsense_c64* smaps,
+                           const nrsense_c64* m, nrsense_c64* xpad, cudaStream_t s) {
   coil_fanout_pad_kernel<<<blocks_for(g.nvox * C, 256), 256, 0, s>>>(
       g, C, deapod, reinterpret_cast<const float2*>(smaps), reinterpret_cast<const float2*>(m),
       reinterpret_cast<float2*>(xpad));
   return 1;
 }
 
-int launch_image_to_padded(const Geo& g, int C, const float* deapod,
-                            const nrsense_c64* v, nrsense_c64* xpad, cudaStream_t s) {
+int launch_image_to_padded(const Geo& g, int C, const float* deapod, const nrsense_c64* v,
+                           nrsense_c64* xpad, cudaStream_t s) {
   image_to_padded_kernel<<<blocks_for(g.nvox * C, 256), 256, 0, s>>>(
       g, C, deapod, reinterpret_cast<const float2*>(v), reinterpret_cast<float2*>(xpad));
   return 1;
 }
 
-int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C,
-                          const PointSet& ps, const nrsense_c64* grid, nrsense_c64* y,
-                          cudaStream_t s) {
-  const auto* gp = reinterpret_cast<const float2*>(grid);
-  auto* yp = reinterpret_cast<float2*>(y);
-  return W == 4 ? interp_dispatch<4>(g, kc, C, ps, gp, yp, s)
-                : interp_dispatch<6>(g, kc, C, ps, gp, yp, s);
+cudaError_t configure_kernels() {
+  cudaError_t e = configure_spread_kernels();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(interp_tile_kernel<4, 8>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(interp_smem<4, 8>()));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(interp_tile_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(interp_smem<4, 4>()));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(interp_tile_kernel<6, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(interp_smem<6, 4>()));
+  return e;
 }
 
-int launch_crop_coilsum(const Geo& g, int C, const float* deapod,
-                         const nrsense_c64* smaps, const nrsense_c64* xg,
-                         nrsense_c64* w, cudaStream_t s) {
+int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, const PointSet& ps,
+                         const nrsense_c64* grid, nrsense_c64* y, cudaStream_t s) {
+  if (ps.npts == 0 || ps.n_iitems == 0) return 0;
+  const auto* gp = reinterpret_cast<const float2*>(grid);
+  auto* yp = reinterpret_cast<float2*>(y);
+  if (W == 4 && C > 4) {
+    const dim3 gd(ps.n_iitems, (C + 7) / 8);
+    interp_tile_kernel<4, 8><<<gd, 256, interp_smem<4, 8>(), s>>>(g, kc, C, ps.tp, ps.iitems,
+                                                                   ps.qs, ps.perm, gp, yp);
+  } else if (W == 4) {
+    const dim3 gd(ps.n_iitems, 1);
+    interp_tile_kernel<4, 4><<<gd, 256, interp_smem<4, 4>(), s>>>(g, kc, C, ps.tp, ps.iitems,
+                                                                   ps.qs, ps.perm, gp, yp);
+  } else {
+    const dim3 gd(ps.n_iitems, (C + 3) / 4);
+    interp_tile_kernel<6, 4><<<gd, 256, interp_smem<6, 4>(), s>>>(g, kc, C, ps.tp, ps.iitems,
+                                                                   ps.qs, ps.perm, gp, yp);
+  }
+  return 1;
+}
+
+int launch_crop_coilsum(const Geo& g, int C, const float* deapod, const nrsense_c64* smaps,
+                        const nrsense_c64* xg, nrsense_c64* w, cudaStream_t s) {
   crop_coilsum_kernel<<<blocks_for(g.nvox, 256), 256, 0, s>>>(
       g, C, deapod, reinterpret_cast<const float2*>(smaps), reinterpret_cast<const float2*>(xg),
       reinterpret_cast<float2*>(w));
   return 1;
 }
 
-int launch_crop_to_coils(const Geo& g, int C, const float* deapod,
-                          const nrsense_c64* xg, nrsense_c64* v, cudaStream_t s) {
+int launch_crop_to_coils(const Geo& g, int C, const float* deapod, const nrsense_c64* xg,
+                         nrsense_c64* v, cudaStream_t s) {
   crop_to_coils_kernel<<<blocks_for(g.nvox * C, 256), 256, 0, s>>>(
       g, C, deapod, reinterpret_cast<const float2*>(xg), reinterpret_cast<float2*>(v));
   return 1;

@@ -1,199 +1,493 @@
 // Projection Cores P^(k) (k-space gridding) and P_j^(i) (adjoint image-space
 // gridding): spread point values onto the oversampled grid,
-//     grid[g, c] = sum_p c3(q_p - g) vals[p, c]
+//     grid[c][g] = sum_p c3(q_p - g) vals[p, c]
 // (section "k-space Gridding", Projection Core; section "Image-space
 // Gridding", adjoint diagram).
 //
-// Output-stationary and atomic-free: each CTA owns one 8x8x8 grid tile (and a
-// chunk of coils), reads the plan-time list of points whose W^3 footprint
-// touches the tile, and accumulates in shared memory.  Warp w owns tile plane
-// w (axis 0), so every shared-memory address is updated by one warp only, in
-// list order: the result is bitwise deterministic.  A heavy tile is split over
-// several CTAs that write partial tiles to scratch; a second kernel adds the
-// partials in a fixed order.
+// Output-stationary and atomic-free: each CTA owns one grid tile (and a chunk
+// of coils), reads the plan-time list of points whose W^3 footprint touches
+// the tile, and accumulates in shared memory.  Every tile plane (axis 0) is
+// owned by one warp (or half-warp).  The plan sorts each tile's list by the
+// plane offset of the point's first tap, so the owner of a plane visits the
+// points that touch it as one contiguous range; every shared-memory address
+// is updated by one warp only, in list order, so the result is bitwise
+// deterministic.  A heavy tile is split over several CTAs that write partial
+// tiles to scratch; a second kernel adds the partials in a fixed order.
 #include "plan_internal.h"
 
 namespace nrs {
 
 namespace {
 
-constexpr int kTile = kSpreadTile;  // tile edge (grid points); 8 warps own 8 planes
-constexpr int kStage = 32;        // points staged per round
 constexpr int kThreads = 256;
 
-template <int W, int CC>
-__global__ void __launch_bounds__(kThreads) spread_kernel(
+struct TileOrigin {
+  int o0, o1, o2, e0, e1, e2;
+};
+
+__device__ __forceinline__ TileOrigin tile_origin(const Geo& g, const TilePlan& tp, int tile) {
+  const int tz = tile / (tp.nt1 * tp.nt2);
+  const int rem = tile - tz * (tp.nt1 * tp.nt2);
+  const int ty = rem / tp.nt2;
+  const int tx = rem - ty * tp.nt2;
+  TileOrigin t;
+  t.o0 = tz * tp.t0;
+  t.o1 = ty * tp.t1;
+  t.o2 = tx * tp.t2;
+  t.e0 = min(tp.t0, g.g0 - t.o0);
+  t.e1 = min(tp.t1, g.g1 - t.o1);
+  t.e2 = min(tp.t2, g.g2 - t.o2);
+  return t;
+}
+
+// Stage `cnt` list entries: per-axis weights, first-tap offsets from the tile
+// origin (in (-W, T)), and CC values.
+template <int W, int T, int CC, int R>
+__device__ __forceinline__ void stage_round(const Geo& g, const KernelCoefs& kc, int C, int coil0,
+                                            const TileOrigin& to, const int2* __restrict__ lst,
+                                            int cnt, const float4* __restrict__ qs,
+                                            const float2* __restrict__ vals, float (*s_w)[3][W],
+                                            int (*s_r)[3], float2 (*s_val)[CC], int tid) {
+  for (int i = tid; i < cnt * 3; i += kThreads) {
+    const int p = i / 3, a = i - 3 * p;
+    const int si = __ldg(&lst[p].x);
+    const float4 q = __ldg(qs + si);
+    int b0, b1, b2;
+    unpack_base(__float_as_uint(q.w), b0, b1, b2);
+    float w[W];
+    kernel_weights<W>(a == 0 ? q.x : (a == 1 ? q.y : q.z), kc, w);
+#pragma unroll
+    for (int t = 0; t < W; ++t) s_w[p][a][t] = w[t];
+    const int Ga = a == 0 ? g.g0 : (a == 1 ? g.g1 : g.g2);
+    int r = a == 0 ? b0 - to.o0 : (a == 1 ? b1 - to.o1 : b2 - to.o2);
+    if (r < 0) r += Ga;
+    if (r >= T) r -= Ga;
+    s_r[p][a] = r;
+  }
+  for (int i = tid; i < cnt * CC; i += kThreads) {
+    const int p = i / CC, c = i - p * CC;
+    const int row = __ldg(&lst[p].y);
+    s_val[p][c] = (coil0 + c < C) ? __ldg(vals + (long long)row * C + coil0 + c)
+                                  : make_float2(0.f, 0.f);
+  }
+}
+
+// s_bin[b] = first staged entry with r0 + W - 1 >= b (entries sorted by r0);
+// offsets are clamped so a malformed list cannot index out of range.
+template <int W, int T>
+__device__ __forceinline__ void bin_round(int (*s_r)[3], int* s_bin, int cnt, int tid) {
+  if (tid < cnt) {
+    const int r = min(max(s_r[tid][0], 1 - W), T - 1) + W - 1;
+    const int rp = tid == 0 ? -1 : min(max(s_r[tid - 1][0], 1 - W), T - 1) + W - 1;
+    for (int bb = rp + 1; bb <= r; ++bb) s_bin[bb] = tid;
+    if (tid == cnt - 1)
+      for (int bb = r + 1; bb < W + T; ++bb) s_bin[bb] = cnt;
+  }
+}
+
+template <int T, int CC>
+__device__ __forceinline__ void write_tile(const Geo& g, int C, int coil0, const TileOrigin& to,
+                                          const SpreadItem& it, const float2* acc,
+                                          float2* __restrict__ grid, float2* __restrict__ scratch,
+                                          int tid) {
+  constexpr int kPts = T * T * T;
+  if (it.slot < 0) {
+    for (int i = tid; i < kPts * CC; i += kThreads) {
+      const int c = i / kPts;
+      const int pt = i - c * kPts;
+      const int lx = pt % T, ly = (pt / T) % T, lz = pt / (T * T);
+      if (lz < to.e0 && ly < to.e1 && lx < to.e2 && coil0 + c < C) {
+        const long long gi = ((long long)(to.o0 + lz) * g.g1 + (to.o1 + ly)) * g.g2 + (to.o2 + lx);
+        grid[(long long)(coil0 + c) * g.ngrid + gi] = acc[pt * CC + c];
+      }
+    }
+  } else {
+    float2* dst = scratch + ((long long)it.slot * gridDim.y + blockIdx.y) * (kPts * CC);
+    for (int i = tid; i < kPts * CC; i += kThreads) dst[i] = acc[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// W = 4, CC in {2, 4, 8} coils, 8^3 tiles.  Warp w owns plane w and streams
+// its own range of the item's list (no CTA-wide barriers): in batches of 32,
+// lane p stages point p (the plane's z weight times the y weights, the x
+// weights, offsets and CC values) into the warp's shared buffer, then the
+// warp applies the batch with lane = (coil pair, tap x, row), each lane
+// updating two coils of one grid point with a 128-bit read-modify-write.
+template <int CC>
+struct CoilStage {
+  float wzy[4];
+  float wx[4];
+  int r1, r2, pad0, pad1;
+  float2 val[CC];
+};
+
+template <int CC>
+__global__ void __launch_bounds__(kThreads) spread_coils_kernel(
     Geo g, KernelCoefs kc, int C, TilePlan tp, const SpreadItem* __restrict__ items,
-    const int32_t* __restrict__ list, const float4* __restrict__ qs,
-    const int32_t* __restrict__ perm, const float2* __restrict__ vals,
-    float2* __restrict__ grid, float2* __restrict__ scratch) {
+    const int32_t* __restrict__ bins, const int2* __restrict__ list,
+    const float4* __restrict__ qs, const float2* __restrict__ vals, float2* __restrict__ grid,
+    float2* __restrict__ scratch) {
+  constexpr int W = 4, T = 8, B = 32, NB = W + T + 1;
+  static_assert(CC == 2 || CC == 4 || CC == 8, "coil chunk");
   extern __shared__ float4 smem_raw[];
-  float2* acc = reinterpret_cast<float2*>(smem_raw);  // [8][8][8][CC]
-  __shared__ float s_w[kStage][3][W];
-  __shared__ int s_rel[kStage][3];
-  __shared__ float2 s_val[kStage][CC];
+  float2* acc = reinterpret_cast<float2*>(smem_raw);  // [T][T][T][CC]
+  __shared__ __align__(16) CoilStage<CC> stg[kThreads / 32][B];
 
   const SpreadItem it = items[blockIdx.x];
   const int coil0 = blockIdx.y * CC;
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const TileOrigin to = tile_origin(g, tp, it.tile);
+  for (int i = tid; i < T * T * T * CC; i += kThreads) acc[i] = make_float2(0.f, 0.f);
+  __syncthreads();
 
-  const int tz = it.tile / (tp.nt1 * tp.nt2);
-  const int rem = it.tile - tz * (tp.nt1 * tp.nt2);
-  const int ty = rem / tp.nt2;
-  const int tx = rem - ty * tp.nt2;
-  const int o0 = tz * kTile, o1 = ty * kTile, o2 = tx * kTile;
-  const int e0 = min(kTile, g.g0 - o0), e1 = min(kTile, g.g1 - o1), e2 = min(kTile, g.g2 - o2);
-
-  for (int i = tid; i < kTile * kTile * kTile * CC; i += kThreads) acc[i] = make_float2(0.f, 0.f);
-
-  const int n = it.end - it.begin;
-  for (int base = 0; base < n; base += kStage) {
-    const int cnt = min(kStage, n - base);
-    __syncthreads();  // previous round fully consumed (and acc zeroed)
-    if (tid < cnt * 3) {
-      const int p = tid / 3, a = tid - 3 * (tid / 3);
-      const int si = list[it.begin + base + p];
-      const float4 q = __ldg(qs + si);
-      int b[3];
-      unpack_base(__float_as_uint(q.w), b[0], b[1], b[2]);
-      const float f = a == 0 ? q.x : (a == 1 ? q.y : q.z);
-      float w[W];
-      kernel_weights<W>(f, kc, w);
+  const int lz = warp;
+  if (lz < to.e0) {
+    const int32_t* ib = bins + (long long)blockIdx.x * NB;
+    const int beg = it.begin + __ldg(ib + min(lz, NB - 1));
+    const int end = it.begin + __ldg(ib + min(lz + W, NB - 1));
+    // lane = (coil pair q, tap x, row half): a quarter-warp covers 128
+    // contiguous bytes of one row (conflict-free 128-bit accesses)
+    constexpr int NQ = CC / 2;               // coil pairs per point
+    constexpr int LPR = NQ * W;               // lanes per tap row
+    constexpr int RPI = 32 / LPR;             // rows per iteration
+    const int q = lane % NQ, tx = (lane / NQ) % W, tyh = lane / LPR;
+    CoilStage<CC>* st = stg[warp];
+    for (int base = beg; base < end; base += B) {
+      const int n = min(B, end - base);
+      if (lane < n) {
+        const int2 e = __ldg(list + base + lane);
+        const float4 qq = __ldg(qs + e.x);
+        int b0, b1, b2;
+        unpack_base(__float_as_uint(qq.w), b0, b1, b2);
+        int r0 = b0 - to.o0, r1 = b1 - to.o1, r2 = b2 - to.o2;
+        if (r0 < 0) r0 += g.g0;
+        if (r0 >= T) r0 -= g.g0;
+        if (r1 < 0) r1 += g.g1;
+        if (r1 >= T) r1 -= g.g1;
+        if (r2 < 0) r2 += g.g2;
+        if (r2 >= T) r2 -= g.g2;
+        float wz[W], wy[W], wx[W];
+        kernel_weights<W>(qq.x, kc, wz);
+        kernel_weights<W>(qq.y, kc, wy);
+        kernel_weights<W>(qq.z, kc, wx);
+        const int t0 = lz - r0;
+        const float wzt = ((unsigned)t0 < (unsigned)W) ? select_tap<W>(wz, t0) : 0.f;
+        CoilStage<CC>& d = st[lane];
 #pragma unroll
-      for (int t = 0; t < W; ++t) s_w[p][a][t] = w[t];
-      const int o = a == 0 ? o0 : (a == 1 ? o1 : o2);
-      const int G = a == 0 ? g.g0 : (a == 1 ? g.g1 : g.g2);
-      int r = b[a] - o;
-      if (r < 0) r += G;
-      s_rel[p][a] = r;  // first tap's offset from the tile origin, mod G
-    }
-    for (int i = tid; i < cnt * CC; i += kThreads) {
-      const int p = i / CC, c = i - p * CC;
-      const int si = list[it.begin + base + p];
-      s_val[p][c] = (coil0 + c < C) ? __ldg(vals + (long long)__ldg(perm + si) * C + coil0 + c)
-                                    : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    // warp `warp` owns plane lz = warp
-    const int lz = warp;
-    if (lz < e0) {
-      for (int p = 0; p < cnt; ++p) {
-        int t0 = lz - s_rel[p][0];
-        if (t0 < 0) t0 += g.g0;
-        if (t0 >= W) continue;  // warp-uniform
-        const float wz = s_w[p][0][t0];
-        const int r1 = s_rel[p][1], r2 = s_rel[p][2];
-        // combos (c fastest, then tap x, then tap y)
-        for (int k = lane; k < CC * W * W; k += 32) {
-          const int c = k % CC;
-          const int tx2 = (k / CC) % W;
-          const int ty1 = k / (CC * W);
-          int ly = r1 + ty1;
-          if (ly >= g.g1) ly -= g.g1;
-          int lx = r2 + tx2;
-          if (lx >= g.g2) lx -= g.g2;
-          if (ly < e1 && lx < e2) {
-            const float w = wz * s_w[p][1][ty1] * s_w[p][2][tx2];
-            const float2 v = s_val[p][c];
-            float2* a = acc + ((lz * kTile + ly) * kTile + lx) * CC + c;
-            float2 cur = *a;
+        for (int t = 0; t < W; ++t) {
+          d.wzy[t] = wzt * wy[t];
+          d.wx[t] = wx[t];
+        }
+        d.r1 = r1;
+        d.r2 = r2;
+        const float2* src = vals + (long long)e.y * C + coil0;
+#pragma unroll
+        for (int c = 0; c < CC; ++c)
+          d.val[c] = (coil0 + c < C) ? __ldg(src + c) : make_float2(0.f, 0.f);
+      }
+      __syncwarp();
+      for (int p = 0; p < n; ++p) {
+        const CoilStage<CC>& d = st[p];
+        const int lx = d.r2 + tx;
+        const float4 v = reinterpret_cast<const float4*>(d.val)[q];
+        const float wxt = d.wx[tx];
+#pragma unroll
+        for (int k = 0; k < (W + RPI - 1) / RPI; ++k) {
+          const int ty = tyh + RPI * k;
+          const int ly = d.r1 + ty;
+          if (ty < W && (unsigned)ly < (unsigned)to.e1 && (unsigned)lx < (unsigned)to.e2) {
+            const float w = d.wzy[ty & (W - 1)] * wxt;
+            float4* a = reinterpret_cast<float4*>(acc + ((lz * T + ly) * T + lx) * CC) + q;
+            float4 cur = *a;
             cur.x = fmaf(w, v.x, cur.x);
             cur.y = fmaf(w, v.y, cur.y);
+            cur.z = fmaf(w, v.z, cur.z);
+            cur.w = fmaf(w, v.w, cur.w);
             *a = cur;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  write_tile<T, CC>(g, C, coil0, to, it, acc, grid, scratch, tid);
+}
+
+// ---------------------------------------------------------------------------
+// W = 4, one channel (image space), 16^3 tiles.  Warp w owns planes 2w and
+// 2w+1 (one per half-warp) and streams the union of their list ranges, with
+// the same per-warp staging as above; lane = (tap x, tap y, plane).
+struct SingleStage {
+  float wzy[2][4];
+  float wx[4];
+  int r1, r2;
+  float2 val;
+};
+
+__global__ void __launch_bounds__(kThreads) spread_single_kernel(
+    Geo g, KernelCoefs kc, TilePlan tp, const SpreadItem* __restrict__ items,
+    const int32_t* __restrict__ bins, const int2* __restrict__ list,
+    const float4* __restrict__ qs, const float2* __restrict__ vals, float2* __restrict__ grid,
+    float2* __restrict__ scratch) {
+  constexpr int W = 4, T = 16, B = 32, NB = W + T + 1;
+  constexpr int RS = T + 4;  // padded row stride: 4 tap rows hit disjoint banks
+  extern __shared__ float4 smem_raw[];
+  float2* acc = reinterpret_cast<float2*>(smem_raw);  // [T][T][RS]
+  __shared__ SingleStage stg[kThreads / 32][B];
+
+  const SpreadItem it = items[blockIdx.x];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const TileOrigin to = tile_origin(g, tp, it.tile);
+  for (int i = tid; i < T * T * RS; i += kThreads) acc[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+
+  const int z0 = 2 * warp;
+  if (z0 < to.e0) {
+    const int32_t* ib = bins + (long long)blockIdx.x * NB;
+    const int beg = it.begin + __ldg(ib + min(z0, NB - 1));
+    const int end = it.begin + __ldg(ib + min(z0 + W + 1, NB - 1));
+    const int tx = lane & 3, ty = (lane >> 2) & 3, hz = lane >> 4;
+    const int lz = z0 + hz;
+    SingleStage* st = stg[warp];
+    for (int base = beg; base < end; base += B) {
+      const int n = min(B, end - base);
+      if (lane < n) {
+        const int2 e = __ldg(list + base + lane);
+        const float4 q = __ldg(qs + e.x);
+        int b0, b1, b2;
+        unpack_base(__float_as_uint(q.w), b0, b1, b2);
+        int r0 = b0 - to.o0, r1 = b1 - to.o1, r2 = b2 - to.o2;
+        if (r0 < 0) r0 += g.g0;
+        if (r0 >= T) r0 -= g.g0;
+        if (r1 < 0) r1 += g.g1;
+        if (r1 >= T) r1 -= g.g1;
+        if (r2 < 0) r2 += g.g2;
+        if (r2 >= T) r2 -= g.g2;
+        float wz[W], wy[W], wx[W];
+        kernel_weights<W>(q.x, kc, wz);
+        kernel_weights<W>(q.y, kc, wy);
+        kernel_weights<W>(q.z, kc, wx);
+        const int ta = z0 - r0, tb = z0 + 1 - r0;
+        const float wa = ((unsigned)ta < (unsigned)W) ? select_tap<W>(wz, ta) : 0.f;
+        const float wb = ((unsigned)tb < (unsigned)W && z0 + 1 < to.e0) ? select_tap<W>(wz, tb) : 0.f;
+        SingleStage& d = st[lane];
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+          d.wzy[0][t] = wa * wy[t];
+          d.wzy[1][t] = wb * wy[t];
+          d.wx[t] = wx[t];
+        }
+        d.r1 = r1;
+        d.r2 = r2;
+        d.val = __ldg(vals + e.y);
+      }
+      __syncwarp();
+      for (int p = 0; p < n; ++p) {
+        const SingleStage& d = st[p];
+        const int ly = d.r1 + ty, lx = d.r2 + tx;
+        if ((unsigned)ly < (unsigned)to.e1 && (unsigned)lx < (unsigned)to.e2 && lz < to.e0) {
+          const float w = d.wzy[hz][ty] * d.wx[tx];
+          float2* a = acc + (lz * T + ly) * RS + lx;
+          float2 cur = *a;
+          cur.x = fmaf(w, d.val.x, cur.x);
+          cur.y = fmaf(w, d.val.y, cur.y);
+          *a = cur;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // write the tile (or partial tile), dropping the row padding
+  constexpr int kPts = T * T * T;
+  if (it.slot < 0) {
+    for (int i = tid; i < kPts; i += kThreads) {
+      const int lx = i % T, ly = (i / T) % T, lz = i / (T * T);
+      if (lz < to.e0 && ly < to.e1 && lx < to.e2) {
+        const long long gi = ((long long)(to.o0 + lz) * g.g1 + (to.o1 + ly)) * g.g2 + (to.o2 + lx);
+        grid[gi] = acc[(lz * T + ly) * RS + lx];
+      }
+    }
+  } else {
+    float2* dst = scratch + (long long)it.slot * kPts;
+    for (int i = tid; i < kPts; i += kThreads) {
+      const int lx = i % T, ly = (i / T) % T, lz = i / (T * T);
+      dst[i] = acc[(lz * T + ly) * RS + lx];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Generic kernel (any W <= kMaxWidth, any CC), 8^3 tiles, warp per plane,
+// lanes over (coil, tap x, tap y) combinations.
+template <int W, int CC>
+__global__ void __launch_bounds__(kThreads) spread_generic_kernel(
+    Geo g, KernelCoefs kc, int C, TilePlan tp, const SpreadItem* __restrict__ items,
+    const int2* __restrict__ list, const float4* __restrict__ qs,
+    const float2* __restrict__ vals, float2* __restrict__ grid, float2* __restrict__ scratch) {
+  constexpr int T = 8, R = 64;
+  extern __shared__ float4 smem_raw[];
+  float2* acc = reinterpret_cast<float2*>(smem_raw);  // [T][T][T][CC]
+  __shared__ float s_w[R][3][W];
+  __shared__ int s_r[R][3];
+  __shared__ float2 s_val[R][CC];
+  __shared__ int s_bin[W + T];
+
+  const SpreadItem it = items[blockIdx.x];
+  const int coil0 = blockIdx.y * CC;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const TileOrigin to = tile_origin(g, tp, it.tile);
+  for (int i = tid; i < T * T * T * CC; i += kThreads) acc[i] = make_float2(0.f, 0.f);
+
+  const int n = it.end - it.begin;
+  for (int base = 0; base < n; base += R) {
+    const int cnt = min(R, n - base);
+    __syncthreads();
+    stage_round<W, T, CC, R>(g, kc, C, coil0, to, list + it.begin + base, cnt, qs, vals, s_w, s_r,
+                             s_val, tid);
+    __syncthreads();
+    bin_round<W, T>(s_r, s_bin, cnt, tid);
+    __syncthreads();
+    const int lz = warp;
+    if (lz < to.e0) {
+      const int pend = s_bin[lz + W];
+      for (int p = s_bin[lz]; p < pend; ++p) {
+        const int t0 = lz - s_r[p][0];
+        if ((unsigned)t0 >= (unsigned)W) continue;
+        const float wz = s_w[p][0][t0];
+        const int r1 = s_r[p][1], r2 = s_r[p][2];
+#pragma unroll
+        for (int k0 = 0; k0 < (CC * W * W + 31) / 32; ++k0) {
+          const int k = lane + 32 * k0;
+          if (k < CC * W * W) {
+            const int c = k % CC;
+            const int tx2 = (k / CC) % W;
+            const int ty1 = k / (CC * W);
+            const int ly = r1 + ty1, lx = r2 + tx2;
+            if ((unsigned)ly < (unsigned)to.e1 && (unsigned)lx < (unsigned)to.e2) {
+              const float w = wz * s_w[p][1][ty1] * s_w[p][2][tx2];
+              const float2 v = s_val[p][c];
+              float2* a = acc + ((lz * T + ly) * T + lx) * CC + c;
+              float2 cur = *a;
+              cur.x = fmaf(w, v.x, cur.x);
+              cur.y = fmaf(w, v.y, cur.y);
+              *a = cur;
+            }
           }
         }
       }
     }
   }
   __syncthreads();
-  // write the tile (or the partial tile)
-  if (it.slot < 0) {
-    for (int i = tid; i < kTile * kTile * kTile * CC; i += kThreads) {
-      const int c = i % CC;
-      const int pt = i / CC;
-      const int lx = pt % kTile, ly = (pt / kTile) % kTile, lz = pt / (kTile * kTile);
-      if (lz < e0 && ly < e1 && lx < e2 && coil0 + c < C) {
-        const long long gi = ((long long)(o0 + lz) * g.g1 + (o1 + ly)) * g.g2 + (o2 + lx);
-        grid[gi * C + coil0 + c] = acc[i];
-      }
-    }
-  } else {
-    float2* dst = scratch + ((long long)it.slot * gridDim.y + blockIdx.y) * (kTile * kTile * kTile * CC);
-    for (int i = tid; i < kTile * kTile * kTile * CC; i += kThreads) dst[i] = acc[i];
-  }
+  write_tile<T, CC>(g, C, coil0, to, it, acc, grid, scratch, tid);
 }
 
 // Sum the partial tiles of split tiles in slot order (deterministic).
-template <int CC>
+template <int T, int CC>
 __global__ void reduce_kernel(Geo g, int C, TilePlan tp, const ReduceItem* __restrict__ red,
                               const float2* __restrict__ scratch, float2* __restrict__ grid) {
   const ReduceItem r = red[blockIdx.x];
   const int coil0 = blockIdx.y * CC;
-  const int tz = r.tile / (tp.nt1 * tp.nt2);
-  const int rem = r.tile - tz * (tp.nt1 * tp.nt2);
-  const int ty = rem / tp.nt2;
-  const int tx = rem - ty * tp.nt2;
-  const int o0 = tz * kTile, o1 = ty * kTile, o2 = tx * kTile;
-  const int e0 = min(kTile, g.g0 - o0), e1 = min(kTile, g.g1 - o1), e2 = min(kTile, g.g2 - o2);
-  const long long tile_elems = kTile * kTile * kTile * CC;
+  const TileOrigin to = tile_origin(g, tp, r.tile);
+  constexpr int kPts = T * T * T;
+  const long long tile_elems = kPts * CC;
   for (int i = threadIdx.x; i < tile_elems; i += blockDim.x) {
-    const int c = i % CC;
-    const int pt = i / CC;
-    const int lx = pt % kTile, ly = (pt / kTile) % kTile, lz = pt / (kTile * kTile);
+    const int c = i / kPts;
+    const int pt = i - c * kPts;
+    const int lx = pt % T, ly = (pt / T) % T, lz = pt / (T * T);
     float2 s = make_float2(0.f, 0.f);
     for (int k = 0; k < r.count; ++k) {
-      const float2 v = scratch[((long long)(r.first + k) * gridDim.y + blockIdx.y) * tile_elems + i];
+      const float2 v =
+          scratch[((long long)(r.first + k) * gridDim.y + blockIdx.y) * tile_elems + pt * CC + c];
       s.x += v.x;
       s.y += v.y;
     }
-    if (lz < e0 && ly < e1 && lx < e2 && coil0 + c < C) {
-      const long long gi = ((long long)(o0 + lz) * g.g1 + (o1 + ly)) * g.g2 + (o2 + lx);
-      grid[gi * C + coil0 + c] = s;
+    if (lz < to.e0 && ly < to.e1 && lx < to.e2 && coil0 + c < C) {
+      const long long gi = ((long long)(to.o0 + lz) * g.g1 + (to.o1 + ly)) * g.g2 + (to.o2 + lx);
+      grid[(long long)(coil0 + c) * g.ngrid + gi] = s;
     }
   }
 }
 
-template <int W, int CC>
-int spread_dispatch(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& tp,
-                     const PointSet& ps, const float2* vals, float2* grid, float2* scratch,
-                     cudaStream_t s) {
-  const int coil_chunks = (C + CC - 1) / CC;
-  const size_t smem = size_t(kTile) * kTile * kTile * CC * sizeof(float2);  // <= 32 KB
-  dim3 grid_dim(ps.n_items, coil_chunks);
-  spread_kernel<W, CC><<<grid_dim, kThreads, smem, s>>>(g, kc, C, tp, ps.items, ps.list, ps.qs,
-                                                        ps.perm, vals, grid, scratch);
-  if (ps.n_reduces > 0) {
-    dim3 rd(ps.n_reduces, coil_chunks);
-    reduce_kernel<CC><<<rd, 256, 0, s>>>(g, C, tp, ps.reduces, scratch, grid);
-    return 2;
-  }
+template <int T, int CC>
+int launch_reduce(const Geo& g, int C, const PointSet& ps, int chunks, float2* grid,
+                  const float2* scratch, cudaStream_t s) {
+  if (ps.n_reduces == 0) return 0;
+  reduce_kernel<T, CC><<<dim3(ps.n_reduces, chunks), 256, 0, s>>>(g, C, ps.tp, ps.reduces,
+                                                                  scratch, grid);
   return 1;
+}
+
+template <int CC>
+int dispatch_coils(const Geo& g, const KernelCoefs& kc, int C, const PointSet& ps,
+                   const float2* vals, float2* grid, float2* scratch, cudaStream_t s) {
+  const int chunks = (C + CC - 1) / CC;
+  const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2);
+  spread_coils_kernel<CC><<<dim3(ps.n_items, chunks), kThreads, smem, s>>>(
+      g, kc, C, ps.tp, ps.items, ps.bins, ps.list, ps.qs, vals, grid, scratch);
+  return 1 + launch_reduce<8, CC>(g, C, ps, chunks, grid, scratch, s);
+}
+
+template <int W, int CC>
+int dispatch_generic(const Geo& g, const KernelCoefs& kc, int C, const PointSet& ps,
+                     const float2* vals, float2* grid, float2* scratch, cudaStream_t s) {
+  const int chunks = (C + CC - 1) / CC;
+  const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2);
+  spread_generic_kernel<W, CC><<<dim3(ps.n_items, chunks), kThreads, smem, s>>>(
+      g, kc, C, ps.tp, ps.items, ps.list, ps.qs, vals, grid, scratch);
+  return 1 + launch_reduce<8, CC>(g, C, ps, chunks, grid, scratch, s);
 }
 
 }  // namespace
 
-int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
-                   const PointSet& ps, const nrsense_c64* vals, nrsense_c64* grid,
-                   nrsense_c64* scratch, int32_t* status, cudaStream_t s) {
+cudaError_t configure_spread_kernels() {
+  const int big = 96 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(spread_coils_kernel<8>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(spread_coils_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(spread_coils_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(spread_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             big);
+  return e;
+}
+
+int spread_tile_edge(int W, int C, int gmin) {
+  return (W == 4 && C == 1 && gmin >= 16 + W - 1) ? 16 : 8;
+}
+
+int spread_coil_chunk(int C) { return C == 1 ? 1 : (C <= 2 ? 2 : (C <= 4 ? 4 : 8)); }
+
+int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const PointSet& ps,
+                  const nrsense_c64* vals, nrsense_c64* grid, nrsense_c64* scratch,
+                  int32_t* status, cudaStream_t s) {
   (void)status;
   if (ps.n_items == 0) return 0;
   const auto* v = reinterpret_cast<const float2*>(vals);
   auto* gr = reinterpret_cast<float2*>(grid);
   auto* sc = reinterpret_cast<float2*>(scratch);
   if (W == 4) {
-    if (C == 1) return spread_dispatch<4, 1>(g, kc, C, tp, ps, v, gr, sc, s);
-    else if (C <= 2) return spread_dispatch<4, 2>(g, kc, C, tp, ps, v, gr, sc, s);
-    else if (C <= 4) return spread_dispatch<4, 4>(g, kc, C, tp, ps, v, gr, sc, s);
-    else return spread_dispatch<4, 8>(g, kc, C, tp, ps, v, gr, sc, s);
-  } else {
-    if (C == 1) return spread_dispatch<6, 1>(g, kc, C, tp, ps, v, gr, sc, s);
-    else if (C <= 2) return spread_dispatch<6, 2>(g, kc, C, tp, ps, v, gr, sc, s);
-    else if (C <= 4) return spread_dispatch<6, 4>(g, kc, C, tp, ps, v, gr, sc, s);
-    else return spread_dispatch<6, 8>(g, kc, C, tp, ps, v, gr, sc, s);
+    if (C == 1 && ps.tp.t0 == 16) {
+      const size_t smem = size_t(16 * 16 * 20) * sizeof(float2);  // 40 KB, padded rows
+      spread_single_kernel<<<dim3(ps.n_items, 1), kThreads, smem, s>>>(
+          g, kc, ps.tp, ps.items, ps.bins, ps.list, ps.qs, v, gr, sc);
+      return 1 + launch_reduce<16, 1>(g, 1, ps, 1, gr, sc, s);
+    }
+    if (C == 1) return dispatch_generic<4, 1>(g, kc, C, ps, v, gr, sc, s);
+    if (C <= 2) return dispatch_coils<2>(g, kc, C, ps, v, gr, sc, s);
+    if (C <= 4) return dispatch_coils<4>(g, kc, C, ps, v, gr, sc, s);
+    return dispatch_coils<8>(g, kc, C, ps, v, gr, sc, s);
   }
+  if (C == 1) return dispatch_generic<6, 1>(g, kc, C, ps, v, gr, sc, s);
+  if (C <= 2) return dispatch_generic<6, 2>(g, kc, C, ps, v, gr, sc, s);
+  if (C <= 4) return dispatch_generic<6, 4>(g, kc, C, ps, v, gr, sc, s);
+  return dispatch_generic<6, 8>(g, kc, C, ps, v, gr, sc, s);
 }
-
-int spread_coil_chunk(int C) { return C == 1 ? 1 : (C <= 2 ? 2 : (C <= 4 ? 4 : 8)); }
 
 }  // namespace nrs

@@ -66,16 +66,6 @@ nrsense_status upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
     if (_st != NRSENSE_OK) return _st;         \
   } while (0)
 
-// (C, nvox) -> (nvox, C) transpose of the coil maps
-__global__ void transpose_maps_kernel(long long nvox, int C, const float2* __restrict__ in,
-                                      float2* __restrict__ out) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= nvox * C) return;
-  const long long v = t / C;
-  const int c = int(t - v * C);
-  out[t] = in[(long long)c * nvox + v];
-}
-
 struct HostPoint {
   float f[3];
   int b[3];
@@ -96,10 +86,66 @@ inline void decompose(double q, int G, int W, int* base, float* frac) {
 inline int tile_of(int idx, int tile) { return idx / tile; }
 
 // Sort points into tiles, build halo lists and work items, upload.
-nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, PointSet* ps,
-                              cudaStream_t s) {
+// Morton (Z-order) code of a tile, 10 bits per axis: work items in this
+// order keep neighbouring tiles (which share halo data) close in time.
+uint64_t morton3(const TilePlan& tp, long long tile) {
+  const long long tz = tile / ((long long)tp.nt1 * tp.nt2);
+  const long long rem = tile - tz * tp.nt1 * tp.nt2;
+  const long long ty = rem / tp.nt2, tx = rem - ty * tp.nt2;
+  uint64_t m = 0;
+  for (int b = 0; b < 10; ++b) {
+    m |= uint64_t((tx >> b) & 1) << (3 * b);
+    m |= uint64_t((ty >> b) & 1) << (3 * b + 1);
+    m |= uint64_t((tz >> b) & 1) << (3 * b + 2);
+  }
+  return m;
+}
+
+TilePlan make_tileplan(const Geo& g, int T) {
+  TilePlan tp;
+  tp.t0 = tp.t1 = tp.t2 = T;
+  tp.nt0 = (g.g0 + T - 1) / T;
+  tp.nt1 = (g.g1 + T - 1) / T;
+  tp.nt2 = (g.g2 + T - 1) / T;
+  tp.ntiles = (long long)tp.nt0 * tp.nt1 * tp.nt2;
+  return tp;
+}
+
+// Mark every tile touched by a footprint of the given points.
+void mark_touched_tiles(const nrsense_plan_s* p, const TilePlan& tp,
+                        const std::vector<HostPoint>& pts, std::vector<char>& mask) {
   const Geo& g = p->geo;
-  const TilePlan& tp = p->tiles;
+  const int gsz[3] = {g.g0, g.g1, g.g2};
+  const int tsz[3] = {tp.t0, tp.t1, tp.t2};
+  for (const HostPoint& h : pts) {
+    int tl[3][2], nt[3];
+    for (int a = 0; a < 3; ++a) {
+      nt[a] = 0;
+      for (int t = 0; t < p->W; ++t) {
+        int gi = h.b[a] + t;
+        if (gi >= gsz[a]) gi -= gsz[a];
+        const int ti = gi / tsz[a];
+        if (nt[a] == 0 || tl[a][nt[a] - 1] != ti) {
+          if (nt[a] < 2) tl[a][nt[a]++] = ti;
+        }
+      }
+    }
+    for (int a = 0; a < nt[0]; ++a)
+      for (int b = 0; b < nt[1]; ++b)
+        for (int c = 0; c < nt[2]; ++c)
+          mask[((long long)tl[0][a] * tp.nt1 + tl[1][b]) * tp.nt2 + tl[2][c]] = 1;
+  }
+}
+
+// write_mask: tiles that must be written even without points of this set
+// (NULL = every tile).
+// tp: tiles of this set; write_mask: tiles that must be written even without
+// points (NULL = every tile); interp: also build interpolation work items.
+nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, PointSet* ps,
+                              const TilePlan& tp, const std::vector<char>* write_mask,
+                              bool interp, cudaStream_t s) {
+  const Geo& g = p->geo;
+  ps->tp = tp;
   const int W = p->W;
   const long long npts = (long long)pts.size();
   ps->npts = npts;
@@ -113,12 +159,28 @@ nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, Po
     const long long t = ((long long)tile_of(h.b[0], tp.t0) * tp.nt1 + tile_of(h.b[1], tp.t1)) *
                             tp.nt2 + tile_of(h.b[2], tp.t2);
     const int cell = ((h.b[0] % tp.t0) * tp.t1 + (h.b[1] % tp.t1)) * tp.t2 + (h.b[2] % tp.t2);
-    key[i] = t * 4096 + cell;
+    key[i] = t * 4096 + cell;  // cell < T^3 <= 4096
   }
   std::vector<int32_t> order(npts);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
                    [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  // interpolation items: sorted ranges of points sharing a first-tap tile
+  std::vector<SpreadItem> iitems;
+  if (interp) {
+    long long b = 0;
+    while (b < npts) {
+      const long long t = key[order[b]] / 4096;
+      long long e = b;
+      while (e < npts && key[order[e]] / 4096 == t) ++e;
+      for (long long cb = b; cb < e; cb += kInterpMaxItem)
+        iitems.push_back({int32_t(t), int32_t(cb), int32_t(std::min(e, cb + kInterpMaxItem)), -1});
+      b = e;
+    }
+    std::stable_sort(iitems.begin(), iitems.end(), [&](const SpreadItem& a, const SpreadItem& b) {
+      return morton3(tp, a.tile) < morton3(tp, b.tile);
+    });
+  }
   key.clear();
   key.shrink_to_fit();
 
@@ -163,7 +225,7 @@ nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, Po
   for (long long t = 0; t < tp.ntiles; ++t) counts[t + 1] += counts[t];
   const long long list_len = counts[tp.ntiles];
   if (list_len >= (1ll << 31)) return NRSENSE_ERR_ARG;
-  std::vector<int32_t> list(list_len);
+  std::vector<int32_t> list(list_len);  // sorted indices; paired with rows below
   std::vector<int64_t> fill(counts.begin(), counts.end() - 1);
   for (long long s_i = 0; s_i < npts; ++s_i) {
     const HostPoint& h = pts[order[s_i]];
@@ -175,8 +237,33 @@ nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, Po
           list[fill[((long long)t0[a] * tp.nt1 + t1[b]) * tp.nt2 + t2[c]]++] = int32_t(s_i);
   }
   ps->list_len = list_len;
+  // within each tile, order the points by the plane offset of their first tap
+  // (axis 0) relative to the tile origin, so the spreading warp that owns a
+  // plane finds its points in one contiguous range (stable: ties keep order)
+  {
+    const int nb = W + tp.t0;  // offsets in (-W, T)
+    std::vector<int32_t> tmp;
+    std::vector<int64_t> bcount(nb + 1);
+    for (long long t = 0; t < tp.ntiles; ++t) {
+      const long long b = counts[t], e = counts[t + 1];
+      if (e - b < 2) continue;
+      const int o0 = int(t / ((long long)tp.nt1 * tp.nt2)) * tp.t0;
+      auto key = [&](int32_t si) {
+        int r = pts[order[si]].b[0] - o0;
+        if (r < 0) r += g.g0;
+        if (r >= tp.t0) r -= g.g0;
+        return r + W - 1;
+      };
+      std::fill(bcount.begin(), bcount.end(), 0);
+      for (long long i = b; i < e; ++i) bcount[key(list[i]) + 1]++;
+      for (int k = 0; k < nb; ++k) bcount[k + 1] += bcount[k];
+      tmp.assign(list.begin() + b, list.begin() + e);
+      for (int32_t si : tmp) list[b + bcount[key(si)]++] = si;
+    }
+  }
 
-  // work items: every tile (empty tiles write zeros); heavy tiles split
+  // work items: occupied tiles, plus empty tiles in write_mask (they write
+  // zeros); heavy tiles split
   std::vector<SpreadItem> items;
   std::vector<ReduceItem> reds;
   int slots = 0, occupied = 0;
@@ -184,39 +271,74 @@ nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, Po
     const long long b = counts[t], e = counts[t + 1];
     const long long L = e - b;
     if (L > 0) occupied++;
+    if (L == 0 && write_mask != nullptr && !(*write_mask)[t]) continue;
     if (L <= kSpreadMaxItem) {
       items.push_back({int32_t(t), int32_t(b), int32_t(e), -1});
     } else {
+      // deal the (r0-sorted) entries round-robin into chunks, so every chunk
+      // spans all planes of the tile and keeps the r0 order
       const int nchunk = int((L + kSpreadMaxItem - 1) / kSpreadMaxItem);
-      const long long step = (L + nchunk - 1) / nchunk;
+      std::vector<int32_t> seg(list.begin() + b, list.begin() + e);
+      long long w = b;
       ReduceItem r{int32_t(t), slots, nchunk, 0};
       for (int k = 0; k < nchunk; ++k) {
-        const long long cb = std::min(e, b + k * step), ce = std::min(e, cb + step);
-        items.push_back({int32_t(t), int32_t(cb), int32_t(ce), slots + k});
+        const long long cb = w;
+        for (long long i = k; i < L; i += nchunk) list[w++] = seg[i];
+        items.push_back({int32_t(t), int32_t(cb), int32_t(w), slots + k});
       }
       slots += nchunk;
       reds.push_back(r);
     }
   }
-  // heaviest first for load balance
-  std::stable_sort(items.begin(), items.end(), [](const SpreadItem& a, const SpreadItem& b) {
-    return (a.end - a.begin) > (b.end - b.begin);
+  // Morton order of tiles (chunks of a tile stay adjacent)
+  std::stable_sort(items.begin(), items.end(), [&](const SpreadItem& a, const SpreadItem& b) {
+    return morton3(tp, a.tile) < morton3(tp, b.tile);
   });
   ps->n_items = int(items.size());
   ps->n_reduces = int(reds.size());
   ps->n_slots = slots;
   ps->n_occupied = occupied;
+  ps->n_iitems = int(iitems.size());
+  // per item: first entry of each first-tap plane offset bin (list sorted by
+  // r0 within every tile, so within every item)
+  const int nb = W + tp.t0 + 1;
+  std::vector<int32_t> bins((size_t)items.size() * nb);
+  for (size_t k = 0; k < items.size(); ++k) {
+    const SpreadItem& itm = items[k];
+    const int o0 = int(itm.tile / ((long long)tp.nt1 * tp.nt2)) * tp.t0;
+    int32_t* bk = bins.data() + k * nb;
+    int e = itm.begin;
+    for (int bb = 0; bb < nb - 1; ++bb) {
+      // advance past entries with r0 + W - 1 < bb
+      while (e < itm.end) {
+        int r = pts[order[list[e]]].b[0] - o0;
+        if (r < 0) r += g.g0;
+        if (r >= tp.t0) r -= g.g0;
+        if (r + W - 1 >= bb) break;
+        ++e;
+      }
+      bk[bb] = e - itm.begin;
+    }
+    bk[nb - 1] = itm.end - itm.begin;
+  }
+  std::vector<int2> list2(list_len);
+  for (long long i = 0; i < list_len; ++i) list2[i] = make_int2(list[i], perm[list[i]]);
+  std::vector<int32_t>().swap(list);
 
   NRS_TRY(dev_alloc_n(p, &ps->qs, npts));
   NRS_TRY(dev_alloc_n(p, &ps->perm, npts));
   NRS_TRY(dev_alloc_n(p, &ps->list, std::max<long long>(list_len, 1)));
-  NRS_TRY(dev_alloc_n(p, &ps->items, (long long)items.size()));
+  NRS_TRY(dev_alloc_n(p, &ps->items, std::max<long long>((long long)items.size(), 1)));
+  NRS_TRY(dev_alloc_n(p, &ps->bins, std::max<long long>((long long)bins.size(), 1)));
   NRS_TRY(dev_alloc_n(p, &ps->reduces, std::max<long long>((long long)reds.size(), 1)));
+  NRS_TRY(dev_alloc_n(p, &ps->iitems, std::max<long long>((long long)iitems.size(), 1)));
   NRS_TRY(upload(ps->qs, qs, s));
   NRS_TRY(upload(ps->perm, perm, s));
-  NRS_TRY(upload(ps->list, list, s));
+  NRS_TRY(upload(ps->list, list2, s));
   NRS_TRY(upload(ps->items, items, s));
+  NRS_TRY(upload(ps->bins, bins, s));
   NRS_TRY(upload(ps->reduces, reds, s));
+  NRS_TRY(upload(ps->iitems, iitems, s));
   return NRSENSE_OK;
 }
 
@@ -245,6 +367,9 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   g.osf = d.osf;
   g.g0 = d.osf * d.n[0]; g.g1 = d.osf * d.n[1]; g.g2 = d.osf * d.n[2];
   if (g.g0 > 1024 || g.g1 > 1024 || g.g2 > 1024) return NRSENSE_ERR_ARG;  // 10-bit packed taps
+  // a tile and a kernel footprint must not wrap onto each other
+  const int gmin = kSpreadTile + d.kb_width - 1;
+  if (g.g0 < gmin || g.g1 < gmin || g.g2 < gmin) return NRSENSE_ERR_ARG;
   g.nvox = (long long)g.n0 * g.n1 * g.n2;
   g.ngrid = (long long)g.g0 * g.g1 * g.g2;
   if ((long long)p->P * g.nvox >= (1ll << 31)) return NRSENSE_ERR_ARG;
@@ -255,12 +380,10 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   if (!(p->beta > 0)) return NRSENSE_ERR_ARG;
   p->poly_err = fit_kernel_polys(p->W, p->beta, &p->kc);
 
-  TilePlan& tp = p->tiles;
-  tp.t0 = tp.t1 = tp.t2 = kSpreadTile;
-  tp.nt0 = (g.g0 + tp.t0 - 1) / tp.t0;
-  tp.nt1 = (g.g1 + tp.t1 - 1) / tp.t1;
-  tp.nt2 = (g.g2 + tp.t2 - 1) / tp.t2;
-  tp.ntiles = (long long)tp.nt0 * tp.nt1 * tp.nt2;
+  if (configure_kernels() != cudaSuccess) return NRSENSE_ERR_CUDA;
+  const TilePlan ktiles = make_tileplan(g, kSpreadTile);
+  const TilePlan itiles =
+      make_tileplan(g, spread_tile_edge(p->W, 1, std::min(g.g0, std::min(g.g1, g.g2))));
 
   // deapodization: 1/C(m/G) for m in [-N/2, N/2), per axis
   {
@@ -307,7 +430,7 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
         h.row = int32_t(j * g.nvox + v);
       }
     }
-    NRS_TRY(build_pointset(p, pts, &p->ipts, s));
+    NRS_TRY(build_pointset(p, pts, &p->ipts, itiles, nullptr, /*interp=*/false, s));
   }
 
   // coils and k-space
@@ -323,9 +446,9 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     p->Mtot = tot;
     const long long nm = g.nvox * p->C;
     NRS_TRY(dev_alloc_n(p, &p->smaps, nm));
-    transpose_maps_kernel<<<unsigned((nm + 255) / 256), 256, 0, s>>>(
-        g.nvox, p->C, reinterpret_cast<const float2*>(smaps), reinterpret_cast<float2*>(p->smaps));
-    if (cudaGetLastError() != cudaSuccess) return NRSENSE_ERR_CUDA;
+    if (cudaMemcpyAsync(p->smaps, smaps, size_t(nm) * sizeof(nrsense_c64), cudaMemcpyDeviceToDevice,
+                        s) != cudaSuccess)
+      return NRSENSE_ERR_CUDA;
 
     std::vector<float> hc(size_t(3 * tot));
     if (tot > 0) {
@@ -336,8 +459,10 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     }
     p->kpts.resize(p->P);
     const int gs[3] = {g.g0, g.g1, g.g2};
+    std::vector<std::vector<HostPoint>> all((size_t)p->P);
     for (int j = 0; j < p->P; ++j) {
-      std::vector<HostPoint> pts((size_t)p->M[j]);
+      std::vector<HostPoint>& pts = all[(size_t)j];
+      pts.resize((size_t)p->M[j]);
       for (long long i = 0; i < p->M[j]; ++i) {
         HostPoint& h = pts[(size_t)i];
         for (int a = 0; a < 3; ++a) {
@@ -349,7 +474,14 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
         }
         h.row = int32_t(i);
       }
-      NRS_TRY(build_pointset(p, pts, &p->kpts[j], s));
+    }
+    // all phases share one spread target: each phase writes every tile that
+    // any phase occupies (zeros where it has no points), the rest stay zero
+    std::vector<char> uni((size_t)ktiles.ntiles, 0);
+    for (int j = 0; j < p->P; ++j) mark_touched_tiles(p, ktiles, all[(size_t)j], uni);
+    for (int j = 0; j < p->P; ++j) {
+      NRS_TRY(build_pointset(p, all[(size_t)j], &p->kpts[j], ktiles, &uni, /*interp=*/true, s));
+      std::vector<HostPoint>().swap(all[(size_t)j]);
     }
   }
 
@@ -363,7 +495,9 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   }
   if (p->C > 0) {
     int n[3] = {g.g0, g.g1, g.g2};
-    NRS_TRY(cufft_check(cufftPlanMany(&p->fft_gc, 3, n, n, p->C, 1, n, p->C, 1, CUFFT_C2C, p->C)));
+    // coil-major batch: coil c's grid starts at c * G^3
+    NRS_TRY(cufft_check(cufftPlanMany(&p->fft_gc, 3, n, n, 1, int(g.ngrid), n, 1, int(g.ngrid),
+                                      CUFFT_C2C, p->C)));
     p->have_fft_gc = true;
   }
 
@@ -380,6 +514,11 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   if (p->C > 0) {
     NRS_TRY(dev_alloc_n(p, &p->b_xpad, g.ngrid * p->C));
     NRS_TRY(dev_alloc_n(p, &p->b_xwork, g.ngrid * p->C));
+    NRS_TRY(dev_alloc_n(p, &p->b_xspread, g.ngrid * p->C));
+    // empty tiles of the spread target are never written: zero them once
+    if (cudaMemsetAsync(p->b_xspread, 0, size_t(g.ngrid * p->C) * sizeof(nrsense_c64), s) !=
+        cudaSuccess)
+      return NRSENSE_ERR_CUDA;
     NRS_TRY(dev_alloc_n(p, &p->b_y, std::max<long long>(p->Mtot * p->C, 1)));
     if (cudaMemsetAsync(p->b_xpad, 0, size_t(g.ngrid * p->C) * sizeof(nrsense_c64), s) !=
         cudaSuccess)
@@ -387,13 +526,15 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   }
   // scratch for split tiles: slots x coil chunks x tile x chunk coils
   long long need = 0;
-  const long long tile_pts = (long long)kSpreadTile * kSpreadTile * kSpreadTile;
-  if (!p->identity_warp) need = std::max(need, (long long)p->ipts.n_slots * tile_pts);
+  auto tile_pts = [](const PointSet& ps) {
+    return (long long)ps.tp.t0 * ps.tp.t1 * ps.tp.t2;
+  };
+  if (!p->identity_warp) need = std::max(need, (long long)p->ipts.n_slots * tile_pts(p->ipts));
   if (p->C > 0) {
     const int cc = spread_coil_chunk(p->C);
     const int chunks = (p->C + cc - 1) / cc;
     for (const auto& k : p->kpts)
-      need = std::max(need, (long long)k.n_slots * chunks * tile_pts * cc);
+      need = std::max(need, (long long)k.n_slots * chunks * tile_pts(k) * cc);
   }
   p->scratch_elems = need;
   if (need > 0) NRS_TRY(dev_alloc_n(p, &p->b_scratch, need));
@@ -457,10 +598,11 @@ nrsense_status nrsense_plan_info(nrsense_plan_t p, nrsense_info* out) {
   out->kb_beta = p->beta;
   out->kernel_poly_err = p->poly_err;
   out->total_samples = p->Mtot;
-  out->tile[0] = p->tiles.t0;
-  out->tile[1] = p->tiles.t1;
-  out->tile[2] = p->tiles.t2;
-  out->n_tiles = p->tiles.ntiles;
+  const TilePlan& ktp = p->kpts.empty() ? p->ipts.tp : p->kpts[0].tp;
+  out->tile[0] = ktp.t0;
+  out->tile[1] = ktp.t1;
+  out->tile[2] = ktp.t2;
+  out->n_tiles = ktp.ntiles;
   long long occ = 0, items = 0, split = 0;
   for (const auto& k : p->kpts) {
     occ += k.n_occupied;
@@ -468,7 +610,7 @@ nrsense_status nrsense_plan_info(nrsense_plan_t p, nrsense_info* out) {
     split += k.n_reduces;
   }
   out->occupied_fraction =
-      p->kpts.empty() ? 0.0 : double(occ) / (double(p->tiles.ntiles) * double(p->kpts.size()));
+      p->kpts.empty() ? 0.0 : double(occ) / (double(ktp.ntiles) * double(p->kpts.size()));
   out->spread_items = items;
   out->split_tiles = split;
   out->device_bytes = p->device_bytes;

@@ -11,26 +11,32 @@
 
 namespace nrs {
 
-// Sorted points of one spreading problem (one k-space phase, or all displaced
-// voxels of all phases for the image-space adjoint).
-struct PointSet {
-  long long npts = 0;
-  float4* qs = nullptr;        // sorted: (f0, f1, f2, packed base bits)
-  int32_t* perm = nullptr;     // sorted index -> value row
-  int32_t* list = nullptr;     // per-tile halo lists (sorted indices)
-  SpreadItem* items = nullptr; // spreading work, heaviest first
-  int n_items = 0;
-  ReduceItem* reduces = nullptr;
-  int n_reduces = 0;
-  int n_slots = 0;             // partial tiles needed in scratch
-  int n_occupied = 0;          // tiles with at least one point
-  long long list_len = 0;
-};
-
 struct TilePlan {
   int t0, t1, t2;       // tile size (grid points per axis)
   int nt0, nt1, nt2;    // tiles per axis (last tile may be ragged)
   long long ntiles;
+};
+
+// Sorted points of one gridding problem (one k-space phase, or all displaced
+// voxels of all phases for the image-space adjoint).
+struct PointSet {
+  long long npts = 0;
+  TilePlan tp{};                // tiles of this set's spreading/interpolation
+  float4* qs = nullptr;         // sorted: (f0, f1, f2, packed base bits)
+  int32_t* perm = nullptr;      // sorted index -> value row
+  // spreading: per-tile halo lists of (sorted index, value row)
+  int2* list = nullptr;
+  SpreadItem* items = nullptr;  // heaviest first
+  int32_t* bins = nullptr;      // per item: W + T + 1 plane-offset bin starts (relative)
+  int n_items = 0;
+  ReduceItem* reduces = nullptr;
+  int n_reduces = 0;
+  int n_slots = 0;              // partial tiles needed in scratch
+  int n_occupied = 0;           // tiles with at least one point in their halo lists
+  long long list_len = 0;
+  // interpolation: sorted ranges of the points whose first tap lies in a tile
+  SpreadItem* iitems = nullptr;
+  int n_iitems = 0;
 };
 
 }  // namespace nrs
@@ -47,22 +53,22 @@ struct nrsense_plan_s {
   // tables
   float* deapod = nullptr;       // 1/C(m/G) for m in [-N/2, N/2), per axis, offsets 0, n0, n0+n1
   float* disp = nullptr;         // (P, 3, nvox)
-  nrsense_c64* smaps = nullptr;  // (nvox, C) interleaved
+  nrsense_c64* smaps = nullptr;  // (C, nvox) coil-major
 
   // k-space
   std::vector<long long> M, off;
   long long Mtot = 0;
   std::vector<nrs::PointSet> kpts;  // per phase
   nrs::PointSet ipts;               // displaced voxels of all phases
-  nrs::TilePlan tiles{};
 
   // work buffers
   nrsense_c64* b_xhat = nullptr;   // N^3
   nrsense_c64* b_upad = nullptr;   // G^3, zero outside the K_N block
   nrsense_c64* b_ugrid = nullptr;  // G^3
   nrsense_c64* b_m = nullptr;      // P * N^3
-  nrsense_c64* b_xpad = nullptr;   // G^3 * C, zero outside the centred N^3 block
-  nrsense_c64* b_xwork = nullptr;  // G^3 * C
+  nrsense_c64* b_xpad = nullptr;   // C * G^3, zero outside the centred N^3 block
+  nrsense_c64* b_xwork = nullptr;  // C * G^3 (FFT outputs)
+  nrsense_c64* b_xspread = nullptr;  // C * G^3 spread target; empty tiles stay zero
   nrsense_c64* b_y = nullptr;      // Mtot * C
   nrsense_c64* b_tmp = nullptr;    // N^3 (normal operator scratch)
   nrsense_c64* b_scratch = nullptr;  // partial tiles
@@ -129,6 +135,9 @@ int launch_image_to_padded(const Geo& g, int C, const float* deapod,
 int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C,
                           const PointSet& ps, const nrsense_c64* grid, nrsense_c64* y,
                           cudaStream_t s);
+// one-time kernel attributes (large dynamic shared memory); plan time
+cudaError_t configure_kernels();
+cudaError_t configure_spread_kernels();
 int launch_crop_coilsum(const Geo& g, int C, const float* deapod,
                          const nrsense_c64* smaps, const nrsense_c64* xg,
                          nrsense_c64* w, cudaStream_t s);
@@ -136,13 +145,18 @@ int launch_crop_to_coils(const Geo& g, int C, const float* deapod,
                           const nrsense_c64* xg, nrsense_c64* v, cudaStream_t s);
 
 // spreading (both domains)
-int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
-                   const PointSet& ps, const nrsense_c64* vals, nrsense_c64* grid,
-                   nrsense_c64* scratch, int32_t* status, cudaStream_t s);
-// coils handled by one spreading CTA, and the tile edge used by the kernels
+int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const PointSet& ps,
+                  const nrsense_c64* vals, nrsense_c64* grid, nrsense_c64* scratch,
+                  int32_t* status, cudaStream_t s);
+// coils handled by one spreading CTA
 int spread_coil_chunk(int C);
+// tile edge of a point set: 16 for the single-channel W=4 spread (image
+// space) on grids of at least 16 + W - 1 points per axis, 8 otherwise
+int spread_tile_edge(int W, int C, int gmin);
 constexpr int kSpreadTile = 8;
 // largest number of list entries one spreading CTA processes
 constexpr int kSpreadMaxItem = 1024;
+// largest number of points one interpolation CTA processes
+constexpr int kInterpMaxItem = 1024;
 
 }  // namespace nrs
