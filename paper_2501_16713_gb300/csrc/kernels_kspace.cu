@@ -92,10 +92,11 @@ __global__ void __launch_bounds__(256) interp_tile_kernel(
   const int o0 = tz * T, o1 = ty * T, o2 = tx * T;
   if (threadIdx.x < W * kNumCoef) s_coef[threadIdx.x / kNumCoef][threadIdx.x % kNumCoef] =
       kc.c[threadIdx.x / kNumCoef][threadIdx.x % kNumCoef];
-  // stage: consecutive threads walk x, so global reads coalesce along rows
+  // stage: lanes walk (coil, x) with the coil fastest, so shared writes are
+  // contiguous and each global sector (4 consecutive x of one coil) is fully used
   for (int i = threadIdx.x; i < CC * H3; i += blockDim.x) {
-    const int c = i / H3;
-    const int r = i - c * H3;
+    const int c = i % CC;
+    const int r = i / CC;
     const int z = r / (H * H), yy = (r / H) % H, x = r % H;
     const int gz = wrap_once(o0 + z, g.g0), gy = wrap_once(o1 + yy, g.g1),
               gx = wrap_once(o2 + x, g.g2);

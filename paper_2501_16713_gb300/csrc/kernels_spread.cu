@@ -92,13 +92,14 @@ __device__ __forceinline__ void write_tile(const Geo& g, int C, int coil0, const
                                           int tid) {
   constexpr int kPts = T * T * T;
   if (it.slot < 0) {
+    // coil fastest across lanes: contiguous shared reads, full global sectors
     for (int i = tid; i < kPts * CC; i += kThreads) {
-      const int c = i / kPts;
-      const int pt = i - c * kPts;
+      const int c = i % CC;
+      const int pt = i / CC;
       const int lx = pt % T, ly = (pt / T) % T, lz = pt / (T * T);
       if (lz < to.e0 && ly < to.e1 && lx < to.e2 && coil0 + c < C) {
         const long long gi = ((long long)(to.o0 + lz) * g.g1 + (to.o1 + ly)) * g.g2 + (to.o2 + lx);
-        grid[(long long)(coil0 + c) * g.ngrid + gi] = acc[pt * CC + c];
+        grid[(long long)(coil0 + c) * g.ngrid + gi] = acc[i];
       }
     }
   } else {
@@ -394,13 +395,13 @@ __global__ void reduce_kernel(Geo g, int C, TilePlan tp, const ReduceItem* __res
   constexpr int kPts = T * T * T;
   const long long tile_elems = kPts * CC;
   for (int i = threadIdx.x; i < tile_elems; i += blockDim.x) {
-    const int c = i / kPts;
-    const int pt = i - c * kPts;
+    const int c = i % CC;
+    const int pt = i / CC;
     const int lx = pt % T, ly = (pt / T) % T, lz = pt / (T * T);
     float2 s = make_float2(0.f, 0.f);
     for (int k = 0; k < r.count; ++k) {
       const float2 v =
-          scratch[((long long)(r.first + k) * gridDim.y + blockIdx.y) * tile_elems + pt * CC + c];
+          scratch[((long long)(r.first + k) * gridDim.y + blockIdx.y) * tile_elems + i];
       s.x += v.x;
       s.y += v.y;
     }
