@@ -175,6 +175,37 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t plan, int32_t phase,
                                       void* stream);
 
 /*
+ * nrsense_solve_cg - conjugate gradients on the Tikhonov-regularised normal
+ * equations (sum_j A_j^H A_j + lambda I) x = sum_j A_j^H y_j, the regularised
+ * least-squares form of the reconstruction problem (reconstruction
+ * optimisation equation, with lambda ||x||^2 in place of the wavelet L1 term).
+ *   y_dev        k-space data, layout of nrsense_apply_forward's output (device).
+ *   lambda       Tikhonov weight (>= 0; > 0 makes the system positive definite).
+ *   tol          stop when ||r_k|| <= tol ||b|| (recursive residual, x0 = 0 unless
+ *                NRSENSE_CG_X0).
+ *   maxit        iteration limit (0 .. 2^20).
+ *   flags        NRSENSE_CG_X0: x_dev holds the initial guess; NRSENSE_CG_GRAPH:
+ *                iterations are captured once as a CUDA graph (per plan, x_dev,
+ *                lambda) and replayed.
+ *   x_dev        image (device): initial guess (with NRSENSE_CG_X0) and solution.
+ *   iters_host   receives the number of iterations (may be NULL).
+ *   res_hist_host receives ||r_k|| / ||b|| for k = 0 .. iters (maxit + 1 doubles
+ *                of room; may be NULL).
+ *   true_res_host receives ||b - E x|| / ||b||, recomputed once at exit (may be NULL).
+ * Inner products, alpha, beta and norms are FP64 on the device; vectors are FP32.
+ * The first call allocates the plan's CG workspace (four image vectors, an
+ * internal stream).  The call synchronises the device at chunk boundaries and
+ * at exit.  Returns NRSENSE_ERR_BREAKDOWN on non-positive curvature or
+ * non-finite scalars, NRSENSE_ERR_NOT_CONVERGED if maxit is reached above tol.
+ */
+#define NRSENSE_CG_X0     (1u << 0)
+#define NRSENSE_CG_GRAPH  (1u << 1)
+nrsense_status nrsense_solve_cg(nrsense_plan_t plan, const nrsense_c64* y_dev, double lambda,
+                                double tol, int32_t maxit, uint32_t flags, nrsense_c64* x_dev,
+                                int32_t* iters_host, double* res_hist_host, double* true_res_host,
+                                void* stream);
+
+/*
  * nrsense_device_status - read (and with clear != 0, reset) the plan's
  * latched device status word; synchronises `stream`.  *out_host receives
  * NRSENSE_OK or the first device-side error (ERR_BOUNDS, ERR_TIMEOUT).

@@ -28,6 +28,7 @@ SOURCES = [
     "kernels_image.cu",
     "kernels_kspace.cu",
     "kernels_spread.cu",
+    "solver.cu",
 ]
 HEADERS = ["common.cuh", "plan_internal.h", "kb_host.h"]
 

@@ -41,6 +41,8 @@ struct PointSet {
 
 }  // namespace nrs
 
+struct nrsense_cg_ws;  // CG workspace (solver.cu)
+
 struct nrsense_plan_s {
   nrsense_desc desc{};
   nrs::Geo geo{};
@@ -87,6 +89,8 @@ struct nrsense_plan_s {
   std::vector<int> prof_stage;           // stage of each recorded pair
   long long launches = 0;                // own kernels launched (always counted)
   long long launches_at_start = 0;
+
+  nrsense_cg_ws* cg = nullptr;  // allocated by the first nrsense_solve_cg
 };
 
 namespace nrs {
@@ -150,6 +154,8 @@ int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const Point
                   int32_t* status, cudaStream_t s);
 // coils handled by one spreading CTA
 int spread_coil_chunk(int C);
+// free the CG workspace of a plan (solver.cu)
+void cg_release(nrsense_plan_s* p);
 // tile edge of a point set: 16 for the single-channel W=4 spread (image
 // space) on grids of at least 16 + W - 1 points per axis, 8 otherwise
 int spread_tile_edge(int W, int C, int gmin);

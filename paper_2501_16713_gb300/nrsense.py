@@ -66,7 +66,12 @@ _SIGS = {
     "nrsense_profile_stop": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                              ctypes.POINTER(ctypes.c_int64)],
     "nrsense_stage_name": [ctypes.c_int32],
+    "nrsense_solve_cg": [_VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                         ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_int32),
+                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _VP],
 }
+CG_X0 = 1
+CG_GRAPH = 2
 NUM_STAGES = 13
 _STRING_RESULT = ("nrsense_status_string", "nrsense_stage_name")
 
@@ -282,6 +287,35 @@ class Plan:
                "nrsense_profile_stop")
         names = [self.lib.nrsense_stage_name(i).decode() for i in range(NUM_STAGES)]
         return {n: (ms[i], cnt[i]) for i, n in enumerate(names)}, own.value
+
+    def solve_cg(self, y, lam, tol=1e-4, maxit=100, x0=None, graph=False, stream=None,
+                 check=True, out=None):
+        """CG on (sum_j A_j^H A_j + lam I) x = sum_j A_j^H y_j.
+
+        Returns (x, iterations, residual history, true relative residual,
+        status code).  With check=True a breakdown raises; not reaching tol
+        does not."""
+        import torch
+        _need(y, torch.complex64, self.forward_shape(), "y")
+        if x0 is not None:
+            _need(x0, torch.complex64, self.shape, "x0")
+            if out is not None and out.data_ptr() != x0.data_ptr():
+                out.copy_(x0)
+                x = out
+            else:
+                x = x0
+        else:
+            x = self._img() if out is None else _need(out, torch.complex64, self.shape, "out")
+        it = ctypes.c_int32()
+        hist = (ctypes.c_double * (int(maxit) + 1))()
+        tres = ctypes.c_double()
+        flags = (CG_X0 if x0 is not None else 0) | (CG_GRAPH if graph else 0)
+        code = self.lib.nrsense_solve_cg(self._h, _ptr(y), float(lam), float(tol), int(maxit),
+                                         flags, _ptr(x), ctypes.byref(it), hist,
+                                         ctypes.byref(tres), _stream(stream))
+        if check and code not in (OK, -6):
+            _check(code, "nrsense_solve_cg")
+        return x, it.value, list(hist[: it.value + 1]), tres.value, code
 
     def phase_slice(self, y, j):
         """Rows of phase j in a stacked (sum M_j, C) k-space array."""
