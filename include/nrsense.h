@@ -206,6 +206,30 @@ nrsense_status nrsense_solve_cg(nrsense_plan_t plan, const nrsense_c64* y_dev, d
                                 void* stream);
 
 /*
+ * nrsense_dot_noalloc - <x, y> = sum_i conj(x_i) y_i in FP64, for callers that
+ * cannot allocate device memory.  The paper has no counterpart: this is a
+ * variant of the CG solver's inner-product kernel that needs no plan and
+ * calls no allocator.  Some callers may not call cudaMalloc (their device
+ * memory belongs to another allocator or a fixed pool, or they run where an
+ * allocation could block), so they can create no plan; they pass the inputs
+ * and the output, and the block partial sums go to a fixed 256 KB array that
+ * the library holds on every GPU where it is loaded, until the process exits.
+ *   x_dev, y_dev  n complex values each (device, read only).
+ *   n             0 <= n <= NRSENSE_DOT_NOALLOC_MAX_N; larger n is rejected
+ *                 with NRSENSE_ERR_ARG before anything is launched.
+ *   out_dev       two doubles (device): real and imaginary part of the sum.
+ *   stream        stream for the two kernels; asynchronous.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * on a device share the one array: calls that overlap on the GPU (different
+ * streams, no ordering) race and must not be issued.  Returns NRSENSE_ERR_CUDA
+ * if the address lookup or a launch fails.
+ */
+#define NRSENSE_DOT_NOALLOC_MAX_N (16384LL * 4096LL)
+nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* y_dev, int64_t n,
+                                   double* out_dev, void* stream);
+
+/*
  * nrsense_device_status - read (and with clear != 0, reset) the plan's
  * latched device status word; synchronises `stream`.  *out_host receives
  * NRSENSE_OK or the first device-side error (ERR_BOUNDS, ERR_TIMEOUT).

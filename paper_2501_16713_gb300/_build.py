@@ -29,6 +29,7 @@ SOURCES = [
     "kernels_kspace.cu",
     "kernels_spread.cu",
     "solver.cu",
+    "noalloc.cu",
 ]
 HEADERS = ["common.cuh", "plan_internal.h", "kb_host.h"]
 

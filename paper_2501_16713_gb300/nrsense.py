@@ -66,6 +66,7 @@ _SIGS = {
     "nrsense_profile_stop": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                              ctypes.POINTER(ctypes.c_int64)],
     "nrsense_stage_name": [ctypes.c_int32],
+    "nrsense_dot_noalloc": [_VP, _VP, ctypes.c_int64, _VP, _VP],
     "nrsense_solve_cg": [_VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                          ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_int32),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _VP],
@@ -126,6 +127,26 @@ def _need(t, dtype, shape, name):
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     return t
+
+
+DOT_NOALLOC_MAX_N = 16384 * 4096
+
+
+def dot_noalloc(x, y, out=None, stream=None):
+    """<x, y> in FP64 through nrsense_dot_noalloc (no plan, no allocation by
+    the library).  x, y: contiguous complex64 CUDA tensors of equal size;
+    out: a float64 CUDA tensor of 2 elements (allocated here if omitted -- the
+    library call itself allocates nothing).  Returns out."""
+    import torch
+    lib = load()
+    _need(x, torch.complex64, None, "x")
+    _need(y, torch.complex64, tuple(x.shape), "y")
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=x.device)
+    _need(out, torch.float64, (2,), "out")
+    _check(lib.nrsense_dot_noalloc(_ptr(x), _ptr(y), int(x.numel()), _ptr(out), _stream(stream)),
+           "nrsense_dot_noalloc")
+    return out
 
 
 class Plan:
