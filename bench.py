@@ -226,7 +226,8 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     build()
-    w = synth.workload(args.workload)
+    w = synth.workload(args.workload,
+                       phases=None if args.phases is None else list(range(args.phases)))
     spec = w["spec"]
     shape = spec.shape
     disp = torch.from_numpy(np.stack(w["disp"])).to(dev)
@@ -367,6 +368,8 @@ def main():
     ap.add_argument("--workload", default="sense128")
     ap.add_argument("--lam", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--phases", type=int, default=None,
+                    help="use only the first K phases (a smaller case for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -409,7 +412,7 @@ def main():
     result, w = run_gpu(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            e, desc = oracle_cost(w, frac=1.0 / 8)
+            e, desc = oracle_cost(w, frac=0.5)
             result["cpu_baseline"] = {"value": 1.0 / e, "unit": UNIT, "cores": 1,
                                       "kind": "oracle", "sample": desc}
         else:
