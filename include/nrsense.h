@@ -81,6 +81,8 @@ typedef struct {
   int32_t n_coils;     /* C >= 0; 0 = image-space warp only (no S, no G_j) */
   int32_t precision;   /* NRSENSE_FP32 */
   uint32_t flags;      /* NRSENSE_* flags */
+  int32_t phase_chunk; /* phases processed per launch (1..16); 0 = as many as half of the
+                          free device memory at plan time allows */
 } nrsense_desc;
 
 /* Plan-time facts, for benchmarking and tests. */
@@ -95,6 +97,7 @@ typedef struct {
   int64_t spread_items;      /* work items of the k-space spread (all phases) */
   int64_t split_tiles;       /* tiles split across several work items */
   int64_t device_bytes;      /* device memory held by the plan (excl. cuFFT work) */
+  int32_t phase_chunk;       /* phases per launch actually used */
 } nrsense_info;
 
 /*

@@ -10,6 +10,9 @@
 //  S^H G_j^H (per phase):                   K7 (P^(k), into a buffer whose
 //        empty tiles stay zero) -> F_G^H (batched, out of place) ->
 //        K8 (Z^H, 1/c, S^H)
+#include <algorithm>
+#include <cstring>
+
 #include "plan_internal.h"
 
 using namespace nrs;
@@ -44,6 +47,56 @@ nrsense_status launched() {
     p->launches += (call);                          \
   } while (0)
 
+cufftHandle gc_plan(nrsense_plan_s* p, int nph) {
+  for (auto& fp : p->fft_gc_plans)
+    if (fp.first == nph) return fp.second;
+  return 0;
+}
+
+// Phase table of phases [j0, j1) of the k-space point sets; value/output rows
+// of phase j start at off_j - row_base.
+PhaseTable kspace_table(const nrsense_plan_s* p, int j0, int j1, bool spread, long long row_base) {
+  PhaseTable t;
+  std::memset(&t, 0, sizeof(t));
+  t.nphase = j1 - j0;
+  int ai = 0, ar = 0, as = 0;
+  for (int jj = 0; jj < t.nphase; ++jj) {
+    const PointSet& ps = p->kpts[j0 + jj];
+    t.qs[jj] = ps.qs;
+    t.perm[jj] = ps.perm;
+    t.list[jj] = ps.list;
+    t.bins[jj] = ps.bins;
+    t.items[jj] = spread ? ps.items : ps.iitems;
+    t.reduces[jj] = ps.reduces;
+    t.row0[jj] = p->off[j0 + jj] - row_base;
+    t.item0[jj] = ai;
+    ai += spread ? ps.n_items : ps.n_iitems;
+    t.red0[jj] = ar;
+    ar += spread ? ps.n_reduces : 0;
+    t.slot0[jj] = as;
+    as += ps.n_slots;
+  }
+  t.item0[t.nphase] = ai;
+  t.red0[t.nphase] = ar;
+  return t;
+}
+
+PhaseTable image_table(const nrsense_plan_s* p) {
+  PhaseTable t;
+  std::memset(&t, 0, sizeof(t));
+  const PointSet& ps = p->ipts;
+  t.nphase = 1;
+  t.qs[0] = ps.qs;
+  t.perm[0] = ps.perm;
+  t.list[0] = ps.list;
+  t.bins[0] = ps.bins;
+  t.items[0] = ps.items;
+  t.reduces[0] = ps.reduces;
+  t.item0[1] = ps.n_items;
+  t.red0[1] = ps.n_reduces;
+  return t;
+}
+
 // m (P x nvox) = T_j x for all phases
 nrsense_status warp_forward(nrsense_plan_s* p, const nrsense_c64* x, nrsense_c64* m,
                             cudaStream_t s) {
@@ -68,8 +121,9 @@ nrsense_status warp_adjoint(nrsense_plan_s* p, const nrsense_c64* m, nrsense_c64
     STAGE(VECTOR, launch_sum_phases(g, p->P, m, x, s));
     return launched();
   }
-  STAGE(SPREAD_IMAGE, launch_spread(g, p->W, p->kc, 1, p->ipts, m, p->b_ugrid,
-                                     p->b_scratch, p->d_status, s));
+  const PhaseTable t = image_table(p);
+  STAGE(SPREAD_IMAGE, launch_spread(g, p->W, p->kc, 1, p->itiles, t, m, p->b_ugrid, p->b_scratch,
+                                    p->d_status, s));
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_ugrid, p->b_ugrid, CUFFT_FORWARD));
   STAGE(CROP_DEAPOD, launch_crop_deapod(g, p->deapod, p->b_ugrid, x, s));
@@ -77,26 +131,31 @@ nrsense_status warp_adjoint(nrsense_plan_s* p, const nrsense_c64* m, nrsense_c64
   return fft(p, NRSENSE_STAGE_FFT_N, p->fft_n, s, x, x, CUFFT_INVERSE);
 }
 
-// y_j (M_j x C) = G_j S m_j
-nrsense_status sense_phase_forward(nrsense_plan_s* p, int j, const nrsense_c64* mj,
-                                   nrsense_c64* yj, cudaStream_t s) {
+// y rows of phases [j0, j1) (row off_j - row_base of y) = G_j S m_j, where m
+// holds the chunk's warped images consecutively.
+nrsense_status sense_chunk_forward(nrsense_plan_s* p, int j0, int j1, const nrsense_c64* m,
+                                   nrsense_c64* y, long long row_base, cudaStream_t s) {
   const Geo& g = p->geo;
-  STAGE(COIL_FANOUT, launch_coil_fanout_pad(g, p->C, p->deapod, p->smaps, mj, p->b_xpad, s));
+  const int nph = j1 - j0;
+  STAGE(COIL_FANOUT, launch_coil_fanout_pad(g, p->C, nph, p->deapod, p->smaps, m, p->b_xpad, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, p->fft_gc, s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
-  STAGE(INTERP_KSPACE, launch_interp_kspace(g, p->W, p->kc, p->C, p->kpts[j], p->b_xwork, yj, s));
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, nph), s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
+  const PhaseTable t = kspace_table(p, j0, j1, /*spread=*/false, row_base);
+  STAGE(INTERP_KSPACE, launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork, y, s));
   return launched();
 }
 
-// w_j (nvox) = S^H G_j^H y_j
-nrsense_status sense_phase_adjoint(nrsense_plan_s* p, int j, const nrsense_c64* yj,
-                                   nrsense_c64* wj, cudaStream_t s) {
+// w (nph x nvox) = S^H G_j^H y_j for phases [j0, j1)
+nrsense_status sense_chunk_adjoint(nrsense_plan_s* p, int j0, int j1, const nrsense_c64* y,
+                                   long long row_base, nrsense_c64* w, cudaStream_t s) {
   const Geo& g = p->geo;
-  STAGE(SPREAD_KSPACE, launch_spread(g, p->W, p->kc, p->C, p->kpts[j], yj,
-                                     p->b_xspread, p->b_scratch, p->d_status, s));
+  const int nph = j1 - j0;
+  const PhaseTable t = kspace_table(p, j0, j1, /*spread=*/true, row_base);
+  STAGE(SPREAD_KSPACE, launch_spread(g, p->W, p->kc, p->C, p->ktiles, t, y, p->b_xspread,
+                                     p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, p->fft_gc, s, p->b_xspread, p->b_xwork, CUFFT_INVERSE));
-  STAGE(CROP_COILSUM, launch_crop_coilsum(g, p->C, p->deapod, p->smaps, p->b_xwork, wj, s));
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, nph), s, p->b_xspread, p->b_xwork, CUFFT_INVERSE));
+  STAGE(CROP_COILSUM, launch_crop_coilsum(g, p->C, nph, p->deapod, p->smaps, p->b_xwork, w, s));
   return launched();
 }
 
@@ -124,8 +183,9 @@ nrsense_status nrsense_kspace_forward(nrsense_plan_t p, int32_t phase, const nrs
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   STAGE(COIL_FANOUT, launch_image_to_padded(p->geo, p->C, p->deapod, v, p->b_xpad, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, p->fft_gc, s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
-  STAGE(INTERP_KSPACE, launch_interp_kspace(p->geo, p->W, p->kc, p->C, p->kpts[phase], p->b_xwork, y, s));
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, 1), s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
+  const PhaseTable t = kspace_table(p, phase, phase + 1, false, p->off[phase]);
+  STAGE(INTERP_KSPACE, launch_interp_kspace(p->geo, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork, y, s));
   return launched();
 }
 
@@ -135,10 +195,11 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t p, int32_t phase, const nrs
   if (p->C == 0) return NRSENSE_ERR_STATE;
   if (phase < 0 || phase >= p->P) return NRSENSE_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  STAGE(SPREAD_KSPACE, launch_spread(p->geo, p->W, p->kc, p->C, p->kpts[phase], y,
-                                     p->b_xspread, p->b_scratch, p->d_status, s));
+  const PhaseTable t = kspace_table(p, phase, phase + 1, true, p->off[phase]);
+  STAGE(SPREAD_KSPACE, launch_spread(p->geo, p->W, p->kc, p->C, p->ktiles, t, y, p->b_xspread,
+                                     p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, p->fft_gc, s, p->b_xspread, p->b_xwork, CUFFT_INVERSE));
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, 1), s, p->b_xspread, p->b_xwork, CUFFT_INVERSE));
   STAGE(CROP_COILSUM, launch_crop_to_coils(p->geo, p->C, p->deapod, p->b_xwork, v, s));
   return launched();
 }
@@ -149,9 +210,9 @@ nrsense_status nrsense_apply_forward(nrsense_plan_t p, const nrsense_c64* x, nrs
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->C == 0) return warp_forward(p, x, y, s);
   NRS_TRY(warp_forward(p, x, p->b_m, s));
-  for (int j = 0; j < p->P; ++j) {
-    if (p->M[j] == 0) continue;
-    NRS_TRY(sense_phase_forward(p, j, p->b_m + (long long)j * p->geo.nvox, y + p->off[j] * p->C, s));
+  for (int j0 = 0; j0 < p->P; j0 += p->phase_chunk) {
+    const int j1 = std::min(p->P, j0 + p->phase_chunk);
+    NRS_TRY(sense_chunk_forward(p, j0, j1, p->b_m + (long long)j0 * p->geo.nvox, y, 0, s));
   }
   return NRSENSE_OK;
 }
@@ -161,14 +222,9 @@ nrsense_status nrsense_apply_adjoint(nrsense_plan_t p, const nrsense_c64* y, nrs
   if (p == nullptr || x == nullptr || y == nullptr) return NRSENSE_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->C == 0) return warp_adjoint(p, y, x, s);
-  for (int j = 0; j < p->P; ++j) {
-    nrsense_c64* wj = p->b_m + (long long)j * p->geo.nvox;
-    if (p->M[j] == 0) {
-      if (cudaMemsetAsync(wj, 0, size_t(p->geo.nvox) * sizeof(nrsense_c64), s) != cudaSuccess)
-        return NRSENSE_ERR_CUDA;
-      continue;
-    }
-    NRS_TRY(sense_phase_adjoint(p, j, y + p->off[j] * p->C, wj, s));
+  for (int j0 = 0; j0 < p->P; j0 += p->phase_chunk) {
+    const int j1 = std::min(p->P, j0 + p->phase_chunk);
+    NRS_TRY(sense_chunk_adjoint(p, j0, j1, y, 0, p->b_m + (long long)j0 * p->geo.nvox, s));
   }
   return warp_adjoint(p, p->b_m, x, s);
 }
@@ -179,16 +235,11 @@ nrsense_status nrsense_apply_normal(nrsense_plan_t p, const nrsense_c64* x, doub
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   NRS_TRY(warp_forward(p, x, p->b_m, s));
   if (p->C > 0) {
-    for (int j = 0; j < p->P; ++j) {
-      nrsense_c64* mj = p->b_m + (long long)j * p->geo.nvox;
-      if (p->M[j] == 0) {
-        if (cudaMemsetAsync(mj, 0, size_t(p->geo.nvox) * sizeof(nrsense_c64), s) != cudaSuccess)
-          return NRSENSE_ERR_CUDA;
-        continue;
-      }
-      nrsense_c64* yj = p->b_y + p->off[j] * p->C;
-      NRS_TRY(sense_phase_forward(p, j, mj, yj, s));
-      NRS_TRY(sense_phase_adjoint(p, j, yj, mj, s));
+    for (int j0 = 0; j0 < p->P; j0 += p->phase_chunk) {
+      const int j1 = std::min(p->P, j0 + p->phase_chunk);
+      nrsense_c64* mj = p->b_m + (long long)j0 * p->geo.nvox;
+      NRS_TRY(sense_chunk_forward(p, j0, j1, mj, p->b_y, 0, s));
+      NRS_TRY(sense_chunk_adjoint(p, j0, j1, p->b_y, 0, mj, s));
     }
   }
   NRS_TRY(warp_adjoint(p, p->b_m, out, s));

@@ -56,6 +56,33 @@ struct SpreadItem {
 // bins[b] = first entry with r0 + W - 1 >= b, b = 0 .. W + T - 1.
 constexpr int kMaxBins = kMaxWidth + 16;
 
+// Up to kMaxChunkPhases motion states are processed by one launch.  The
+// per-phase point data stay in their own arrays; a launch receives this table
+// by value and finds the phase of a CTA from the item prefix sums.
+constexpr int kMaxChunkPhases = 16;
+struct SpreadItem;
+struct ReduceItem;
+struct PhaseTable {
+  const float4* qs[kMaxChunkPhases];
+  const int32_t* perm[kMaxChunkPhases];
+  const int2* list[kMaxChunkPhases];
+  const int32_t* bins[kMaxChunkPhases];
+  const SpreadItem* items[kMaxChunkPhases];
+  const ReduceItem* reduces[kMaxChunkPhases];
+  long long row0[kMaxChunkPhases];    // first value/output row of the phase
+  int item0[kMaxChunkPhases + 1];     // prefix sums of the launch's items per phase
+  int red0[kMaxChunkPhases + 1];      // prefix sums of reduce items per phase
+  int slot0[kMaxChunkPhases];         // first scratch slot of the phase
+  int nphase;
+};
+
+// Phase slot of work item `i` of a launch (linear search; nphase is small).
+__device__ __forceinline__ int phase_of(const int* prefix, int nphase, int i) {
+  int jj = 0;
+  while (jj + 1 < nphase && i >= prefix[jj + 1]) ++jj;
+  return jj;
+}
+
 // A split tile: partial tiles in scratch slots [first, first + count).
 struct ReduceItem {
   int32_t tile;

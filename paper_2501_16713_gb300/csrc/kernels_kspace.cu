@@ -35,20 +35,24 @@ __device__ __forceinline__ VoxelPos voxel_pos(const Geo& g, const float* __restr
 }
 
 // K5: v_{j,c}[n'] = S_c[n] m_j[n] / C3(n'/G) written into the centred N^3 block
-// of the zero-padded coil grids (steps S, 1/c* and Z).  Thread = (coil, voxel).
-__global__ void coil_fanout_pad_kernel(Geo g, int C, const float* __restrict__ dtab,
+// of the zero-padded coil grids (steps S, 1/c* and Z), for the nph phases of
+// a chunk at once.  Thread = (phase, coil, voxel); grid slot of (phase jj,
+// coil c) is jj * C + c.
+__global__ void coil_fanout_pad_kernel(Geo g, int C, int nph, const float* __restrict__ dtab,
                                        const float2* __restrict__ smaps,  // [C][nvox]
-                                       const float2* __restrict__ m,
-                                       float2* __restrict__ xpad) {         // [C][G^3]
+                                       const float2* __restrict__ m,      // [nph][nvox]
+                                       float2* __restrict__ xpad) {       // [nph*C][G^3]
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= g.nvox * C) return;
-  const int c = int(t / g.nvox);
-  const long long idx = t - (long long)c * g.nvox;
+  if (t >= g.nvox * C * nph) return;
+  const long long sc = t / g.nvox;  // jj * C + c
+  const int c = int(sc % C);
+  const long long jj = sc / C;
+  const long long idx = t - sc * g.nvox;
   const VoxelPos vp = voxel_pos(g, dtab, idx);
-  const float2 mv = __ldg(m + idx);
-  const float2 sv = __ldg(smaps + t);
+  const float2 mv = __ldg(m + jj * g.nvox + idx);
+  const float2 sv = __ldg(smaps + (long long)c * g.nvox + idx);
   const float w = vp.deapod;
-  xpad[(long long)c * g.ngrid + vp.grid] =
+  xpad[sc * g.ngrid + vp.grid] =
       make_float2((sv.x * mv.x - sv.y * mv.y) * w, (sv.x * mv.y + sv.y * mv.x) * w);
 }
 
@@ -75,15 +79,19 @@ __global__ void image_to_padded_kernel(Geo g, int C, const float* __restrict__ d
 // sums are reduced by shuffles at the end.
 template <int W, int CC>
 __global__ void __launch_bounds__(256) interp_tile_kernel(
-    Geo g, KernelCoefs kc, int C, TilePlan tp, const SpreadItem* __restrict__ items,
-    const float4* __restrict__ qs, const int32_t* __restrict__ perm,
-    const float2* __restrict__ grid, float2* __restrict__ y) {
+    Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ grids,
+    float2* __restrict__ y) {
   constexpr int T = 8, H = T + W - 1, H3 = H * H * H;
   constexpr int NQ = CC / 2, LPS = W * NQ, SPW = 32 / LPS;  // lanes/sample, samples/warp
   extern __shared__ float4 smem_raw[];
   float2* halo = reinterpret_cast<float2*>(smem_raw);  // [H][H][H][CC]
   __shared__ float s_coef[W][kNumCoef];
-  const SpreadItem it = items[blockIdx.x];
+  const int jj = phase_of(pt.item0, pt.nphase, blockIdx.x);
+  const SpreadItem it = pt.items[jj][blockIdx.x - pt.item0[jj]];
+  const float4* __restrict__ qs = pt.qs[jj];
+  const int32_t* __restrict__ perm = pt.perm[jj];
+  const float2* __restrict__ grid = grids + (long long)jj * C * g.ngrid;
+  const long long row0 = pt.row0[jj];
   const int coil0 = blockIdx.y * CC;
   const int tz = it.tile / (tp.nt1 * tp.nt2);
   const int rem = it.tile - tz * (tp.nt1 * tp.nt2);
@@ -192,7 +200,7 @@ __global__ void __launch_bounds__(256) interp_tile_kernel(
     }
     if (live && txl == 0) {
       const int c0 = coil0 + 2 * q;
-      float2* out = y + (long long)__ldg(perm + s) * C + c0;
+      float2* out = y + (row0 + __ldg(perm + s)) * C + c0;
       if ((C & 1) == 0 && c0 + 1 < C) {
         reinterpret_cast<float4*>(out)[0] = acc;
       } else {
@@ -209,22 +217,25 @@ constexpr size_t interp_smem() {
 }
 
 // K8: w_j[n] = sum_c conj(S_c[n]) Xt_c[n' mod G] / C3(n'/G) (steps Z^H, 1/c of
-// k-space gridding, then S^H).  Thread = voxel.
-__global__ void crop_coilsum_kernel(Geo g, int C, const float* __restrict__ dtab,
+// k-space gridding, then S^H), for the nph phases of a chunk.  Thread = (phase, voxel).
+__global__ void crop_coilsum_kernel(Geo g, int C, int nph, const float* __restrict__ dtab,
                                     const float2* __restrict__ smaps,  // [C][nvox]
-                                    const float2* __restrict__ xg,     // [C][G^3]
-                                    float2* __restrict__ w) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= g.nvox) return;
+                                    const float2* __restrict__ xg,     // [nph*C][G^3]
+                                    float2* __restrict__ w) {          // [nph][nvox]
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= g.nvox * nph) return;
+  const long long jj = t / g.nvox;
+  const long long idx = t - jj * g.nvox;
   const VoxelPos vp = voxel_pos(g, dtab, idx);
+  const float2* xs = xg + jj * C * g.ngrid + vp.grid;
   float ar = 0.f, ai = 0.f;
   for (int c = 0; c < C; ++c) {
     const float2 s = __ldg(smaps + (long long)c * g.nvox + idx);
-    const float2 v = __ldg(xg + (long long)c * g.ngrid + vp.grid);
+    const float2 v = __ldg(xs + (long long)c * g.ngrid);
     ar = fmaf(s.x, v.x, fmaf(s.y, v.y, ar));
     ai = fmaf(s.x, v.y, fmaf(-s.y, v.x, ai));
   }
-  w[idx] = make_float2(ar * vp.deapod, ai * vp.deapod);
+  w[t] = make_float2(ar * vp.deapod, ai * vp.deapod);
 }
 
 // Stage variant of K8 without S^H: padded grids -> coil images (C, N^3).
@@ -245,11 +256,12 @@ inline unsigned blocks_for(long long n, int threads) {
 
 }  // namespace
 
-int launch_coil_fanout_pad(const Geo& g, int C, const float* deapod, const nrsense_c64* smaps,
-                           const nrsense_c64* m, nrsense_c64* xpad, cudaStream_t s) {
-  coil_fanout_pad_kernel<<<blocks_for(g.nvox * C, 256), 256, 0, s>>>(
-      g, C, deapod, reinterpret_cast<const float2*>(smaps), reinterpret_cast<const float2*>(m),
-      reinterpret_cast<float2*>(xpad));
+int launch_coil_fanout_pad(const Geo& g, int C, int nph, const float* deapod,
+                           const nrsense_c64* smaps, const nrsense_c64* m, nrsense_c64* xpad,
+                           cudaStream_t s) {
+  coil_fanout_pad_kernel<<<blocks_for(g.nvox * C * nph, 256), 256, 0, s>>>(
+      g, C, nph, deapod, reinterpret_cast<const float2*>(smaps),
+      reinterpret_cast<const float2*>(m), reinterpret_cast<float2*>(xpad));
   return 1;
 }
 
@@ -275,32 +287,32 @@ cudaError_t configure_kernels() {
   return e;
 }
 
-int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, const PointSet& ps,
-                         const nrsense_c64* grid, nrsense_c64* y, cudaStream_t s) {
-  if (ps.npts == 0 || ps.n_iitems == 0) return 0;
-  const auto* gp = reinterpret_cast<const float2*>(grid);
+int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
+                         const PhaseTable& pt, const nrsense_c64* grids, nrsense_c64* y,
+                         cudaStream_t s) {
+  const int nitems = pt.item0[pt.nphase];
+  if (nitems == 0) return 0;
+  const auto* gp = reinterpret_cast<const float2*>(grids);
   auto* yp = reinterpret_cast<float2*>(y);
   if (W == 4 && C > 4) {
-    const dim3 gd(ps.n_iitems, (C + 7) / 8);
-    interp_tile_kernel<4, 8><<<gd, 256, interp_smem<4, 8>(), s>>>(g, kc, C, ps.tp, ps.iitems,
-                                                                   ps.qs, ps.perm, gp, yp);
+    const dim3 gd(nitems, (C + 7) / 8);
+    interp_tile_kernel<4, 8><<<gd, 256, interp_smem<4, 8>(), s>>>(g, kc, C, tp, pt, gp, yp);
   } else if (W == 4) {
-    const dim3 gd(ps.n_iitems, 1);
-    interp_tile_kernel<4, 4><<<gd, 256, interp_smem<4, 4>(), s>>>(g, kc, C, ps.tp, ps.iitems,
-                                                                   ps.qs, ps.perm, gp, yp);
+    interp_tile_kernel<4, 4><<<dim3(nitems, 1), 256, interp_smem<4, 4>(), s>>>(g, kc, C, tp, pt,
+                                                                               gp, yp);
   } else {
-    const dim3 gd(ps.n_iitems, (C + 3) / 4);
-    interp_tile_kernel<6, 4><<<gd, 256, interp_smem<6, 4>(), s>>>(g, kc, C, ps.tp, ps.iitems,
-                                                                   ps.qs, ps.perm, gp, yp);
+    const dim3 gd(nitems, (C + 3) / 4);
+    interp_tile_kernel<6, 4><<<gd, 256, interp_smem<6, 4>(), s>>>(g, kc, C, tp, pt, gp, yp);
   }
   return 1;
 }
 
-int launch_crop_coilsum(const Geo& g, int C, const float* deapod, const nrsense_c64* smaps,
-                        const nrsense_c64* xg, nrsense_c64* w, cudaStream_t s) {
-  crop_coilsum_kernel<<<blocks_for(g.nvox, 256), 256, 0, s>>>(
-      g, C, deapod, reinterpret_cast<const float2*>(smaps), reinterpret_cast<const float2*>(xg),
-      reinterpret_cast<float2*>(w));
+int launch_crop_coilsum(const Geo& g, int C, int nph, const float* deapod,
+                        const nrsense_c64* smaps, const nrsense_c64* xg, nrsense_c64* w,
+                        cudaStream_t s) {
+  crop_coilsum_kernel<<<blocks_for(g.nvox * nph, 256), 256, 0, s>>>(
+      g, C, nph, deapod, reinterpret_cast<const float2*>(smaps),
+      reinterpret_cast<const float2*>(xg), reinterpret_cast<float2*>(w));
   return 1;
 }
 

@@ -46,8 +46,9 @@ template <int W, int T, int CC, int R>
 __device__ __forceinline__ void stage_round(const Geo& g, const KernelCoefs& kc, int C, int coil0,
                                             const TileOrigin& to, const int2* __restrict__ lst,
                                             int cnt, const float4* __restrict__ qs,
-                                            const float2* __restrict__ vals, float (*s_w)[3][W],
-                                            int (*s_r)[3], float2 (*s_val)[CC], int tid) {
+                                            const float2* __restrict__ vals, long long row0,
+                                            float (*s_w)[3][W], int (*s_r)[3], float2 (*s_val)[CC],
+                                            int tid) {
   for (int i = tid; i < cnt * 3; i += kThreads) {
     const int p = i / 3, a = i - 3 * p;
     const int si = __ldg(&lst[p].x);
@@ -66,9 +67,8 @@ __device__ __forceinline__ void stage_round(const Geo& g, const KernelCoefs& kc,
   }
   for (int i = tid; i < cnt * CC; i += kThreads) {
     const int p = i / CC, c = i - p * CC;
-    const int row = __ldg(&lst[p].y);
-    s_val[p][c] = (coil0 + c < C) ? __ldg(vals + (long long)row * C + coil0 + c)
-                                  : make_float2(0.f, 0.f);
+    const long long row = row0 + __ldg(&lst[p].y);
+    s_val[p][c] = (coil0 + c < C) ? __ldg(vals + row * C + coil0 + c) : make_float2(0.f, 0.f);
   }
 }
 
@@ -87,11 +87,11 @@ __device__ __forceinline__ void bin_round(int (*s_r)[3], int* s_bin, int cnt, in
 
 template <int T, int CC>
 __device__ __forceinline__ void write_tile(const Geo& g, int C, int coil0, const TileOrigin& to,
-                                          const SpreadItem& it, const float2* acc,
+                                          int slot, const float2* acc,
                                           float2* __restrict__ grid, float2* __restrict__ scratch,
                                           int tid) {
   constexpr int kPts = T * T * T;
-  if (it.slot < 0) {
+  if (slot < 0) {
     // coil fastest across lanes: contiguous shared reads, full global sectors
     for (int i = tid; i < kPts * CC; i += kThreads) {
       const int c = i % CC;
@@ -103,9 +103,25 @@ __device__ __forceinline__ void write_tile(const Geo& g, int C, int coil0, const
       }
     }
   } else {
-    float2* dst = scratch + ((long long)it.slot * gridDim.y + blockIdx.y) * (kPts * CC);
+    float2* dst = scratch + ((long long)slot * gridDim.y + blockIdx.y) * (kPts * CC);
     for (int i = tid; i < kPts * CC; i += kThreads) dst[i] = acc[i];
   }
+}
+
+// Resolve a launch's work item through the phase table.
+struct ItemRef {
+  SpreadItem it;
+  int jj, local;
+};
+__device__ __forceinline__ ItemRef item_ref(const PhaseTable& pt) {
+  ItemRef r;
+  r.jj = phase_of(pt.item0, pt.nphase, blockIdx.x);
+  r.local = blockIdx.x - pt.item0[r.jj];
+  r.it = pt.items[r.jj][r.local];
+  return r;
+}
+__device__ __forceinline__ int scratch_slot(const PhaseTable& pt, const ItemRef& r) {
+  return r.it.slot < 0 ? -1 : pt.slot0[r.jj] + r.it.slot;
 }
 
 // ---------------------------------------------------------------------------
@@ -125,17 +141,20 @@ struct CoilStage {
 
 template <int CC>
 __global__ void __launch_bounds__(kThreads) spread_coils_kernel(
-    Geo g, KernelCoefs kc, int C, TilePlan tp, const SpreadItem* __restrict__ items,
-    const int32_t* __restrict__ bins, const int2* __restrict__ list,
-    const float4* __restrict__ qs, const float2* __restrict__ vals, float2* __restrict__ grid,
-    float2* __restrict__ scratch) {
+    Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
+    float2* __restrict__ grids, float2* __restrict__ scratch) {
   constexpr int W = 4, T = 8, B = 32, NB = W + T + 1;
   static_assert(CC == 2 || CC == 4 || CC == 8, "coil chunk");
   extern __shared__ float4 smem_raw[];
   float2* acc = reinterpret_cast<float2*>(smem_raw);  // [T][T][T][CC]
   __shared__ __align__(16) CoilStage<CC> stg[kThreads / 32][B];
 
-  const SpreadItem it = items[blockIdx.x];
+  const ItemRef ir = item_ref(pt);
+  const SpreadItem it = ir.it;
+  const int2* __restrict__ list = pt.list[ir.jj];
+  const float4* __restrict__ qs = pt.qs[ir.jj];
+  const long long row0 = pt.row0[ir.jj];
+  float2* __restrict__ grid = grids + (long long)ir.jj * C * g.ngrid;
   const int coil0 = blockIdx.y * CC;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TileOrigin to = tile_origin(g, tp, it.tile);
@@ -144,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) spread_coils_kernel(
 
   const int lz = warp;
   if (lz < to.e0) {
-    const int32_t* ib = bins + (long long)blockIdx.x * NB;
+    const int32_t* ib = pt.bins[ir.jj] + (long long)ir.local * NB;
     const int beg = it.begin + __ldg(ib + min(lz, NB - 1));
     const int end = it.begin + __ldg(ib + min(lz + W, NB - 1));
     // lane = (coil pair q, tap x, row half): a quarter-warp covers 128
@@ -182,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) spread_coils_kernel(
         }
         d.r1 = r1;
         d.r2 = r2;
-        const float2* src = vals + (long long)e.y * C + coil0;
+        const float2* src = vals + (row0 + e.y) * C + coil0;
 #pragma unroll
         for (int c = 0; c < CC; ++c)
           d.val[c] = (coil0 + c < C) ? __ldg(src + c) : make_float2(0.f, 0.f);
@@ -213,7 +232,7 @@ __global__ void __launch_bounds__(kThreads) spread_coils_kernel(
     }
   }
   __syncthreads();
-  write_tile<T, CC>(g, C, coil0, to, it, acc, grid, scratch, tid);
+  write_tile<T, CC>(g, C, coil0, to, scratch_slot(pt, ir), acc, grid, scratch, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -228,17 +247,20 @@ struct SingleStage {
 };
 
 __global__ void __launch_bounds__(kThreads) spread_single_kernel(
-    Geo g, KernelCoefs kc, TilePlan tp, const SpreadItem* __restrict__ items,
-    const int32_t* __restrict__ bins, const int2* __restrict__ list,
-    const float4* __restrict__ qs, const float2* __restrict__ vals, float2* __restrict__ grid,
-    float2* __restrict__ scratch) {
+    Geo g, KernelCoefs kc, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
+    float2* __restrict__ grids, float2* __restrict__ scratch) {
   constexpr int W = 4, T = 16, B = 32, NB = W + T + 1;
   constexpr int RS = T + 4;  // padded row stride: 4 tap rows hit disjoint banks
   extern __shared__ float4 smem_raw[];
   float2* acc = reinterpret_cast<float2*>(smem_raw);  // [T][T][RS]
   __shared__ SingleStage stg[kThreads / 32][B];
 
-  const SpreadItem it = items[blockIdx.x];
+  const ItemRef ir = item_ref(pt);
+  const SpreadItem it = ir.it;
+  const int2* __restrict__ list = pt.list[ir.jj];
+  const float4* __restrict__ qs = pt.qs[ir.jj];
+  const long long row0 = pt.row0[ir.jj];
+  float2* __restrict__ grid = grids + (long long)ir.jj * g.ngrid;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TileOrigin to = tile_origin(g, tp, it.tile);
   for (int i = tid; i < T * T * RS; i += kThreads) acc[i] = make_float2(0.f, 0.f);
@@ -246,7 +268,7 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
 
   const int z0 = 2 * warp;
   if (z0 < to.e0) {
-    const int32_t* ib = bins + (long long)blockIdx.x * NB;
+    const int32_t* ib = pt.bins[ir.jj] + (long long)ir.local * NB;
     const int beg = it.begin + __ldg(ib + min(z0, NB - 1));
     const int end = it.begin + __ldg(ib + min(z0 + W + 1, NB - 1));
     const int tx = lane & 3, ty = (lane >> 2) & 3, hz = lane >> 4;
@@ -282,7 +304,7 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
         }
         d.r1 = r1;
         d.r2 = r2;
-        d.val = __ldg(vals + e.y);
+        d.val = __ldg(vals + row0 + e.y);
       }
       __syncwarp();
       for (int p = 0; p < n; ++p) {
@@ -303,7 +325,8 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
   __syncthreads();
   // write the tile (or partial tile), dropping the row padding
   constexpr int kPts = T * T * T;
-  if (it.slot < 0) {
+  const int slot = scratch_slot(pt, ir);
+  if (slot < 0) {
     for (int i = tid; i < kPts; i += kThreads) {
       const int lx = i % T, ly = (i / T) % T, lz = i / (T * T);
       if (lz < to.e0 && ly < to.e1 && lx < to.e2) {
@@ -312,7 +335,7 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
       }
     }
   } else {
-    float2* dst = scratch + (long long)it.slot * kPts;
+    float2* dst = scratch + (long long)slot * kPts;
     for (int i = tid; i < kPts; i += kThreads) {
       const int lx = i % T, ly = (i / T) % T, lz = i / (T * T);
       dst[i] = acc[(lz * T + ly) * RS + lx];
@@ -325,9 +348,8 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
 // lanes over (coil, tap x, tap y) combinations.
 template <int W, int CC>
 __global__ void __launch_bounds__(kThreads) spread_generic_kernel(
-    Geo g, KernelCoefs kc, int C, TilePlan tp, const SpreadItem* __restrict__ items,
-    const int2* __restrict__ list, const float4* __restrict__ qs,
-    const float2* __restrict__ vals, float2* __restrict__ grid, float2* __restrict__ scratch) {
+    Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
+    float2* __restrict__ grids, float2* __restrict__ scratch) {
   constexpr int T = 8, R = 64;
   extern __shared__ float4 smem_raw[];
   float2* acc = reinterpret_cast<float2*>(smem_raw);  // [T][T][T][CC]
@@ -336,7 +358,11 @@ __global__ void __launch_bounds__(kThreads) spread_generic_kernel(
   __shared__ float2 s_val[R][CC];
   __shared__ int s_bin[W + T];
 
-  const SpreadItem it = items[blockIdx.x];
+  const ItemRef ir = item_ref(pt);
+  const SpreadItem it = ir.it;
+  const int2* __restrict__ list = pt.list[ir.jj];
+  const float4* __restrict__ qs = pt.qs[ir.jj];
+  float2* __restrict__ grid = grids + (long long)ir.jj * C * g.ngrid;
   const int coil0 = blockIdx.y * CC;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TileOrigin to = tile_origin(g, tp, it.tile);
@@ -346,8 +372,8 @@ __global__ void __launch_bounds__(kThreads) spread_generic_kernel(
   for (int base = 0; base < n; base += R) {
     const int cnt = min(R, n - base);
     __syncthreads();
-    stage_round<W, T, CC, R>(g, kc, C, coil0, to, list + it.begin + base, cnt, qs, vals, s_w, s_r,
-                             s_val, tid);
+    stage_round<W, T, CC, R>(g, kc, C, coil0, to, list + it.begin + base, cnt, qs, vals,
+                             pt.row0[ir.jj], s_w, s_r, s_val, tid);
     __syncthreads();
     bin_round<W, T>(s_r, s_bin, cnt, tid);
     __syncthreads();
@@ -382,14 +408,17 @@ __global__ void __launch_bounds__(kThreads) spread_generic_kernel(
     }
   }
   __syncthreads();
-  write_tile<T, CC>(g, C, coil0, to, it, acc, grid, scratch, tid);
+  write_tile<T, CC>(g, C, coil0, to, scratch_slot(pt, ir), acc, grid, scratch, tid);
 }
 
 // Sum the partial tiles of split tiles in slot order (deterministic).
 template <int T, int CC>
-__global__ void reduce_kernel(Geo g, int C, TilePlan tp, const ReduceItem* __restrict__ red,
-                              const float2* __restrict__ scratch, float2* __restrict__ grid) {
-  const ReduceItem r = red[blockIdx.x];
+__global__ void reduce_kernel(Geo g, int C, TilePlan tp, PhaseTable pt,
+                              const float2* __restrict__ scratch, float2* __restrict__ grids) {
+  const int jj = phase_of(pt.red0, pt.nphase, blockIdx.x);
+  ReduceItem r = pt.reduces[jj][blockIdx.x - pt.red0[jj]];
+  r.first += pt.slot0[jj];
+  float2* __restrict__ grid = grids + (long long)jj * C * g.ngrid;
   const int coil0 = blockIdx.y * CC;
   const TileOrigin to = tile_origin(g, tp, r.tile);
   constexpr int kPts = T * T * T;
@@ -413,32 +442,34 @@ __global__ void reduce_kernel(Geo g, int C, TilePlan tp, const ReduceItem* __res
 }
 
 template <int T, int CC>
-int launch_reduce(const Geo& g, int C, const PointSet& ps, int chunks, float2* grid,
-                  const float2* scratch, cudaStream_t s) {
-  if (ps.n_reduces == 0) return 0;
-  reduce_kernel<T, CC><<<dim3(ps.n_reduces, chunks), 256, 0, s>>>(g, C, ps.tp, ps.reduces,
-                                                                  scratch, grid);
+int launch_reduce(const Geo& g, int C, const TilePlan& tp, const PhaseTable& pt, int chunks,
+                  float2* grids, const float2* scratch, cudaStream_t s) {
+  const int nred = pt.red0[pt.nphase];
+  if (nred == 0) return 0;
+  reduce_kernel<T, CC><<<dim3(nred, chunks), 256, 0, s>>>(g, C, tp, pt, scratch, grids);
   return 1;
 }
 
 template <int CC>
-int dispatch_coils(const Geo& g, const KernelCoefs& kc, int C, const PointSet& ps,
-                   const float2* vals, float2* grid, float2* scratch, cudaStream_t s) {
+int dispatch_coils(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& tp,
+                   const PhaseTable& pt, const float2* vals, float2* grids, float2* scratch,
+                   cudaStream_t s) {
   const int chunks = (C + CC - 1) / CC;
   const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2);
-  spread_coils_kernel<CC><<<dim3(ps.n_items, chunks), kThreads, smem, s>>>(
-      g, kc, C, ps.tp, ps.items, ps.bins, ps.list, ps.qs, vals, grid, scratch);
-  return 1 + launch_reduce<8, CC>(g, C, ps, chunks, grid, scratch, s);
+  spread_coils_kernel<CC><<<dim3(pt.item0[pt.nphase], chunks), kThreads, smem, s>>>(
+      g, kc, C, tp, pt, vals, grids, scratch);
+  return 1 + launch_reduce<8, CC>(g, C, tp, pt, chunks, grids, scratch, s);
 }
 
 template <int W, int CC>
-int dispatch_generic(const Geo& g, const KernelCoefs& kc, int C, const PointSet& ps,
-                     const float2* vals, float2* grid, float2* scratch, cudaStream_t s) {
+int dispatch_generic(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& tp,
+                     const PhaseTable& pt, const float2* vals, float2* grids, float2* scratch,
+                     cudaStream_t s) {
   const int chunks = (C + CC - 1) / CC;
   const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2);
-  spread_generic_kernel<W, CC><<<dim3(ps.n_items, chunks), kThreads, smem, s>>>(
-      g, kc, C, ps.tp, ps.items, ps.list, ps.qs, vals, grid, scratch);
-  return 1 + launch_reduce<8, CC>(g, C, ps, chunks, grid, scratch, s);
+  spread_generic_kernel<W, CC><<<dim3(pt.item0[pt.nphase], chunks), kThreads, smem, s>>>(
+      g, kc, C, tp, pt, vals, grids, scratch);
+  return 1 + launch_reduce<8, CC>(g, C, tp, pt, chunks, grids, scratch, s);
 }
 
 }  // namespace
@@ -465,30 +496,30 @@ int spread_tile_edge(int W, int C, int gmin) {
 
 int spread_coil_chunk(int C) { return C == 1 ? 1 : (C <= 2 ? 2 : (C <= 4 ? 4 : 8)); }
 
-int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const PointSet& ps,
-                  const nrsense_c64* vals, nrsense_c64* grid, nrsense_c64* scratch,
-                  int32_t* status, cudaStream_t s) {
+int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
+                  const PhaseTable& pt, const nrsense_c64* vals, nrsense_c64* grids,
+                  nrsense_c64* scratch, int32_t* status, cudaStream_t s) {
   (void)status;
-  if (ps.n_items == 0) return 0;
+  if (pt.item0[pt.nphase] == 0) return 0;
   const auto* v = reinterpret_cast<const float2*>(vals);
-  auto* gr = reinterpret_cast<float2*>(grid);
+  auto* gr = reinterpret_cast<float2*>(grids);
   auto* sc = reinterpret_cast<float2*>(scratch);
   if (W == 4) {
-    if (C == 1 && ps.tp.t0 == 16) {
+    if (C == 1 && tp.t0 == 16) {
       const size_t smem = size_t(16 * 16 * 20) * sizeof(float2);  // 40 KB, padded rows
-      spread_single_kernel<<<dim3(ps.n_items, 1), kThreads, smem, s>>>(
-          g, kc, ps.tp, ps.items, ps.bins, ps.list, ps.qs, v, gr, sc);
-      return 1 + launch_reduce<16, 1>(g, 1, ps, 1, gr, sc, s);
+      spread_single_kernel<<<dim3(pt.item0[pt.nphase], 1), kThreads, smem, s>>>(g, kc, tp, pt, v,
+                                                                                 gr, sc);
+      return 1 + launch_reduce<16, 1>(g, 1, tp, pt, 1, gr, sc, s);
     }
-    if (C == 1) return dispatch_generic<4, 1>(g, kc, C, ps, v, gr, sc, s);
-    if (C <= 2) return dispatch_coils<2>(g, kc, C, ps, v, gr, sc, s);
-    if (C <= 4) return dispatch_coils<4>(g, kc, C, ps, v, gr, sc, s);
-    return dispatch_coils<8>(g, kc, C, ps, v, gr, sc, s);
+    if (C == 1) return dispatch_generic<4, 1>(g, kc, C, tp, pt, v, gr, sc, s);
+    if (C <= 2) return dispatch_coils<2>(g, kc, C, tp, pt, v, gr, sc, s);
+    if (C <= 4) return dispatch_coils<4>(g, kc, C, tp, pt, v, gr, sc, s);
+    return dispatch_coils<8>(g, kc, C, tp, pt, v, gr, sc, s);
   }
-  if (C == 1) return dispatch_generic<6, 1>(g, kc, C, ps, v, gr, sc, s);
-  if (C <= 2) return dispatch_generic<6, 2>(g, kc, C, ps, v, gr, sc, s);
-  if (C <= 4) return dispatch_generic<6, 4>(g, kc, C, ps, v, gr, sc, s);
-  return dispatch_generic<6, 8>(g, kc, C, ps, v, gr, sc, s);
+  if (C == 1) return dispatch_generic<6, 1>(g, kc, C, tp, pt, v, gr, sc, s);
+  if (C <= 2) return dispatch_generic<6, 2>(g, kc, C, tp, pt, v, gr, sc, s);
+  if (C <= 4) return dispatch_generic<6, 4>(g, kc, C, tp, pt, v, gr, sc, s);
+  return dispatch_generic<6, 8>(g, kc, C, tp, pt, v, gr, sc, s);
 }
 
 }  // namespace nrs

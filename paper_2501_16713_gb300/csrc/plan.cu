@@ -149,7 +149,6 @@ nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, Po
   const int W = p->W;
   const long long npts = (long long)pts.size();
   ps->npts = npts;
-  if (npts == 0) return NRSENSE_OK;
   if (npts >= (1ll << 31)) return NRSENSE_ERR_ARG;
 
   // primary key: tile of the first tap; secondary: cell inside the tile
@@ -325,8 +324,8 @@ nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, Po
   for (long long i = 0; i < list_len; ++i) list2[i] = make_int2(list[i], perm[list[i]]);
   std::vector<int32_t>().swap(list);
 
-  NRS_TRY(dev_alloc_n(p, &ps->qs, npts));
-  NRS_TRY(dev_alloc_n(p, &ps->perm, npts));
+  NRS_TRY(dev_alloc_n(p, &ps->qs, std::max<long long>(npts, 1)));
+  NRS_TRY(dev_alloc_n(p, &ps->perm, std::max<long long>(npts, 1)));
   NRS_TRY(dev_alloc_n(p, &ps->list, std::max<long long>(list_len, 1)));
   NRS_TRY(dev_alloc_n(p, &ps->items, std::max<long long>((long long)items.size(), 1)));
   NRS_TRY(dev_alloc_n(p, &ps->bins, std::max<long long>((long long)bins.size(), 1)));
@@ -384,6 +383,8 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   const TilePlan ktiles = make_tileplan(g, kSpreadTile);
   const TilePlan itiles =
       make_tileplan(g, spread_tile_edge(p->W, 1, std::min(g.g0, std::min(g.g1, g.g2))));
+  p->ktiles = ktiles;
+  p->itiles = itiles;
 
   // deapodization: 1/C(m/G) for m in [-N/2, N/2), per axis
   {
@@ -494,11 +495,32 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     p->have_fft_g = true;
   }
   if (p->C > 0) {
+    // phases per launch: as many as half of the free memory allows (three
+    // coil-grid buffers per phase plus about one for cuFFT's work area)
+    const long long per_phase = 4LL * p->C * g.ngrid * (long long)sizeof(nrsense_c64);
+    int pc = d.phase_chunk;
+    if (pc <= 0) {
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return NRSENSE_ERR_CUDA;
+      pc = int(std::max<long long>(1, (long long)(free_b / 2) / per_phase));
+    }
+    pc = std::max(1, std::min(pc, std::min(p->P, kMaxChunkPhases)));
+    p->phase_chunk = pc;
+    // one cuFFT plan per batch size used: a full chunk, the last partial
+    // chunk, and a single phase (stage calls)
+    std::vector<int> sizes = {pc, 1};
+    if (p->P % pc) sizes.push_back(p->P % pc);
     int n[3] = {g.g0, g.g1, g.g2};
-    // coil-major batch: coil c's grid starts at c * G^3
-    NRS_TRY(cufft_check(cufftPlanMany(&p->fft_gc, 3, n, n, 1, int(g.ngrid), n, 1, int(g.ngrid),
-                                      CUFFT_C2C, p->C)));
-    p->have_fft_gc = true;
+    for (int nb : sizes) {
+      bool have = false;
+      for (auto& fp : p->fft_gc_plans) have |= (fp.first == nb);
+      if (have) continue;
+      cufftHandle h;
+      // coil-major batch: grid (phase jj, coil c) starts at (jj * C + c) * G^3
+      NRS_TRY(cufft_check(cufftPlanMany(&h, 3, n, n, 1, int(g.ngrid), n, 1, int(g.ngrid),
+                                        CUFFT_C2C, nb * p->C)));
+      p->fft_gc_plans.push_back({nb, h});
+    }
   }
 
   // work buffers
@@ -512,15 +534,16 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
       return NRSENSE_ERR_CUDA;
   }
   if (p->C > 0) {
-    NRS_TRY(dev_alloc_n(p, &p->b_xpad, g.ngrid * p->C));
-    NRS_TRY(dev_alloc_n(p, &p->b_xwork, g.ngrid * p->C));
-    NRS_TRY(dev_alloc_n(p, &p->b_xspread, g.ngrid * p->C));
+    const long long cg = g.ngrid * p->C * p->phase_chunk;
+    NRS_TRY(dev_alloc_n(p, &p->b_xpad, cg));
+    NRS_TRY(dev_alloc_n(p, &p->b_xwork, cg));
+    NRS_TRY(dev_alloc_n(p, &p->b_xspread, cg));
     // empty tiles of the spread target are never written: zero them once
-    if (cudaMemsetAsync(p->b_xspread, 0, size_t(g.ngrid * p->C) * sizeof(nrsense_c64), s) !=
+    if (cudaMemsetAsync(p->b_xspread, 0, size_t(cg) * sizeof(nrsense_c64), s) !=
         cudaSuccess)
       return NRSENSE_ERR_CUDA;
     NRS_TRY(dev_alloc_n(p, &p->b_y, std::max<long long>(p->Mtot * p->C, 1)));
-    if (cudaMemsetAsync(p->b_xpad, 0, size_t(g.ngrid * p->C) * sizeof(nrsense_c64), s) !=
+    if (cudaMemsetAsync(p->b_xpad, 0, size_t(cg) * sizeof(nrsense_c64), s) !=
         cudaSuccess)
       return NRSENSE_ERR_CUDA;
   }
@@ -533,8 +556,11 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   if (p->C > 0) {
     const int cc = spread_coil_chunk(p->C);
     const int chunks = (p->C + cc - 1) / cc;
-    for (const auto& k : p->kpts)
-      need = std::max(need, (long long)k.n_slots * chunks * tile_pts(k) * cc);
+    for (int j0 = 0; j0 < p->P; j0 += p->phase_chunk) {
+      long long slots = 0;
+      for (int j = j0; j < std::min(p->P, j0 + p->phase_chunk); ++j) slots += p->kpts[j].n_slots;
+      need = std::max(need, slots * chunks * tile_pts(p->kpts[j0]) * cc);
+    }
   }
   p->scratch_elems = need;
   if (need > 0) NRS_TRY(dev_alloc_n(p, &p->b_scratch, need));
@@ -548,7 +574,8 @@ void release(nrsense_plan_s* p) {
   p->prof_events.clear();
   if (p->have_fft_n) cufftDestroy(p->fft_n);
   if (p->have_fft_g) cufftDestroy(p->fft_g);
-  if (p->have_fft_gc) cufftDestroy(p->fft_gc);
+  for (auto& fp : p->fft_gc_plans) cufftDestroy(fp.second);
+  p->fft_gc_plans.clear();
   for (void* a : p->allocations) cudaFree(a);
   p->allocations.clear();
 }
@@ -615,6 +642,7 @@ nrsense_status nrsense_plan_info(nrsense_plan_t p, nrsense_info* out) {
   out->spread_items = items;
   out->split_tiles = split;
   out->device_bytes = p->device_bytes;
+  out->phase_chunk = p->phase_chunk;
   return NRSENSE_OK;
 }
 

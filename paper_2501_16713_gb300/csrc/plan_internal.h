@@ -62,23 +62,27 @@ struct nrsense_plan_s {
   long long Mtot = 0;
   std::vector<nrs::PointSet> kpts;  // per phase
   nrs::PointSet ipts;               // displaced voxels of all phases
+  nrs::TilePlan ktiles{}, itiles{};  // k-space and image-space tiles
+  int phase_chunk = 1;              // phases per launch
 
   // work buffers
   nrsense_c64* b_xhat = nullptr;   // N^3
   nrsense_c64* b_upad = nullptr;   // G^3, zero outside the K_N block
   nrsense_c64* b_ugrid = nullptr;  // G^3
   nrsense_c64* b_m = nullptr;      // P * N^3
-  nrsense_c64* b_xpad = nullptr;   // C * G^3, zero outside the centred N^3 block
-  nrsense_c64* b_xwork = nullptr;  // C * G^3 (FFT outputs)
-  nrsense_c64* b_xspread = nullptr;  // C * G^3 spread target; empty tiles stay zero
+  // coil grids of one phase chunk, (phase_chunk * C) x G^3 each
+  nrsense_c64* b_xpad = nullptr;     // zero outside the centred N^3 blocks
+  nrsense_c64* b_xwork = nullptr;    // FFT outputs
+  nrsense_c64* b_xspread = nullptr;  // spread target; tiles no phase occupies stay zero
   nrsense_c64* b_y = nullptr;      // Mtot * C
   nrsense_c64* b_tmp = nullptr;    // N^3 (normal operator scratch)
   nrsense_c64* b_scratch = nullptr;  // partial tiles
   long long scratch_elems = 0;
   int32_t* d_status = nullptr;
 
-  cufftHandle fft_n = 0, fft_g = 0, fft_gc = 0;
-  bool have_fft_n = false, have_fft_g = false, have_fft_gc = false;
+  cufftHandle fft_n = 0, fft_g = 0;
+  bool have_fft_n = false, have_fft_g = false;
+  std::vector<std::pair<int, cufftHandle>> fft_gc_plans;  // (phases per batch, plan)
 
   long long device_bytes = 0;
   std::vector<void*> allocations;
@@ -131,27 +135,29 @@ int launch_sum_phases(const Geo& g, int P, const nrsense_c64* m, nrsense_c64* x,
                        cudaStream_t s);
 
 // k space
-int launch_coil_fanout_pad(const Geo& g, int C, const float* deapod,
-                            const nrsense_c64* smaps, const nrsense_c64* m,
-                            nrsense_c64* xpad, cudaStream_t s);
+int launch_coil_fanout_pad(const Geo& g, int C, int nph, const float* deapod,
+                           const nrsense_c64* smaps, const nrsense_c64* m, nrsense_c64* xpad,
+                           cudaStream_t s);
 int launch_image_to_padded(const Geo& g, int C, const float* deapod,
                             const nrsense_c64* v, nrsense_c64* xpad, cudaStream_t s);
-int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C,
-                          const PointSet& ps, const nrsense_c64* grid, nrsense_c64* y,
-                          cudaStream_t s);
+int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
+                         const PhaseTable& pt, const nrsense_c64* grids, nrsense_c64* y,
+                         cudaStream_t s);
 // one-time kernel attributes (large dynamic shared memory); plan time
 cudaError_t configure_kernels();
 cudaError_t configure_spread_kernels();
-int launch_crop_coilsum(const Geo& g, int C, const float* deapod,
-                         const nrsense_c64* smaps, const nrsense_c64* xg,
-                         nrsense_c64* w, cudaStream_t s);
+int launch_crop_coilsum(const Geo& g, int C, int nph, const float* deapod,
+                        const nrsense_c64* smaps, const nrsense_c64* xg, nrsense_c64* w,
+                        cudaStream_t s);
 int launch_crop_to_coils(const Geo& g, int C, const float* deapod,
                           const nrsense_c64* xg, nrsense_c64* v, cudaStream_t s);
 
 // spreading (both domains)
-int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const PointSet& ps,
-                  const nrsense_c64* vals, nrsense_c64* grid, nrsense_c64* scratch,
-                  int32_t* status, cudaStream_t s);
+// Spread the phases of `pt` (values at rows row0[jj] + perm of vals) into
+// consecutive grid slots (phase jj at grids + jj * C * G^3).
+int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
+                  const PhaseTable& pt, const nrsense_c64* vals, nrsense_c64* grids,
+                  nrsense_c64* scratch, int32_t* status, cudaStream_t s);
 // coils handled by one spreading CTA
 int spread_coil_chunk(int C);
 // free the CG workspace of a plan (solver.cu)

@@ -36,7 +36,8 @@ class Desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32 * 3), ("osf", ctypes.c_int32),
                 ("kb_width", ctypes.c_int32), ("kb_beta", ctypes.c_double),
                 ("n_phases", ctypes.c_int32), ("n_coils", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("phase_chunk", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -44,7 +45,8 @@ class Info(ctypes.Structure):
                 ("kernel_poly_err", ctypes.c_double), ("total_samples", ctypes.c_int64),
                 ("tile", ctypes.c_int32 * 3), ("n_tiles", ctypes.c_int64),
                 ("occupied_fraction", ctypes.c_double), ("spread_items", ctypes.c_int64),
-                ("split_tiles", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("split_tiles", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("phase_chunk", ctypes.c_int32)]
 
 
 _VP = ctypes.c_void_p
@@ -160,7 +162,7 @@ class Plan:
     """
 
     def __init__(self, shape, disp=None, coords=None, smaps=None, n_phases=None, osf=2,
-                 width=4, beta=0.0, identity_warp=False, stream=None):
+                 width=4, beta=0.0, identity_warp=False, stream=None, phase_chunk=0):
         import torch
         self.lib = load()
         self.shape = tuple(int(s) for s in shape)
@@ -180,6 +182,7 @@ class Plan:
         d.n_phases, d.n_coils = self.n_phases, self.n_coils
         d.precision = FP32
         d.flags = IDENTITY_WARP if identity_warp else 0
+        d.phase_chunk = int(phase_chunk)
         self.counts = [0] * self.n_phases
         cat = None
         if self.n_coils > 0:

@@ -66,9 +66,10 @@ def test_struct_layout_matches_header(tmp_path):
 int main(void) {{
   printf("%zu %zu %zu %zu %zu\\n", sizeof(nrsense_desc), offsetof(nrsense_desc, kb_beta),
          offsetof(nrsense_desc, n_phases), offsetof(nrsense_desc, flags), sizeof(nrsense_c64));
-  printf("%zu %zu %zu %zu %zu\\n", sizeof(nrsense_info), offsetof(nrsense_info, kb_beta),
+  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(nrsense_info), offsetof(nrsense_info, kb_beta),
          offsetof(nrsense_info, tile), offsetof(nrsense_info, n_tiles),
-         offsetof(nrsense_info, device_bytes));
+         offsetof(nrsense_info, device_bytes), offsetof(nrsense_info, phase_chunk));
+  printf("%zu\\n", offsetof(nrsense_desc, phase_chunk));
   return 0;
 }}
 """)
@@ -80,4 +81,5 @@ int main(void) {{
     D, I = nrsense.Desc, nrsense.Info
     assert d == [ctypes.sizeof(D), D.kb_beta.offset, D.n_phases.offset, D.flags.offset, 8]
     assert i == [ctypes.sizeof(I), I.kb_beta.offset, I.tile.offset, I.n_tiles.offset,
-                 I.device_bytes.offset]
+                 I.device_bytes.offset, I.phase_chunk.offset]
+    assert int(out[2]) == D.phase_chunk.offset
