@@ -1,0 +1,155 @@
+"""FP64 oracle of the learned preconditioner network (test infrastructure).
+
+The build target adds a learned preconditioner for the Tikhonov CG solve of
+the reconstruction problem: a small 3D convolutional network M that maps a
+residual r to a search direction z ~ E^{-1} r, used inside flexible CG.  The
+paper itself has no learned component; this module fixes the network's
+definition so the CUDA kernels can be checked against it.
+
+Definition (all arrays channel-first here, (C, D, H, W)):
+  s  = sqrt(mean |r|^2)                       (input scale, not trained)
+  u0 = [Re r, Im r] / s                       (2 channels)
+  h_l = relu(conv_l(h_{l-1}))  for l = 1..4   (16 channels each)
+  o  = conv_5(h_4)                            (2 channels)
+  z  = (u0 + o)  read back as a complex image (residual connection)
+conv_l is a 3x3x3 cross-correlation with zero padding and a bias:
+  conv(x)[o, d, h, w] = b[o] + sum_{c, tz, ty, tx} W[o, c, tz, ty, tx] x[c, d+tz-1, h+ty-1, w+tx-1].
+Flexible CG is invariant to the scale of M's output, so the training loss is
+scale invariant: L = 1 - Re<z, e> / (||z|| ||e||) for the target e = E^{-1} r.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+CHANNELS = (2, 16, 16, 16, 16, 2)
+
+
+def init_params(seed: int, channels=CHANNELS):
+    """He-style random initialisation (weights (Cout, Cin, 3, 3, 3), biases)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    params = []
+    for cin, cout in zip(channels[:-1], channels[1:]):
+        std = np.sqrt(2.0 / (27 * cin))
+        params.append((rng.standard_normal((cout, cin, 3, 3, 3)) * std,
+                       np.zeros(cout)))
+    # start close to the identity map: small last layer
+    w, b = params[-1]
+    params[-1] = (w * 0.1, b)
+    return params
+
+
+def conv3d(x, w, b):
+    """3x3x3 cross-correlation with zero padding; x (Cin, D, H, W)."""
+    cin, D, H, W = x.shape
+    xp = np.zeros((cin, D + 2, H + 2, W + 2))
+    xp[:, 1:-1, 1:-1, 1:-1] = x
+    out = np.zeros((w.shape[0], D, H, W)) + b[:, None, None, None]
+    for tz in range(3):
+        for ty in range(3):
+            for tx in range(3):
+                out += np.einsum("oc,cdhw->odhw", w[:, :, tz, ty, tx],
+                                 xp[:, tz:tz + D, ty:ty + H, tx:tx + W])
+    return out
+
+
+def conv3d_backward(x, w, dy):
+    """Gradients of sum(dy * conv3d(x, w, b)) w.r.t. x, w and b."""
+    cin, D, H, W = x.shape
+    xp = np.zeros((cin, D + 2, H + 2, W + 2))
+    xp[:, 1:-1, 1:-1, 1:-1] = x
+    dxp = np.zeros_like(xp)
+    dw = np.zeros_like(w)
+    for tz in range(3):
+        for ty in range(3):
+            for tx in range(3):
+                sl = (slice(None), slice(tz, tz + D), slice(ty, ty + H), slice(tx, tx + W))
+                dw[:, :, tz, ty, tx] = np.einsum("odhw,cdhw->oc", dy, xp[sl])
+                dxp[sl] += np.einsum("oc,odhw->cdhw", w[:, :, tz, ty, tx], dy)
+    db = dy.sum(axis=(1, 2, 3))
+    return dxp[:, 1:-1, 1:-1, 1:-1], dw, db
+
+
+def input_scale(r):
+    return float(np.sqrt(np.mean(np.abs(r) ** 2)))
+
+
+def forward(params, r):
+    """z = M(r) and the activations needed by backward."""
+    s = input_scale(r)
+    u0 = np.stack([r.real, r.imag]) / s
+    acts = [u0]
+    h = u0
+    for l, (w, b) in enumerate(params):
+        h = conv3d(h, w, b)
+        if l < len(params) - 1:
+            h = np.maximum(h, 0.0)
+        acts.append(h)
+    zc = u0 + acts[-1]
+    return zc[0] + 1j * zc[1], acts
+
+
+def loss(z, e):
+    """1 - Re<z, e> / (||z|| ||e||)."""
+    nz, ne = np.linalg.norm(z), np.linalg.norm(e)
+    return 1.0 - np.real(np.vdot(z, e)) / (nz * ne)
+
+
+def loss_grad_z(z, e):
+    """dL/dz as a complex array (derivative w.r.t. Re z + i d/d Im z)."""
+    nz, ne = np.linalg.norm(z), np.linalg.norm(e)
+    c = np.real(np.vdot(z, e))
+    return -(e / (nz * ne) - c * z / (nz ** 3 * ne))
+
+
+def backward(params, acts, dz):
+    """Parameter gradients given dL/dz (the residual path has no parameters)."""
+    grads = [None] * len(params)
+    g = np.stack([dz.real, dz.imag])
+    for l in range(len(params) - 1, -1, -1):
+        w, b = params[l]
+        if l < len(params) - 1:
+            g = g * (acts[l + 1] > 0)
+        gx, gw, gb = conv3d_backward(acts[l], w, g)
+        grads[l] = (gw, gb)
+        g = gx
+    return grads
+
+
+def loss_and_grads(params, r, e):
+    z, acts = forward(params, r)
+    L = loss(z, e)
+    grads = backward(params, acts, loss_grad_z(z, e))
+    return L, grads
+
+
+def adam_step(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba); state = (t, m, v) lists."""
+    t, m, v = state
+    t += 1
+    new = []
+    for i, ((w, b), (gw, gb)) in enumerate(zip(params, grads)):
+        out = []
+        for k, (p, gp) in enumerate(((w, gw), (b, gb))):
+            m[i][k] = beta1 * m[i][k] + (1 - beta1) * gp
+            v[i][k] = beta2 * v[i][k] + (1 - beta2) * gp * gp
+            mh = m[i][k] / (1 - beta1 ** t)
+            vh = v[i][k] / (1 - beta2 ** t)
+            out.append(p - lr * mh / (np.sqrt(vh) + eps))
+        new.append(tuple(out))
+    return new, (t, m, v)
+
+
+def adam_init(params):
+    z = [[np.zeros_like(w), np.zeros_like(b)] for w, b in params]
+    z2 = [[np.zeros_like(w), np.zeros_like(b)] for w, b in params]
+    return (0, z, z2)
+
+
+def bf16_round(a):
+    """Round float values to bfloat16 (round to nearest even), returned as float64."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = (u + 0x7FFF + lsb) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)

@@ -1,0 +1,110 @@
+"""Pins of the FP64 preconditioner-network oracle (CPU only)."""
+
+import numpy as np
+import pytest
+import scipy.ndimage
+
+from oracle import cnn
+
+
+def _rng(s=0):
+    return np.random.Generator(np.random.PCG64(s))
+
+
+def test_conv3d_matches_scipy_correlate():
+    rng = _rng(1)
+    x = rng.standard_normal((3, 5, 6, 7))
+    w = rng.standard_normal((4, 3, 3, 3, 3))
+    b = rng.standard_normal(4)
+    got = cnn.conv3d(x, w, b)
+    for o in range(4):
+        ref = b[o] + sum(scipy.ndimage.correlate(x[c], w[o, c], mode="constant", cval=0.0)
+                         for c in range(3))
+        assert np.allclose(got[o], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_conv3d_delta_kernel_is_identity():
+    rng = _rng(2)
+    x = rng.standard_normal((4, 5, 5, 5))
+    w = np.zeros((4, 4, 3, 3, 3))
+    for c in range(4):
+        w[c, c, 1, 1, 1] = 1.0
+    assert np.array_equal(cnn.conv3d(x, w, np.zeros(4)), x)
+
+
+def test_conv3d_backward_finite_differences():
+    rng = _rng(3)
+    x = rng.standard_normal((2, 4, 5, 3))
+    w = rng.standard_normal((3, 2, 3, 3, 3))
+    b = rng.standard_normal(3)
+    dy = rng.standard_normal((3, 4, 5, 3))
+    f = lambda xx, ww, bb: np.sum(dy * cnn.conv3d(xx, ww, bb))
+    dx, dw, db = cnn.conv3d_backward(x, w, dy)
+    h = 1e-6
+    for _ in range(10):
+        i = tuple(rng.integers(0, s) for s in x.shape)
+        xp, xm = x.copy(), x.copy()
+        xp[i] += h
+        xm[i] -= h
+        assert abs((f(xp, w, b) - f(xm, w, b)) / (2 * h) - dx[i]) < 1e-6 * (1 + abs(dx[i]))
+        j = tuple(rng.integers(0, s) for s in w.shape)
+        wp, wm = w.copy(), w.copy()
+        wp[j] += h
+        wm[j] -= h
+        assert abs((f(x, wp, b) - f(x, wm, b)) / (2 * h) - dw[j]) < 1e-6 * (1 + abs(dw[j]))
+    assert np.allclose(db, dy.sum(axis=(1, 2, 3)))
+
+
+def test_network_gradients_finite_differences():
+    rng = _rng(4)
+    params = cnn.init_params(5)
+    # non-zero biases so every path is exercised
+    params = [(w, rng.standard_normal(b.shape) * 0.1) for w, b in params]
+    shape = (4, 5, 4)
+    r = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    e = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    L0, grads = cnn.loss_and_grads(params, r, e)
+    assert 0.0 <= L0 <= 2.0
+    h = 1e-6
+    for l in range(len(params)):
+        for _ in range(4):
+            w, b = params[l]
+            j = tuple(rng.integers(0, s) for s in w.shape)
+            pp = [(ww.copy(), bb.copy()) for ww, bb in params]
+            pm = [(ww.copy(), bb.copy()) for ww, bb in params]
+            pp[l][0][j] += h
+            pm[l][0][j] -= h
+            fd = (cnn.loss_and_grads(pp, r, e)[0] - cnn.loss_and_grads(pm, r, e)[0]) / (2 * h)
+            assert abs(fd - grads[l][0][j]) < 1e-6 * (1 + abs(fd)), (l, j)
+        k = int(rng.integers(0, b.shape[0]))
+        pp = [(ww.copy(), bb.copy()) for ww, bb in params]
+        pm = [(ww.copy(), bb.copy()) for ww, bb in params]
+        pp[l][1][k] += h
+        pm[l][1][k] -= h
+        fd = (cnn.loss_and_grads(pp, r, e)[0] - cnn.loss_and_grads(pm, r, e)[0]) / (2 * h)
+        assert abs(fd - grads[l][1][k]) < 1e-6 * (1 + abs(fd))
+
+
+def test_loss_is_scale_invariant_and_zero_at_target():
+    rng = _rng(6)
+    z = rng.standard_normal(50) + 1j * rng.standard_normal(50)
+    assert cnn.loss(z, 3.7 * z) == pytest.approx(0.0, abs=1e-14)
+    e = rng.standard_normal(50) + 1j * rng.standard_normal(50)
+    assert cnn.loss(2.5 * z, e) == pytest.approx(cnn.loss(z, e), abs=1e-14)
+
+
+def test_adam_first_step_textbook():
+    # first Adam step moves each parameter by lr * sign(grad) (bias-corrected m/sqrt(v))
+    params = [(np.array([[[[[1.0]]]]]), np.array([0.5]))]
+    grads = [(np.array([[[[[0.3]]]]]), np.array([-2.0]))]
+    new, state = cnn.adam_step(params, grads, cnn.adam_init(params), lr=0.01)
+    assert new[0][0].item() == pytest.approx(1.0 - 0.01, abs=1e-9)
+    assert new[0][1].item() == pytest.approx(0.5 + 0.01, abs=1e-9)
+
+
+def test_bf16_round_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = _rng(7)
+    a = (rng.standard_normal(1000) * 10 ** rng.uniform(-5, 5, 1000)).astype(np.float32)
+    ref = torch.from_numpy(a).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(cnn.bf16_round(a), ref)
