@@ -74,16 +74,25 @@ def input_scale(r):
     return float(np.sqrt(np.mean(np.abs(r) ** 2)))
 
 
-def forward(params, r):
-    """z = M(r) and the activations needed by backward."""
+def _identity(a):
+    return a
+
+
+def forward(params, r, rnd=_identity):
+    """z = M(r) and the activations needed by backward.
+
+    rnd is applied to the network input and to every hidden activation (the
+    values a reduced-precision implementation stores between layers, e.g.
+    bf16_round); the identity gives the exact definition.  The residual path
+    u0 and the last layer's output are not rounded."""
     s = input_scale(r)
     u0 = np.stack([r.real, r.imag]) / s
-    acts = [u0]
-    h = u0
+    h = rnd(u0)
+    acts = [h]
     for l, (w, b) in enumerate(params):
         h = conv3d(h, w, b)
         if l < len(params) - 1:
-            h = np.maximum(h, 0.0)
+            h = rnd(np.maximum(h, 0.0))
         acts.append(h)
     zc = u0 + acts[-1]
     return zc[0] + 1j * zc[1], acts
@@ -102,24 +111,27 @@ def loss_grad_z(z, e):
     return -(e / (nz * ne) - c * z / (nz ** 3 * ne))
 
 
-def backward(params, acts, dz):
-    """Parameter gradients given dL/dz (the residual path has no parameters)."""
+def backward(params, acts, dz, rnd=_identity):
+    """Parameter gradients given dL/dz (the residual path has no parameters).
+
+    rnd is applied to dL/do and to every back-propagated activation gradient
+    after its ReLU mask (identity: the exact definition)."""
     grads = [None] * len(params)
-    g = np.stack([dz.real, dz.imag])
+    g = rnd(np.stack([dz.real, dz.imag]))
     for l in range(len(params) - 1, -1, -1):
         w, b = params[l]
         if l < len(params) - 1:
-            g = g * (acts[l + 1] > 0)
+            g = rnd(g * (acts[l + 1] > 0))
         gx, gw, gb = conv3d_backward(acts[l], w, g)
         grads[l] = (gw, gb)
         g = gx
     return grads
 
 
-def loss_and_grads(params, r, e):
-    z, acts = forward(params, r)
+def loss_and_grads(params, r, e, rnd=_identity):
+    z, acts = forward(params, r, rnd)
     L = loss(z, e)
-    grads = backward(params, acts, loss_grad_z(z, e))
+    grads = backward(params, acts, loss_grad_z(z, e), rnd)
     return L, grads
 
 
