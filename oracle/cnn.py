@@ -14,8 +14,14 @@ Definition (all arrays channel-first here, (C, D, H, W)):
   z  = (u0 + o)  read back as a complex image (residual connection)
 conv_l is a 3x3x3 cross-correlation with zero padding and a bias:
   conv(x)[o, d, h, w] = b[o] + sum_{c, tz, ty, tx} W[o, c, tz, ty, tx] x[c, d+tz-1, h+ty-1, w+tx-1].
-Flexible CG is invariant to the scale of M's output, so the training loss is
-scale invariant: L = 1 - Re<z, e> / (||z|| ||e||) for the target e = E^{-1} r.
+Flexible CG is invariant to the scale of M's output, so the training losses
+are scale invariant.  For the target e = E^{-1} r (so E e = r):
+  cosine loss  L = 1 - Re<z, e> / (||z|| ||e||);
+  energy loss  L = 1 - c |c| / (<z, E z> <e, r>),  c = Re<z, r>:
+the fraction of the error energy ||e||_E^2 = <e, r> left after an exact line
+search from the current iterate along z (Re<z, E e> = c); a direction with
+c < 0 points uphill and scores above 1.  The energy loss weights errors by E,
+as CG's convergence does.
 """
 
 from __future__ import annotations
@@ -111,6 +117,22 @@ def loss_grad_z(z, e):
     return -(e / (nz * ne) - c * z / (nz ** 3 * ne))
 
 
+def loss_energy(z, r, e, Ez):
+    """1 - c|c| / (<z, E z> <e, r>), c = Re<z, r>; Ez = E z."""
+    c = np.real(np.vdot(z, r))
+    zEz = np.real(np.vdot(z, Ez))
+    er = np.real(np.vdot(e, r))
+    return 1.0 - c * abs(c) / (zEz * er)
+
+
+def loss_energy_grad_z(z, r, e, Ez):
+    """dL/dz of the energy loss (E Hermitian: d<z, E z>/dz = 2 E z)."""
+    c = np.real(np.vdot(z, r))
+    zEz = np.real(np.vdot(z, Ez))
+    er = np.real(np.vdot(e, r))
+    return -2.0 * abs(c) * r / (zEz * er) + 2.0 * c * abs(c) * Ez / (zEz ** 2 * er)
+
+
 def backward(params, acts, dz, rnd=_identity):
     """Parameter gradients given dL/dz (the residual path has no parameters).
 
@@ -132,6 +154,16 @@ def loss_and_grads(params, r, e, rnd=_identity):
     z, acts = forward(params, r, rnd)
     L = loss(z, e)
     grads = backward(params, acts, loss_grad_z(z, e), rnd)
+    return L, grads
+
+
+def loss_and_grads_energy(params, r, e, E, rnd=_identity):
+    """Energy loss and parameter gradients; E is a callable applying the
+    (Hermitian positive definite) system operator to an image."""
+    z, acts = forward(params, r, rnd)
+    Ez = E(z)
+    L = loss_energy(z, r, e, Ez)
+    grads = backward(params, acts, loss_energy_grad_z(z, r, e, Ez), rnd)
     return L, grads
 
 

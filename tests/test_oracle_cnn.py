@@ -108,3 +108,55 @@ def test_bf16_round_matches_torch():
     a = (rng.standard_normal(1000) * 10 ** rng.uniform(-5, 5, 1000)).astype(np.float32)
     ref = torch.from_numpy(a).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(cnn.bf16_round(a), ref)
+
+
+def _spd(rng, n):
+    a = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return a.conj().T @ a + 0.5 * np.eye(n)
+
+
+def test_energy_loss_zero_at_target_and_line_search_identity():
+    # L(e) = 0; for any z, 1 - L(z) is the energy fraction removed by the
+    # exact line search x + a z (computed here by brute minimisation over a)
+    rng = _rng(8)
+    n = 12
+    E = _spd(rng, n)
+    e = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    r = E @ e
+    assert cnn.loss_energy(e, r, e, E @ e) == pytest.approx(0.0, abs=1e-12)
+    z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    err = lambda a: np.real(np.vdot(e - a * z, E @ (e - a * z)))
+    coarse = np.linspace(-5, 5, 2001)
+    a0 = coarse[np.argmin([err(t) for t in coarse])]
+    fine = np.linspace(a0 - 0.01, a0 + 0.01, 4001)
+    best = min(err(t) for t in fine)
+    removed = 1.0 - best / err(0.0)
+    c = np.real(np.vdot(z, r))
+    L = cnn.loss_energy(z, r, e, E @ z)
+    assert (1.0 - L) * np.sign(c) == pytest.approx(removed, abs=1e-6)
+    assert cnn.loss_energy(-z, r, e, E @ -z) == pytest.approx(1.0 + removed, abs=1e-6)
+
+
+def test_energy_loss_network_gradients_finite_differences():
+    rng = _rng(9)
+    params = cnn.init_params(10)
+    params = [(w, rng.standard_normal(b.shape) * 0.1) for w, b in params]
+    shape = (3, 4, 3)
+    n = int(np.prod(shape))
+    Em = _spd(rng, n)
+    E = lambda v: (Em @ v.ravel()).reshape(shape)
+    e = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    r = E(e)
+    L0, grads = cnn.loss_and_grads_energy(params, r, e, E)
+    h = 1e-6
+    f = lambda pp: cnn.loss_and_grads_energy(pp, r, e, E)[0]
+    for l in range(len(params)):
+        for _ in range(3):
+            w, b = params[l]
+            j = tuple(rng.integers(0, s) for s in w.shape)
+            pp = [(ww.copy(), bb.copy()) for ww, bb in params]
+            pm = [(ww.copy(), bb.copy()) for ww, bb in params]
+            pp[l][0][j] += h
+            pm[l][0][j] -= h
+            fd = (f(pp) - f(pm)) / (2 * h)
+            assert abs(fd - grads[l][0][j]) < 1e-6 * (1 + abs(fd)), (l, j)
