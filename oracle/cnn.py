@@ -76,6 +76,21 @@ def conv3d_backward(x, w, dy):
     return dxp[:, 1:-1, 1:-1, 1:-1], dw, db
 
 
+def conv3d_transpose(y, w):
+    """Adjoint of conv3d(., w, 0) with respect to its input: x = W^T y."""
+    cout, D, H, W = y.shape
+    yp = np.zeros((cout, D + 2, H + 2, W + 2))
+    yp[:, 1:-1, 1:-1, 1:-1] = y
+    x = np.zeros((w.shape[1], D, H, W))
+    # x[c, p] = sum_{o, t} w[o, c, t] y[o, p - t + 1]: correlation with flipped taps
+    for tz in range(3):
+        for ty in range(3):
+            for tx in range(3):
+                x += np.einsum("oc,odhw->cdhw", w[:, :, tz, ty, tx],
+                               yp[:, 2 - tz:2 - tz + D, 2 - ty:2 - ty + H, 2 - tx:2 - tx + W])
+    return x
+
+
 def input_scale(r):
     return float(np.sqrt(np.mean(np.abs(r) ** 2)))
 
@@ -165,6 +180,65 @@ def loss_and_grads_energy(params, r, e, E, rnd=_identity):
     L = loss_energy(z, r, e, Ez)
     grads = backward(params, acts, loss_energy_grad_z(z, r, e, Ez), rnd)
     return L, grads
+
+
+# ---------------------------------------------------------------------------
+# Symmetric form.  The same five layers (biases unused) define a map N with
+# ReLU masks D_l set by the forward pass, and the network returns
+#   z = u0 + N^T (N u0),   N = W_5 D_4 W_4 D_3 W_3 D_2 W_2 D_1 W_1,
+# i.e. for fixed masks z = (I + J^T J) u0 with J the Jacobian of N: a symmetric
+# positive definite map, as CG-type methods expect of a preconditioner.
+
+def forward_spd(params, r, rnd=_identity):
+    """z of the symmetric form and the intermediates backward_spd needs."""
+    s = input_scale(r)
+    u0 = np.stack([r.real, r.imag]) / s
+    h = [rnd(u0)]
+    for l, (w, _) in enumerate(params):
+        y = conv3d(h[-1], w, np.zeros(w.shape[0]))
+        h.append(rnd(np.maximum(y, 0.0)) if l < len(params) - 1 else rnd(y))
+    # transposed chain: u_l = D_l W_{l+1}^T u_{l+1}, u_5 = h_5
+    u = [None] * len(params) + [h[-1]]
+    for l in range(len(params) - 1, 0, -1):
+        u[l] = rnd(conv3d_transpose(u[l + 1], params[l][0]) * (h[l] > 0))
+    o = conv3d_transpose(u[1], params[0][0])
+    zc = u0 + o
+    return zc[0] + 1j * zc[1], (h, u)
+
+
+def backward_spd(params, inter, dz, rnd=_identity):
+    """Weight gradients of the symmetric form given dL/dz (biases: zero)."""
+    h, u = inter
+    L = len(params)
+    gw = [np.zeros_like(w) for w, _ in params]
+    # through the transposed chain: o = W_1^T u_1, u_l = D_l W_{l+1}^T u_{l+1}
+    g = rnd(np.stack([dz.real, dz.imag]))
+    for l in range(L):
+        # o_l = W_{l+1}^T u_{l+1} with upstream g: dW = correlation of u_{l+1} and g
+        _, dw, _ = conv3d_backward(g, params[l][0], u[l + 1])
+        gw[l] += dw
+        y = conv3d(g, params[l][0], np.zeros(params[l][0].shape[0]))
+        g = rnd(y * (h[l + 1] > 0)) if l < L - 1 else rnd(y)
+    # g is now dL/dh_5: back through the forward chain h_l = D_l W_l h_{l-1}
+    for l in range(L - 1, -1, -1):
+        if l < L - 1:
+            g = rnd(g * (h[l + 1] > 0))
+        gx, dw, _ = conv3d_backward(h[l], params[l][0], g)
+        gw[l] += dw
+        g = gx
+    return [(w, np.zeros(b.shape)) for w, (_, b) in zip(gw, params)]
+
+
+def loss_and_grads_spd(params, r, e, E=None, rnd=_identity):
+    """Loss and gradients of the symmetric form: cosine loss (E None) or the
+    energy loss with the operator callable E."""
+    z, inter = forward_spd(params, r, rnd)
+    if E is None:
+        L, dz = loss(z, e), loss_grad_z(z, e)
+    else:
+        Ez = E(z)
+        L, dz = loss_energy(z, r, e, Ez), loss_energy_grad_z(z, r, e, Ez)
+    return L, backward_spd(params, inter, dz, rnd)
 
 
 def adam_step(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -160,3 +160,69 @@ def test_energy_loss_network_gradients_finite_differences():
             pm[l][0][j] -= h
             fd = (f(pp) - f(pm)) / (2 * h)
             assert abs(fd - grads[l][0][j]) < 1e-6 * (1 + abs(fd)), (l, j)
+
+
+def test_conv3d_transpose_is_adjoint():
+    rng = _rng(11)
+    x = rng.standard_normal((3, 4, 5, 6))
+    y = rng.standard_normal((2, 4, 5, 6))
+    w = rng.standard_normal((2, 3, 3, 3, 3))
+    lhs = np.sum(y * cnn.conv3d(x, w, np.zeros(2)))
+    rhs = np.sum(x * cnn.conv3d_transpose(y, w))
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+
+
+def test_symmetric_form_is_spd_for_fixed_masks():
+    # with every mask fixed the map r -> z * s is (I + J^T J): check
+    # symmetry and positivity through a linear network (no ReLU effect:
+    # weights chosen so every hidden activation is positive for these inputs)
+    rng = _rng(12)
+    params = cnn.init_params(13)
+    shape = (4, 4, 4)
+    # a network whose hidden layers see only positive inputs is linear: use
+    # |W| for the hidden layers and positive inputs
+    params = [(np.abs(w) if l in (1, 2, 3) else w, b) for l, (w, b) in enumerate(params)]
+    z1, (h, _) = cnn.forward_spd(params, np.ones(shape) + 0j)
+    # directional check with the dense Jacobian of o = N^T N u0 at fixed masks
+    n = 2 * int(np.prod(shape))
+
+    def o_of(u0):
+        hh = [u0]
+        for l, (w, _) in enumerate(params):
+            y = cnn.conv3d(hh[-1], w, np.zeros(w.shape[0]))
+            hh.append(y * (h[l + 1] > 0) if l < len(params) - 1 else y)
+        u = hh[-1]
+        for l in range(len(params) - 1, 0, -1):
+            u = cnn.conv3d_transpose(u, params[l][0]) * (h[l] > 0)
+        return cnn.conv3d_transpose(u, params[0][0])
+
+    basis = np.eye(n).reshape(n, 2, *shape)
+    M = np.stack([o_of(b).ravel() for b in basis], axis=1) + np.eye(n)
+    assert np.allclose(M, M.T, atol=1e-10)
+    assert np.linalg.eigvalsh(M).min() >= 1.0 - 1e-10
+
+
+def test_symmetric_form_gradients_finite_differences():
+    rng = _rng(14)
+    params = [(w, np.zeros_like(b)) for w, b in cnn.init_params(15)]
+    params[-1] = (params[-1][0] * 10, params[-1][1])
+    shape = (3, 4, 3)
+    n = int(np.prod(shape))
+    Em = _spd(rng, n)
+    E = lambda v: (Em @ v.ravel()).reshape(shape)
+    e = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    r = E(e)
+    for EE in (None, E):
+        L0, grads = cnn.loss_and_grads_spd(params, r, e, EE)
+        h = 1e-6
+        f = lambda pp: cnn.loss_and_grads_spd(pp, r, e, EE)[0]
+        for l in range(len(params)):
+            for _ in range(3):
+                w, b = params[l]
+                j = tuple(rng.integers(0, s) for s in w.shape)
+                pp = [(ww.copy(), bb.copy()) for ww, bb in params]
+                pm = [(ww.copy(), bb.copy()) for ww, bb in params]
+                pp[l][0][j] += h
+                pm[l][0][j] -= h
+                fd = (f(pp) - f(pm)) / (2 * h)
+                assert abs(fd - grads[l][0][j]) < 1e-6 * (1 + abs(fd)), (EE is None, l, j)
