@@ -65,6 +65,7 @@ typedef int32_t nrsense_status;
 typedef struct { float re, im; } nrsense_c64;
 
 typedef struct nrsense_plan_s* nrsense_plan_t;
+typedef struct nrsense_cnn_s* nrsense_cnn_t;
 
 /* precision of the gridding grids (desc.precision) */
 #define NRSENSE_FP32            0  /* FP32 storage and accumulation */
@@ -209,6 +210,126 @@ nrsense_status nrsense_solve_cg(nrsense_plan_t plan, const nrsense_c64* y_dev, d
                                 void* stream);
 
 /*
+ * nrsense_solve_cg_record - nrsense_solve_cg that also records iterates, to
+ * generate training pairs for the preconditioner network.  Before iteration
+ * k = 0, 1, ... (while k < capacity and the solve has not converged) it
+ * stores the recursive residual r_k in rec_r_dev[k] and, at exit, the error
+ * x_final - x_k in rec_e_dev[k]; since E (x* - x_k) = r_k, a converged x_final
+ * makes (r_k, e_k) an input/target pair of the preconditioner.
+ *   rec_r_dev, rec_e_dev  capacity x (n0 n1 n2) complex each (device, written).
+ *   capacity              >= 0 (0 records nothing).
+ *   rec_count_host        receives the number of recorded pairs.
+ * NRSENSE_CG_GRAPH is not accepted here (ERR_ARG): recording synchronises the
+ * host once per iteration.  Other arguments, results and errors as
+ * nrsense_solve_cg.
+ */
+nrsense_status nrsense_solve_cg_record(nrsense_plan_t plan, const nrsense_c64* y_dev, double lambda,
+                                       double tol, int32_t maxit, uint32_t flags,
+                                       nrsense_c64* x_dev, int32_t* iters_host,
+                                       double* res_hist_host, double* true_res_host,
+                                       nrsense_c64* rec_r_dev, nrsense_c64* rec_e_dev,
+                                       int32_t capacity, int32_t* rec_count_host, void* stream);
+
+/*
+ * nrsense_solve_fcg - flexible conjugate gradients (FCG(1), Polak-Ribiere
+ * coefficient) on the same normal equations, preconditioned by the network
+ * `net` (z_k = M(r_k)); net = NULL gives the unpreconditioned iteration in
+ * the same form.  The paper has no preconditioner: this is the learned
+ * preconditioner added to the Tikhonov CG solve.
+ *   alpha = Re<r, z> / Re<p, E p>,  beta = -alpha Re<z_new, E p> / Re<z, r>.
+ * A network output with Re<r, z> <= 0 or non-finite falls back to z = r and
+ * restarts (beta = 0); *fallbacks_host (may be NULL) receives how often.
+ * net must have the plan's image shape (ERR_ARG otherwise) and is used, not
+ * modified; its activation buffers are shared, so no other call on net may
+ * overlap the solve.  Arguments, flags (NRSENSE_CG_X0, NRSENSE_CG_GRAPH),
+ * results and errors as nrsense_solve_cg; the convergence test uses the
+ * recursive residual ||r_k|| <= tol ||b||.
+ */
+nrsense_status nrsense_solve_fcg(nrsense_plan_t plan, nrsense_cnn_t net, const nrsense_c64* y_dev,
+                                 double lambda, double tol, int32_t maxit, uint32_t flags,
+                                 nrsense_c64* x_dev, int32_t* iters_host, double* res_hist_host,
+                                 double* true_res_host, int32_t* fallbacks_host, void* stream);
+
+/*
+ * Preconditioner network M (no counterpart in the paper).  For a residual
+ * image r (n0, n1, n2) complex:
+ *   s = sqrt(mean |r|^2),  u0 = [Re r, Im r] / s  (2 channels),
+ *   h_l = relu(conv_l(h_{l-1})), l = 1..4 (16 channels),  o = conv_5(h_4),
+ *   z = u0 + o read as a complex image (z = 0 when r = 0),
+ * conv_l: 3x3x3 cross-correlation with zero padding plus a bias, channels
+ * 2 -> 16 -> 16 -> 16 -> 16 -> 2.  Training loss for a target e:
+ *   L = 1 - Re<z, e> / (||z|| ||e||)  (L = 1 and no gradient if z or e is 0).
+ * Weights and activations are BF16 on the device with FP32 accumulation
+ * (tensor cores); master weights, gradients and Adam moments are FP32; the
+ * input scale and the loss are FP64 reductions.
+ *
+ * Parameter layout (host arrays of nrsense_cnn_num_params() floats): layer by
+ * layer, W_l as C-order (Cout, Cin, 3, 3, 3) with W[o, c, tz, ty, tx]
+ * multiplying input voxel (z + tz - 1, y + ty - 1, x + tx - 1), then b_l (Cout).
+ *
+ * nrsense_cnn_create     network for images of shape n_host[3] (each 1..4096),
+ *                        all parameters zero; allocates its activations
+ *                        (7 x 32 bytes + 8 bytes per voxel, 12 x 32 + 8 in the
+ *                        symmetric form); synchronises stream.  flags:
+ *                        NRSENSE_CNN_SYMMETRIC selects the symmetric form
+ *                          z = u0 + N^T N u0,
+ *                        N = W_5 D_4 W_4 D_3 W_3 D_2 W_2 D_1 W_1 the same five
+ *                        convolutions without biases, D_l the ReLU masks of the
+ *                        forward pass, N^T the transposed convolutions in
+ *                        reverse order with the same masks: for fixed masks
+ *                        z = (I + J^T J) u0 is symmetric positive definite in
+ *                        u0, as CG-type methods expect of a preconditioner.
+ *                        Biases are ignored and never updated in this form.
+ * nrsense_cnn_init_params He initialisation from a seeded generator
+ *                        (splitmix64 + Box-Muller), last layer scaled by 0.1,
+ *                        biases zero; resets the Adam state.
+ * nrsense_cnn_set_params / get_params  host copies in the layout above
+ *                        (count must equal nrsense_cnn_num_params(); set rejects
+ *                        non-finite values and resets the Adam state).
+ * nrsense_cnn_apply      z_dev = M(r_dev), both (n0, n1, n2) complex device
+ *                        arrays; asynchronous.
+ * nrsense_cnn_gradients  forward + backward for one pair (r_dev, e_dev); the
+ *                        parameter gradients are written (accumulate = 0) or
+ *                        added (accumulate != 0) to the device gradient buffer;
+ *                        *loss_host (may be NULL; then asynchronous) receives L.
+ *                        plan == NULL: the cosine loss above.  plan != NULL
+ *                        (same image shape, else ERR_ARG): the energy loss
+ *                          L = 1 - c|c| / (<z, E z> <e, r>),  c = Re<z, r>,
+ *                        E = sum_j A_j^H A_j + lambda I of the plan, the error
+ *                        energy left after a line search along z when E e = r
+ *                        (one nrsense_apply_normal per call; the first such
+ *                        call allocates an image buffer).
+ * nrsense_cnn_get_grads  host copy of the gradient buffer (layout above).
+ * nrsense_cnn_adam_step  one Adam update with gradient grad_scale * buffer
+ *                        (e.g. 1 / pairs accumulated); asynchronous.  flags:
+ *                        NRSENSE_CNN_FREEZE_BIAS leaves the biases unchanged.
+ * nrsense_cnn_launches   the network's own kernel launches so far.
+ * Errors: ERR_ARG (null handle or pointer, bad shape or count, bad Adam
+ * constants), ERR_OOM, ERR_CUDA.  A handle is not thread-safe.
+ */
+#define NRSENSE_CNN_SYMMETRIC (1u << 0)
+nrsense_status nrsense_cnn_create(const int32_t* n_host, uint32_t flags, void* stream,
+                                  nrsense_cnn_t* out);
+nrsense_status nrsense_cnn_destroy(nrsense_cnn_t net);
+int64_t nrsense_cnn_num_params(void);
+nrsense_status nrsense_cnn_init_params(nrsense_cnn_t net, uint64_t seed, void* stream);
+nrsense_status nrsense_cnn_set_params(nrsense_cnn_t net, const float* params_host, int64_t count,
+                                      void* stream);
+nrsense_status nrsense_cnn_get_params(nrsense_cnn_t net, float* params_host, int64_t count,
+                                      void* stream);
+nrsense_status nrsense_cnn_apply(nrsense_cnn_t net, const nrsense_c64* r_dev, nrsense_c64* z_dev,
+                                 void* stream);
+nrsense_status nrsense_cnn_gradients(nrsense_cnn_t net, nrsense_plan_t plan, double lambda,
+                                     const nrsense_c64* r_dev, const nrsense_c64* e_dev,
+                                     int32_t accumulate, double* loss_host, void* stream);
+nrsense_status nrsense_cnn_get_grads(nrsense_cnn_t net, float* grads_host, int64_t count,
+                                     void* stream);
+#define NRSENSE_CNN_FREEZE_BIAS (1u << 0)
+nrsense_status nrsense_cnn_adam_step(nrsense_cnn_t net, float lr, float grad_scale, float beta1,
+                                     float beta2, float eps, uint32_t flags, void* stream);
+nrsense_status nrsense_cnn_launches(nrsense_cnn_t net, int64_t* out_host);
+
+/*
  * nrsense_dot_noalloc - <x, y> = sum_i conj(x_i) y_i in FP64, for callers that
  * cannot allocate device memory.  The paper has no counterpart: this is a
  * variant of the CG solver's inner-product kernel that needs no plan and
@@ -249,7 +370,7 @@ nrsense_status nrsense_device_status(nrsense_plan_t plan, int32_t clear, int32_t
  * count_host[s]; *own_kernels_host receives the number of the library's own
  * CUDA kernels launched in the window (cuFFT kernels excluded).
  */
-#define NRSENSE_NUM_STAGES 13
+#define NRSENSE_NUM_STAGES 14
 #define NRSENSE_STAGE_FFT_N          0  /* cuFFT, N^3 */
 #define NRSENSE_STAGE_FFT_G          1  /* cuFFT, G^3 single grid */
 #define NRSENSE_STAGE_FFT_GC         2  /* cuFFT, G^3 x C batched */
@@ -263,6 +384,7 @@ nrsense_status nrsense_device_status(nrsense_plan_t plan, int32_t clear, int32_t
 #define NRSENSE_STAGE_CROP_COILSUM  10  /* K8 */
 #define NRSENSE_STAGE_VECTOR        11  /* elementwise vector kernels */
 #define NRSENSE_STAGE_SOLVER        12  /* CG reductions and updates */
+#define NRSENSE_STAGE_CNN           13  /* preconditioner network inside flexible CG */
 nrsense_status nrsense_profile_start(nrsense_plan_t plan, int32_t max_launches);
 nrsense_status nrsense_profile_stop(nrsense_plan_t plan, double* ms_host, int64_t* count_host,
                                     int64_t* own_kernels_host);

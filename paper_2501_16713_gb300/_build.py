@@ -30,6 +30,7 @@ SOURCES = [
     "kernels_spread.cu",
     "solver.cu",
     "noalloc.cu",
+    "cnn.cu",
 ]
 HEADERS = ["common.cuh", "plan_internal.h", "kb_host.h"]
 

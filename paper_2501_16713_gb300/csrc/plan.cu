@@ -682,7 +682,8 @@ nrsense_status nrsense_profile_stop(nrsense_plan_t p, double* ms, int64_t* count
 const char* nrsense_stage_name(int32_t st) {
   static const char* names[NRSENSE_NUM_STAGES] = {
       "fft_n", "fft_g", "fft_gc", "deapod_pad", "interp_image", "spread_image", "crop_deapod",
-      "coil_fanout_pad", "interp_kspace", "spread_kspace", "crop_coilsum", "vector", "solver"};
+      "coil_fanout_pad", "interp_kspace", "spread_kspace", "crop_coilsum", "vector", "solver",
+      "cnn"};
   return (st >= 0 && st < NRSENSE_NUM_STAGES) ? names[st] : "unknown";
 }
 

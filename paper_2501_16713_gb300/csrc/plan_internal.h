@@ -42,6 +42,7 @@ struct PointSet {
 }  // namespace nrs
 
 struct nrsense_cg_ws;  // CG workspace (solver.cu)
+struct nrsense_cnn_s;  // preconditioner network (cnn.cu)
 
 struct nrsense_plan_s {
   nrsense_desc desc{};
@@ -117,6 +118,14 @@ struct StageMark {
 }  // namespace nrs
 
 namespace nrs {
+
+// ---- preconditioner network (cnn.cu) --------------------------------------
+long long cnn_nvox(const nrsense_cnn_s* net);
+bool cnn_shape_matches(const nrsense_cnn_s* net, int n0, int n1, int n2);
+// z = M(r) on stream s, no host synchronisation; sumsq_dev (may be null) is an
+// FP64 sum of |r|^2 already on the device.  Returns the kernels launched.
+long long cnn_apply_async(nrsense_cnn_s* net, const float2* r, const double* sumsq_dev, float2* z,
+                          cudaStream_t s);
 
 // ---- launchers (kernels_*.cu) -------------------------------------------
 // image space

@@ -13,6 +13,16 @@
 // the solve, launches the iteration chunks (optionally as a captured CUDA
 // graph) and reads the iteration count and residual history at the end (and
 // the converged flag between chunks).
+//
+// Flexible CG (Notay's FCG(1), Polak-Ribiere form) takes z_k = M(r_k) from
+// the learned preconditioner network, a nonlinear map, so the search
+// directions are re-conjugated only against the previous one:
+//   alpha = Re<r, z> / Re<p, E p>,  beta = Re<z_new, r_new - r> / Re<z, r>
+//         = -alpha Re<z_new, E p> / Re<z, r>,  p = z_new + beta p.
+// Real parts of the complex inner products are the inner product of the
+// equivalent real system, on which E is symmetric positive definite.  When the
+// network returns a direction with Re<r, z> <= 0 (not a descent direction)
+// the iteration falls back to z = r and restarts (beta = 0): a plain CG step.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -37,6 +47,9 @@ struct CgState {
   int done;       // converged, broken down or maxit reached
   int status;     // NRSENSE_OK or NRSENSE_ERR_BREAKDOWN
   int maxit;
+  double rz;      // flexible CG: Re<r, z>
+  int fb;         // flexible CG: this step falls back to z = r
+  int n_fb;       // flexible CG: fallbacks taken
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -97,6 +110,9 @@ __global__ void cg_init_kernel(const double* __restrict__ partial, const double*
     st->beta = 0.0;
     st->maxit = maxit;
     st->status = NRSENSE_OK;
+    st->rz = rr;
+    st->fb = 0;
+    st->n_fb = 0;
     const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
     hist[0] = rel;
     st->done = (bb == 0.0 || rr <= st->tol2 || maxit <= 0) ? 1 : 0;
@@ -104,17 +120,20 @@ __global__ void cg_init_kernel(const double* __restrict__ partial, const double*
 }
 
 // alpha = <r,r> / <p, E p>; breakdown on non-positive or non-finite curvature.
-__global__ void cg_alpha_kernel(const double* __restrict__ partial, int nb, CgState* st) {
+// (flexible CG: alpha = Re<r, z> / <p, E p>)
+__global__ void cg_alpha_kernel(const double* __restrict__ partial, int nb, CgState* st,
+                                int flexible) {
   const double pAp = sum_partials(partial, nb);
   if (threadIdx.x == 0) {
+    const double num = flexible ? st->rz : st->rr;
     if (st->done) {
       st->alpha = 0.0;
-    } else if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(st->rr)) {
+    } else if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(num)) {
       st->alpha = 0.0;
       st->status = NRSENSE_ERR_BREAKDOWN;
       st->done = 1;
     } else {
-      st->alpha = st->rr / pAp;
+      st->alpha = num / pAp;
     }
   }
 }
@@ -182,6 +201,99 @@ __global__ void cg_update_p_kernel(const float2* __restrict__ r, float2* __restr
   }
 }
 
+// Flexible CG: record |r|^2 after the update and test convergence.
+__global__ void fcg_check_kernel(const double* __restrict__ partial, int nb, CgState* st,
+                                 double* hist) {
+  const double rr_new = sum_partials(partial, nb);
+  if (threadIdx.x == 0 && !st->done) {
+    st->rr = rr_new;
+    st->iter += 1;
+    hist[st->iter] = sqrt(rr_new / st->bb);
+    if (rr_new <= st->tol2 || st->iter >= st->maxit) st->done = 1;
+    if (!isfinite(rr_new)) {
+      st->status = NRSENSE_ERR_BREAKDOWN;
+      st->done = 1;
+    }
+  }
+}
+
+// partial = Re<z, r>, partial[nb..] = Re<z, q> (q may be null: not needed).
+__global__ void __launch_bounds__(kRedThreads) dot2_partial_kernel(
+    const float2* __restrict__ z, const float2* __restrict__ r, const float2* __restrict__ q,
+    long long n, double* __restrict__ partial) {
+  double a = 0.0, b = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 zi = z[i], ri = r[i];
+    a = fma((double)zi.x, (double)ri.x, fma((double)zi.y, (double)ri.y, a));
+    if (q) {
+      const float2 qi = q[i];
+      b = fma((double)zi.x, (double)qi.x, fma((double)zi.y, (double)qi.y, b));
+    }
+  }
+  a = block_sum(a);
+  b = block_sum(b);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = a;
+    partial[gridDim.x + blockIdx.x] = b;
+  }
+}
+
+// Flexible CG direction coefficient.  start != 0: first direction (beta = 0).
+// Non-descent network output (Re<r, z> <= 0 or non-finite): z = r, beta = 0.
+__global__ void fcg_beta_kernel(const double* __restrict__ partial, int nb, CgState* st, int start) {
+  const double rz_new = sum_partials(partial, nb);
+  const double zq = sum_partials(partial + nb, nb);
+  if (threadIdx.x == 0) {
+    if (st->done && !start) {
+      st->beta = 0.0;
+      return;
+    }
+    if (!(rz_new > 0.0) || !isfinite(rz_new) || !isfinite(zq)) {
+      st->fb = 1;
+      st->n_fb += 1;
+      st->beta = 0.0;
+      st->rz = st->rr;
+    } else {
+      st->fb = 0;
+      st->beta = start ? 0.0 : -st->alpha * zq / st->rz;
+      st->rz = rz_new;
+    }
+  }
+}
+
+// p = (fb ? r : z) + beta p; p = (fb ? r : z) when beta == 0.
+__global__ void fcg_update_p_kernel(const float2* __restrict__ z, const float2* __restrict__ r,
+                                    float2* __restrict__ p, long long n,
+                                    const CgState* __restrict__ st, int start) {
+  if (st->done && !start) return;
+  const float b = (float)st->beta;
+  const float2* __restrict__ src = st->fb ? r : z;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 si = src[i];
+    float2 pi = si;
+    if (b != 0.0f) {
+      pi = p[i];
+      pi.x = fmaf(b, pi.x, si.x);
+      pi.y = fmaf(b, pi.y, si.y);
+    }
+    p[i] = pi;
+  }
+}
+
+// e_k = x - e_k (recorded iterates become errors against the final iterate)
+__global__ void rsub_kernel(const float2* __restrict__ x, float2* __restrict__ e, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 a = x[i];
+    float2 v = e[i];
+    v.x = a.x - v.x;
+    v.y = a.y - v.y;
+    e[i] = v;
+  }
+}
+
 // r = b - E x (r holds b on entry, Ex holds E x)
 __global__ void sub_kernel(float2* __restrict__ r, const float2* __restrict__ ex, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -210,6 +322,7 @@ nrsense_status launched() {
 
 struct nrsense_cg_ws {
   nrsense_c64 *r = nullptr, *p = nullptr, *Ep = nullptr, *b = nullptr;
+  nrsense_c64* z = nullptr;    // flexible CG only (allocated on first use)
   double* partial = nullptr;   // 2 * kRedBlocks
   CgState* st = nullptr;
   double* hist = nullptr;
@@ -219,6 +332,8 @@ struct nrsense_cg_ws {
   cudaGraphExec_t gexec = nullptr;
   // what the captured graph baked in
   const void* g_x = nullptr;
+  const void* g_net = nullptr;
+  int g_mode = -1;
   double g_lambda = 0.0;
   int g_chunk = 0;
 };
@@ -236,6 +351,7 @@ void cg_release(nrsense_plan_s* p) {
   cudaFree(w->p);
   cudaFree(w->Ep);
   cudaFree(w->b);
+  cudaFree(w->z);
   cudaFree(w->partial);
   cudaFree(w->st);
   cudaFree(w->hist);
@@ -247,12 +363,12 @@ void cg_release(nrsense_plan_s* p) {
 
 namespace {
 
-nrsense_status cg_workspace(nrsense_plan_s* p, int maxit) {
+nrsense_status cg_workspace(nrsense_plan_s* p, int maxit, bool flexible) {
+  const size_t vb = size_t(p->geo.nvox) * sizeof(nrsense_c64);
   if (!p->cg) {
     p->cg = new (std::nothrow) nrsense_cg_ws();
     if (!p->cg) return NRSENSE_ERR_OOM;
     nrsense_cg_ws* w = p->cg;
-    const size_t vb = size_t(p->geo.nvox) * sizeof(nrsense_c64);
     if (cudaMalloc(&w->r, vb) != cudaSuccess || cudaMalloc(&w->p, vb) != cudaSuccess ||
         cudaMalloc(&w->Ep, vb) != cudaSuccess || cudaMalloc(&w->b, vb) != cudaSuccess ||
         cudaMalloc(&w->partial, 2 * kRedBlocks * sizeof(double)) != cudaSuccess ||
@@ -266,6 +382,11 @@ nrsense_status cg_workspace(nrsense_plan_s* p, int maxit) {
       return NRSENSE_ERR_CUDA;
   }
   nrsense_cg_ws* w = p->cg;
+  if (flexible && !w->z && cudaMalloc(&w->z, vb) != cudaSuccess) {
+    cudaGetLastError();
+    w->z = nullptr;
+    return NRSENSE_ERR_OOM;
+  }
   if (w->hist_cap < maxit + 1) {
     cudaFree(w->hist);
     w->hist = nullptr;
@@ -279,8 +400,32 @@ nrsense_status cg_workspace(nrsense_plan_s* p, int maxit) {
   return NRSENSE_OK;
 }
 
-// One CG iteration on stream s (no host synchronisation).
-nrsense_status cg_iteration(nrsense_plan_s* p, nrsense_c64* x, double lambda, cudaStream_t s) {
+// z = M(r) (the network) or z = r (no network), then the flexible CG
+// coefficient and direction.  start: first direction.
+nrsense_status fcg_direction(nrsense_plan_s* p, nrsense_cnn_s* net, bool start, cudaStream_t s) {
+  nrsense_cg_ws* w = p->cg;
+  const long long n = p->geo.nvox;
+  const float2* r = reinterpret_cast<const float2*>(w->r);
+  const float2* z = r;
+  if (net) {
+    StageMark m(p, NRSENSE_STAGE_CNN, s);
+    p->launches += cnn_apply_async(net, r, &w->st->rr, reinterpret_cast<float2*>(w->z), s);
+    z = reinterpret_cast<const float2*>(w->z);
+  }
+  StageMark m(p, NRSENSE_STAGE_SOLVER, s);
+  dot2_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(
+      z, r, start ? nullptr : reinterpret_cast<const float2*>(w->Ep), n, w->partial);
+  fcg_beta_kernel<<<1, kRedThreads, 0, s>>>(w->partial, kRedBlocks, w->st, start ? 1 : 0);
+  fcg_update_p_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(z, r, reinterpret_cast<float2*>(w->p), n,
+                                                         w->st, start ? 1 : 0);
+  p->launches += 3;
+  return launched();
+}
+
+// One CG (net == nullptr, flexible == false) or flexible CG iteration on
+// stream s, without host synchronisation.
+nrsense_status cg_iteration(nrsense_plan_s* p, nrsense_c64* x, double lambda, bool flexible,
+                            nrsense_cnn_s* net, cudaStream_t s) {
   nrsense_cg_ws* w = p->cg;
   const long long n = p->geo.nvox;
   NRS_TRY(nrsense_apply_normal(p, w->p, lambda, w->Ep, s));
@@ -289,40 +434,51 @@ nrsense_status cg_iteration(nrsense_plan_s* p, nrsense_c64* x, double lambda, cu
     dot_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(
         reinterpret_cast<const float2*>(w->p), reinterpret_cast<const float2*>(w->Ep), n,
         w->partial);
-    cg_alpha_kernel<<<1, kRedThreads, 0, s>>>(w->partial, kRedBlocks, w->st);
+    cg_alpha_kernel<<<1, kRedThreads, 0, s>>>(w->partial, kRedBlocks, w->st, flexible ? 1 : 0);
     cg_update_xr_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(
         reinterpret_cast<float2*>(x), reinterpret_cast<float2*>(w->r),
         reinterpret_cast<const float2*>(w->p), reinterpret_cast<const float2*>(w->Ep), n, w->st,
         w->partial);
-    cg_beta_kernel<<<1, kRedThreads, 0, s>>>(w->partial, kRedBlocks, w->st, w->hist);
-    cg_update_p_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(reinterpret_cast<const float2*>(w->r),
-                                                          reinterpret_cast<float2*>(w->p), n,
-                                                          w->st);
+    if (!flexible) {
+      cg_beta_kernel<<<1, kRedThreads, 0, s>>>(w->partial, kRedBlocks, w->st, w->hist);
+      cg_update_p_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(reinterpret_cast<const float2*>(w->r),
+                                                            reinterpret_cast<float2*>(w->p), n,
+                                                            w->st);
+    } else {
+      fcg_check_kernel<<<1, kRedThreads, 0, s>>>(w->partial, kRedBlocks, w->st, w->hist);
+    }
     p->launches += 5;
   }
+  if (flexible) NRS_TRY(fcg_direction(p, net, false, s));
   return launched();
 }
 
-nrsense_status read_done(nrsense_plan_s* p, cudaStream_t s, int* done) {
-  CgState h;
-  if (cudaMemcpyAsync(&h, p->cg->st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+nrsense_status read_state(nrsense_plan_s* p, cudaStream_t s, CgState* h) {
+  if (cudaMemcpyAsync(h, p->cg->st, sizeof(*h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return NRSENSE_ERR_CUDA;
-  *done = h.done;
   return NRSENSE_OK;
 }
 
-}  // namespace
+struct Record {
+  nrsense_c64* r;   // capacity x N^3
+  nrsense_c64* e;   // capacity x N^3
+  int capacity;
+  int count;
+};
 
-extern "C" {
+struct SolveOut {
+  int32_t* iters;
+  double* res_hist;
+  double* true_res;
+  int32_t* fallbacks;
+};
 
-nrsense_status nrsense_solve_cg(nrsense_plan_t p, const nrsense_c64* y, double lambda, double tol,
-                                int32_t maxit, uint32_t flags, nrsense_c64* x, int32_t* iters,
-                                double* res_hist, double* true_res, void* stream) {
-  if (p == nullptr || y == nullptr || x == nullptr) return NRSENSE_ERR_ARG;
-  if (maxit < 0 || maxit > (1 << 20) || !(tol >= 0.0) || !(lambda >= 0.0)) return NRSENSE_ERR_ARG;
-  cudaStream_t us = static_cast<cudaStream_t>(stream);
-  NRS_TRY(cg_workspace(p, maxit));
+nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
+                          const nrsense_c64* y, double lambda, double tol, int32_t maxit,
+                          uint32_t flags, nrsense_c64* x, const SolveOut& out, Record* rec,
+                          cudaStream_t us) {
+  NRS_TRY(cg_workspace(p, maxit, flexible));
   nrsense_cg_ws* w = p->cg;
   const long long n = p->geo.nvox;
   const size_t vb = size_t(n) * sizeof(nrsense_c64);
@@ -331,7 +487,7 @@ nrsense_status nrsense_solve_cg(nrsense_plan_t p, const nrsense_c64* y, double l
   if (cudaEventRecord(w->ev0, us) != cudaSuccess || cudaStreamWaitEvent(s, w->ev0, 0) != cudaSuccess)
     return NRSENSE_ERR_CUDA;
 
-  // b = sum_j A_j^H y_j;  r = b - E x0 (or b);  p = r
+  // b = sum_j A_j^H y_j;  r = b - E x0 (or b);  p = r (or z = M(r))
   NRS_TRY(nrsense_apply_adjoint(p, y, w->b, s));
   const bool use_x0 = (flags & NRSENSE_CG_X0) != 0;
   {
@@ -355,17 +511,22 @@ nrsense_status nrsense_solve_cg(nrsense_plan_t p, const nrsense_c64* y, double l
   } else {
     if (cudaMemsetAsync(x, 0, vb, s) != cudaSuccess) return NRSENSE_ERR_CUDA;
   }
-  if (cudaMemcpyAsync(w->p, w->r, vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-    return NRSENSE_ERR_CUDA;
   cg_init_kernel<<<1, kRedThreads, 0, s>>>(w->partial, use_x0 ? w->partial + kRedBlocks : nullptr,
                                            kRedBlocks, tol, maxit, w->st, w->hist);
   p->launches += 1;
   NRS_TRY(launched());
+  if (flexible) {
+    NRS_TRY(fcg_direction(p, net, true, s));
+  } else if (cudaMemcpyAsync(w->p, w->r, vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+    return NRSENSE_ERR_CUDA;
+  }
 
   // iterations, in chunks; the converged flag is read between chunks
-  const int chunk = (flags & NRSENSE_CG_GRAPH) ? std::max(1, std::min<int>(maxit, 10)) : 5;
   const bool graph = (flags & NRSENSE_CG_GRAPH) != 0;
-  if (graph && (w->gexec == nullptr || w->g_x != x || w->g_lambda != lambda || w->g_chunk != chunk)) {
+  const int chunk = rec ? 1 : graph ? std::max(1, std::min<int>(maxit, 10)) : 5;
+  const int mode = flexible ? 1 : 0;
+  if (graph && (w->gexec == nullptr || w->g_x != x || w->g_lambda != lambda ||
+                w->g_chunk != chunk || w->g_mode != mode || w->g_net != net)) {
     if (w->gexec) {
       cudaGraphExecDestroy(w->gexec);
       w->gexec = nullptr;
@@ -374,7 +535,8 @@ nrsense_status nrsense_solve_cg(nrsense_plan_t p, const nrsense_c64* y, double l
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess)
       return NRSENSE_ERR_CUDA;
     nrsense_status cst = NRSENSE_OK;
-    for (int k = 0; k < chunk && cst == NRSENSE_OK; ++k) cst = cg_iteration(p, x, lambda, s);
+    for (int k = 0; k < chunk && cst == NRSENSE_OK; ++k)
+      cst = cg_iteration(p, x, lambda, flexible, net, s);
     const cudaError_t e = cudaStreamEndCapture(s, &gph);
     if (cst != NRSENSE_OK) {
       if (gph) cudaGraphDestroy(gph);
@@ -390,29 +552,46 @@ nrsense_status nrsense_solve_cg(nrsense_plan_t p, const nrsense_c64* y, double l
     w->g_x = x;
     w->g_lambda = lambda;
     w->g_chunk = chunk;
+    w->g_mode = mode;
+    w->g_net = net;
   }
-  int done = 0;
-  for (int it = 0; it < maxit && !done; it += chunk) {
-    NRS_TRY(read_done(p, s, &done));
-    if (done) break;
+  CgState h;
+  for (int it = 0; it < maxit; it += chunk) {
+    NRS_TRY(read_state(p, s, &h));
+    if (h.done) break;
+    if (rec && rec->count < rec->capacity) {
+      // iterate k = it before the update: (r_k, x_k); x_k becomes x* - x_k at exit
+      const size_t off = size_t(rec->count) * size_t(n);
+      if (cudaMemcpyAsync(rec->r + off, w->r, vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+          cudaMemcpyAsync(rec->e + off, x, vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return NRSENSE_ERR_CUDA;
+      rec->count += 1;
+    }
     if (graph) {
       if (cudaGraphLaunch(w->gexec, s) != cudaSuccess) return NRSENSE_ERR_CUDA;
       p->launches += 5LL * chunk;  // approximate: kernels of the captured operator not recounted
     } else {
-      for (int k = 0; k < chunk && it + k < maxit; ++k) NRS_TRY(cg_iteration(p, x, lambda, s));
+      for (int k = 0; k < chunk && it + k < maxit; ++k)
+        NRS_TRY(cg_iteration(p, x, lambda, flexible, net, s));
     }
   }
+  if (rec) {
+    for (int k = 0; k < rec->count; ++k)
+      rsub_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(
+          reinterpret_cast<const float2*>(x),
+          reinterpret_cast<float2*>(rec->e + size_t(k) * size_t(n)), n);
+    p->launches += rec->count;
+    NRS_TRY(launched());
+  }
 
-  CgState h;
-  if (cudaMemcpyAsync(&h, w->st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
+  NRS_TRY(read_state(p, s, &h));
+  if (out.iters) *out.iters = h.iter;
+  if (out.fallbacks) *out.fallbacks = h.n_fb;
+  if (out.res_hist && h.iter + 1 > 0 &&
+      cudaMemcpy(out.res_hist, w->hist, size_t(h.iter + 1) * sizeof(double),
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
     return NRSENSE_ERR_CUDA;
-  if (iters) *iters = h.iter;
-  if (res_hist && h.iter + 1 > 0 &&
-      cudaMemcpy(res_hist, w->hist, size_t(h.iter + 1) * sizeof(double), cudaMemcpyDeviceToHost) !=
-          cudaSuccess)
-    return NRSENSE_ERR_CUDA;
-  if (true_res) {
+  if (out.true_res) {
     // true residual ||b - E x|| / ||b||, recomputed once
     NRS_TRY(nrsense_apply_normal(p, x, lambda, w->Ep, s));
     sub_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(reinterpret_cast<float2*>(w->b),
@@ -429,7 +608,7 @@ nrsense_status nrsense_solve_cg(nrsense_plan_t p, const nrsense_c64* y, double l
     for (int i = 0; i < kRedBlocks; ++i) acc += hp[i];
     delete[] hp;
     if (!ok) return NRSENSE_ERR_CUDA;
-    *true_res = h.bb > 0.0 ? std::sqrt(acc / h.bb) : 0.0;
+    *out.true_res = h.bb > 0.0 ? std::sqrt(acc / h.bb) : 0.0;
   }
   // order the caller's stream after the solve
   if (cudaEventRecord(w->ev1, s) != cudaSuccess || cudaStreamWaitEvent(us, w->ev1, 0) != cudaSuccess)
@@ -437,6 +616,52 @@ nrsense_status nrsense_solve_cg(nrsense_plan_t p, const nrsense_c64* y, double l
   if (h.status != NRSENSE_OK) return h.status;
   if (h.rr > h.tol2 && h.bb > 0.0) return NRSENSE_ERR_NOT_CONVERGED;
   return NRSENSE_OK;
+}
+
+bool solve_args_ok(nrsense_plan_t p, const nrsense_c64* y, nrsense_c64* x, double lambda,
+                   double tol, int32_t maxit) {
+  return p != nullptr && y != nullptr && x != nullptr && maxit >= 0 && maxit <= (1 << 20) &&
+         tol >= 0.0 && lambda >= 0.0 && std::isfinite(tol) && std::isfinite(lambda);
+}
+
+}  // namespace
+
+extern "C" {
+
+nrsense_status nrsense_solve_cg(nrsense_plan_t p, const nrsense_c64* y, double lambda, double tol,
+                                int32_t maxit, uint32_t flags, nrsense_c64* x, int32_t* iters,
+                                double* res_hist, double* true_res, void* stream) {
+  if (!solve_args_ok(p, y, x, lambda, tol, maxit)) return NRSENSE_ERR_ARG;
+  const SolveOut out{iters, res_hist, true_res, nullptr};
+  return solve_impl(p, false, nullptr, y, lambda, tol, maxit, flags, x, out, nullptr,
+                    static_cast<cudaStream_t>(stream));
+}
+
+nrsense_status nrsense_solve_cg_record(nrsense_plan_t p, const nrsense_c64* y, double lambda,
+                                       double tol, int32_t maxit, uint32_t flags, nrsense_c64* x,
+                                       int32_t* iters, double* res_hist, double* true_res,
+                                       nrsense_c64* rec_r, nrsense_c64* rec_e, int32_t capacity,
+                                       int32_t* rec_count, void* stream) {
+  if (!solve_args_ok(p, y, x, lambda, tol, maxit) || (flags & NRSENSE_CG_GRAPH) || capacity < 0 ||
+      (capacity > 0 && (rec_r == nullptr || rec_e == nullptr)) || rec_count == nullptr)
+    return NRSENSE_ERR_ARG;
+  Record rec{rec_r, rec_e, capacity, 0};
+  const SolveOut out{iters, res_hist, true_res, nullptr};
+  const nrsense_status st = solve_impl(p, false, nullptr, y, lambda, tol, maxit, flags, x, out,
+                                       &rec, static_cast<cudaStream_t>(stream));
+  *rec_count = rec.count;
+  return st;
+}
+
+nrsense_status nrsense_solve_fcg(nrsense_plan_t p, nrsense_cnn_t net, const nrsense_c64* y,
+                                 double lambda, double tol, int32_t maxit, uint32_t flags,
+                                 nrsense_c64* x, int32_t* iters, double* res_hist,
+                                 double* true_res, int32_t* fallbacks, void* stream) {
+  if (!solve_args_ok(p, y, x, lambda, tol, maxit)) return NRSENSE_ERR_ARG;
+  if (net && !cnn_shape_matches(net, p->geo.n0, p->geo.n1, p->geo.n2)) return NRSENSE_ERR_ARG;
+  const SolveOut out{iters, res_hist, true_res, fallbacks};
+  return solve_impl(p, true, net, y, lambda, tol, maxit, flags, x, out, nullptr,
+                    static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -72,11 +72,37 @@ _SIGS = {
     "nrsense_solve_cg": [_VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                          ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_int32),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _VP],
+    "nrsense_solve_cg_record": [_VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                _VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _VP],
+    "nrsense_solve_fcg": [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                          ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_int32),
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_int32), _VP],
+    "nrsense_cnn_create": [ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32, _VP,
+                           ctypes.POINTER(_VP)],
+    "nrsense_cnn_destroy": [_VP],
+    "nrsense_cnn_num_params": [],
+    "nrsense_cnn_init_params": [_VP, ctypes.c_uint64, _VP],
+    "nrsense_cnn_set_params": [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, _VP],
+    "nrsense_cnn_get_params": [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, _VP],
+    "nrsense_cnn_apply": [_VP, _VP, _VP, _VP],
+    "nrsense_cnn_gradients": [_VP, _VP, ctypes.c_double, _VP, _VP, ctypes.c_int32,
+                              ctypes.POINTER(ctypes.c_double), _VP],
+    "nrsense_cnn_get_grads": [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, _VP],
+    "nrsense_cnn_adam_step": [_VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, ctypes.c_uint32, _VP],
+    "nrsense_cnn_launches": [_VP, ctypes.POINTER(ctypes.c_int64)],
 }
 CG_X0 = 1
 CG_GRAPH = 2
-NUM_STAGES = 13
+NUM_STAGES = 14
 _STRING_RESULT = ("nrsense_status_string", "nrsense_stage_name")
+_INT64_RESULT = ("nrsense_cnn_num_params",)
+CNN_CHANNELS = (2, 16, 16, 16, 16, 2)
+CNN_FREEZE_BIAS = 1
+CNN_SYMMETRIC = 1
 
 _lib = None
 
@@ -93,7 +119,8 @@ def load(path: str | None = None):
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name in _STRING_RESULT else ctypes.c_int32
+        fn.restype = (ctypes.c_char_p if name in _STRING_RESULT else
+                      ctypes.c_int64 if name in _INT64_RESULT else ctypes.c_int32)
     if path is None:
         _lib = lib
     return lib
@@ -341,6 +368,176 @@ class Plan:
             _check(code, "nrsense_solve_cg")
         return x, it.value, list(hist[: it.value + 1]), tres.value, code
 
+    def _x_for(self, x0, out):
+        import torch
+        if x0 is not None:
+            _need(x0, torch.complex64, self.shape, "x0")
+            if out is not None and out.data_ptr() != x0.data_ptr():
+                out.copy_(x0)
+                return out
+            return x0
+        return self._img() if out is None else _need(out, torch.complex64, self.shape, "out")
+
+    def solve_cg_record(self, y, lam, capacity, tol=1e-4, maxit=100, x0=None, stream=None,
+                        check=True):
+        """Plain CG that records training pairs of the preconditioner: for
+        k < capacity, r_k (recursive residual) and e_k = x_final - x_k.
+
+        Returns (x, iterations, residual history, true relative residual,
+        status code, r (K, *shape), e (K, *shape)) with K pairs recorded."""
+        import torch
+        _need(y, torch.complex64, self.forward_shape(), "y")
+        x = self._x_for(x0, None)
+        cap = int(capacity)
+        rec_r = torch.empty((max(cap, 1),) + self.shape, dtype=torch.complex64, device=y.device)
+        rec_e = torch.empty_like(rec_r)
+        it, cnt = ctypes.c_int32(), ctypes.c_int32()
+        hist = (ctypes.c_double * (int(maxit) + 1))()
+        tres = ctypes.c_double()
+        flags = CG_X0 if x0 is not None else 0
+        code = self.lib.nrsense_solve_cg_record(
+            self._h, _ptr(y), float(lam), float(tol), int(maxit), flags, _ptr(x),
+            ctypes.byref(it), hist, ctypes.byref(tres), _ptr(rec_r), _ptr(rec_e), cap,
+            ctypes.byref(cnt), _stream(stream))
+        if check and code not in (OK, -6):
+            _check(code, "nrsense_solve_cg_record")
+        k = cnt.value
+        return (x, it.value, list(hist[: it.value + 1]), tres.value, code, rec_r[:k], rec_e[:k])
+
+    def solve_fcg(self, y, lam, net=None, tol=1e-4, maxit=100, x0=None, graph=False, stream=None,
+                  check=True, out=None):
+        """Flexible CG preconditioned by the network `net` (a Cnn, or None).
+
+        Returns (x, iterations, residual history, true relative residual,
+        status code, fallbacks)."""
+        import torch
+        _need(y, torch.complex64, self.forward_shape(), "y")
+        x = self._x_for(x0, out)
+        it, fb = ctypes.c_int32(), ctypes.c_int32()
+        hist = (ctypes.c_double * (int(maxit) + 1))()
+        tres = ctypes.c_double()
+        flags = (CG_X0 if x0 is not None else 0) | (CG_GRAPH if graph else 0)
+        code = self.lib.nrsense_solve_fcg(
+            self._h, None if net is None else net._h, _ptr(y), float(lam), float(tol), int(maxit),
+            flags, _ptr(x), ctypes.byref(it), hist, ctypes.byref(tres), ctypes.byref(fb),
+            _stream(stream))
+        if check and code not in (OK, -6):
+            _check(code, "nrsense_solve_fcg")
+        return x, it.value, list(hist[: it.value + 1]), tres.value, code, fb.value
+
     def phase_slice(self, y, j):
         """Rows of phase j in a stacked (sum M_j, C) k-space array."""
         return y[int(self.offsets[j]):int(self.offsets[j + 1])]
+
+
+class Cnn:
+    """Preconditioner network M of flexible CG (include/nrsense.h,
+    nrsense_cnn_*): 3x3x3 convolutions 2 -> 16 -> 16 -> 16 -> 16 -> 2 with
+    ReLU between, residual output, BF16 tensor-core kernels.  symmetric=True
+    (the default) selects z = u0 + N^T N u0 (symmetric positive definite for
+    fixed ReLU masks, biases unused); False the plain z = u0 + N(u0)."""
+
+    def __init__(self, shape, seed=None, symmetric=True, stream=None):
+        self.lib = load()
+        self.shape = tuple(int(v) for v in shape)
+        self.symmetric = bool(symmetric)
+        n = (ctypes.c_int32 * 3)(*self.shape)
+        h = ctypes.c_void_p()
+        _check(self.lib.nrsense_cnn_create(n, CNN_SYMMETRIC if symmetric else 0, _stream(stream),
+                                           ctypes.byref(h)),
+               "nrsense_cnn_create")
+        self._h = h
+        self.n_params = int(self.lib.nrsense_cnn_num_params())
+        if seed is not None:
+            self.init(seed, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.nrsense_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, seed, stream=None):
+        _check(self.lib.nrsense_cnn_init_params(self._h, int(seed), _stream(stream)),
+               "nrsense_cnn_init_params")
+
+    @staticmethod
+    def flatten(params):
+        """[(W (cout, cin, 3, 3, 3), b (cout)), ...] -> flat float32 array."""
+        return np.concatenate([np.concatenate([np.asarray(w, np.float32).ravel(),
+                                               np.asarray(b, np.float32).ravel()])
+                               for w, b in params])
+
+    @staticmethod
+    def unflatten(flat):
+        out, k = [], 0
+        for cin, cout in zip(CNN_CHANNELS[:-1], CNN_CHANNELS[1:]):
+            nw = cout * cin * 27
+            out.append((flat[k:k + nw].reshape(cout, cin, 3, 3, 3).copy(),
+                        flat[k + nw:k + nw + cout].copy()))
+            k += nw + cout
+        return out
+
+    def set_params(self, params, stream=None):
+        flat = np.ascontiguousarray(self.flatten(params) if not isinstance(params, np.ndarray)
+                                    else params, dtype=np.float32)
+        if flat.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {flat.size}")
+        fp = flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        _check(self.lib.nrsense_cnn_set_params(self._h, fp, flat.size, _stream(stream)),
+               "nrsense_cnn_set_params")
+
+    def _download(self, fn, where, stream):
+        flat = np.empty(self.n_params, np.float32)
+        fp = flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        _check(fn(self._h, fp, flat.size, _stream(stream)), where)
+        return flat
+
+    def get_params(self, stream=None):
+        return self.unflatten(self._download(self.lib.nrsense_cnn_get_params,
+                                             "nrsense_cnn_get_params", stream))
+
+    def get_grads(self, stream=None):
+        return self.unflatten(self._download(self.lib.nrsense_cnn_get_grads,
+                                             "nrsense_cnn_get_grads", stream))
+
+    def apply(self, r, out=None, stream=None):
+        import torch
+        _need(r, torch.complex64, self.shape, "r")
+        z = torch.empty_like(r) if out is None else _need(out, torch.complex64, self.shape, "out")
+        _check(self.lib.nrsense_cnn_apply(self._h, _ptr(r), _ptr(z), _stream(stream)),
+               "nrsense_cnn_apply")
+        return z
+
+    def gradients(self, r, e, accumulate=False, want_loss=True, plan=None, lam=0.0, stream=None):
+        """Forward + backward for one pair; returns the loss (or None).
+        plan=None: cosine loss; a Plan: energy loss with E = normal(., lam)."""
+        import torch
+        _need(r, torch.complex64, self.shape, "r")
+        _need(e, torch.complex64, self.shape, "e")
+        loss = ctypes.c_double()
+        _check(self.lib.nrsense_cnn_gradients(self._h, None if plan is None else plan._h,
+                                              float(lam), _ptr(r), _ptr(e),
+                                              1 if accumulate else 0,
+                                              ctypes.byref(loss) if want_loss else None,
+                                              _stream(stream)),
+               "nrsense_cnn_gradients")
+        return loss.value if want_loss else None
+
+    def adam_step(self, lr, grad_scale=1.0, beta1=0.9, beta2=0.999, eps=1e-8, freeze_bias=False,
+                  stream=None):
+        _check(self.lib.nrsense_cnn_adam_step(self._h, float(lr), float(grad_scale), float(beta1),
+                                              float(beta2), float(eps),
+                                              CNN_FREEZE_BIAS if freeze_bias else 0,
+                                              _stream(stream)),
+               "nrsense_cnn_adam_step")
+
+    def launches(self):
+        v = ctypes.c_int64()
+        _check(self.lib.nrsense_cnn_launches(self._h, ctypes.byref(v)), "nrsense_cnn_launches")
+        return v.value
