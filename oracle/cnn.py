@@ -183,45 +183,56 @@ def loss_and_grads_energy(params, r, e, E, rnd=_identity):
 
 
 # ---------------------------------------------------------------------------
-# Symmetric form.  The same five layers (biases unused) define a map N with
-# ReLU masks D_l set by the forward pass, and the network returns
-#   z = u0 + N^T (N u0),   N = W_5 D_4 W_4 D_3 W_3 D_2 W_2 D_1 W_1,
-# i.e. for fixed masks z = (I + J^T J) u0 with J the Jacobian of N: a symmetric
+# Symmetric form.  The same five layers (biases unused): N4 = D_4 W_4 D_3 W_3
+# D_2 W_2 D_1 W_1 maps u0 to the 16-channel h_4 (ReLU masks D_l set by the
+# forward pass) and W_5 maps h_4 to 2 channels.  The network returns
+#   z = u0 + N4^T (I + W_5^T W_5) N4 u0,
+# i.e. z = (I + A^T A) u0 with A = [N4; W_5 N4] for fixed masks: a symmetric
 # positive definite map, as CG-type methods expect of a preconditioner.
+# (With W_5 = 0 and first-layer +-finite differences it is I - c Laplacian.)
 
 def forward_spd(params, r, rnd=_identity):
     """z of the symmetric form and the intermediates backward_spd needs."""
     s = input_scale(r)
     u0 = np.stack([r.real, r.imag]) / s
+    L = len(params)
     h = [rnd(u0)]
-    for l, (w, _) in enumerate(params):
-        y = conv3d(h[-1], w, np.zeros(w.shape[0]))
-        h.append(rnd(np.maximum(y, 0.0)) if l < len(params) - 1 else rnd(y))
-    # transposed chain: u_l = D_l W_{l+1}^T u_{l+1}, u_5 = h_5
-    u = [None] * len(params) + [h[-1]]
-    for l in range(len(params) - 1, 0, -1):
+    for l in range(L - 1):
+        w = params[l][0]
+        h.append(rnd(np.maximum(conv3d(h[-1], w, np.zeros(w.shape[0])), 0.0)))
+    w5 = params[L - 1][0]
+    t5 = rnd(conv3d(h[L - 1], w5, np.zeros(w5.shape[0])))
+    # middle: m = h_4 + W_5^T t5, masked by D_4 (h_4 is zero where D_4 is)
+    u = [None] * L
+    u[L - 1] = rnd(h[L - 1] + conv3d_transpose(t5, w5) * (h[L - 1] > 0))
+    # transposed chain: u_l = D_l W_{l+1}^T u_{l+1}, o = W_1^T u_1
+    for l in range(L - 2, 0, -1):
         u[l] = rnd(conv3d_transpose(u[l + 1], params[l][0]) * (h[l] > 0))
     o = conv3d_transpose(u[1], params[0][0])
     zc = u0 + o
-    return zc[0] + 1j * zc[1], (h, u)
+    return zc[0] + 1j * zc[1], (h, u, t5)
 
 
 def backward_spd(params, inter, dz, rnd=_identity):
     """Weight gradients of the symmetric form given dL/dz (biases: zero)."""
-    h, u = inter
+    h, u, t5 = inter
     L = len(params)
     gw = [np.zeros_like(w) for w, _ in params]
-    # through the transposed chain: o = W_1^T u_1, u_l = D_l W_{l+1}^T u_{l+1}
+    zero = lambda w: np.zeros(w.shape[0])
+    # adjoint of the transposed chain o = W_1^T u_1, u_l = D_l W_{l+1}^T u_{l+1}
     g = rnd(np.stack([dz.real, dz.imag]))
-    for l in range(L):
-        # o_l = W_{l+1}^T u_{l+1} with upstream g: dW = correlation of u_{l+1} and g
-        _, dw, _ = conv3d_backward(g, params[l][0], u[l + 1])
-        gw[l] += dw
-        y = conv3d(g, params[l][0], np.zeros(params[l][0].shape[0]))
-        g = rnd(y * (h[l + 1] > 0)) if l < L - 1 else rnd(y)
-    # g is now dL/dh_5: back through the forward chain h_l = D_l W_l h_{l-1}
-    for l in range(L - 1, -1, -1):
-        if l < L - 1:
+    for l in range(L - 1):
+        w = params[l][0]
+        gw[l] += conv3d_backward(g, w, u[l + 1])[1]
+        g = rnd(conv3d(g, w, zero(w)) * (h[l + 1] > 0))
+    # g = dL/dm (masked).  m = h_4 + W_5^T W_5 h_4:
+    w5 = params[L - 1][0]
+    q = rnd(conv3d(g, w5, zero(w5)))
+    gw[L - 1] += conv3d_backward(h[L - 1], w5, q)[1] + conv3d_backward(g, w5, t5)[1]
+    g = rnd(g + conv3d_transpose(q, w5) * (h[L - 1] > 0))   # D_4 dL/dh_4
+    # back through the forward chain h_l = D_l W_l h_{l-1}, l = 4 .. 1
+    for l in range(L - 2, -1, -1):
+        if l < L - 2:
             g = rnd(g * (h[l + 1] > 0))
         gx, dw, _ = conv3d_backward(h[l], params[l][0], g)
         gw[l] += dw

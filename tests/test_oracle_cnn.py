@@ -173,33 +173,71 @@ def test_conv3d_transpose_is_adjoint():
 
 
 def test_symmetric_form_is_spd_for_fixed_masks():
-    # with every mask fixed the map r -> z * s is (I + J^T J): check
-    # symmetry and positivity through a linear network (no ReLU effect:
-    # weights chosen so every hidden activation is positive for these inputs)
+    # with the masks of one forward pass held fixed, u0 -> o is a linear map;
+    # build its dense matrix column by column and check I + matrix is
+    # symmetric with eigenvalues >= 1
     rng = _rng(12)
     params = cnn.init_params(13)
     shape = (4, 4, 4)
-    # a network whose hidden layers see only positive inputs is linear: use
-    # |W| for the hidden layers and positive inputs
-    params = [(np.abs(w) if l in (1, 2, 3) else w, b) for l, (w, b) in enumerate(params)]
-    z1, (h, _) = cnn.forward_spd(params, np.ones(shape) + 0j)
-    # directional check with the dense Jacobian of o = N^T N u0 at fixed masks
-    n = 2 * int(np.prod(shape))
+    r = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    _, (h, _, _) = cnn.forward_spd(params, r)
+    L = len(params)
+    zero = lambda w: np.zeros(w.shape[0])
 
     def o_of(u0):
-        hh = [u0]
-        for l, (w, _) in enumerate(params):
-            y = cnn.conv3d(hh[-1], w, np.zeros(w.shape[0]))
-            hh.append(y * (h[l + 1] > 0) if l < len(params) - 1 else y)
-        u = hh[-1]
-        for l in range(len(params) - 1, 0, -1):
+        hh = u0
+        for l in range(L - 1):
+            hh = cnn.conv3d(hh, params[l][0], zero(params[l][0])) * (h[l + 1] > 0)
+        w5 = params[L - 1][0]
+        u = hh + cnn.conv3d_transpose(cnn.conv3d(hh, w5, zero(w5)), w5) * (h[L - 1] > 0)
+        for l in range(L - 2, 0, -1):
             u = cnn.conv3d_transpose(u, params[l][0]) * (h[l] > 0)
         return cnn.conv3d_transpose(u, params[0][0])
 
+    n = 2 * int(np.prod(shape))
     basis = np.eye(n).reshape(n, 2, *shape)
     M = np.stack([o_of(b).ravel() for b in basis], axis=1) + np.eye(n)
     assert np.allclose(M, M.T, atol=1e-10)
     assert np.linalg.eigvalsh(M).min() >= 1.0 - 1e-10
+    # the forward pass is this map applied to u0 = r / s (masks consistent)
+    z, _ = cnn.forward_spd(params, r)
+    u0 = np.stack([r.real, r.imag]) / cnn.input_scale(r)
+    zz = (M @ u0.ravel()).reshape(u0.shape)
+    assert np.allclose(z, zz[0] + 1j * zz[1], atol=1e-10)
+
+
+def test_symmetric_form_contains_the_laplacian():
+    # first layer +-central differences, identity hidden layers, W_5 = 0:
+    # z = u0 + c (-Laplacian_2h) u0 with the wide (2h) central stencil
+    shape = (6, 5, 7)
+    rng = _rng(16)
+    params = []
+    for cin, cout in zip(cnn.CHANNELS[:-1], cnn.CHANNELS[1:]):
+        params.append((np.zeros((cout, cin, 3, 3, 3)), np.zeros(cout)))
+    w1 = params[0][0]
+    for a in range(3):
+        for comp in range(2):
+            ch = 4 * a + 2 * comp
+            idx_p = [1, 1, 1]
+            idx_m = [1, 1, 1]
+            idx_p[a], idx_m[a] = 2, 0
+            w1[ch, comp][tuple(idx_p)], w1[ch, comp][tuple(idx_m)] = 0.5, -0.5
+            w1[ch + 1, comp][tuple(idx_p)], w1[ch + 1, comp][tuple(idx_m)] = -0.5, 0.5
+    for l in (1, 2, 3):
+        for ch in range(12):
+            params[l][0][ch, ch, 1, 1, 1] = 1.0
+    r = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    z, _ = cnn.forward_spd(params, r)
+    u0 = r / cnn.input_scale(r)
+    # -sum_a D_a^T D_a u0 with D_a the central difference (zero padding)
+    def dc(v, a):
+        p = np.pad(v, 1)
+        sl_p = [slice(1, -1)] * 3
+        sl_m = [slice(1, -1)] * 3
+        sl_p[a], sl_m[a] = slice(2, None), slice(0, -2)
+        return 0.5 * (p[tuple(sl_p)] - p[tuple(sl_m)])
+    ref = u0 + sum(-dc(dc(u0, a), a) for a in range(3))
+    assert np.allclose(z, ref, atol=1e-12)
 
 
 def test_symmetric_form_gradients_finite_differences():
