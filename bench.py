@@ -211,6 +211,144 @@ def oracle_cost(w, frac=1.0 / 32, seed=0):
 # GPU leg
 # --------------------------------------------------------------------------
 
+def _lambda_max(plan, shape, dev, iters=20, seed=4):
+    import torch
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    v = torch.randn(shape, dtype=torch.complex64, device=dev, generator=gen)
+    lam = 0.0
+    for _ in range(iters):
+        w = plan.normal(v, 0.0)
+        lam = float(torch.linalg.norm(w) / torch.linalg.norm(v))
+        v = w / torch.linalg.norm(w)
+    return lam
+
+
+def _noisy(plan, x, gen, snr_scale=0.03):
+    import torch
+    y = plan.forward(x)
+    return y + snr_scale * float(y.abs().max()) * torch.randn(
+        y.shape, dtype=torch.complex64, device=y.device, generator=gen)
+
+
+def _timed_solve(fn):
+    """Solve once to warm (graph capture), then time one solve with CUDA events."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    res = fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return res, e0.elapsed_time(e1)
+
+
+def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, seed=5):
+    """Plain CG and flexible CG with `net` to tol on y = A x + noise,
+    lambda = rel_lambda * lambda_max (power iteration); both captured as CUDA
+    graphs (10 iterations per graph launch)."""
+    import torch
+    lam_max = _lambda_max(plan, shape, dev)
+    lam = rel_lambda * lam_max
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    y = _noisy(plan, x, gen)
+    out = torch.empty(shape, dtype=torch.complex64, device=dev)
+    (cg, ms_cg) = _timed_solve(lambda: plan.solve_cg(y, lam, tol=tol, maxit=maxit, graph=True,
+                                                     out=out))
+    x_cg = out.clone()
+    (fcg, ms_f) = _timed_solve(lambda: plan.solve_fcg(y, lam, net, tol=tol, maxit=maxit,
+                                                      graph=True, out=out))
+    diff = float((out - x_cg).norm() / x_cg.norm())
+    return {"tol": tol, "lambda": lam, "lambda_rel": rel_lambda, "lambda_max": lam_max,
+            "plain": {"iters": cg[1], "ms": round(ms_cg, 2), "true_res": cg[3]},
+            "fcg": {"iters": fcg[1], "ms": round(ms_f, 2), "true_res": fcg[3],
+                    "fallbacks": fcg[5]},
+            "speedup": round(ms_cg / ms_f, 3), "solution_rel_diff": diff}
+
+
+def run_precond(args):
+    """Learned preconditioner end to end on the 128^3 8-coil 4-phase geometry:
+    training pairs from plain-CG runs on random right-hand sides, training on
+    the GPU (symmetric form, cosine loss; one network from a random start, one
+    from the Laplacian construction; blocks kept by flexible-CG iterations on
+    a held-out problem), then plain CG vs flexible CG on the phantom data."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2501_16713_gb300 import Cnn, Plan, build, precond
+
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = synth.workload("sense128")
+    shape = w["spec"].shape
+    plan = Plan(shape, disp=torch.from_numpy(np.stack(w["disp"])).to(dev),
+                coords=[torch.from_numpy(c).to(dev) for c in w["coords"]],
+                smaps=torch.from_numpy(w["smaps"]).to(dev))
+    x = torch.from_numpy(w["x"]).to(dev)
+    lam = 1e-3 * _lambda_max(plan, shape, dev)
+    gen = torch.Generator(device=dev).manual_seed(40)
+
+    def rhs(i):
+        xr = torch.randn(shape, dtype=torch.complex64, device=dev, generator=gen)
+        for _ in range(i % 4):
+            for ax in range(3):
+                xr = 0.5 * xr + 0.25 * (torch.roll(xr, 1, ax) + torch.roll(xr, -1, ax))
+        return _noisy(plan, xr, gen)
+
+    t0 = time.perf_counter()
+    rs, es, iters = [], [], []
+    for i in range(args.pair_runs):
+        r, e, it = precond.generate_pairs(plan, [rhs(i)], lam, tol=1e-5, maxit=500, per_run=60)
+        rs.append(r[::2].clone())
+        es.append(e[::2].clone())
+        iters += it
+        del r, e
+    r = torch.cat(rs)
+    e = torch.cat(es)
+    del rs, es
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    y_val = rhs(1)
+    score = lambda net: precond.fcg_iterations(plan, y_val, lam, net)
+    blocks = [(300, 1e-3, 3e-4), (300, 3e-4, 1e-4), (300, 1e-4, 3e-5)]
+    t1 = time.perf_counter()
+    nets = {}
+    for name in ("random_init", "laplacian_init"):
+        net = Cnn(shape, seed=1)
+        if name == "laplacian_init":
+            net.set_params(precond.laplacian_params(args.lap_c))
+        hist = precond.train_select(net, r, e, blocks, score)
+        nets[name] = (net, hist)
+    t_train = time.perf_counter() - t1
+    res = {}
+    for name, (net, hist) in nets.items():
+        res[name] = {"selection": [{"block": b, "loss": (None if l != l else round(l, 4)),
+                                    "val_iters": sc} for b, l, sc in hist],
+                     **cg_compare(plan, x, shape, dev, net)}
+    best = min(res, key=lambda k: res[k]["fcg"]["ms"])
+    cmp = res[best]
+    line = {"metric": "CG time to 1e-4 relative residual (flexible CG + learned preconditioner)",
+            "value": cmp["fcg"]["ms"], "unit": "ms", "higher_is_better": False,
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": cmp["fcg"]["ms"],
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 operator, bf16 network",
+            "data": "synthetic (seeded phantom, random right-hand sides for training)",
+            "config": {"workload": "precond128", "image": list(shape), "coils": w["spec"].n_coils,
+                       "phases": len(w["coords"]), "lambda_rel": 1e-3,
+                       "pairs": int(r.shape[0]), "pair_runs": args.pair_runs,
+                       "pair_run_iters": iters, "pairs_s": round(t_pairs, 1),
+                       "train_s": round(t_train, 1), "blocks": blocks,
+                       "network": "symmetric form z = u0 + N4^T (I + W5^T W5) N4 u0, "
+                                  "5 conv 3x3x3, 2-16-16-16-16-2, BF16",
+                       "laplacian_c": args.lap_c, "selected": best},
+            "plain_ms": cmp["plain"]["ms"], "speedup_vs_plain": cmp["speedup"],
+            "results": res}
+    plan.close()
+    return line
+
+
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -286,6 +424,18 @@ def run_gpu(args, rank, world, local_rank):
     ms_adj = e0.elapsed_time(e1) / 3
     del y
 
+    # CG to 1e-4 relative residual: plain vs flexible CG (Laplacian-initialised
+    # symmetric network, untrained); outside the timed region
+    cg = None
+    if world == 1 and not args.no_cg:
+        from paper_2501_16713_gb300 import Cnn, precond
+        net = Cnn(shape)
+        net.set_params(precond.laplacian_params(args.lap_c))
+        cg = cg_compare(plan, x, shape, dev, net)
+        cg["network"] = (f"symmetric form, Laplacian construction c={args.lap_c}, untrained "
+                         "(bench.py --workload precond128 trains)")
+        net.close()
+
     # end to end through the public API with host buffers
     xh = torch.from_numpy(w["x"]).pin_memory()
     oh = torch.empty(shape, dtype=torch.complex64).pin_memory()
@@ -354,6 +504,7 @@ def run_gpu(args, rank, world, local_rank):
         "forward_ms": round(ms_fwd, 3), "adjoint_ms": round(ms_adj, 3),
         "breakdown": breakdown,
         "clocks": clk,
+        "cg": cg,
     }
     plan.close()
     return result, w
@@ -370,8 +521,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phases", type=int, default=None,
                     help="use only the first K phases (a smaller case for profiling)")
+    ap.add_argument("--no-cg", action="store_true", help="skip the CG comparison")
+    ap.add_argument("--lap-c", type=float, default=30.0)
+    ap.add_argument("--pair-runs", type=int, default=70)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+
+    if args.workload == "precond128" and args.impl == "ours":
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps(run_precond(args)), flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -380,6 +539,10 @@ def main():
     if args.impl == "reference":
         # the oracle on the host cores; rank 0 only
         if rank != 0:
+            return
+        if args.workload == "precond128":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the learned-preconditioner workload has no CPU reference arm"}))
             return
         import synth
         w = synth.workload(args.workload)

@@ -269,16 +269,17 @@ nrsense_status nrsense_solve_fcg(nrsense_plan_t plan, nrsense_cnn_t net, const n
  *
  * nrsense_cnn_create     network for images of shape n_host[3] (each 1..4096),
  *                        all parameters zero; allocates its activations
- *                        (7 x 32 bytes + 8 bytes per voxel, 12 x 32 + 8 in the
+ *                        (7 x 32 bytes + 8 bytes per voxel, 13 x 32 + 8 in the
  *                        symmetric form); synchronises stream.  flags:
  *                        NRSENSE_CNN_SYMMETRIC selects the symmetric form
- *                          z = u0 + N^T N u0,
- *                        N = W_5 D_4 W_4 D_3 W_3 D_2 W_2 D_1 W_1 the same five
- *                        convolutions without biases, D_l the ReLU masks of the
- *                        forward pass, N^T the transposed convolutions in
- *                        reverse order with the same masks: for fixed masks
- *                        z = (I + J^T J) u0 is symmetric positive definite in
- *                        u0, as CG-type methods expect of a preconditioner.
+ *                          z = u0 + N4^T (I + W5^T W5) N4 u0,
+ *                        N4 = D_4 W_4 D_3 W_3 D_2 W_2 D_1 W_1 the first four
+ *                        convolutions without biases (D_l: ReLU masks of the
+ *                        forward pass), W_5 the fifth, ^T the transposed
+ *                        convolutions in reverse order with the same masks: for
+ *                        fixed masks z = (I + A^T A) u0, A = [N4; W_5 N4],
+ *                        symmetric positive definite in u0, as CG-type methods
+ *                        expect of a preconditioner.
  *                        Biases are ignored and never updated in this form.
  * nrsense_cnn_init_params He initialisation from a seeded generator
  *                        (splitmix64 + Box-Muller), last layer scaled by 0.1,

@@ -73,7 +73,10 @@ struct Scalars {
   double k1, k2;   // dL/dz = k2 z - k1 e
 };
 
-enum Epilogue { kReluBf16 = 0, kMaskBf16 = 1, kResidualC64 = 2, kLinearBf16 = 3 };
+// kReluBf16: relu(acc + b); kMaskBf16: acc where mask > 0, else 0;
+// kResidualC64: z = u0 + acc (channels 0, 1); kLinearBf16: acc + b;
+// kAddMaskBf16: addend + (acc where mask > 0, else 0)
+enum Epilogue { kReluBf16 = 0, kMaskBf16 = 1, kResidualC64 = 2, kLinearBf16 = 3, kAddMaskBf16 = 4 };
 
 struct ConvArgs {
   Vol v;
@@ -81,7 +84,8 @@ struct ConvArgs {
   const bf16* wpk;      // [27][16][kVS] packed weights
   const float* bias;    // [16] or null
   int epi;
-  const bf16* mask;     // kMaskBf16: ReLU mask source [n][16]
+  const bf16* mask;     // kMaskBf16 / kAddMaskBf16: ReLU mask source [n][16]
+  const bf16* addend;   // kAddMaskBf16: [n][16]
   bf16* out;            // kReluBf16 / kMaskBf16 output [n][16]
   const float2* r;      // kResidualC64: network input residual
   const Scalars* sc;
@@ -237,10 +241,16 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_kernel(ConvArgs a) {
         if (a.epi == kReluBf16) {
           f0 = fmaxf(f0, 0.f);
           f1 = fmaxf(f1, 0.f);
-        } else if (a.epi == kMaskBf16) {
+        } else if (a.epi == kMaskBf16 || a.epi == kAddMaskBf16) {
           const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + vox * kCh + o);
           f0 = __bfloat162float(mk.x) > 0.f ? f0 : 0.f;
           f1 = __bfloat162float(mk.y) > 0.f ? f1 : 0.f;
+          if (a.epi == kAddMaskBf16) {
+            const __nv_bfloat162 ad =
+                *reinterpret_cast<const __nv_bfloat162*>(a.addend + vox * kCh + o);
+            f0 += __bfloat162float(ad.x);
+            f1 += __bfloat162float(ad.y);
+          }
         }
         *reinterpret_cast<__nv_bfloat162*>(a.out + vox * kCh + o) = __floats2bfloat162_rn(f0, f1);
       }
@@ -554,9 +564,9 @@ struct nrsense_cnn_s {
   int device = 0;
   int wg_grid = 0;
   bf16* act[kLayers] = {};  // a0 .. a4 (inference uses a0, a1 as ping-pong)
-  bf16* gb[2] = {};         // gradient ping-pong
-  bool spd = false;         // symmetric form z = u0 + N^T N u0
-  bf16* h5 = nullptr;       // symmetric form: N u0 (2 channels, padded)
+  bf16* gb[3] = {};         // gradient ping-pong (+ one more in the symmetric form)
+  bool spd = false;         // symmetric form z = u0 + N4^T (I + W5^T W5) N4 u0
+  bf16* h5 = nullptr;       // symmetric form: t5 = W5 h4 (2 channels, padded)
   bf16* ut[4] = {};         // symmetric form: transposed chain u_1 .. u_4
   float2* zbuf = nullptr;   // training forward output
   float2* ezbuf = nullptr;  // E z for the energy loss (allocated on first use)
@@ -586,8 +596,9 @@ nrsense_status cuda_ok() {
 }
 
 void conv(nrsense_cnn_s* net, int layer, bool backward, const bf16* in, int epi, const bf16* mask,
-          bf16* out, const float2* r, float2* z, cudaStream_t s) {
+          bf16* out, const float2* r, float2* z, cudaStream_t s, const bf16* addend = nullptr) {
   ConvArgs a;
+  a.addend = addend;
   a.v = net->vol;
   a.in = in;
   a.wpk = (backward ? net->wbwd : net->wfwd) + size_t(layer) * kPack;
@@ -615,18 +626,17 @@ void forward(nrsense_cnn_s* net, const float2* r, const double* sumsq_dev, float
   input_kernel<<<ew_grid(n), 256, 0, s>>>(r, n, net->sc, net->act[0]);
   net->launches += 2;
   if (net->spd) {
-    // h_l = D_l W_l h_{l-1} (l = 1..4), h_5 = W_5 h_4
+    // h_l = D_l W_l h_{l-1} (l = 1..4), t5 = W5 h4
     for (int l = 0; l < kLayers - 1; ++l)
       conv(net, l, false, net->act[l], kReluBf16, nullptr, net->act[l + 1], nullptr, nullptr, s);
     conv(net, kLayers - 1, false, net->act[kLayers - 1], kLinearBf16, nullptr, net->h5, nullptr,
          nullptr, s);
-    // u_l = D_l W_{l+1}^T u_{l+1} (u_5 = h_5), z = u0 + W_1^T u_1
-    const bf16* cur = net->h5;
-    for (int l = kLayers - 1; l >= 1; --l) {
-      conv(net, l, true, cur, kMaskBf16, net->act[l], net->ut[l - 1], nullptr, nullptr, s);
-      cur = net->ut[l - 1];
-    }
-    conv(net, 0, true, cur, kResidualC64, nullptr, nullptr, r, z, s);
+    // u_4 = h4 + D_4 W5^T t5 (= D_4 m), u_l = D_l W_{l+1}^T u_{l+1}, z = u0 + W_1^T u_1
+    conv(net, kLayers - 1, true, net->h5, kAddMaskBf16, net->act[kLayers - 1], net->ut[kLayers - 2],
+         nullptr, nullptr, s, net->act[kLayers - 1]);
+    for (int l = kLayers - 2; l >= 1; --l)
+      conv(net, l, true, net->ut[l], kMaskBf16, net->act[l], net->ut[l - 1], nullptr, nullptr, s);
+    conv(net, 0, true, net->ut[0], kResidualC64, nullptr, nullptr, r, z, s);
     return;
   }
   for (int l = 0; l < kLayers - 1; ++l) {
@@ -786,6 +796,7 @@ nrsense_status nrsense_cnn_create(const int32_t* n_host, uint32_t flags, void* s
   for (int l = 0; l < kLayers && ok; ++l) ok = (net->act[l] = (bf16*)dalloc(net, ab)) != nullptr;
   for (int k = 0; k < 2 && ok; ++k) ok = (net->gb[k] = (bf16*)dalloc(net, ab)) != nullptr;
   if (net->spd) {
+    ok = ok && (net->gb[2] = (bf16*)dalloc(net, ab)) != nullptr;
     ok = ok && (net->h5 = (bf16*)dalloc(net, ab)) != nullptr;
     for (int k = 0; k < 4 && ok; ++k) ok = (net->ut[k] = (bf16*)dalloc(net, ab)) != nullptr;
   }
@@ -921,30 +932,43 @@ nrsense_status nrsense_cnn_gradients(nrsense_cnn_t net, nrsense_plan_t plan, dou
   loss_grad_kernel<<<ew_grid(n), 256, 0, s>>>(U, V, n, net->sc, net->gb[0]);
   net->launches += 3;
   int cur = 0;
-  bool acc_fwd = accumulate != 0;
   if (net->spd) {
     // adjoint of the transposed chain o = W_1^T u_1, u_l = D_l W_{l+1}^T u_{l+1}:
-    // with g = dL/d(W_{l+1}^T u_{l+1}), dW_{l+1} += wgrad(g, u_{l+1}) and the
-    // gradient passes on as D_{l+1} W_{l+1} g (a masked forward convolution)
-    for (int l = 0; l < kLayers; ++l) {
-      const bf16* ul = l < kLayers - 1 ? net->ut[l] : net->h5;
-      wgrad(net, l, net->gb[cur], ul, accumulate != 0, s);
-      if (l < kLayers - 1)
-        conv(net, l, false, net->gb[cur], kMaskBf16, net->act[l + 1], net->gb[cur ^ 1], nullptr,
-             nullptr, s);
-      else
-        conv(net, l, false, net->gb[cur], kLinearBf16, nullptr, net->gb[cur ^ 1], nullptr, nullptr,
-             s);
+    // dW_{l+1} (+)= wgrad(g, u_{l+1}); the gradient passes on as D_{l+1} W_{l+1} g
+    for (int l = 0; l < kLayers - 1; ++l) {
+      wgrad(net, l, net->gb[cur], net->ut[l], accumulate != 0, s);
+      conv(net, l, false, net->gb[cur], kMaskBf16, net->act[l + 1], net->gb[cur ^ 1], nullptr,
+           nullptr, s);
       cur ^= 1;
     }
-    acc_fwd = true;  // gb[cur] = dL/dh_5: continue through the forward chain
-  }
-  // backward through the forward chain: g holds dL/d(output of layer l)
-  for (int l = kLayers - 1; l >= 0; --l) {
-    wgrad(net, l, net->act[l], net->gb[cur], acc_fwd, s);
-    if (l > 0) {
-      conv(net, l, true, net->gb[cur], kMaskBf16, net->act[l], net->gb[cur ^ 1], nullptr, nullptr, s);
-      cur ^= 1;
+    // gb[cur] = dL/dm (masked); middle m = h4 + W5^T W5 h4 with q = W5 dL/dm:
+    // dW5 = wgrad(h4, q) + wgrad(dL/dm, t5), D_4 dL/dh4 = dL/dm + D_4 W5^T q
+    const int L5 = kLayers - 1;
+    bf16* q = net->gb[2];
+    conv(net, L5, false, net->gb[cur], kLinearBf16, nullptr, q, nullptr, nullptr, s);
+    wgrad(net, L5, net->act[L5], q, accumulate != 0, s);
+    wgrad(net, L5, net->gb[cur], net->h5, true, s);
+    conv(net, L5, true, q, kAddMaskBf16, net->act[L5], net->gb[cur ^ 1], nullptr, nullptr, s,
+         net->gb[cur]);
+    cur ^= 1;
+    // back through the forward chain h_l = D_l W_l h_{l-1}, l = 4 .. 1
+    for (int l = L5 - 1; l >= 0; --l) {
+      wgrad(net, l, net->act[l], net->gb[cur], true, s);
+      if (l > 0) {
+        conv(net, l, true, net->gb[cur], kMaskBf16, net->act[l], net->gb[cur ^ 1], nullptr, nullptr,
+             s);
+        cur ^= 1;
+      }
+    }
+  } else {
+    // backward through the forward chain: g holds dL/d(output of layer l)
+    for (int l = kLayers - 1; l >= 0; --l) {
+      wgrad(net, l, net->act[l], net->gb[cur], accumulate != 0, s);
+      if (l > 0) {
+        conv(net, l, true, net->gb[cur], kMaskBf16, net->act[l], net->gb[cur ^ 1], nullptr, nullptr,
+             s);
+        cur ^= 1;
+      }
     }
   }
   nrsense_status st = cuda_ok();

@@ -434,8 +434,9 @@ class Cnn:
     """Preconditioner network M of flexible CG (include/nrsense.h,
     nrsense_cnn_*): 3x3x3 convolutions 2 -> 16 -> 16 -> 16 -> 16 -> 2 with
     ReLU between, residual output, BF16 tensor-core kernels.  symmetric=True
-    (the default) selects z = u0 + N^T N u0 (symmetric positive definite for
-    fixed ReLU masks, biases unused); False the plain z = u0 + N(u0)."""
+    (the default) selects z = u0 + N4^T (I + W5^T W5) N4 u0 (symmetric
+    positive definite for fixed ReLU masks, biases unused); False the plain
+    z = u0 + N(u0)."""
 
     def __init__(self, shape, seed=None, symmetric=True, stream=None):
         self.lib = load()

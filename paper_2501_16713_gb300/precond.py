@@ -18,7 +18,32 @@ import math
 
 import numpy as np
 
-from .nrsense import Cnn, Plan
+from .nrsense import CNN_CHANNELS, Cnn, Plan
+
+
+def laplacian_params(c):
+    """Parameters of the symmetric form (z = u0 + N4^T (I + W5^T W5) N4 u0)
+    that make it z = u0 - c L u0, L the zero-padded Laplacian built from
+    central differences (first layer: +-sqrt(c) times the central difference
+    along each axis of each of Re, Im; hidden layers: identity on those 12
+    channels; W5 = 0).  For fixed masks the ReLU pairs cancel, so the map is
+    linear, symmetric and positive definite: a local approximation of the
+    inverse of a normal operator whose k-space weight grows as |k|^-2."""
+    params = [(np.zeros((co, ci, 3, 3, 3), np.float32), np.zeros(co, np.float32))
+              for ci, co in zip(CNN_CHANNELS[:-1], CNN_CHANNELS[1:])]
+    w1 = params[0][0]
+    a = 0.5 * math.sqrt(c)
+    for ax in range(3):
+        for comp in range(2):
+            ch = 4 * ax + 2 * comp
+            ip, im = [1, 1, 1], [1, 1, 1]
+            ip[ax], im[ax] = 2, 0
+            w1[ch, comp][tuple(ip)], w1[ch, comp][tuple(im)] = a, -a
+            w1[ch + 1, comp][tuple(ip)], w1[ch + 1, comp][tuple(im)] = -a, a
+    for l in (1, 2, 3):
+        for ch in range(12):
+            params[l][0][ch, ch, 1, 1, 1] = 1.0
+    return params
 
 
 def generate_pairs(plan: Plan, ys, lam, tol=1e-5, maxit=200, per_run=None, keep_last=None):
@@ -80,3 +105,29 @@ def mean_loss(net: Cnn, r, e, plan: Plan | None = None, lam=0.0):
     for i in range(r.shape[0]):
         tot += net.gradients(r[i], e[i], plan=plan, lam=lam)
     return tot / max(1, r.shape[0])
+
+
+def fcg_iterations(plan: Plan, y, lam, net, tol=1e-4, maxit=500):
+    """Flexible-CG iterations to tol on one problem (a validation score)."""
+    _, it, _, _, code, _ = plan.solve_fcg(y, lam, net, tol=tol, maxit=maxit)
+    return it if code == 0 else maxit + 1
+
+
+def train_select(net: Cnn, r, e, blocks, score, seed=0, log=None):
+    """Train in blocks [(steps, lr, lr_final), ...] and keep the parameters
+    with the lowest score(net) (e.g. fcg_iterations on held-out data),
+    including the starting point.  Returns [(block, loss, score), ...]."""
+    best_score = score(net)
+    best = net.get_params()
+    hist = [(-1, float("nan"), best_score)]
+    for k, (steps, lr, lr_final) in enumerate(blocks):
+        losses = train(net, r, e, steps, lr=lr, lr_final=lr_final, seed=seed + k,
+                       log_every=max(1, steps // 4))
+        sc = score(net)
+        hist.append((k, losses[-1], sc))
+        if log:
+            log(f"block {k}: loss {losses[-1]:.4f}, score {sc}")
+        if sc < best_score:
+            best_score, best = sc, net.get_params()
+    net.set_params(best)
+    return hist
