@@ -349,6 +349,174 @@ def run_precond(args):
     return line
 
 
+def run_cg192(args):
+    """Batched CG workload: 192^3, 16 coils, 6 phases with uneven (Poisson-drawn)
+    sample counts, Tikhonov lambda = 1e-3 lambda_max, 30 CG iterations captured
+    in one CUDA graph; FP32 operator, FP64 inner products."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2501_16713_gb300 import Plan, build
+
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = synth.workload("cg192")
+    shape = w["spec"].shape
+    t0 = time.perf_counter()
+    plan = Plan(shape, disp=torch.from_numpy(np.stack(w["disp"])).to(dev),
+                coords=[torch.from_numpy(c).to(dev) for c in w["coords"]],
+                smaps=torch.from_numpy(w["smaps"]).to(dev))
+    t_plan = time.perf_counter() - t0
+    info = plan.info()
+    x = torch.from_numpy(w["x"]).to(dev)
+    lam_max = _lambda_max(plan, shape, dev)
+    lam = 1e-3 * lam_max
+    gen = torch.Generator(device=dev).manual_seed(6)
+    y = _noisy(plan, x, gen)
+    out = torch.empty(shape, dtype=torch.complex64, device=dev)
+    iters = 30
+    for _ in range(max(1, args.warmup - 2)):
+        plan.solve_cg(y, lam, tol=0.0, maxit=iters, graph=True, out=out)
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(vis.split(",")[0] if vis else "0")
+    clocks.start()
+    time.sleep(0.3)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(args.steps, 3))
+    e0.record(s)
+    for _ in range(reps):
+        res = plan.solve_cg(y, lam, tol=0.0, maxit=iters, graph=True, out=out)
+    e1.record(s)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / reps
+    # one E apply alone, for applies/s
+    for _ in range(2):
+        plan.normal(x, lam, out)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(5):
+        plan.normal(x, lam, out)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms_e = e0.elapsed_time(e1) / 5
+    hist = res[2]
+    line = {"metric": "CG: 30 iterations in one CUDA graph", "value": ms, "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": reps, "warmup": args.warmup,
+            "ms_per_step": ms, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64/f32 operator, f64 CG scalars", "data": "synthetic",
+            "config": {"workload": "cg192", "image": list(shape), "coils": w["spec"].n_coils,
+                       "phases": len(plan.counts), "samples_per_phase": plan.counts,
+                       "lambda": lam, "lambda_rel": 1e-3, "iterations": iters,
+                       "phase_chunk": info["phase_chunk"], "plan_s": round(t_plan, 1),
+                       "device_bytes": info["device_bytes"]},
+            "ms_per_iteration": ms / iters, "normal_applies_per_s": 1000.0 / ms_e,
+            "rel_residual_after_30": hist[-1] if hist else None,
+            "residual_history": [float(f"{h:.3e}") for h in hist[::5]],
+            "clocks": clk}
+    plan.close()
+    return line
+
+
+def run_sweep256(args):
+    """Precision sweep on the 256^3, 32-coil, 8-phase workload (4 M samples per
+    phase): for FP32, BF16 storage and compensated FP32 spreading, E applies/s
+    and the error against the FP64 oracle.  The oracle references (phase 0,
+    coils 0..3: the warp T_0 x on the central 64^3 crop, A_0 x at a seeded 1%
+    subset of phase 0's samples, A^H y on the crop for y nonzero only on that
+    subset) were written by tests/golden/make_sweep256_oracle.py; the full
+    32-coil 8-phase FP64 operator does not fit a bench run.  Adjointness is
+    measured on the full GPU operator with random x, y."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2501_16713_gb300 import Plan, build
+
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    w = synth.workload("sweep256")
+    spec = w["spec"]
+    shape = spec.shape
+    t_gen = time.perf_counter() - t0
+    ref = np.load(os.path.join(ROOT, "tests", "golden", "sweep256_oracle.npz"))
+    sub, y_sub, n_ref_coils = ref["sub"], ref["y_sub"], int(ref["n_coils"])
+    m0c, y_ref, xa_refc = ref["warp_crop"], ref["y_ref"], ref["adj_crop"]
+    crop = tuple(slice(s_ // 2 - 32, s_ // 2 + 32) for s_ in shape)
+    M0 = w["coords"][0].shape[0]
+
+    x = torch.from_numpy(w["x"]).to(dev)
+    variants = {}
+    names = {0: "fp32", 1: "bf16_store", 2: "fp32_compensated"}
+    for precision in (0, 1, 2):
+        t1 = time.perf_counter()
+        plan = Plan(shape, disp=torch.from_numpy(np.stack(w["disp"])).to(dev),
+                    coords=[torch.from_numpy(c).to(dev) for c in w["coords"]],
+                    smaps=torch.from_numpy(w["smaps"]).to(dev), precision=precision)
+        t_plan = time.perf_counter() - t1
+        info = plan.info()
+        out = torch.empty_like(x)
+        for _ in range(2):
+            plan.normal(x, 0.0, out)
+        torch.cuda.synchronize()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(s)
+        for _ in range(reps):
+            plan.normal(x, 0.0, out)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        m = plan.warp_forward(x)[0][crop].cpu().numpy()
+        e_warp = float(np.linalg.norm(m - m0c) / np.linalg.norm(m0c))
+        y = plan.forward(x)
+        y0 = plan.phase_slice(y, 0)[torch.from_numpy(sub).to(dev), :n_ref_coils].cpu().numpy()
+        e_fwd = float(np.linalg.norm(y0 - y_ref) / np.linalg.norm(y_ref))
+        yin = torch.zeros_like(y)
+        rows = torch.from_numpy(sub).to(dev) + int(plan.offsets[0])
+        yin[rows, :n_ref_coils] = torch.from_numpy(y_sub).to(dev)
+        xa = plan.adjoint(yin)[crop].cpu().numpy()
+        e_adj = float(np.linalg.norm(xa - xa_refc) / np.linalg.norm(xa_refc))
+        gen = torch.Generator(device=dev).manual_seed(7)
+        xr = torch.randn(shape, dtype=torch.complex64, device=dev, generator=gen)
+        yr = torch.randn(y.shape, dtype=torch.complex64, device=dev, generator=gen)
+        d = lambda a: a.flatten().to(torch.complex128)
+        Ax, Ahy = plan.forward(xr), plan.adjoint(yr)
+        adj = abs(complex(torch.vdot(d(yr), d(Ax)) - torch.vdot(d(Ahy), d(xr)))) / float(
+            torch.linalg.norm(d(Ax)) * torch.linalg.norm(d(yr)))
+        variants[names[precision]] = {
+            "normal_ms": round(ms, 2), "normal_applies_per_s": 1000.0 / ms,
+            "err_warp_crop64": e_warp, "err_forward_subset": e_fwd, "err_adjoint_crop64": e_adj,
+            "adjointness": adj, "plan_s": round(t_plan, 1), "phase_chunk": info["phase_chunk"],
+            "device_bytes": info["device_bytes"]}
+        del y, yin, Ax, Ahy, yr, out
+        plan.close()
+        torch.cuda.empty_cache()
+    base = variants["fp32"]["normal_ms"]
+    for v_ in variants.values():
+        v_["speedup_vs_fp32"] = round(base / v_["normal_ms"], 3)
+    line = {"metric": "precision sweep: E applies/s and error vs FP64 oracle per variant",
+            "value": variants["fp32"]["normal_applies_per_s"], "unit": "applies/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": 3, "warmup": 2,
+            "ms_per_step": base, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64/f32 (bf16 grid storage in one variant)", "data": "synthetic",
+            "config": {"workload": "sweep256", "image": list(shape), "coils": spec.n_coils,
+                       "phases": len(w["coords"]), "samples_per_phase": M0,
+                       "oracle": f"phase 0, coils 0..{n_ref_coils - 1}; 64^3 centre crop; "
+                                 f"{sub.size} samples (1%); stored complex64 "
+                                 "(tests/golden/sweep256_oracle.npz)",
+                       "generate_s": round(t_gen, 1)},
+            "variants": variants}
+    return line
+
+
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -527,9 +695,10 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
-    if args.workload == "precond128" and args.impl == "ours":
+    special = {"precond128": run_precond, "cg192": run_cg192, "sweep256": run_sweep256}
+    if args.workload in special and args.impl == "ours":
         if int(os.environ.get("RANK", "0")) == 0:
-            print(json.dumps(run_precond(args)), flush=True)
+            print(json.dumps(special[args.workload](args)), flush=True)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

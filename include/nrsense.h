@@ -68,7 +68,14 @@ typedef struct nrsense_plan_s* nrsense_plan_t;
 typedef struct nrsense_cnn_s* nrsense_cnn_t;
 
 /* precision of the gridding grids (desc.precision) */
-#define NRSENSE_FP32            0  /* FP32 storage and accumulation */
+#define NRSENSE_FP32             0  /* FP32 storage and accumulation */
+#define NRSENSE_BF16_STORE       1  /* k-space coil grids stored as complex BF16 (round to
+                                       nearest even), FP32 arithmetic in every kernel, cuFFT
+                                       BF16 transforms of the coil grids; every oversampled
+                                       grid size must be a power of two */
+#define NRSENSE_FP32_COMPENSATED 2  /* FP32 storage; spreading (W = 4 only) accumulates with
+                                       compensated summation (FMA residual + TwoSum per
+                                       update, compensation added at write-out) */
 
 /* desc.flags */
 #define NRSENSE_IDENTITY_WARP   (1u << 0)  /* T_j = I for every phase (plain SENSE) */
@@ -80,7 +87,7 @@ typedef struct {
   double  kb_beta;     /* Kaiser-Bessel beta; 0 selects Beatty's formula */
   int32_t n_phases;    /* P >= 1 */
   int32_t n_coils;     /* C >= 0; 0 = image-space warp only (no S, no G_j) */
-  int32_t precision;   /* NRSENSE_FP32 */
+  int32_t precision;   /* NRSENSE_FP32, NRSENSE_BF16_STORE or NRSENSE_FP32_COMPENSATED */
   uint32_t flags;      /* NRSENSE_* flags */
   int32_t phase_chunk; /* phases processed per launch (1..16); 0 = as many as half of the
                           free device memory at plan time allows */
@@ -190,7 +197,9 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t plan, int32_t phase,
  *   maxit        iteration limit (0 .. 2^20).
  *   flags        NRSENSE_CG_X0: x_dev holds the initial guess; NRSENSE_CG_GRAPH:
  *                iterations are captured once as a CUDA graph (per plan, x_dev,
- *                lambda) and replayed.
+ *                lambda) and replayed: with tol = 0 (a fixed iteration count)
+ *                min(maxit, 64) iterations form one graph, otherwise 10, with
+ *                the converged flag read between graph launches.
  *   x_dev        image (device): initial guess (with NRSENSE_CG_X0) and solution.
  *   iters_host   receives the number of iterations (may be NULL).
  *   res_hist_host receives ||r_k|| / ||b|| for k = 0 .. iters (maxit + 1 doubles

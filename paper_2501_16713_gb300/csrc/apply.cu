@@ -10,6 +10,8 @@
 //  S^H G_j^H (per phase):                   K7 (P^(k), into a buffer whose
 //        empty tiles stay zero) -> F_G^H (batched, out of place) ->
 //        K8 (Z^H, 1/c, S^H)
+#include <cufftXt.h>
+
 #include <algorithm>
 #include <cstring>
 
@@ -25,14 +27,16 @@ namespace {
     if (_st != NRSENSE_OK) return _st; \
   } while (0)
 
-nrsense_status fft(nrsense_plan_s* p, int stage, cufftHandle h, cudaStream_t s, nrsense_c64* in,
-                   nrsense_c64* out, int dir) {
+nrsense_status fft(nrsense_plan_s* p, int stage, cufftHandle h, cudaStream_t s, void* in,
+                   void* out, int dir) {
   StageMark mark(p, stage, s);
   if (cufftSetStream(h, s) != CUFFT_SUCCESS) return NRSENSE_ERR_CUFFT;
-  if (cufftExecC2C(h, reinterpret_cast<cufftComplex*>(in), reinterpret_cast<cufftComplex*>(out),
-                   dir) != CUFFT_SUCCESS)
-    return NRSENSE_ERR_CUFFT;
-  return NRSENSE_OK;
+  // the batched coil-grid transforms of a BF16-storage plan are cufftXt plans
+  const cufftResult r =
+      (stage == NRSENSE_STAGE_FFT_GC && p->grid_bf16)
+          ? cufftXtExec(h, in, out, dir)
+          : cufftExecC2C(h, static_cast<cufftComplex*>(in), static_cast<cufftComplex*>(out), dir);
+  return r == CUFFT_SUCCESS ? NRSENSE_OK : NRSENSE_ERR_CUFFT;
 }
 
 nrsense_status launched() {
@@ -122,8 +126,8 @@ nrsense_status warp_adjoint(nrsense_plan_s* p, const nrsense_c64* m, nrsense_c64
     return launched();
   }
   const PhaseTable t = image_table(p);
-  STAGE(SPREAD_IMAGE, launch_spread(g, p->W, p->kc, 1, p->itiles, t, m, p->b_ugrid, p->b_scratch,
-                                    p->d_status, s));
+  STAGE(SPREAD_IMAGE, launch_spread(g, p->W, p->kc, 1, p->itiles, t, m, p->b_ugrid, false,
+                                    p->comp_spread, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_ugrid, p->b_ugrid, CUFFT_FORWARD));
   STAGE(CROP_DEAPOD, launch_crop_deapod(g, p->deapod, p->b_ugrid, x, s));
@@ -137,11 +141,13 @@ nrsense_status sense_chunk_forward(nrsense_plan_s* p, int j0, int j1, const nrse
                                    nrsense_c64* y, long long row_base, cudaStream_t s) {
   const Geo& g = p->geo;
   const int nph = j1 - j0;
-  STAGE(COIL_FANOUT, launch_coil_fanout_pad(g, p->C, nph, p->deapod, p->smaps, m, p->b_xpad, s));
+  STAGE(COIL_FANOUT, launch_coil_fanout_pad(g, p->C, nph, p->deapod, p->smaps, m, p->b_xpad,
+                                            p->grid_bf16, s));
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, nph), s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
   const PhaseTable t = kspace_table(p, j0, j1, /*spread=*/false, row_base);
-  STAGE(INTERP_KSPACE, launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork, y, s));
+  STAGE(INTERP_KSPACE, launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
+                                            p->grid_bf16, y, s));
   return launched();
 }
 
@@ -152,10 +158,11 @@ nrsense_status sense_chunk_adjoint(nrsense_plan_s* p, int j0, int j1, const nrse
   const int nph = j1 - j0;
   const PhaseTable t = kspace_table(p, j0, j1, /*spread=*/true, row_base);
   STAGE(SPREAD_KSPACE, launch_spread(g, p->W, p->kc, p->C, p->ktiles, t, y, p->b_xspread,
-                                     p->b_scratch, p->d_status, s));
+                                     p->grid_bf16, p->comp_spread, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, nph), s, p->b_xspread, p->b_xwork, CUFFT_INVERSE));
-  STAGE(CROP_COILSUM, launch_crop_coilsum(g, p->C, nph, p->deapod, p->smaps, p->b_xwork, w, s));
+  STAGE(CROP_COILSUM, launch_crop_coilsum(g, p->C, nph, p->deapod, p->smaps, p->b_xwork,
+                                          p->grid_bf16, w, s));
   return launched();
 }
 
@@ -181,11 +188,12 @@ nrsense_status nrsense_kspace_forward(nrsense_plan_t p, int32_t phase, const nrs
   if (p->C == 0) return NRSENSE_ERR_STATE;
   if (phase < 0 || phase >= p->P) return NRSENSE_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  STAGE(COIL_FANOUT, launch_image_to_padded(p->geo, p->C, p->deapod, v, p->b_xpad, s));
+  STAGE(COIL_FANOUT, launch_image_to_padded(p->geo, p->C, p->deapod, v, p->b_xpad, p->grid_bf16, s));
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, 1), s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
   const PhaseTable t = kspace_table(p, phase, phase + 1, false, p->off[phase]);
-  STAGE(INTERP_KSPACE, launch_interp_kspace(p->geo, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork, y, s));
+  STAGE(INTERP_KSPACE, launch_interp_kspace(p->geo, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
+                                            p->grid_bf16, y, s));
   return launched();
 }
 
@@ -197,10 +205,10 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t p, int32_t phase, const nrs
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const PhaseTable t = kspace_table(p, phase, phase + 1, true, p->off[phase]);
   STAGE(SPREAD_KSPACE, launch_spread(p->geo, p->W, p->kc, p->C, p->ktiles, t, y, p->b_xspread,
-                                     p->b_scratch, p->d_status, s));
+                                     p->grid_bf16, p->comp_spread, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, 1), s, p->b_xspread, p->b_xwork, CUFFT_INVERSE));
-  STAGE(CROP_COILSUM, launch_crop_to_coils(p->geo, p->C, p->deapod, p->b_xwork, v, s));
+  STAGE(CROP_COILSUM, launch_crop_to_coils(p->geo, p->C, p->deapod, p->b_xwork, p->grid_bf16, v, s));
   return launched();
 }
 

@@ -1,6 +1,7 @@
 // Shared device-side definitions of the nonrigid SENSE library (sm_103a).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -121,8 +122,43 @@ __device__ __forceinline__ void cp_async_8(void* smem, const void* gmem, bool va
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem),
                "r"(src_size));
 }
+__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem, bool valid) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int src_size = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem),
+               "r"(src_size));
+}
+// asynchronous copy of one stored grid value (complex FP32: 8 bytes; complex BF16: 4)
+template <typename GT>
+__device__ __forceinline__ void cp_async_grid(GT* smem, const GT* gmem, bool valid) {
+  if constexpr (sizeof(GT) == 8)
+    cp_async_8(smem, gmem, valid);
+  else
+    cp_async_4(smem, gmem, valid);
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Storage of the k-space coil grids: complex FP32 (float2) or complex BF16
+// (__nv_bfloat162, round to nearest even); arithmetic is FP32 either way.
+using bf162 = __nv_bfloat162;
+__device__ __forceinline__ float2 grid_ld(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 grid_ld(const bf162* p) {
+  const unsigned u = __ldg(reinterpret_cast<const unsigned*>(p));
+  return __bfloat1622float2(*reinterpret_cast<const bf162*>(&u));
+}
+__device__ __forceinline__ void grid_st(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void grid_st(bf162* p, float2 v) { *p = __float22bfloat162_rn(v); }
+// two consecutive stored values (coils 2q, 2q+1) from shared memory as float4
+__device__ __forceinline__ float4 grid_ld2_shared(const float2* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+__device__ __forceinline__ float4 grid_ld2_shared(const bf162* p) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const bf162*>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const bf162*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
 }
 
 __device__ __forceinline__ int wrap_once(int i, int g) {

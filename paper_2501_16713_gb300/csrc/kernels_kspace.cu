@@ -38,10 +38,11 @@ __device__ __forceinline__ VoxelPos voxel_pos(const Geo& g, const float* __restr
 // of the zero-padded coil grids (steps S, 1/c* and Z), for the nph phases of
 // a chunk at once.  Thread = (phase, coil, voxel); grid slot of (phase jj,
 // coil c) is jj * C + c.
+template <typename GT>
 __global__ void coil_fanout_pad_kernel(Geo g, int C, int nph, const float* __restrict__ dtab,
                                        const float2* __restrict__ smaps,  // [C][nvox]
                                        const float2* __restrict__ m,      // [nph][nvox]
-                                       float2* __restrict__ xpad) {       // [nph*C][G^3]
+                                       GT* __restrict__ xpad) {           // [nph*C][G^3]
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.nvox * C * nph) return;
   const long long sc = t / g.nvox;  // jj * C + c
@@ -52,20 +53,21 @@ __global__ void coil_fanout_pad_kernel(Geo g, int C, int nph, const float* __res
   const float2 mv = __ldg(m + jj * g.nvox + idx);
   const float2 sv = __ldg(smaps + (long long)c * g.nvox + idx);
   const float w = vp.deapod;
-  xpad[sc * g.ngrid + vp.grid] =
-      make_float2((sv.x * mv.x - sv.y * mv.y) * w, (sv.x * mv.y + sv.y * mv.x) * w);
+  grid_st(xpad + sc * g.ngrid + vp.grid,
+          make_float2((sv.x * mv.x - sv.y * mv.y) * w, (sv.x * mv.y + sv.y * mv.x) * w));
 }
 
 // Stage variant of K5 without S: coil images v (C, N^3) -> padded grids.
+template <typename GT>
 __global__ void image_to_padded_kernel(Geo g, int C, const float* __restrict__ dtab,
-                                       const float2* __restrict__ v, float2* __restrict__ xpad) {
+                                       const float2* __restrict__ v, GT* __restrict__ xpad) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.nvox * C) return;
   const int c = int(t / g.nvox);
   const long long idx = t - (long long)c * g.nvox;
   const VoxelPos vp = voxel_pos(g, dtab, idx);
   const float2 vv = __ldg(v + t);
-  xpad[(long long)c * g.ngrid + vp.grid] = make_float2(vv.x * vp.deapod, vv.y * vp.deapod);
+  grid_st(xpad + (long long)c * g.ngrid + vp.grid, make_float2(vv.x * vp.deapod, vv.y * vp.deapod));
 }
 
 // K6: y_{j,s,c} = sum_taps c3(q_s - g) X_{j,c}[g] (Backprojection Core B^(k)).
@@ -77,20 +79,20 @@ __global__ void image_to_padded_kernel(Geo g, int C, const float* __restrict__ d
 // conflicts); each lane evaluates only its own tap's weights (coefficients
 // in shared memory), gets the other axes' by shuffles, and the tap-x partial
 // sums are reduced by shuffles at the end.
-template <int W, int CC>
+template <int W, int CC, typename GT>
 __global__ void __launch_bounds__(256) interp_tile_kernel(
-    Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ grids,
+    Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const GT* __restrict__ grids,
     float2* __restrict__ y) {
   constexpr int T = 8, H = T + W - 1, H3 = H * H * H;
   constexpr int NQ = CC / 2, LPS = W * NQ, SPW = 32 / LPS;  // lanes/sample, samples/warp
   extern __shared__ float4 smem_raw[];
-  float2* halo = reinterpret_cast<float2*>(smem_raw);  // [H][H][H][CC]
+  GT* halo = reinterpret_cast<GT*>(smem_raw);  // [H][H][H][CC] stored values
   __shared__ float s_coef[W][kNumCoef];
   const int jj = phase_of(pt.item0, pt.nphase, blockIdx.x);
   const SpreadItem it = pt.items[jj][blockIdx.x - pt.item0[jj]];
   const float4* __restrict__ qs = pt.qs[jj];
   const int32_t* __restrict__ perm = pt.perm[jj];
-  const float2* __restrict__ grid = grids + (long long)jj * C * g.ngrid;
+  const GT* __restrict__ grid = grids + (long long)jj * C * g.ngrid;
   const long long row0 = pt.row0[jj];
   const int coil0 = blockIdx.y * CC;
   const int tz = it.tile / (tp.nt1 * tp.nt2);
@@ -109,10 +111,10 @@ __global__ void __launch_bounds__(256) interp_tile_kernel(
     const int gz = wrap_once(o0 + z, g.g0), gy = wrap_once(o1 + yy, g.g1),
               gx = wrap_once(o2 + x, g.g2);
     const bool valid = coil0 + c < C;
-    const float2* src =
+    const GT* src =
         grid + (valid ? (long long)(coil0 + c) * g.ngrid + ((long long)gz * g.g1 + gy) * g.g2 + gx
                       : 0);
-    cp_async_8(halo + r * CC + c, src, valid);
+    cp_async_grid(halo + r * CC + c, src, valid);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -162,13 +164,13 @@ __global__ void __launch_bounds__(256) interp_tile_kernel(
     }
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (live) {
-      const float4* base4 = reinterpret_cast<const float4*>(halo + ((l0 * H + l1) * H + l2 + txl) * CC) + q;
+      const GT* base = halo + ((l0 * H + l1) * H + l2 + txl) * CC + 2 * q;
 #pragma unroll
       for (int t0 = 0; t0 < W; ++t0) {
 #pragma unroll
         for (int t1 = 0; t1 < W; ++t1) {
           const float w = w0[t0] * w1[t1] * w2t;
-          const float4 v = base4[((t0 * H + t1) * H) * (CC / 2)];
+          const float4 v = grid_ld2_shared(base + ((t0 * H + t1) * H) * CC);
           acc.x = fmaf(w, v.x, acc.x);
           acc.y = fmaf(w, v.y, acc.y);
           acc.z = fmaf(w, v.z, acc.z);
@@ -211,27 +213,28 @@ __global__ void __launch_bounds__(256) interp_tile_kernel(
   }
 }
 
-template <int W, int CC>
+template <int W, int CC, typename GT>
 constexpr size_t interp_smem() {
-  return size_t(8 + W - 1) * (8 + W - 1) * (8 + W - 1) * CC * sizeof(float2);
+  return size_t(8 + W - 1) * (8 + W - 1) * (8 + W - 1) * CC * sizeof(GT);
 }
 
 // K8: w_j[n] = sum_c conj(S_c[n]) Xt_c[n' mod G] / C3(n'/G) (steps Z^H, 1/c of
 // k-space gridding, then S^H), for the nph phases of a chunk.  Thread = (phase, voxel).
+template <typename GT>
 __global__ void crop_coilsum_kernel(Geo g, int C, int nph, const float* __restrict__ dtab,
                                     const float2* __restrict__ smaps,  // [C][nvox]
-                                    const float2* __restrict__ xg,     // [nph*C][G^3]
+                                    const GT* __restrict__ xg,         // [nph*C][G^3]
                                     float2* __restrict__ w) {          // [nph][nvox]
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.nvox * nph) return;
   const long long jj = t / g.nvox;
   const long long idx = t - jj * g.nvox;
   const VoxelPos vp = voxel_pos(g, dtab, idx);
-  const float2* xs = xg + jj * C * g.ngrid + vp.grid;
+  const GT* xs = xg + jj * C * g.ngrid + vp.grid;
   float ar = 0.f, ai = 0.f;
   for (int c = 0; c < C; ++c) {
     const float2 s = __ldg(smaps + (long long)c * g.nvox + idx);
-    const float2 v = __ldg(xs + (long long)c * g.ngrid);
+    const float2 v = grid_ld(xs + (long long)c * g.ngrid);
     ar = fmaf(s.x, v.x, fmaf(s.y, v.y, ar));
     ai = fmaf(s.x, v.y, fmaf(-s.y, v.x, ai));
   }
@@ -239,14 +242,15 @@ __global__ void crop_coilsum_kernel(Geo g, int C, int nph, const float* __restri
 }
 
 // Stage variant of K8 without S^H: padded grids -> coil images (C, N^3).
+template <typename GT>
 __global__ void crop_to_coils_kernel(Geo g, int C, const float* __restrict__ dtab,
-                                     const float2* __restrict__ xg, float2* __restrict__ v) {
+                                     const GT* __restrict__ xg, float2* __restrict__ v) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.nvox * C) return;
   const int c = int(t / g.nvox);
   const long long idx = t - (long long)c * g.nvox;
   const VoxelPos vp = voxel_pos(g, dtab, idx);
-  const float2 x = __ldg(xg + (long long)c * g.ngrid + vp.grid);
+  const float2 x = grid_ld(xg + (long long)c * g.ngrid + vp.grid);
   v[t] = make_float2(x.x * vp.deapod, x.y * vp.deapod);
 }
 
@@ -257,69 +261,98 @@ inline unsigned blocks_for(long long n, int threads) {
 }  // namespace
 
 int launch_coil_fanout_pad(const Geo& g, int C, int nph, const float* deapod,
-                           const nrsense_c64* smaps, const nrsense_c64* m, nrsense_c64* xpad,
+                           const nrsense_c64* smaps, const nrsense_c64* m, void* xpad, bool bf16,
                            cudaStream_t s) {
-  coil_fanout_pad_kernel<<<blocks_for(g.nvox * C * nph, 256), 256, 0, s>>>(
-      g, C, nph, deapod, reinterpret_cast<const float2*>(smaps),
-      reinterpret_cast<const float2*>(m), reinterpret_cast<float2*>(xpad));
+  const auto* sm = reinterpret_cast<const float2*>(smaps);
+  const auto* mm = reinterpret_cast<const float2*>(m);
+  const unsigned nb = blocks_for(g.nvox * C * nph, 256);
+  if (bf16)
+    coil_fanout_pad_kernel<<<nb, 256, 0, s>>>(g, C, nph, deapod, sm, mm, static_cast<bf162*>(xpad));
+  else
+    coil_fanout_pad_kernel<<<nb, 256, 0, s>>>(g, C, nph, deapod, sm, mm, static_cast<float2*>(xpad));
   return 1;
 }
 
 int launch_image_to_padded(const Geo& g, int C, const float* deapod, const nrsense_c64* v,
-                           nrsense_c64* xpad, cudaStream_t s) {
-  image_to_padded_kernel<<<blocks_for(g.nvox * C, 256), 256, 0, s>>>(
-      g, C, deapod, reinterpret_cast<const float2*>(v), reinterpret_cast<float2*>(xpad));
+                           void* xpad, bool bf16, cudaStream_t s) {
+  const auto* vv = reinterpret_cast<const float2*>(v);
+  const unsigned nb = blocks_for(g.nvox * C, 256);
+  if (bf16)
+    image_to_padded_kernel<<<nb, 256, 0, s>>>(g, C, deapod, vv, static_cast<bf162*>(xpad));
+  else
+    image_to_padded_kernel<<<nb, 256, 0, s>>>(g, C, deapod, vv, static_cast<float2*>(xpad));
   return 1;
 }
 
+namespace {
+template <int W, int CC, typename GT>
+cudaError_t set_interp_smem() {
+  return cudaFuncSetAttribute(interp_tile_kernel<W, CC, GT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(interp_smem<W, CC, GT>()));
+}
+
+template <typename GT>
+void interp_dispatch(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
+                     const PhaseTable& pt, const GT* gp, float2* yp, int nitems, cudaStream_t s) {
+  if (W == 4 && C > 4) {
+    const dim3 gd(nitems, (C + 7) / 8);
+    interp_tile_kernel<4, 8, GT><<<gd, 256, interp_smem<4, 8, GT>(), s>>>(g, kc, C, tp, pt, gp, yp);
+  } else if (W == 4) {
+    interp_tile_kernel<4, 4, GT><<<dim3(nitems, 1), 256, interp_smem<4, 4, GT>(), s>>>(
+        g, kc, C, tp, pt, gp, yp);
+  } else {
+    const dim3 gd(nitems, (C + 3) / 4);
+    interp_tile_kernel<6, 4, GT><<<gd, 256, interp_smem<6, 4, GT>(), s>>>(g, kc, C, tp, pt, gp, yp);
+  }
+}
+}  // namespace
+
 cudaError_t configure_kernels() {
   cudaError_t e = configure_spread_kernels();
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(interp_tile_kernel<4, 8>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(interp_smem<4, 8>()));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(interp_tile_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(interp_smem<4, 4>()));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(interp_tile_kernel<6, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(interp_smem<6, 4>()));
+  if (e == cudaSuccess) e = set_interp_smem<4, 8, float2>();
+  if (e == cudaSuccess) e = set_interp_smem<4, 4, float2>();
+  if (e == cudaSuccess) e = set_interp_smem<6, 4, float2>();
+  if (e == cudaSuccess) e = set_interp_smem<4, 8, bf162>();
+  if (e == cudaSuccess) e = set_interp_smem<4, 4, bf162>();
+  if (e == cudaSuccess) e = set_interp_smem<6, 4, bf162>();
   return e;
 }
 
 int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
-                         const PhaseTable& pt, const nrsense_c64* grids, nrsense_c64* y,
+                         const PhaseTable& pt, const void* grids, bool bf16, nrsense_c64* y,
                          cudaStream_t s) {
   const int nitems = pt.item0[pt.nphase];
   if (nitems == 0) return 0;
-  const auto* gp = reinterpret_cast<const float2*>(grids);
   auto* yp = reinterpret_cast<float2*>(y);
-  if (W == 4 && C > 4) {
-    const dim3 gd(nitems, (C + 7) / 8);
-    interp_tile_kernel<4, 8><<<gd, 256, interp_smem<4, 8>(), s>>>(g, kc, C, tp, pt, gp, yp);
-  } else if (W == 4) {
-    interp_tile_kernel<4, 4><<<dim3(nitems, 1), 256, interp_smem<4, 4>(), s>>>(g, kc, C, tp, pt,
-                                                                               gp, yp);
-  } else {
-    const dim3 gd(nitems, (C + 3) / 4);
-    interp_tile_kernel<6, 4><<<gd, 256, interp_smem<6, 4>(), s>>>(g, kc, C, tp, pt, gp, yp);
-  }
+  if (bf16)
+    interp_dispatch(g, W, kc, C, tp, pt, static_cast<const bf162*>(grids), yp, nitems, s);
+  else
+    interp_dispatch(g, W, kc, C, tp, pt, static_cast<const float2*>(grids), yp, nitems, s);
   return 1;
 }
 
 int launch_crop_coilsum(const Geo& g, int C, int nph, const float* deapod,
-                        const nrsense_c64* smaps, const nrsense_c64* xg, nrsense_c64* w,
+                        const nrsense_c64* smaps, const void* xg, bool bf16, nrsense_c64* w,
                         cudaStream_t s) {
-  crop_coilsum_kernel<<<blocks_for(g.nvox * nph, 256), 256, 0, s>>>(
-      g, C, nph, deapod, reinterpret_cast<const float2*>(smaps),
-      reinterpret_cast<const float2*>(xg), reinterpret_cast<float2*>(w));
+  const auto* sm = reinterpret_cast<const float2*>(smaps);
+  auto* wp = reinterpret_cast<float2*>(w);
+  const unsigned nb = blocks_for(g.nvox * nph, 256);
+  if (bf16)
+    crop_coilsum_kernel<<<nb, 256, 0, s>>>(g, C, nph, deapod, sm, static_cast<const bf162*>(xg), wp);
+  else
+    crop_coilsum_kernel<<<nb, 256, 0, s>>>(g, C, nph, deapod, sm, static_cast<const float2*>(xg), wp);
   return 1;
 }
 
-int launch_crop_to_coils(const Geo& g, int C, const float* deapod, const nrsense_c64* xg,
+int launch_crop_to_coils(const Geo& g, int C, const float* deapod, const void* xg, bool bf16,
                          nrsense_c64* v, cudaStream_t s) {
-  crop_to_coils_kernel<<<blocks_for(g.nvox * C, 256), 256, 0, s>>>(
-      g, C, deapod, reinterpret_cast<const float2*>(xg), reinterpret_cast<float2*>(v));
+  auto* vp = reinterpret_cast<float2*>(v);
+  const unsigned nb = blocks_for(g.nvox * C, 256);
+  if (bf16)
+    crop_to_coils_kernel<<<nb, 256, 0, s>>>(g, C, deapod, static_cast<const bf162*>(xg), vp);
+  else
+    crop_to_coils_kernel<<<nb, 256, 0, s>>>(g, C, deapod, static_cast<const float2*>(xg), vp);
   return 1;
 }
 

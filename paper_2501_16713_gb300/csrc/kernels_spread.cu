@@ -13,6 +13,14 @@
 // is updated by one warp only, in list order, so the result is bitwise
 // deterministic.  A heavy tile is split over several CTAs that write partial
 // tiles to scratch; a second kernel adds the partials in a fixed order.
+//
+// Storage and accumulation variants: the k-space coil grids are stored as
+// complex FP32 or complex BF16 (accumulation is FP32 in shared memory either
+// way); the W = 4 kernels optionally accumulate with an error-free
+// transformation (compensated summation: the rounding error of every product
+// (FMA residual) and of every addition (TwoSum) is summed in a companion
+// array and added at write-out), which removes the growth of the
+// accumulation error with the number of points per grid value.
 #include "plan_internal.h"
 
 namespace nrs {
@@ -85,12 +93,20 @@ __device__ __forceinline__ void bin_round(int (*s_r)[3], int* s_bin, int cnt, in
   }
 }
 
-template <int T, int CC>
+template <int T, int CC, typename GT>
 __device__ __forceinline__ void write_tile(const Geo& g, int C, int coil0, const TileOrigin& to,
-                                          int slot, const float2* acc,
-                                          float2* __restrict__ grid, float2* __restrict__ scratch,
+                                          int slot, const float2* acc, const float2* comp,
+                                          GT* __restrict__ grid, float2* __restrict__ scratch,
                                           int tid) {
   constexpr int kPts = T * T * T;
+  auto value = [&](int i) {
+    float2 v = acc[i];
+    if (comp) {
+      v.x += comp[i].x;
+      v.y += comp[i].y;
+    }
+    return v;
+  };
   if (slot < 0) {
     // coil fastest across lanes: contiguous shared reads, full global sectors
     for (int i = tid; i < kPts * CC; i += kThreads) {
@@ -99,13 +115,25 @@ __device__ __forceinline__ void write_tile(const Geo& g, int C, int coil0, const
       const int lx = pt % T, ly = (pt / T) % T, lz = pt / (T * T);
       if (lz < to.e0 && ly < to.e1 && lx < to.e2 && coil0 + c < C) {
         const long long gi = ((long long)(to.o0 + lz) * g.g1 + (to.o1 + ly)) * g.g2 + (to.o2 + lx);
-        grid[(long long)(coil0 + c) * g.ngrid + gi] = acc[i];
+        grid_st(grid + (long long)(coil0 + c) * g.ngrid + gi, value(i));
       }
     }
   } else {
     float2* dst = scratch + ((long long)slot * gridDim.y + blockIdx.y) * (kPts * CC);
-    for (int i = tid; i < kPts * CC; i += kThreads) dst[i] = acc[i];
+    for (int i = tid; i < kPts * CC; i += kThreads) dst[i] = value(i);
   }
+}
+
+// acc += w * v with the rounding errors of the product and the sum added to
+// comp (FMA residual + TwoSum; Ogita, Rump & Oishi's compensated dot product)
+__device__ __forceinline__ void comp_fma(float w, float v, float& acc, float& comp) {
+  const float p = w * v;
+  const float ep = fmaf(w, v, -p);
+  const float s = acc + p;
+  const float bb = s - acc;
+  const float es = (acc - (s - bb)) + (p - bb);
+  acc = s;
+  comp += es + ep;
 }
 
 // Resolve a launch's work item through the phase table.
@@ -139,14 +167,15 @@ struct CoilStage {
   float2 val[CC];
 };
 
-template <int CC>
+template <int CC, typename GT, bool COMP>
 __global__ void __launch_bounds__(kThreads) spread_coils_kernel(
     Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
-    float2* __restrict__ grids, float2* __restrict__ scratch) {
+    GT* __restrict__ grids, float2* __restrict__ scratch) {
   constexpr int W = 4, T = 8, B = 32, NB = W + T + 1;
   static_assert(CC == 2 || CC == 4 || CC == 8, "coil chunk");
   extern __shared__ float4 smem_raw[];
   float2* acc = reinterpret_cast<float2*>(smem_raw);  // [T][T][T][CC]
+  float2* comp = COMP ? acc + T * T * T * CC : nullptr;  // compensation terms
   __shared__ __align__(16) CoilStage<CC> stg[kThreads / 32][B];
 
   const ItemRef ir = item_ref(pt);
@@ -154,11 +183,12 @@ __global__ void __launch_bounds__(kThreads) spread_coils_kernel(
   const int2* __restrict__ list = pt.list[ir.jj];
   const float4* __restrict__ qs = pt.qs[ir.jj];
   const long long row0 = pt.row0[ir.jj];
-  float2* __restrict__ grid = grids + (long long)ir.jj * C * g.ngrid;
+  GT* __restrict__ grid = grids + (long long)ir.jj * C * g.ngrid;
   const int coil0 = blockIdx.y * CC;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TileOrigin to = tile_origin(g, tp, it.tile);
-  for (int i = tid; i < T * T * T * CC; i += kThreads) acc[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < T * T * T * CC * (COMP ? 2 : 1); i += kThreads)
+    acc[i] = make_float2(0.f, 0.f);
   __syncthreads();
 
   const int lz = warp;
@@ -218,12 +248,23 @@ __global__ void __launch_bounds__(kThreads) spread_coils_kernel(
           const int ly = d.r1 + ty;
           if (ty < W && (unsigned)ly < (unsigned)to.e1 && (unsigned)lx < (unsigned)to.e2) {
             const float w = d.wzy[ty & (W - 1)] * wxt;
-            float4* a = reinterpret_cast<float4*>(acc + ((lz * T + ly) * T + lx) * CC) + q;
+            const int off = ((lz * T + ly) * T + lx) * CC;
+            float4* a = reinterpret_cast<float4*>(acc + off) + q;
             float4 cur = *a;
-            cur.x = fmaf(w, v.x, cur.x);
-            cur.y = fmaf(w, v.y, cur.y);
-            cur.z = fmaf(w, v.z, cur.z);
-            cur.w = fmaf(w, v.w, cur.w);
+            if constexpr (COMP) {
+              float4* ca = reinterpret_cast<float4*>(comp + off) + q;
+              float4 cc = *ca;
+              comp_fma(w, v.x, cur.x, cc.x);
+              comp_fma(w, v.y, cur.y, cc.y);
+              comp_fma(w, v.z, cur.z, cc.z);
+              comp_fma(w, v.w, cur.w, cc.w);
+              *ca = cc;
+            } else {
+              cur.x = fmaf(w, v.x, cur.x);
+              cur.y = fmaf(w, v.y, cur.y);
+              cur.z = fmaf(w, v.z, cur.z);
+              cur.w = fmaf(w, v.w, cur.w);
+            }
             *a = cur;
           }
         }
@@ -232,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) spread_coils_kernel(
     }
   }
   __syncthreads();
-  write_tile<T, CC>(g, C, coil0, to, scratch_slot(pt, ir), acc, grid, scratch, tid);
+  write_tile<T, CC, GT>(g, C, coil0, to, scratch_slot(pt, ir), acc, comp, grid, scratch, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -246,6 +287,7 @@ struct SingleStage {
   float2 val;
 };
 
+template <bool COMP>
 __global__ void __launch_bounds__(kThreads) spread_single_kernel(
     Geo g, KernelCoefs kc, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
     float2* __restrict__ grids, float2* __restrict__ scratch) {
@@ -253,6 +295,7 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
   constexpr int RS = T + 4;  // padded row stride: 4 tap rows hit disjoint banks
   extern __shared__ float4 smem_raw[];
   float2* acc = reinterpret_cast<float2*>(smem_raw);  // [T][T][RS]
+  float2* comp = COMP ? acc + T * T * RS : nullptr;
   __shared__ SingleStage stg[kThreads / 32][B];
 
   const ItemRef ir = item_ref(pt);
@@ -263,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
   float2* __restrict__ grid = grids + (long long)ir.jj * g.ngrid;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TileOrigin to = tile_origin(g, tp, it.tile);
-  for (int i = tid; i < T * T * RS; i += kThreads) acc[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < T * T * RS * (COMP ? 2 : 1); i += kThreads) acc[i] = make_float2(0.f, 0.f);
   __syncthreads();
 
   const int z0 = 2 * warp;
@@ -312,11 +355,18 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
         const int ly = d.r1 + ty, lx = d.r2 + tx;
         if ((unsigned)ly < (unsigned)to.e1 && (unsigned)lx < (unsigned)to.e2 && lz < to.e0) {
           const float w = d.wzy[hz][ty] * d.wx[tx];
-          float2* a = acc + (lz * T + ly) * RS + lx;
-          float2 cur = *a;
-          cur.x = fmaf(w, d.val.x, cur.x);
-          cur.y = fmaf(w, d.val.y, cur.y);
-          *a = cur;
+          const int off = (lz * T + ly) * RS + lx;
+          float2 cur = acc[off];
+          if constexpr (COMP) {
+            float2 cc = comp[off];
+            comp_fma(w, d.val.x, cur.x, cc.x);
+            comp_fma(w, d.val.y, cur.y, cc.y);
+            comp[off] = cc;
+          } else {
+            cur.x = fmaf(w, d.val.x, cur.x);
+            cur.y = fmaf(w, d.val.y, cur.y);
+          }
+          acc[off] = cur;
         }
       }
       __syncwarp();
@@ -326,19 +376,28 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
   // write the tile (or partial tile), dropping the row padding
   constexpr int kPts = T * T * T;
   const int slot = scratch_slot(pt, ir);
+  auto value = [&](int lz, int ly, int lx) {
+    const int off = (lz * T + ly) * RS + lx;
+    float2 v = acc[off];
+    if constexpr (COMP) {
+      v.x += comp[off].x;
+      v.y += comp[off].y;
+    }
+    return v;
+  };
   if (slot < 0) {
     for (int i = tid; i < kPts; i += kThreads) {
       const int lx = i % T, ly = (i / T) % T, lz = i / (T * T);
       if (lz < to.e0 && ly < to.e1 && lx < to.e2) {
         const long long gi = ((long long)(to.o0 + lz) * g.g1 + (to.o1 + ly)) * g.g2 + (to.o2 + lx);
-        grid[gi] = acc[(lz * T + ly) * RS + lx];
+        grid[gi] = value(lz, ly, lx);
       }
     }
   } else {
     float2* dst = scratch + (long long)slot * kPts;
     for (int i = tid; i < kPts; i += kThreads) {
       const int lx = i % T, ly = (i / T) % T, lz = i / (T * T);
-      dst[i] = acc[(lz * T + ly) * RS + lx];
+      dst[i] = value(lz, ly, lx);
     }
   }
 }
@@ -346,10 +405,10 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
 // ---------------------------------------------------------------------------
 // Generic kernel (any W <= kMaxWidth, any CC), 8^3 tiles, warp per plane,
 // lanes over (coil, tap x, tap y) combinations.
-template <int W, int CC>
+template <int W, int CC, typename GT>
 __global__ void __launch_bounds__(kThreads) spread_generic_kernel(
     Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
-    float2* __restrict__ grids, float2* __restrict__ scratch) {
+    GT* __restrict__ grids, float2* __restrict__ scratch) {
   constexpr int T = 8, R = 64;
   extern __shared__ float4 smem_raw[];
   float2* acc = reinterpret_cast<float2*>(smem_raw);  // [T][T][T][CC]
@@ -362,7 +421,7 @@ __global__ void __launch_bounds__(kThreads) spread_generic_kernel(
   const SpreadItem it = ir.it;
   const int2* __restrict__ list = pt.list[ir.jj];
   const float4* __restrict__ qs = pt.qs[ir.jj];
-  float2* __restrict__ grid = grids + (long long)ir.jj * C * g.ngrid;
+  GT* __restrict__ grid = grids + (long long)ir.jj * C * g.ngrid;
   const int coil0 = blockIdx.y * CC;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TileOrigin to = tile_origin(g, tp, it.tile);
@@ -408,17 +467,18 @@ __global__ void __launch_bounds__(kThreads) spread_generic_kernel(
     }
   }
   __syncthreads();
-  write_tile<T, CC>(g, C, coil0, to, scratch_slot(pt, ir), acc, grid, scratch, tid);
+  write_tile<T, CC, GT>(g, C, coil0, to, scratch_slot(pt, ir), acc, nullptr, grid, scratch, tid);
 }
 
-// Sum the partial tiles of split tiles in slot order (deterministic).
-template <int T, int CC>
+// Sum the partial tiles of split tiles in slot order (deterministic); COMP:
+// Neumaier's compensated summation of the partials.
+template <int T, int CC, typename GT, bool COMP>
 __global__ void reduce_kernel(Geo g, int C, TilePlan tp, PhaseTable pt,
-                              const float2* __restrict__ scratch, float2* __restrict__ grids) {
+                              const float2* __restrict__ scratch, GT* __restrict__ grids) {
   const int jj = phase_of(pt.red0, pt.nphase, blockIdx.x);
   ReduceItem r = pt.reduces[jj][blockIdx.x - pt.red0[jj]];
   r.first += pt.slot0[jj];
-  float2* __restrict__ grid = grids + (long long)jj * C * g.ngrid;
+  GT* __restrict__ grid = grids + (long long)jj * C * g.ngrid;
   const int coil0 = blockIdx.y * CC;
   const TileOrigin to = tile_origin(g, tp, r.tile);
   constexpr int kPts = T * T * T;
@@ -427,66 +487,106 @@ __global__ void reduce_kernel(Geo g, int C, TilePlan tp, PhaseTable pt,
     const int c = i % CC;
     const int pt = i / CC;
     const int lx = pt % T, ly = (pt / T) % T, lz = pt / (T * T);
-    float2 s = make_float2(0.f, 0.f);
+    float2 s = make_float2(0.f, 0.f), e = make_float2(0.f, 0.f);
     for (int k = 0; k < r.count; ++k) {
       const float2 v =
           scratch[((long long)(r.first + k) * gridDim.y + blockIdx.y) * tile_elems + i];
-      s.x += v.x;
-      s.y += v.y;
+      if constexpr (COMP) {
+        const float tx = s.x + v.x, ty = s.y + v.y;
+        e.x += fabsf(s.x) >= fabsf(v.x) ? (s.x - tx) + v.x : (v.x - tx) + s.x;
+        e.y += fabsf(s.y) >= fabsf(v.y) ? (s.y - ty) + v.y : (v.y - ty) + s.y;
+        s.x = tx;
+        s.y = ty;
+      } else {
+        s.x += v.x;
+        s.y += v.y;
+      }
+    }
+    if constexpr (COMP) {
+      s.x += e.x;
+      s.y += e.y;
     }
     if (lz < to.e0 && ly < to.e1 && lx < to.e2 && coil0 + c < C) {
       const long long gi = ((long long)(to.o0 + lz) * g.g1 + (to.o1 + ly)) * g.g2 + (to.o2 + lx);
-      grid[(long long)(coil0 + c) * g.ngrid + gi] = s;
+      grid_st(grid + (long long)(coil0 + c) * g.ngrid + gi, s);
     }
   }
 }
 
-template <int T, int CC>
+template <int T, int CC, typename GT, bool COMP = false>
 int launch_reduce(const Geo& g, int C, const TilePlan& tp, const PhaseTable& pt, int chunks,
-                  float2* grids, const float2* scratch, cudaStream_t s) {
+                  GT* grids, const float2* scratch, cudaStream_t s) {
   const int nred = pt.red0[pt.nphase];
   if (nred == 0) return 0;
-  reduce_kernel<T, CC><<<dim3(nred, chunks), 256, 0, s>>>(g, C, tp, pt, scratch, grids);
+  reduce_kernel<T, CC, GT, COMP><<<dim3(nred, chunks), 256, 0, s>>>(g, C, tp, pt, scratch, grids);
   return 1;
 }
 
-template <int CC>
+template <int CC, typename GT, bool COMP>
 int dispatch_coils(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& tp,
-                   const PhaseTable& pt, const float2* vals, float2* grids, float2* scratch,
+                   const PhaseTable& pt, const float2* vals, GT* grids, float2* scratch,
                    cudaStream_t s) {
   const int chunks = (C + CC - 1) / CC;
-  const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2);
-  spread_coils_kernel<CC><<<dim3(pt.item0[pt.nphase], chunks), kThreads, smem, s>>>(
+  const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2) * (COMP ? 2 : 1);
+  spread_coils_kernel<CC, GT, COMP><<<dim3(pt.item0[pt.nphase], chunks), kThreads, smem, s>>>(
       g, kc, C, tp, pt, vals, grids, scratch);
-  return 1 + launch_reduce<8, CC>(g, C, tp, pt, chunks, grids, scratch, s);
+  return 1 + launch_reduce<8, CC, GT, COMP>(g, C, tp, pt, chunks, grids, scratch, s);
 }
 
-template <int W, int CC>
+template <int W, int CC, typename GT>
 int dispatch_generic(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& tp,
-                     const PhaseTable& pt, const float2* vals, float2* grids, float2* scratch,
+                     const PhaseTable& pt, const float2* vals, GT* grids, float2* scratch,
                      cudaStream_t s) {
   const int chunks = (C + CC - 1) / CC;
   const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2);
-  spread_generic_kernel<W, CC><<<dim3(pt.item0[pt.nphase], chunks), kThreads, smem, s>>>(
+  spread_generic_kernel<W, CC, GT><<<dim3(pt.item0[pt.nphase], chunks), kThreads, smem, s>>>(
       g, kc, C, tp, pt, vals, grids, scratch);
-  return 1 + launch_reduce<8, CC>(g, C, tp, pt, chunks, grids, scratch, s);
+  return 1 + launch_reduce<8, CC, GT>(g, C, tp, pt, chunks, grids, scratch, s);
+}
+
+template <typename GT, bool COMP>
+int spread_multi(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
+                 const PhaseTable& pt, const float2* v, GT* gr, float2* sc, cudaStream_t s) {
+  if (W == 4) {
+    if (C == 1) return dispatch_generic<4, 1, GT>(g, kc, C, tp, pt, v, gr, sc, s);
+    if (C <= 2) return dispatch_coils<2, GT, COMP>(g, kc, C, tp, pt, v, gr, sc, s);
+    if (C <= 4) return dispatch_coils<4, GT, COMP>(g, kc, C, tp, pt, v, gr, sc, s);
+    return dispatch_coils<8, GT, COMP>(g, kc, C, tp, pt, v, gr, sc, s);
+  }
+  if (C == 1) return dispatch_generic<6, 1, GT>(g, kc, C, tp, pt, v, gr, sc, s);
+  if (C <= 2) return dispatch_generic<6, 2, GT>(g, kc, C, tp, pt, v, gr, sc, s);
+  if (C <= 4) return dispatch_generic<6, 4, GT>(g, kc, C, tp, pt, v, gr, sc, s);
+  return dispatch_generic<6, 8, GT>(g, kc, C, tp, pt, v, gr, sc, s);
+}
+
+template <typename GT, bool COMP>
+cudaError_t set_coils_smem() {
+  const int big = 96 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(spread_coils_kernel<8, GT, COMP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(spread_coils_kernel<4, GT, COMP>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(spread_coils_kernel<2, GT, COMP>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  return e;
 }
 
 }  // namespace
 
 cudaError_t configure_spread_kernels() {
   const int big = 96 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(spread_coils_kernel<8>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaError_t e = set_coils_smem<float2, false>();
+  if (e == cudaSuccess) e = set_coils_smem<float2, true>();
+  if (e == cudaSuccess) e = set_coils_smem<bf162, false>();
+  if (e == cudaSuccess) e = set_coils_smem<bf162, true>();
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(spread_coils_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             big);
+    e = cudaFuncSetAttribute(spread_single_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(spread_coils_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(spread_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             big);
+    e = cudaFuncSetAttribute(spread_single_kernel<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e;
 }
 
@@ -497,29 +597,30 @@ int spread_tile_edge(int W, int C, int gmin) {
 int spread_coil_chunk(int C) { return C == 1 ? 1 : (C <= 2 ? 2 : (C <= 4 ? 4 : 8)); }
 
 int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
-                  const PhaseTable& pt, const nrsense_c64* vals, nrsense_c64* grids,
-                  nrsense_c64* scratch, int32_t* status, cudaStream_t s) {
+                  const PhaseTable& pt, const nrsense_c64* vals, void* grids, bool bf16,
+                  bool comp, nrsense_c64* scratch, int32_t* status, cudaStream_t s) {
   (void)status;
   if (pt.item0[pt.nphase] == 0) return 0;
   const auto* v = reinterpret_cast<const float2*>(vals);
-  auto* gr = reinterpret_cast<float2*>(grids);
   auto* sc = reinterpret_cast<float2*>(scratch);
-  if (W == 4) {
-    if (C == 1 && tp.t0 == 16) {
-      const size_t smem = size_t(16 * 16 * 20) * sizeof(float2);  // 40 KB, padded rows
-      spread_single_kernel<<<dim3(pt.item0[pt.nphase], 1), kThreads, smem, s>>>(g, kc, tp, pt, v,
-                                                                                 gr, sc);
-      return 1 + launch_reduce<16, 1>(g, 1, tp, pt, 1, gr, sc, s);
+  if (W == 4 && C == 1 && tp.t0 == 16 && !bf16) {
+    // single channel (image space), FP32 grid
+    auto* gr = static_cast<float2*>(grids);
+    const size_t smem = size_t(16 * 16 * 20) * sizeof(float2) * (comp ? 2 : 1);
+    if (comp) {
+      spread_single_kernel<true><<<dim3(pt.item0[pt.nphase], 1), kThreads, smem, s>>>(g, kc, tp, pt,
+                                                                                       v, gr, sc);
+      return 1 + launch_reduce<16, 1, float2, true>(g, 1, tp, pt, 1, gr, sc, s);
     }
-    if (C == 1) return dispatch_generic<4, 1>(g, kc, C, tp, pt, v, gr, sc, s);
-    if (C <= 2) return dispatch_coils<2>(g, kc, C, tp, pt, v, gr, sc, s);
-    if (C <= 4) return dispatch_coils<4>(g, kc, C, tp, pt, v, gr, sc, s);
-    return dispatch_coils<8>(g, kc, C, tp, pt, v, gr, sc, s);
+    spread_single_kernel<false><<<dim3(pt.item0[pt.nphase], 1), kThreads, smem, s>>>(
+        g, kc, tp, pt, v, gr, sc);
+    return 1 + launch_reduce<16, 1, float2>(g, 1, tp, pt, 1, gr, sc, s);
   }
-  if (C == 1) return dispatch_generic<6, 1>(g, kc, C, tp, pt, v, gr, sc, s);
-  if (C <= 2) return dispatch_generic<6, 2>(g, kc, C, tp, pt, v, gr, sc, s);
-  if (C <= 4) return dispatch_generic<6, 4>(g, kc, C, tp, pt, v, gr, sc, s);
-  return dispatch_generic<6, 8>(g, kc, C, tp, pt, v, gr, sc, s);
+  if (bf16)
+    return comp ? spread_multi<bf162, true>(g, W, kc, C, tp, pt, v, static_cast<bf162*>(grids), sc, s)
+                : spread_multi<bf162, false>(g, W, kc, C, tp, pt, v, static_cast<bf162*>(grids), sc, s);
+  return comp ? spread_multi<float2, true>(g, W, kc, C, tp, pt, v, static_cast<float2*>(grids), sc, s)
+              : spread_multi<float2, false>(g, W, kc, C, tp, pt, v, static_cast<float2*>(grids), sc, s);
 }
 
 }  // namespace nrs

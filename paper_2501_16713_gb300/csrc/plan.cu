@@ -17,6 +17,8 @@
 #include <vector>
 
 #include "kb_host.h"
+#include <cufftXt.h>
+
 #include "plan_internal.h"
 
 using namespace nrs;
@@ -354,10 +356,20 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   if (d.osf < 2 || d.osf > 4) return NRSENSE_ERR_ARG;
   if (d.kb_width != 4 && d.kb_width != 6) return NRSENSE_ERR_ARG;
   if (d.n_phases < 1 || d.n_coils < 0) return NRSENSE_ERR_ARG;
-  if (d.precision != NRSENSE_FP32) return NRSENSE_ERR_ARG;
+  if (d.precision != NRSENSE_FP32 && d.precision != NRSENSE_BF16_STORE &&
+      d.precision != NRSENSE_FP32_COMPENSATED)
+    return NRSENSE_ERR_ARG;
+  if (d.precision == NRSENSE_FP32_COMPENSATED && d.kb_width != 4) return NRSENSE_ERR_ARG;
+  if (d.precision == NRSENSE_BF16_STORE)  // cuFFT's BF16 transforms: power-of-two sizes
+    for (int a = 0; a < 3; ++a) {
+      const int ga = d.osf * d.n[a];
+      if (ga & (ga - 1)) return NRSENSE_ERR_ARG;
+    }
   if (!(d.kb_beta >= 0.0) || !std::isfinite(d.kb_beta)) return NRSENSE_ERR_ARG;
   p->desc = d;
   p->identity_warp = (d.flags & NRSENSE_IDENTITY_WARP) != 0;
+  p->grid_bf16 = d.precision == NRSENSE_BF16_STORE;
+  p->comp_spread = d.precision == NRSENSE_FP32_COMPENSATED;
   p->P = d.n_phases;
   p->C = d.n_coils;
   p->W = d.kb_width;
@@ -497,7 +509,8 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   if (p->C > 0) {
     // phases per launch: as many as half of the free memory allows (three
     // coil-grid buffers per phase plus about one for cuFFT's work area)
-    const long long per_phase = 4LL * p->C * g.ngrid * (long long)sizeof(nrsense_c64);
+    const long long elem = p->grid_bf16 ? 4 : 8;  // bytes per stored complex value
+    const long long per_phase = 4LL * p->C * g.ngrid * elem;
     int pc = d.phase_chunk;
     if (pc <= 0) {
       size_t free_b = 0, total_b = 0;
@@ -511,14 +524,27 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     std::vector<int> sizes = {pc, 1};
     if (p->P % pc) sizes.push_back(p->P % pc);
     int n[3] = {g.g0, g.g1, g.g2};
+    long long nl[3] = {g.g0, g.g1, g.g2};
     for (int nb : sizes) {
       bool have = false;
       for (auto& fp : p->fft_gc_plans) have |= (fp.first == nb);
       if (have) continue;
       cufftHandle h;
       // coil-major batch: grid (phase jj, coil c) starts at (jj * C + c) * G^3
-      NRS_TRY(cufft_check(cufftPlanMany(&h, 3, n, n, 1, int(g.ngrid), n, 1, int(g.ngrid),
-                                        CUFFT_C2C, nb * p->C)));
+      if (p->grid_bf16) {
+        NRS_TRY(cufft_check(cufftCreate(&h)));
+        size_t work = 0;
+        const cufftResult r =
+            cufftXtMakePlanMany(h, 3, nl, nl, 1, g.ngrid, CUDA_C_16BF, nl, 1, g.ngrid, CUDA_C_16BF,
+                                (long long)nb * p->C, &work, CUDA_C_16BF);
+        if (r != CUFFT_SUCCESS) {
+          cufftDestroy(h);
+          return NRSENSE_ERR_CUFFT;
+        }
+      } else {
+        NRS_TRY(cufft_check(cufftPlanMany(&h, 3, n, n, 1, int(g.ngrid), n, 1, int(g.ngrid),
+                                          CUFFT_C2C, nb * p->C)));
+      }
       p->fft_gc_plans.push_back({nb, h});
     }
   }
@@ -534,18 +560,14 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
       return NRSENSE_ERR_CUDA;
   }
   if (p->C > 0) {
-    const long long cg = g.ngrid * p->C * p->phase_chunk;
-    NRS_TRY(dev_alloc_n(p, &p->b_xpad, cg));
-    NRS_TRY(dev_alloc_n(p, &p->b_xwork, cg));
-    NRS_TRY(dev_alloc_n(p, &p->b_xspread, cg));
+    const size_t cgb = size_t(g.ngrid) * p->C * p->phase_chunk * (p->grid_bf16 ? 4 : 8);
+    NRS_TRY(dev_alloc(p, &p->b_xpad, cgb));
+    NRS_TRY(dev_alloc(p, &p->b_xwork, cgb));
+    NRS_TRY(dev_alloc(p, &p->b_xspread, cgb));
     // empty tiles of the spread target are never written: zero them once
-    if (cudaMemsetAsync(p->b_xspread, 0, size_t(cg) * sizeof(nrsense_c64), s) !=
-        cudaSuccess)
-      return NRSENSE_ERR_CUDA;
+    if (cudaMemsetAsync(p->b_xspread, 0, cgb, s) != cudaSuccess) return NRSENSE_ERR_CUDA;
     NRS_TRY(dev_alloc_n(p, &p->b_y, std::max<long long>(p->Mtot * p->C, 1)));
-    if (cudaMemsetAsync(p->b_xpad, 0, size_t(cg) * sizeof(nrsense_c64), s) !=
-        cudaSuccess)
-      return NRSENSE_ERR_CUDA;
+    if (cudaMemsetAsync(p->b_xpad, 0, cgb, s) != cudaSuccess) return NRSENSE_ERR_CUDA;
   }
   // scratch for split tiles: slots x coil chunks x tile x chunk coils
   long long need = 0;

@@ -72,9 +72,13 @@ struct nrsense_plan_s {
   nrsense_c64* b_ugrid = nullptr;  // G^3
   nrsense_c64* b_m = nullptr;      // P * N^3
   // coil grids of one phase chunk, (phase_chunk * C) x G^3 each
-  nrsense_c64* b_xpad = nullptr;     // zero outside the centred N^3 blocks
-  nrsense_c64* b_xwork = nullptr;    // FFT outputs
-  nrsense_c64* b_xspread = nullptr;  // spread target; tiles no phase occupies stay zero
+  // coil grids, phase_chunk * C * G^3 values each, complex FP32 or (grid_bf16)
+  // complex BF16
+  void* b_xpad = nullptr;     // zero outside the centred N^3 blocks
+  void* b_xwork = nullptr;    // FFT outputs
+  void* b_xspread = nullptr;  // spread target; tiles no phase occupies stay zero
+  bool grid_bf16 = false;     // desc.precision == NRSENSE_BF16_STORE
+  bool comp_spread = false;   // desc.precision == NRSENSE_FP32_COMPENSATED
   nrsense_c64* b_y = nullptr;      // Mtot * C
   nrsense_c64* b_tmp = nullptr;    // N^3 (normal operator scratch)
   nrsense_c64* b_scratch = nullptr;  // partial tiles
@@ -144,29 +148,31 @@ int launch_sum_phases(const Geo& g, int P, const nrsense_c64* m, nrsense_c64* x,
                        cudaStream_t s);
 
 // k space
+// Coil grids are complex FP32 (bf16 == false) or complex BF16 (bf16 == true).
 int launch_coil_fanout_pad(const Geo& g, int C, int nph, const float* deapod,
-                           const nrsense_c64* smaps, const nrsense_c64* m, nrsense_c64* xpad,
+                           const nrsense_c64* smaps, const nrsense_c64* m, void* xpad, bool bf16,
                            cudaStream_t s);
-int launch_image_to_padded(const Geo& g, int C, const float* deapod,
-                            const nrsense_c64* v, nrsense_c64* xpad, cudaStream_t s);
+int launch_image_to_padded(const Geo& g, int C, const float* deapod, const nrsense_c64* v,
+                           void* xpad, bool bf16, cudaStream_t s);
 int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
-                         const PhaseTable& pt, const nrsense_c64* grids, nrsense_c64* y,
+                         const PhaseTable& pt, const void* grids, bool bf16, nrsense_c64* y,
                          cudaStream_t s);
 // one-time kernel attributes (large dynamic shared memory); plan time
 cudaError_t configure_kernels();
 cudaError_t configure_spread_kernels();
 int launch_crop_coilsum(const Geo& g, int C, int nph, const float* deapod,
-                        const nrsense_c64* smaps, const nrsense_c64* xg, nrsense_c64* w,
+                        const nrsense_c64* smaps, const void* xg, bool bf16, nrsense_c64* w,
                         cudaStream_t s);
-int launch_crop_to_coils(const Geo& g, int C, const float* deapod,
-                          const nrsense_c64* xg, nrsense_c64* v, cudaStream_t s);
+int launch_crop_to_coils(const Geo& g, int C, const float* deapod, const void* xg, bool bf16,
+                         nrsense_c64* v, cudaStream_t s);
 
 // spreading (both domains)
 // Spread the phases of `pt` (values at rows row0[jj] + perm of vals) into
-// consecutive grid slots (phase jj at grids + jj * C * G^3).
+// consecutive grid slots (phase jj at grids + jj * C * G^3); comp selects
+// compensated accumulation (W = 4 kernels).
 int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
-                  const PhaseTable& pt, const nrsense_c64* vals, nrsense_c64* grids,
-                  nrsense_c64* scratch, int32_t* status, cudaStream_t s);
+                  const PhaseTable& pt, const nrsense_c64* vals, void* grids, bool bf16,
+                  bool comp, nrsense_c64* scratch, int32_t* status, cudaStream_t s);
 // coils handled by one spreading CTA
 int spread_coil_chunk(int C);
 // free the CG workspace of a plan (solver.cu)

@@ -36,6 +36,7 @@ namespace {
 
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 1184;  // fixed grid: deterministic summation order (8 x 148)
+constexpr int kGraphMax = 64;     // iterations captured in one graph (fixed-count solves)
 
 struct CgState {
   double rr;      // <r, r>
@@ -523,7 +524,12 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
 
   // iterations, in chunks; the converged flag is read between chunks
   const bool graph = (flags & NRSENSE_CG_GRAPH) != 0;
-  const int chunk = rec ? 1 : graph ? std::max(1, std::min<int>(maxit, 10)) : 5;
+  // graph chunks: a fixed-count solve (tol == 0) is one graph of up to kGraphMax
+  // iterations; a tolerance-driven solve replays 10-iteration graphs and reads
+  // the converged flag between them (iterations after convergence are no-ops)
+  const int chunk = rec ? 1
+                  : graph ? std::max(1, std::min<int>(maxit, tol == 0.0 ? kGraphMax : 10))
+                          : 5;
   const int mode = flexible ? 1 : 0;
   if (graph && (w->gexec == nullptr || w->g_x != x || w->g_lambda != lambda ||
                 w->g_chunk != chunk || w->g_mode != mode || w->g_net != net)) {

@@ -23,6 +23,8 @@ STATUS = {
     -9: "call not valid for this plan",
 }
 FP32 = 0
+BF16_STORE = 1
+FP32_COMPENSATED = 2
 IDENTITY_WARP = 1
 
 
@@ -189,7 +191,8 @@ class Plan:
     """
 
     def __init__(self, shape, disp=None, coords=None, smaps=None, n_phases=None, osf=2,
-                 width=4, beta=0.0, identity_warp=False, stream=None, phase_chunk=0):
+                 width=4, beta=0.0, identity_warp=False, stream=None, phase_chunk=0,
+                 precision=FP32):
         import torch
         self.lib = load()
         self.shape = tuple(int(s) for s in shape)
@@ -207,7 +210,7 @@ class Plan:
         d.n[:] = self.shape
         d.osf, d.kb_width, d.kb_beta = int(osf), int(width), float(beta)
         d.n_phases, d.n_coils = self.n_phases, self.n_coils
-        d.precision = FP32
+        d.precision = int(precision)
         d.flags = IDENTITY_WARP if identity_warp else 0
         d.phase_chunk = int(phase_chunk)
         self.counts = [0] * self.n_phases
