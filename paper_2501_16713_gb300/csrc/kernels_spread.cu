@@ -277,6 +277,126 @@ __global__ void __launch_bounds__(kThreads) spread_coils_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// W = 4, CC coils, 8^3 tiles, register accumulation.  Warp w owns plane w of
+// the tile; lane (x = lane % 8, yh = lane / 8) owns the two grid points
+// (w, yh, x) and (w, yh + 4, x) for all CC coils in registers.  The warp
+// streams its plane's range of the list with the same per-warp staging as
+// spread_coils_kernel; every lane then adds each staged point's contribution
+// to its own two points (zero weight outside the point's 4 x 4 footprint in
+// the plane), so nothing is read back from or written to shared memory per
+// update.  The result (and the order of every sum) is the same per grid value
+// as for the shared-memory kernel: list order within the item.
+template <int CC, typename GT>
+__global__ void __launch_bounds__(kThreads) spread_coils_reg_kernel(
+    Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
+    GT* __restrict__ grids, float2* __restrict__ scratch) {
+  constexpr int W = 4, T = 8, B = 32, NB = W + T + 1;
+  static_assert(CC == 2 || CC == 4 || CC == 8, "coil chunk");
+  __shared__ __align__(16) CoilStage<CC> stg[kThreads / 32][B];
+
+  const ItemRef ir = item_ref(pt);
+  const SpreadItem it = ir.it;
+  const int2* __restrict__ list = pt.list[ir.jj];
+  const float4* __restrict__ qs = pt.qs[ir.jj];
+  const long long row0 = pt.row0[ir.jj];
+  GT* __restrict__ grid = grids + (long long)ir.jj * C * g.ngrid;
+  const int coil0 = blockIdx.y * CC;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TileOrigin to = tile_origin(g, tp, it.tile);
+  const int lz = warp, x = lane & 7, yh = lane >> 3;
+
+  float2 acc[2][CC];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int c = 0; c < CC; ++c) acc[h][c] = make_float2(0.f, 0.f);
+
+  if (lz < to.e0) {
+    const int32_t* ib = pt.bins[ir.jj] + (long long)ir.local * NB;
+    const int beg = it.begin + __ldg(ib + min(lz, NB - 1));
+    const int end = it.begin + __ldg(ib + min(lz + W, NB - 1));
+    CoilStage<CC>* st = stg[warp];
+    for (int base = beg; base < end; base += B) {
+      const int n = min(B, end - base);
+      if (lane < n) {
+        const int2 e = __ldg(list + base + lane);
+        const float4 qq = __ldg(qs + e.x);
+        int b0, b1, b2;
+        unpack_base(__float_as_uint(qq.w), b0, b1, b2);
+        int r0 = b0 - to.o0, r1 = b1 - to.o1, r2 = b2 - to.o2;
+        if (r0 < 0) r0 += g.g0;
+        if (r0 >= T) r0 -= g.g0;
+        if (r1 < 0) r1 += g.g1;
+        if (r1 >= T) r1 -= g.g1;
+        if (r2 < 0) r2 += g.g2;
+        if (r2 >= T) r2 -= g.g2;
+        float wz[W], wy[W], wx[W];
+        kernel_weights<W>(qq.x, kc, wz);
+        kernel_weights<W>(qq.y, kc, wy);
+        kernel_weights<W>(qq.z, kc, wx);
+        const int t0 = lz - r0;
+        const float wzt = ((unsigned)t0 < (unsigned)W) ? select_tap<W>(wz, t0) : 0.f;
+        CoilStage<CC>& d = st[lane];
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+          d.wzy[t] = wzt * wy[t];
+          d.wx[t] = wx[t];
+        }
+        d.r1 = r1;
+        d.r2 = r2;
+        const float2* src = vals + (row0 + e.y) * C + coil0;
+#pragma unroll
+        for (int c = 0; c < CC; ++c)
+          d.val[c] = (coil0 + c < C) ? __ldg(src + c) : make_float2(0.f, 0.f);
+      }
+      __syncwarp();
+      for (int p = 0; p < n; ++p) {
+        const CoilStage<CC>& d = st[p];
+        const int tx = x - d.r2, ty0 = yh - d.r1, ty1 = ty0 + 4;
+        const float wxv = (unsigned)tx < (unsigned)W ? d.wx[tx & (W - 1)] : 0.f;
+        const float w0 = (unsigned)ty0 < (unsigned)W ? d.wzy[ty0 & (W - 1)] * wxv : 0.f;
+        const float w1 = (unsigned)ty1 < (unsigned)W ? d.wzy[ty1 & (W - 1)] * wxv : 0.f;
+#pragma unroll
+        for (int c2 = 0; c2 < CC / 2; ++c2) {
+          const float4 v = reinterpret_cast<const float4*>(d.val)[c2];
+          acc[0][2 * c2].x = fmaf(w0, v.x, acc[0][2 * c2].x);
+          acc[0][2 * c2].y = fmaf(w0, v.y, acc[0][2 * c2].y);
+          acc[0][2 * c2 + 1].x = fmaf(w0, v.z, acc[0][2 * c2 + 1].x);
+          acc[0][2 * c2 + 1].y = fmaf(w0, v.w, acc[0][2 * c2 + 1].y);
+          acc[1][2 * c2].x = fmaf(w1, v.x, acc[1][2 * c2].x);
+          acc[1][2 * c2].y = fmaf(w1, v.y, acc[1][2 * c2].y);
+          acc[1][2 * c2 + 1].x = fmaf(w1, v.z, acc[1][2 * c2 + 1].x);
+          acc[1][2 * c2 + 1].y = fmaf(w1, v.w, acc[1][2 * c2 + 1].y);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // write out: rows yh and yh + 4 of plane lz (outside the grid: not written)
+  const int slot = scratch_slot(pt, ir);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int ly = yh + 4 * h;
+    if (slot < 0) {
+      if (lz < to.e0 && ly < to.e1 && x < to.e2) {
+        const long long gi = ((long long)(to.o0 + lz) * g.g1 + (to.o1 + ly)) * g.g2 + (to.o2 + x);
+#pragma unroll
+        for (int c = 0; c < CC; ++c)
+          if (coil0 + c < C) grid_st(grid + (long long)(coil0 + c) * g.ngrid + gi, acc[h][c]);
+      }
+    } else {
+      float2* dst = scratch + ((long long)slot * gridDim.y + blockIdx.y) * (T * T * T * CC) +
+                    ((lz * T + ly) * T + x) * CC;
+#pragma unroll
+      for (int c2 = 0; c2 < CC / 2; ++c2)
+        reinterpret_cast<float4*>(dst)[c2] =
+            make_float4(acc[h][2 * c2].x, acc[h][2 * c2].y, acc[h][2 * c2 + 1].x,
+                        acc[h][2 * c2 + 1].y);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // W = 4, one channel (image space), 16^3 tiles.  Warp w owns planes 2w and
 // 2w+1 (one per half-warp) and streams the union of their list ranges, with
 // the same per-warp staging as above; lane = (tap x, tap y, plane).
@@ -527,9 +647,15 @@ int dispatch_coils(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& t
                    const PhaseTable& pt, const float2* vals, GT* grids, float2* scratch,
                    cudaStream_t s) {
   const int chunks = (C + CC - 1) / CC;
-  const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2) * (COMP ? 2 : 1);
-  spread_coils_kernel<CC, GT, COMP><<<dim3(pt.item0[pt.nphase], chunks), kThreads, smem, s>>>(
-      g, kc, C, tp, pt, vals, grids, scratch);
+  const dim3 grid(pt.item0[pt.nphase], chunks);
+  if constexpr (COMP) {
+    const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2) * 2;
+    spread_coils_kernel<CC, GT, true><<<grid, kThreads, smem, s>>>(g, kc, C, tp, pt, vals, grids,
+                                                                   scratch);
+  } else {
+    spread_coils_reg_kernel<CC, GT><<<grid, kThreads, 0, s>>>(g, kc, C, tp, pt, vals, grids,
+                                                              scratch);
+  }
   return 1 + launch_reduce<8, CC, GT, COMP>(g, C, tp, pt, chunks, grids, scratch, s);
 }
 
