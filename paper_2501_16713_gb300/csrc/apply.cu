@@ -28,14 +28,25 @@ namespace {
   } while (0)
 
 nrsense_status fft(nrsense_plan_s* p, int stage, cufftHandle h, cudaStream_t s, void* in,
-                   void* out, int dir) {
+                   void* out, int dir, int nph = 0) {
   StageMark mark(p, stage, s);
   if (cufftSetStream(h, s) != CUFFT_SUCCESS) return NRSENSE_ERR_CUFFT;
-  // the batched coil-grid transforms of a BF16-storage plan are cufftXt plans
+  if (stage == NRSENSE_STAGE_FFT_GC && p->grid_bf16) {
+    // BF16 coil grids: cufftXt plans of fewer than 2^31 elements, run as
+    // consecutive full sub-batches over the nph * C grids
+    const long long total = (long long)nph * p->C;
+    const long long sub = bf16_sub_batch(total, p->geo.ngrid);  // as at plan time
+    if (sub < 1) return NRSENSE_ERR_CUFFT;
+    const size_t step = size_t(sub) * size_t(p->geo.ngrid) * 4;  // bytes of sub grids
+    for (long long k = 0; k < total; k += sub) {
+      char* i = static_cast<char*>(in) + size_t(k / sub) * step;
+      char* o = static_cast<char*>(out) + size_t(k / sub) * step;
+      if (cufftXtExec(h, i, o, dir) != CUFFT_SUCCESS) return NRSENSE_ERR_CUFFT;
+    }
+    return NRSENSE_OK;
+  }
   const cufftResult r =
-      (stage == NRSENSE_STAGE_FFT_GC && p->grid_bf16)
-          ? cufftXtExec(h, in, out, dir)
-          : cufftExecC2C(h, static_cast<cufftComplex*>(in), static_cast<cufftComplex*>(out), dir);
+      cufftExecC2C(h, static_cast<cufftComplex*>(in), static_cast<cufftComplex*>(out), dir);
   return r == CUFFT_SUCCESS ? NRSENSE_OK : NRSENSE_ERR_CUFFT;
 }
 
@@ -144,7 +155,8 @@ nrsense_status sense_chunk_forward(nrsense_plan_s* p, int j0, int j1, const nrse
   STAGE(COIL_FANOUT, launch_coil_fanout_pad(g, p->C, nph, p->deapod, p->smaps, m, p->b_xpad,
                                             p->grid_bf16, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, nph), s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, nph), s, p->b_xpad, p->b_xwork, CUFFT_FORWARD,
+              nph));
   const PhaseTable t = kspace_table(p, j0, j1, /*spread=*/false, row_base);
   STAGE(INTERP_KSPACE, launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
                                             p->grid_bf16, y, s));
@@ -160,7 +172,8 @@ nrsense_status sense_chunk_adjoint(nrsense_plan_s* p, int j0, int j1, const nrse
   STAGE(SPREAD_KSPACE, launch_spread(g, p->W, p->kc, p->C, p->ktiles, t, y, p->b_xspread,
                                      p->grid_bf16, p->comp_spread, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, nph), s, p->b_xspread, p->b_xwork, CUFFT_INVERSE));
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, nph), s, p->b_xspread, p->b_xwork, CUFFT_INVERSE,
+              nph));
   STAGE(CROP_COILSUM, launch_crop_coilsum(g, p->C, nph, p->deapod, p->smaps, p->b_xwork,
                                           p->grid_bf16, w, s));
   return launched();
@@ -190,7 +203,7 @@ nrsense_status nrsense_kspace_forward(nrsense_plan_t p, int32_t phase, const nrs
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   STAGE(COIL_FANOUT, launch_image_to_padded(p->geo, p->C, p->deapod, v, p->b_xpad, p->grid_bf16, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, 1), s, p->b_xpad, p->b_xwork, CUFFT_FORWARD));
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, 1), s, p->b_xpad, p->b_xwork, CUFFT_FORWARD, 1));
   const PhaseTable t = kspace_table(p, phase, phase + 1, false, p->off[phase]);
   STAGE(INTERP_KSPACE, launch_interp_kspace(p->geo, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
                                             p->grid_bf16, y, s));
@@ -207,7 +220,7 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t p, int32_t phase, const nrs
   STAGE(SPREAD_KSPACE, launch_spread(p->geo, p->W, p->kc, p->C, p->ktiles, t, y, p->b_xspread,
                                      p->grid_bf16, p->comp_spread, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, 1), s, p->b_xspread, p->b_xwork, CUFFT_INVERSE));
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, 1), s, p->b_xspread, p->b_xwork, CUFFT_INVERSE, 1));
   STAGE(CROP_COILSUM, launch_crop_to_coils(p->geo, p->C, p->deapod, p->b_xwork, p->grid_bf16, v, s));
   return launched();
 }

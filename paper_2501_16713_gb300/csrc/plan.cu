@@ -523,7 +523,6 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     // chunk, and a single phase (stage calls)
     std::vector<int> sizes = {pc, 1};
     if (p->P % pc) sizes.push_back(p->P % pc);
-    int n[3] = {g.g0, g.g1, g.g2};
     long long nl[3] = {g.g0, g.g1, g.g2};
     for (int nb : sizes) {
       bool have = false;
@@ -534,16 +533,28 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
       if (p->grid_bf16) {
         NRS_TRY(cufft_check(cufftCreate(&h)));
         size_t work = 0;
+        const long long batch = bf16_sub_batch((long long)nb * p->C, g.ngrid);
+        if (batch < 1) {
+          cufftDestroy(h);
+          return NRSENSE_ERR_ARG;
+        }
         const cufftResult r =
             cufftXtMakePlanMany(h, 3, nl, nl, 1, g.ngrid, CUDA_C_16BF, nl, 1, g.ngrid, CUDA_C_16BF,
-                                (long long)nb * p->C, &work, CUDA_C_16BF);
+                                batch, &work, CUDA_C_16BF);
         if (r != CUFFT_SUCCESS) {
           cufftDestroy(h);
           return NRSENSE_ERR_CUFFT;
         }
       } else {
-        NRS_TRY(cufft_check(cufftPlanMany(&h, 3, n, n, 1, int(g.ngrid), n, 1, int(g.ngrid),
-                                          CUFFT_C2C, nb * p->C)));
+        // 64-bit planning: a batch of coil grids can exceed 2^31 elements
+        NRS_TRY(cufft_check(cufftCreate(&h)));
+        size_t work = 0;
+        const cufftResult r = cufftMakePlanMany64(h, 3, nl, nl, 1, g.ngrid, nl, 1, g.ngrid,
+                                                  CUFFT_C2C, (long long)nb * p->C, &work);
+        if (r != CUFFT_SUCCESS) {
+          cufftDestroy(h);
+          return NRSENSE_ERR_CUFFT;
+        }
       }
       p->fft_gc_plans.push_back({nb, h});
     }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cufft.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -89,6 +90,7 @@ struct nrsense_plan_s {
   bool have_fft_n = false, have_fft_g = false;
   std::vector<std::pair<int, cufftHandle>> fft_gc_plans;  // (phases per batch, plan)
 
+
   long long device_bytes = 0;
   std::vector<void*> allocations;
 
@@ -103,6 +105,17 @@ struct nrsense_plan_s {
 };
 
 namespace nrs {
+// Transforms per cuFFT execution of `total` BF16 coil grids of `ngrid` points:
+// cuFFT's BF16 plans hold fewer than 2^31 elements, so the batch runs as
+// consecutive sub-batches; the size is the largest divisor of total under
+// that limit (every sub-batch is full).  0 if one grid alone is too large.
+inline long long bf16_sub_batch(long long total, long long ngrid) {
+  const long long limit = ((1LL << 31) - 1) / ngrid;
+  for (long long d = std::min(total, limit); d >= 1; --d)
+    if (total % d == 0) return d;
+  return 0;
+}
+
 // RAII stage marker: records an event pair around a stage when profiling.
 struct StageMark {
   nrsense_plan_s* p;
