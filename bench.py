@@ -369,6 +369,7 @@ def run_cg192(args):
                 coords=[torch.from_numpy(c).to(dev) for c in w["coords"]],
                 smaps=torch.from_numpy(w["smaps"]).to(dev))
     t_plan = time.perf_counter() - t0
+    tuning = plan.autotune(reps=3)
     info = plan.info()
     x = torch.from_numpy(w["x"]).to(dev)
     lam_max = _lambda_max(plan, shape, dev)
@@ -413,6 +414,7 @@ def run_cg192(args):
                        "phases": len(plan.counts), "samples_per_phase": plan.counts,
                        "lambda": lam, "lambda_rel": 1e-3, "iterations": iters,
                        "phase_chunk": info["phase_chunk"], "plan_s": round(t_plan, 1),
+                       "tuning": tuning,
                        "device_bytes": info["device_bytes"]},
             "ms_per_iteration": ms / iters, "normal_applies_per_s": 1000.0 / ms_e,
             "rel_residual_after_30": hist[-1] if hist else None,
@@ -547,6 +549,7 @@ def run_gpu(args, rank, world, local_rank):
     coords = [torch.from_numpy(c).to(dev) for c in w["coords"]]
     plan = Plan(shape, disp=disp, coords=coords, smaps=smaps)
     del disp, smaps, coords
+    tuning = plan.autotune(reps=3)  # launch choices, timed on this plan (untimed region)
     info = plan.info()
     x = torch.from_numpy(w["x"]).to(dev)
     out = torch.empty_like(x)
@@ -661,6 +664,7 @@ def run_gpu(args, rank, world, local_rank):
         "config": {"workload": args.workload, "image": list(shape), "coils": spec.n_coils,
                    "phases": len(M), "samples_per_phase": M, "osf": 2, "kb_width": 4,
                    "lambda": args.lam, "parallelism": f"replicas x{world}",
+                   "tuning": tuning,
                    "l2": "inputs larger than L2: per-phase coil grids 1.07 GB, "
                          "E touches ~12 GB per step; no flush"},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),

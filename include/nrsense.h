@@ -364,6 +364,32 @@ nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* 
                                    double* out_dev, void* stream);
 
 /*
+ * Autotuning of the launch choices of a plan (no counterpart in the paper).
+ * nrsense_plan_autotune times, on the plan's own k-space point sets (first
+ * phase chunk) and internal buffers, the k-space spreading kernel with
+ * register accumulation and with shared-memory accumulation, and the k-space
+ * interpolation with 8 and with 4 coils per CTA (reps launches each, after
+ * one warm-up launch, CUDA events on `stream`; synchronises), keeps the
+ * faster of each in the plan and reports times and choices in *out (host).
+ * The compensated precision always uses shared-memory accumulation; plans
+ * without coils have nothing to tune (*out holds the current choices).
+ * nrsense_plan_set_tuning applies stored choices (e.g. a cache keyed by the
+ * geometry).  Both change only speed: every choice computes the same values.
+ * Errors: ERR_ARG (null, reps outside 1..100, unknown choice), ERR_CUDA.
+ */
+#define NRSENSE_TUNE_SPREAD_REGISTER 1
+#define NRSENSE_TUNE_SPREAD_SHARED   2
+typedef struct {
+  int32_t spread_variant;  /* NRSENSE_TUNE_SPREAD_* */
+  int32_t interp_coils;    /* coils per interpolation CTA: 8 or 4 */
+  double  spread_ms[2];    /* measured: register, shared */
+  double  interp_ms[2];    /* measured: 8 coils, 4 coils */
+} nrsense_tuning;
+nrsense_status nrsense_plan_autotune(nrsense_plan_t plan, int32_t reps, nrsense_tuning* out_host,
+                                     void* stream);
+nrsense_status nrsense_plan_set_tuning(nrsense_plan_t plan, const nrsense_tuning* tuning_host);
+
+/*
  * nrsense_device_status - read (and with clear != 0, reset) the plan's
  * latched device status word; synchronises `stream`.  *out_host receives
  * NRSENSE_OK or the first device-side error (ERR_BOUNDS, ERR_TIMEOUT).

@@ -138,7 +138,7 @@ nrsense_status warp_adjoint(nrsense_plan_s* p, const nrsense_c64* m, nrsense_c64
   }
   const PhaseTable t = image_table(p);
   STAGE(SPREAD_IMAGE, launch_spread(g, p->W, p->kc, 1, p->itiles, t, m, p->b_ugrid, false,
-                                    p->comp_spread, p->b_scratch, p->d_status, s));
+                                    p->comp_spread, p->spread_variant, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_ugrid, p->b_ugrid, CUFFT_FORWARD));
   STAGE(CROP_DEAPOD, launch_crop_deapod(g, p->deapod, p->b_ugrid, x, s));
@@ -159,7 +159,7 @@ nrsense_status sense_chunk_forward(nrsense_plan_s* p, int j0, int j1, const nrse
               nph));
   const PhaseTable t = kspace_table(p, j0, j1, /*spread=*/false, row_base);
   STAGE(INTERP_KSPACE, launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
-                                            p->grid_bf16, y, s));
+                                            p->grid_bf16, y, p->interp_coils, s));
   return launched();
 }
 
@@ -170,7 +170,7 @@ nrsense_status sense_chunk_adjoint(nrsense_plan_s* p, int j0, int j1, const nrse
   const int nph = j1 - j0;
   const PhaseTable t = kspace_table(p, j0, j1, /*spread=*/true, row_base);
   STAGE(SPREAD_KSPACE, launch_spread(g, p->W, p->kc, p->C, p->ktiles, t, y, p->b_xspread,
-                                     p->grid_bf16, p->comp_spread, p->b_scratch, p->d_status, s));
+                                     p->grid_bf16, p->comp_spread, p->spread_variant, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, nph), s, p->b_xspread, p->b_xwork, CUFFT_INVERSE,
               nph));
@@ -206,7 +206,7 @@ nrsense_status nrsense_kspace_forward(nrsense_plan_t p, int32_t phase, const nrs
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, 1), s, p->b_xpad, p->b_xwork, CUFFT_FORWARD, 1));
   const PhaseTable t = kspace_table(p, phase, phase + 1, false, p->off[phase]);
   STAGE(INTERP_KSPACE, launch_interp_kspace(p->geo, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
-                                            p->grid_bf16, y, s));
+                                            p->grid_bf16, y, p->interp_coils, s));
   return launched();
 }
 
@@ -218,7 +218,7 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t p, int32_t phase, const nrs
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const PhaseTable t = kspace_table(p, phase, phase + 1, true, p->off[phase]);
   STAGE(SPREAD_KSPACE, launch_spread(p->geo, p->W, p->kc, p->C, p->ktiles, t, y, p->b_xspread,
-                                     p->grid_bf16, p->comp_spread, p->b_scratch, p->d_status, s));
+                                     p->grid_bf16, p->comp_spread, p->spread_variant, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, 1), s, p->b_xspread, p->b_xwork, CUFFT_INVERSE, 1));
   STAGE(CROP_COILSUM, launch_crop_to_coils(p->geo, p->C, p->deapod, p->b_xwork, p->grid_bf16, v, s));
@@ -268,6 +268,74 @@ nrsense_status nrsense_apply_normal(nrsense_plan_t p, const nrsense_c64* x, doub
     STAGE(VECTOR, launch_axpby(p->geo.nvox, x, float(lambda), out, 1.0f, s));
     NRS_TRY(launched());
   }
+  return NRSENSE_OK;
+}
+
+nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t) {
+  if (p == nullptr || t == nullptr) return NRSENSE_ERR_ARG;
+  if (t->spread_variant != NRSENSE_TUNE_SPREAD_REGISTER &&
+      t->spread_variant != NRSENSE_TUNE_SPREAD_SHARED)
+    return NRSENSE_ERR_ARG;
+  if (t->interp_coils != 4 && t->interp_coils != 8) return NRSENSE_ERR_ARG;
+  p->spread_variant = t->spread_variant == NRSENSE_TUNE_SPREAD_REGISTER ? kSpreadRegister
+                                                                         : kSpreadShared;
+  p->interp_coils = t->interp_coils;
+  return NRSENSE_OK;
+}
+
+nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tuning* out,
+                                     void* stream) {
+  if (p == nullptr || out == nullptr || reps < 1 || reps > 100) return NRSENSE_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->spread_variant = p->spread_variant == kSpreadRegister ? NRSENSE_TUNE_SPREAD_REGISTER
+                                                             : NRSENSE_TUNE_SPREAD_SHARED;
+  out->interp_coils = p->interp_coils;
+  if (p->C == 0) return NRSENSE_OK;  // nothing to choose without k space
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Geo& g = p->geo;
+  const int j1 = std::min(p->P, p->phase_chunk);
+  const PhaseTable ts = kspace_table(p, 0, j1, true, 0);
+  const PhaseTable ti = kspace_table(p, 0, j1, false, 0);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return NRSENSE_ERR_CUDA;
+  // times the candidates on the plan's own point sets and internal buffers
+  // (their contents are overwritten by every application)
+  auto time_ms = [&](auto&& launch) -> double {
+    launch();
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) launch();
+    cudaEventRecord(e1, s);
+    float ms = -1.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      return -1.0;
+    return double(ms) / reps;
+  };
+  const int variants[2] = {kSpreadRegister, kSpreadShared};
+  for (int k = 0; k < 2; ++k)
+    out->spread_ms[k] = time_ms([&] {
+      p->launches += launch_spread(g, p->W, p->kc, p->C, p->ktiles, ts, p->b_y, p->b_xspread,
+                                   p->grid_bf16, p->comp_spread, variants[k], p->b_scratch,
+                                   p->d_status, s);
+    });
+  const int chunks[2] = {8, 4};
+  for (int k = 0; k < 2; ++k)
+    out->interp_ms[k] = time_ms([&] {
+      p->launches += launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, ti, p->b_xwork,
+                                          p->grid_bf16, p->b_y, chunks[k], s);
+    });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess) return NRSENSE_ERR_CUDA;
+  for (int k = 0; k < 2; ++k)
+    if (!(out->spread_ms[k] >= 0.0) || !(out->interp_ms[k] >= 0.0)) return NRSENSE_ERR_CUDA;
+  // the compensated variant has only the shared-memory kernel: keep the default there
+  if (!p->comp_spread)
+    p->spread_variant = out->spread_ms[1] < out->spread_ms[0] ? kSpreadShared : kSpreadRegister;
+  p->interp_coils = out->interp_ms[1] < out->interp_ms[0] ? 4 : 8;
+  out->spread_variant = p->spread_variant == kSpreadRegister ? NRSENSE_TUNE_SPREAD_REGISTER
+                                                             : NRSENSE_TUNE_SPREAD_SHARED;
+  out->interp_coils = p->interp_coils;
   return NRSENSE_OK;
 }
 

@@ -294,12 +294,13 @@ cudaError_t set_interp_smem() {
 
 template <typename GT>
 void interp_dispatch(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
-                     const PhaseTable& pt, const GT* gp, float2* yp, int nitems, cudaStream_t s) {
-  if (W == 4 && C > 4) {
+                     const PhaseTable& pt, const GT* gp, float2* yp, int nitems, int coil_chunk,
+                     cudaStream_t s) {
+  if (W == 4 && C > 4 && coil_chunk != 4) {
     const dim3 gd(nitems, (C + 7) / 8);
     interp_tile_kernel<4, 8, GT><<<gd, 256, interp_smem<4, 8, GT>(), s>>>(g, kc, C, tp, pt, gp, yp);
   } else if (W == 4) {
-    interp_tile_kernel<4, 4, GT><<<dim3(nitems, 1), 256, interp_smem<4, 4, GT>(), s>>>(
+    interp_tile_kernel<4, 4, GT><<<dim3(nitems, (C + 3) / 4), 256, interp_smem<4, 4, GT>(), s>>>(
         g, kc, C, tp, pt, gp, yp);
   } else {
     const dim3 gd(nitems, (C + 3) / 4);
@@ -321,14 +322,16 @@ cudaError_t configure_kernels() {
 
 int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                          const PhaseTable& pt, const void* grids, bool bf16, nrsense_c64* y,
-                         cudaStream_t s) {
+                         int coil_chunk, cudaStream_t s) {
   const int nitems = pt.item0[pt.nphase];
   if (nitems == 0) return 0;
   auto* yp = reinterpret_cast<float2*>(y);
   if (bf16)
-    interp_dispatch(g, W, kc, C, tp, pt, static_cast<const bf162*>(grids), yp, nitems, s);
+    interp_dispatch(g, W, kc, C, tp, pt, static_cast<const bf162*>(grids), yp, nitems, coil_chunk,
+                    s);
   else
-    interp_dispatch(g, W, kc, C, tp, pt, static_cast<const float2*>(grids), yp, nitems, s);
+    interp_dispatch(g, W, kc, C, tp, pt, static_cast<const float2*>(grids), yp, nitems,
+                    coil_chunk, s);
   return 1;
 }
 

@@ -645,12 +645,12 @@ int launch_reduce(const Geo& g, int C, const TilePlan& tp, const PhaseTable& pt,
 template <int CC, typename GT, bool COMP>
 int dispatch_coils(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& tp,
                    const PhaseTable& pt, const float2* vals, GT* grids, float2* scratch,
-                   cudaStream_t s) {
+                   int variant, cudaStream_t s) {
   const int chunks = (C + CC - 1) / CC;
   const dim3 grid(pt.item0[pt.nphase], chunks);
-  if constexpr (COMP) {
-    const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2) * 2;
-    spread_coils_kernel<CC, GT, true><<<grid, kThreads, smem, s>>>(g, kc, C, tp, pt, vals, grids,
+  if (COMP || variant == kSpreadShared) {
+    const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2) * (COMP ? 2 : 1);
+    spread_coils_kernel<CC, GT, COMP><<<grid, kThreads, smem, s>>>(g, kc, C, tp, pt, vals, grids,
                                                                    scratch);
   } else {
     spread_coils_reg_kernel<CC, GT><<<grid, kThreads, 0, s>>>(g, kc, C, tp, pt, vals, grids,
@@ -672,12 +672,13 @@ int dispatch_generic(const Geo& g, const KernelCoefs& kc, int C, const TilePlan&
 
 template <typename GT, bool COMP>
 int spread_multi(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
-                 const PhaseTable& pt, const float2* v, GT* gr, float2* sc, cudaStream_t s) {
+                 const PhaseTable& pt, const float2* v, GT* gr, float2* sc, int variant,
+                 cudaStream_t s) {
   if (W == 4) {
     if (C == 1) return dispatch_generic<4, 1, GT>(g, kc, C, tp, pt, v, gr, sc, s);
-    if (C <= 2) return dispatch_coils<2, GT, COMP>(g, kc, C, tp, pt, v, gr, sc, s);
-    if (C <= 4) return dispatch_coils<4, GT, COMP>(g, kc, C, tp, pt, v, gr, sc, s);
-    return dispatch_coils<8, GT, COMP>(g, kc, C, tp, pt, v, gr, sc, s);
+    if (C <= 2) return dispatch_coils<2, GT, COMP>(g, kc, C, tp, pt, v, gr, sc, variant, s);
+    if (C <= 4) return dispatch_coils<4, GT, COMP>(g, kc, C, tp, pt, v, gr, sc, variant, s);
+    return dispatch_coils<8, GT, COMP>(g, kc, C, tp, pt, v, gr, sc, variant, s);
   }
   if (C == 1) return dispatch_generic<6, 1, GT>(g, kc, C, tp, pt, v, gr, sc, s);
   if (C <= 2) return dispatch_generic<6, 2, GT>(g, kc, C, tp, pt, v, gr, sc, s);
@@ -724,7 +725,7 @@ int spread_coil_chunk(int C) { return C == 1 ? 1 : (C <= 2 ? 2 : (C <= 4 ? 4 : 8
 
 int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                   const PhaseTable& pt, const nrsense_c64* vals, void* grids, bool bf16,
-                  bool comp, nrsense_c64* scratch, int32_t* status, cudaStream_t s) {
+                  bool comp, int variant, nrsense_c64* scratch, int32_t* status, cudaStream_t s) {
   (void)status;
   if (pt.item0[pt.nphase] == 0) return 0;
   const auto* v = reinterpret_cast<const float2*>(vals);
@@ -742,11 +743,14 @@ int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TileP
         g, kc, tp, pt, v, gr, sc);
     return 1 + launch_reduce<16, 1, float2>(g, 1, tp, pt, 1, gr, sc, s);
   }
-  if (bf16)
-    return comp ? spread_multi<bf162, true>(g, W, kc, C, tp, pt, v, static_cast<bf162*>(grids), sc, s)
-                : spread_multi<bf162, false>(g, W, kc, C, tp, pt, v, static_cast<bf162*>(grids), sc, s);
-  return comp ? spread_multi<float2, true>(g, W, kc, C, tp, pt, v, static_cast<float2*>(grids), sc, s)
-              : spread_multi<float2, false>(g, W, kc, C, tp, pt, v, static_cast<float2*>(grids), sc, s);
+  if (bf16) {
+    auto* gb = static_cast<bf162*>(grids);
+    return comp ? spread_multi<bf162, true>(g, W, kc, C, tp, pt, v, gb, sc, variant, s)
+                : spread_multi<bf162, false>(g, W, kc, C, tp, pt, v, gb, sc, variant, s);
+  }
+  auto* gf = static_cast<float2*>(grids);
+  return comp ? spread_multi<float2, true>(g, W, kc, C, tp, pt, v, gf, sc, variant, s)
+              : spread_multi<float2, false>(g, W, kc, C, tp, pt, v, gf, sc, variant, s);
 }
 
 }  // namespace nrs

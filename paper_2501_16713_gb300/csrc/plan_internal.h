@@ -79,6 +79,8 @@ struct nrsense_plan_s {
   void* b_xwork = nullptr;    // FFT outputs
   void* b_xspread = nullptr;  // spread target; tiles no phase occupies stay zero
   bool grid_bf16 = false;     // desc.precision == NRSENSE_BF16_STORE
+  int spread_variant = 1;     // kSpreadRegister or kSpreadShared (autotuned)
+  int interp_coils = 8;       // coils per interpolation CTA (autotuned)
   bool comp_spread = false;   // desc.precision == NRSENSE_FP32_COMPENSATED
   nrsense_c64* b_y = nullptr;      // Mtot * C
   nrsense_c64* b_tmp = nullptr;    // N^3 (normal operator scratch)
@@ -167,9 +169,10 @@ int launch_coil_fanout_pad(const Geo& g, int C, int nph, const float* deapod,
                            cudaStream_t s);
 int launch_image_to_padded(const Geo& g, int C, const float* deapod, const nrsense_c64* v,
                            void* xpad, bool bf16, cudaStream_t s);
+// coil_chunk: coils per CTA (8 or 4; W = 4 and C > 4 only, else ignored)
 int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                          const PhaseTable& pt, const void* grids, bool bf16, nrsense_c64* y,
-                         cudaStream_t s);
+                         int coil_chunk, cudaStream_t s);
 // one-time kernel attributes (large dynamic shared memory); plan time
 cudaError_t configure_kernels();
 cudaError_t configure_spread_kernels();
@@ -182,10 +185,12 @@ int launch_crop_to_coils(const Geo& g, int C, const float* deapod, const void* x
 // spreading (both domains)
 // Spread the phases of `pt` (values at rows row0[jj] + perm of vals) into
 // consecutive grid slots (phase jj at grids + jj * C * G^3); comp selects
-// compensated accumulation (W = 4 kernels).
+// compensated accumulation (W = 4 kernels); variant selects register or
+// shared-memory accumulation for the multi-coil W = 4 kernel.
+constexpr int kSpreadRegister = 1, kSpreadShared = 2;
 int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                   const PhaseTable& pt, const nrsense_c64* vals, void* grids, bool bf16,
-                  bool comp, nrsense_c64* scratch, int32_t* status, cudaStream_t s);
+                  bool comp, int variant, nrsense_c64* scratch, int32_t* status, cudaStream_t s);
 // coils handled by one spreading CTA
 int spread_coil_chunk(int C);
 // free the CG workspace of a plan (solver.cu)

@@ -42,6 +42,11 @@ class Desc(ctypes.Structure):
                 ("phase_chunk", ctypes.c_int32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("spread_variant", ctypes.c_int32), ("interp_coils", ctypes.c_int32),
+                ("spread_ms", ctypes.c_double * 2), ("interp_ms", ctypes.c_double * 2)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int32 * 3), ("kb_beta", ctypes.c_double),
                 ("kernel_poly_err", ctypes.c_double), ("total_samples", ctypes.c_int64),
@@ -82,6 +87,8 @@ _SIGS = {
                           ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_int32),
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_int32), _VP],
+    "nrsense_plan_autotune": [_VP, ctypes.c_int32, ctypes.POINTER(Tuning), _VP],
+    "nrsense_plan_set_tuning": [_VP, ctypes.POINTER(Tuning)],
     "nrsense_cnn_create": [ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32, _VP,
                            ctypes.POINTER(_VP)],
     "nrsense_cnn_destroy": [_VP],
@@ -211,6 +218,7 @@ class Plan:
         d.osf, d.kb_width, d.kb_beta = int(osf), int(width), float(beta)
         d.n_phases, d.n_coils = self.n_phases, self.n_coils
         d.precision = int(precision)
+        self.width, self.osf, self.precision = int(width), int(osf), int(precision)
         d.flags = IDENTITY_WARP if identity_warp else 0
         d.phase_chunk = int(phase_chunk)
         self.counts = [0] * self.n_phases
@@ -427,6 +435,45 @@ class Plan:
         if check and code not in (OK, -6):
             _check(code, "nrsense_solve_fcg")
         return x, it.value, list(hist[: it.value + 1]), tres.value, code, fb.value
+
+    def tuning_key(self):
+        """Key of the autotuning cache: geometry, sizes, precision, device."""
+        import torch
+        i = self.info()
+        dev = torch.cuda.get_device_name(torch.cuda.current_device())
+        return (f"{self.shape}|C{self.n_coils}|P{self.n_phases}|W{self.width}|osf{self.osf}|"
+                f"prec{self.precision}|M{self.total_samples}|chunk{i['phase_chunk']}|{dev}")
+
+    def autotune(self, reps=3, cache=None, stream=None):
+        """Pick the faster k-space spreading and interpolation launch choices
+        (nrsense_plan_autotune).  cache: path of a JSON file of earlier
+        choices keyed by tuning_key(); read if it has this key, else tuned
+        here and written back.  Returns the choices (and times when tuned)."""
+        import json
+        key = self.tuning_key()
+        store = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                store = json.load(f)
+        if key in store:
+            t = Tuning()
+            t.spread_variant = int(store[key]["spread_variant"])
+            t.interp_coils = int(store[key]["interp_coils"])
+            _check(self.lib.nrsense_plan_set_tuning(self._h, ctypes.byref(t)),
+                   "nrsense_plan_set_tuning")
+            return dict(store[key], cached=True)
+        t = Tuning()
+        _check(self.lib.nrsense_plan_autotune(self._h, int(reps), ctypes.byref(t), _stream(stream)),
+               "nrsense_plan_autotune")
+        res = {"spread_variant": t.spread_variant, "interp_coils": t.interp_coils,
+               "spread_ms": list(t.spread_ms), "interp_ms": list(t.interp_ms)}
+        if cache:
+            store[key] = res
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(store, f, indent=1)
+            os.replace(tmp, cache)
+        return dict(res, cached=False)
 
     def phase_slice(self, y, j):
         """Rows of phase j in a stacked (sum M_j, C) k-space array."""

@@ -254,3 +254,34 @@ def test_phase_chunking_matches_oracle(chunk):
     y2 = plan.kspace_forward(2, to_dev(v)).cpu().numpy()
     assert rel_l2(y2, O.kspace_forward(geo, v, case["coords"][2])) < TOL_FP32
     plan.close()
+
+
+def test_autotune_choices_compute_the_same_values(tmp_path):
+    # every launch choice (register / shared-memory spreading, 8 / 4 coils per
+    # interpolation CTA) computes bitwise the same operator; the cache file
+    # round-trips the choices
+    import torch
+    shape = (16, 16, 24)
+    case = synth.small_case(shape, 8, 2, [2500, 1800], seed=41)
+    plan = make_plan(case, shape)
+    x = to_dev(case["x"])
+    y0 = plan.forward(x)
+    xa0 = plan.adjoint(y0)
+    cache = str(tmp_path / "tune.json")
+    res = plan.autotune(reps=2, cache=cache)
+    assert not res["cached"] and res["spread_variant"] in (1, 2) and res["interp_coils"] in (4, 8)
+    from paper_2501_16713_gb300.nrsense import Tuning
+    import ctypes
+    for sv in (1, 2):
+        for ic in (8, 4):
+            t = Tuning()
+            t.spread_variant, t.interp_coils = sv, ic
+            assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == 0
+            assert torch.equal(plan.forward(x), y0)
+            assert torch.equal(plan.adjoint(y0), xa0)
+    res2 = plan.autotune(cache=cache)
+    assert res2["cached"] and res2["spread_variant"] == res["spread_variant"]
+    t = Tuning()
+    t.spread_variant, t.interp_coils = 3, 8
+    assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == -1
+    plan.close()
