@@ -211,6 +211,23 @@ def oracle_cost(w, frac=1.0 / 32, seed=0):
 # GPU leg
 # --------------------------------------------------------------------------
 
+def max_over_ranks(value, device, world):
+    """The largest `value` over all ranks (the job's time is its slowest
+    rank's); the identity on a single rank."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ms_max, world):
+    """Whole-job applies/s of `world` replicas, each one apply per step, timed
+    by the slowest rank (weak scaling)."""
+    return world * 1000.0 / ms_max
+
+
 def _lambda_max(plan, shape, dev, iters=20, seed=4):
     import torch
     gen = torch.Generator(device=dev).manual_seed(seed)
@@ -579,10 +596,7 @@ def run_gpu(args, rank, world, local_rank):
     stages, own = plan.profile_stop()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dev, world)
 
     # forward / adjoint split (untimed region; context only)
     y = plan.forward(x)
@@ -631,11 +645,7 @@ def run_gpu(args, rank, world, local_rank):
         plan.normal(xd, args.lam, out)
         oh.copy_(out, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - te) * 1000.0 / ke
-    te_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(te_t.item())
+    e2e_ms = max_over_ranks((time.perf_counter() - te) * 1000.0 / ke, dev, world)
 
     M = plan.counts
     sb = stage_bytes(info, shape, spec.n_coils, len(M), M)
@@ -655,7 +665,7 @@ def run_gpu(args, rank, world, local_rank):
                              if k in sb and v[0] > 0 else None)}
                  for k, v in stages.items() if v[1] > 0}
     result = {
-        "metric": METRIC, "value": world * 1000.0 / ms_max, "unit": UNIT,
+        "metric": METRIC, "value": job_throughput(ms_max, world), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64/f32 (FP32 arithmetic)",
@@ -674,7 +684,7 @@ def run_gpu(args, rank, world, local_rank):
                      "alg_bytes_per_launch": bytes_per_launch,
                      "ms_per_launch": dom_ms / dom_n,
                      "traffic": traffic},
-        "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT,
+        "e2e": {"value": job_throughput(e2e_ms, world), "unit": UNIT,
                 "h2d_bytes_per_step": int(xh.numel() * 8),
                 "d2h_bytes_per_step": int(oh.numel() * 8)},
         "gpu_launches": int(own),
