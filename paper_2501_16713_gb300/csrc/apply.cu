@@ -5,11 +5,11 @@
 //        The first three steps do not depend on j and run once for all phases.
 //  T^H   (adjoint, summed over phases):    K3 (P_j^(i), all phases into one
 //        grid) -> F_G -> K4 (Z^H, 1/C) -> F_N^H
-//  G_j S (per phase):                       K5 (S, 1/c*, Z) -> F_G (C coils
-//        batched) -> K6 (B^(k))
+//  G_j S (per phase):                       K5 (S, 1/c*, Z) -> F_G (C coils,
+//        pruned to the zero padding) -> K6 (B^(k))
 //  S^H G_j^H (per phase):                   K7 (P^(k), into a buffer whose
-//        empty tiles stay zero) -> F_G^H (batched, out of place) ->
-//        K8 (Z^H, 1/c, S^H)
+//        empty tiles stay zero) -> F_G^H (pruned to the cropped planes, out
+//        of place) -> K8 (Z^H, 1/c, S^H)
 #include <cufftXt.h>
 
 #include <algorithm>
@@ -28,26 +28,62 @@ namespace {
   } while (0)
 
 nrsense_status fft(nrsense_plan_s* p, int stage, cufftHandle h, cudaStream_t s, void* in,
-                   void* out, int dir, int nph = 0) {
+                   void* out, int dir) {
   StageMark mark(p, stage, s);
   if (cufftSetStream(h, s) != CUFFT_SUCCESS) return NRSENSE_ERR_CUFFT;
-  if (stage == NRSENSE_STAGE_FFT_GC && p->grid_bf16) {
-    // BF16 coil grids: cufftXt plans of fewer than 2^31 elements, run as
-    // consecutive full sub-batches over the nph * C grids
-    const long long total = (long long)nph * p->C;
-    const long long sub = bf16_sub_batch(total, p->geo.ngrid);  // as at plan time
-    if (sub < 1) return NRSENSE_ERR_CUFFT;
-    const size_t step = size_t(sub) * size_t(p->geo.ngrid) * 4;  // bytes of sub grids
-    for (long long k = 0; k < total; k += sub) {
-      char* i = static_cast<char*>(in) + size_t(k / sub) * step;
-      char* o = static_cast<char*>(out) + size_t(k / sub) * step;
-      if (cufftXtExec(h, i, o, dir) != CUFFT_SUCCESS) return NRSENSE_ERR_CUFFT;
-    }
-    return NRSENSE_OK;
-  }
   const cufftResult r =
       cufftExecC2C(h, static_cast<cufftComplex*>(in), static_cast<cufftComplex*>(out), dir);
   return r == CUFFT_SUCCESS ? NRSENSE_OK : NRSENSE_ERR_CUFFT;
+}
+
+// F_G (dir forward) or F_G^H (dir inverse) of nph * C consecutive coil grids,
+// pruned to the zero padding.  In every grid only the centred n0 z planes,
+// [0, n0/2) and [G0 - n0/2, G0), can hold data on the way in (forward) or are
+// read on the way out (inverse, before the crop); across consecutive grids
+// these planes form blocks of n0 contiguous planes.  Forward: 2D transforms
+// of those blocks from `in` into b_xmid (whose other planes stay zero), then
+// the strided 1D transform along z of every grid into `out`.  Inverse: the 1D
+// transforms along z from `in` into `out`, then the 2D transforms of the
+// blocks in place.  Each output equals the full 3D transform on the planes
+// that are used.
+nrsense_status fft_gc(nrsense_plan_s* p, int nph, void* in, void* out, int dir, cudaStream_t s) {
+  StageMark mark(p, NRSENSE_STAGE_FFT_GC, s);
+  const Geo& g = p->geo;
+  const size_t esz = p->grid_bf16 ? 4 : 8;
+  const size_t plane = size_t(g.g1) * g.g2 * esz;
+  const size_t grid = size_t(g.g0) * plane;
+  const long long n = (long long)nph * p->C;
+  const int half = g.n0 / 2;
+  for (cufftHandle h : {p->fft_p2, p->fft_p2h, p->fft_z})
+    if (cufftSetStream(h, s) != CUFFT_SUCCESS) return NRSENSE_ERR_CUFFT;
+  auto exec = [&](cufftHandle h, char* a, char* b) {
+    const cufftResult r = p->grid_bf16 ? cufftXtExec(h, a, b, dir)
+                                       : cufftExecC2C(h, reinterpret_cast<cufftComplex*>(a),
+                                                      reinterpret_cast<cufftComplex*>(b), dir);
+    return r == CUFFT_SUCCESS;
+  };
+  auto blocks = [&](char* a, char* b) {
+    if (!exec(p->fft_p2h, a, b)) return false;  // grid 0, planes [0, n0/2)
+    for (long long k = 1; k < n; ++k) {         // top of grid k-1 and bottom of grid k
+      const size_t off = size_t(k) * grid - size_t(half) * plane;
+      if (!exec(p->fft_p2, a + off, b + off)) return false;
+    }
+    const size_t last = size_t(n) * grid - size_t(half) * plane;  // top of the last grid
+    return exec(p->fft_p2h, a + last, b + last);
+  };
+  char* ci = static_cast<char*>(in);
+  char* co = static_cast<char*>(out);
+  char* mid = static_cast<char*>(p->b_xmid);
+  if (dir == CUFFT_FORWARD) {
+    if (!blocks(ci, mid)) return NRSENSE_ERR_CUFFT;
+    for (long long k = 0; k < n; ++k)
+      if (!exec(p->fft_z, mid + size_t(k) * grid, co + size_t(k) * grid)) return NRSENSE_ERR_CUFFT;
+  } else {
+    for (long long k = 0; k < n; ++k)
+      if (!exec(p->fft_z, ci + size_t(k) * grid, co + size_t(k) * grid)) return NRSENSE_ERR_CUFFT;
+    if (!blocks(co, co)) return NRSENSE_ERR_CUFFT;
+  }
+  return NRSENSE_OK;
 }
 
 nrsense_status launched() {
@@ -61,12 +97,6 @@ nrsense_status launched() {
     StageMark _mark(p, NRSENSE_STAGE_##stage, s);   \
     p->launches += (call);                          \
   } while (0)
-
-cufftHandle gc_plan(nrsense_plan_s* p, int nph) {
-  for (auto& fp : p->fft_gc_plans)
-    if (fp.first == nph) return fp.second;
-  return 0;
-}
 
 // Phase table of phases [j0, j1) of the k-space point sets; value/output rows
 // of phase j start at off_j - row_base.
@@ -155,8 +185,7 @@ nrsense_status sense_chunk_forward(nrsense_plan_s* p, int j0, int j1, const nrse
   STAGE(COIL_FANOUT, launch_coil_fanout_pad(g, p->C, nph, p->deapod, p->smaps, m, p->b_xpad,
                                             p->grid_bf16, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, nph), s, p->b_xpad, p->b_xwork, CUFFT_FORWARD,
-              nph));
+  NRS_TRY(fft_gc(p, nph, p->b_xpad, p->b_xwork, CUFFT_FORWARD, s));
   const PhaseTable t = kspace_table(p, j0, j1, /*spread=*/false, row_base);
   STAGE(INTERP_KSPACE, launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
                                             p->grid_bf16, y, p->interp_coils, s));
@@ -172,8 +201,7 @@ nrsense_status sense_chunk_adjoint(nrsense_plan_s* p, int j0, int j1, const nrse
   STAGE(SPREAD_KSPACE, launch_spread(g, p->W, p->kc, p->C, p->ktiles, t, y, p->b_xspread,
                                      p->grid_bf16, p->comp_spread, p->spread_variant, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, nph), s, p->b_xspread, p->b_xwork, CUFFT_INVERSE,
-              nph));
+  NRS_TRY(fft_gc(p, nph, p->b_xspread, p->b_xwork, CUFFT_INVERSE, s));
   STAGE(CROP_COILSUM, launch_crop_coilsum(g, p->C, nph, p->deapod, p->smaps, p->b_xwork,
                                           p->grid_bf16, w, s));
   return launched();
@@ -203,7 +231,7 @@ nrsense_status nrsense_kspace_forward(nrsense_plan_t p, int32_t phase, const nrs
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   STAGE(COIL_FANOUT, launch_image_to_padded(p->geo, p->C, p->deapod, v, p->b_xpad, p->grid_bf16, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, 1), s, p->b_xpad, p->b_xwork, CUFFT_FORWARD, 1));
+  NRS_TRY(fft_gc(p, 1, p->b_xpad, p->b_xwork, CUFFT_FORWARD, s));
   const PhaseTable t = kspace_table(p, phase, phase + 1, false, p->off[phase]);
   STAGE(INTERP_KSPACE, launch_interp_kspace(p->geo, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
                                             p->grid_bf16, y, p->interp_coils, s));
@@ -220,7 +248,7 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t p, int32_t phase, const nrs
   STAGE(SPREAD_KSPACE, launch_spread(p->geo, p->W, p->kc, p->C, p->ktiles, t, y, p->b_xspread,
                                      p->grid_bf16, p->comp_spread, p->spread_variant, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_GC, gc_plan(p, 1), s, p->b_xspread, p->b_xwork, CUFFT_INVERSE, 1));
+  NRS_TRY(fft_gc(p, 1, p->b_xspread, p->b_xwork, CUFFT_INVERSE, s));
   STAGE(CROP_COILSUM, launch_crop_to_coils(p->geo, p->C, p->deapod, p->b_xwork, p->grid_bf16, v, s));
   return launched();
 }

@@ -507,10 +507,10 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     p->have_fft_g = true;
   }
   if (p->C > 0) {
-    // phases per launch: as many as half of the free memory allows (three
+    // phases per launch: as many as half of the free memory allows (four
     // coil-grid buffers per phase plus about one for cuFFT's work area)
     const long long elem = p->grid_bf16 ? 4 : 8;  // bytes per stored complex value
-    const long long per_phase = 4LL * p->C * g.ngrid * elem;
+    const long long per_phase = 5LL * p->C * g.ngrid * elem;
     int pc = d.phase_chunk;
     if (pc <= 0) {
       size_t free_b = 0, total_b = 0;
@@ -519,45 +519,39 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     }
     pc = std::max(1, std::min(pc, std::min(p->P, kMaxChunkPhases)));
     p->phase_chunk = pc;
-    // one cuFFT plan per batch size used: a full chunk, the last partial
-    // chunk, and a single phase (stage calls)
-    std::vector<int> sizes = {pc, 1};
-    if (p->P % pc) sizes.push_back(p->P % pc);
-    long long nl[3] = {g.g0, g.g1, g.g2};
-    for (int nb : sizes) {
-      bool have = false;
-      for (auto& fp : p->fft_gc_plans) have |= (fp.first == nb);
-      if (have) continue;
-      cufftHandle h;
-      // coil-major batch: grid (phase jj, coil c) starts at (jj * C + c) * G^3
-      if (p->grid_bf16) {
-        NRS_TRY(cufft_check(cufftCreate(&h)));
-        size_t work = 0;
-        const long long batch = bf16_sub_batch((long long)nb * p->C, g.ngrid);
-        if (batch < 1) {
-          cufftDestroy(h);
-          return NRSENSE_ERR_ARG;
-        }
-        const cufftResult r =
-            cufftXtMakePlanMany(h, 3, nl, nl, 1, g.ngrid, CUDA_C_16BF, nl, 1, g.ngrid, CUDA_C_16BF,
-                                batch, &work, CUDA_C_16BF);
-        if (r != CUFFT_SUCCESS) {
-          cufftDestroy(h);
-          return NRSENSE_ERR_CUFFT;
-        }
-      } else {
-        // 64-bit planning: a batch of coil grids can exceed 2^31 elements
-        NRS_TRY(cufft_check(cufftCreate(&h)));
-        size_t work = 0;
-        const cufftResult r = cufftMakePlanMany64(h, 3, nl, nl, 1, g.ngrid, nl, 1, g.ngrid,
-                                                  CUFFT_C2C, (long long)nb * p->C, &work);
-        if (r != CUFFT_SUCCESS) {
-          cufftDestroy(h);
-          return NRSENSE_ERR_CUFFT;
-        }
+    // pruned coil-grid transforms (FP32 C2C or BF16 through cufftXt)
+    const long long plane = (long long)g.g1 * g.g2;
+    long long n2[2] = {g.g1, g.g2};
+    long long nz[1] = {g.g0};
+    auto make = [&](cufftHandle* h, int rank, long long* n, long long* emb, long long stride,
+                    long long dist, long long batch) -> nrsense_status {
+      if (cufftCreate(h) != CUFFT_SUCCESS) return NRSENSE_ERR_CUFFT;
+      size_t work = 0;
+      const cufftResult r =
+          p->grid_bf16
+              ? cufftXtMakePlanMany(*h, rank, n, emb, stride, dist, CUDA_C_16BF, emb, stride, dist,
+                                    CUDA_C_16BF, batch, &work, CUDA_C_16BF)
+              : cufftMakePlanMany64(*h, rank, n, emb, stride, dist, emb, stride, dist, CUFFT_C2C,
+                                    batch, &work);
+      if (r != CUFFT_SUCCESS) {
+        cufftDestroy(*h);
+        return NRSENSE_ERR_CUFFT;
       }
-      p->fft_gc_plans.push_back({nb, h});
+      return NRSENSE_OK;
+    };
+    NRS_TRY(make(&p->fft_p2, 2, n2, n2, 1, plane, g.n0));
+    nrsense_status st2 = make(&p->fft_p2h, 2, n2, n2, 1, plane, g.n0 / 2);
+    if (st2 != NRSENSE_OK) {
+      cufftDestroy(p->fft_p2);
+      return st2;
     }
+    st2 = make(&p->fft_z, 1, nz, nz, plane, 1, plane);
+    if (st2 != NRSENSE_OK) {
+      cufftDestroy(p->fft_p2);
+      cufftDestroy(p->fft_p2h);
+      return st2;
+    }
+    p->have_gc = true;
   }
 
   // work buffers
@@ -575,6 +569,8 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     NRS_TRY(dev_alloc(p, &p->b_xpad, cgb));
     NRS_TRY(dev_alloc(p, &p->b_xwork, cgb));
     NRS_TRY(dev_alloc(p, &p->b_xspread, cgb));
+    NRS_TRY(dev_alloc(p, &p->b_xmid, cgb));
+    if (cudaMemsetAsync(p->b_xmid, 0, cgb, s) != cudaSuccess) return NRSENSE_ERR_CUDA;
     // empty tiles of the spread target are never written: zero them once
     if (cudaMemsetAsync(p->b_xspread, 0, cgb, s) != cudaSuccess) return NRSENSE_ERR_CUDA;
     NRS_TRY(dev_alloc_n(p, &p->b_y, std::max<long long>(p->Mtot * p->C, 1)));
@@ -607,8 +603,12 @@ void release(nrsense_plan_s* p) {
   p->prof_events.clear();
   if (p->have_fft_n) cufftDestroy(p->fft_n);
   if (p->have_fft_g) cufftDestroy(p->fft_g);
-  for (auto& fp : p->fft_gc_plans) cufftDestroy(fp.second);
-  p->fft_gc_plans.clear();
+  if (p->have_gc) {
+    cufftDestroy(p->fft_p2);
+    cufftDestroy(p->fft_p2h);
+    cufftDestroy(p->fft_z);
+    p->have_gc = false;
+  }
   for (void* a : p->allocations) cudaFree(a);
   p->allocations.clear();
 }

@@ -78,6 +78,7 @@ struct nrsense_plan_s {
   void* b_xpad = nullptr;     // zero outside the centred N^3 blocks
   void* b_xwork = nullptr;    // FFT outputs
   void* b_xspread = nullptr;  // spread target; tiles no phase occupies stay zero
+  void* b_xmid = nullptr;     // forward FFT after the 2D step; planes off the data blocks stay zero
   bool grid_bf16 = false;     // desc.precision == NRSENSE_BF16_STORE
   int spread_variant = 1;     // kSpreadRegister or kSpreadShared (autotuned)
   int interp_coils = 8;       // coils per interpolation CTA (autotuned)
@@ -90,7 +91,15 @@ struct nrsense_plan_s {
 
   cufftHandle fft_n = 0, fft_g = 0;
   bool have_fft_n = false, have_fft_g = false;
-  std::vector<std::pair<int, cufftHandle>> fft_gc_plans;  // (phases per batch, plan)
+  // k-space coil-grid FFTs, pruned to the zero padding: per batch of grids,
+  // 2D transforms over the z-plane blocks that can hold data (the centred
+  // n0 planes: the top n0/2 planes of grid k and the bottom n0/2 of grid k+1
+  // are contiguous; fft_p2 takes n0 planes, fft_p2h n0/2 at the two ends) and
+  // a strided 1D transform along z per grid (fft_z).  The forward direction
+  // goes 2D (into b_xmid, whose other planes stay zero) then z; the inverse
+  // z then 2D in place on the planes the crop reads.
+  cufftHandle fft_p2 = 0, fft_p2h = 0, fft_z = 0;
+  bool have_gc = false;
 
 
   long long device_bytes = 0;
@@ -107,17 +116,6 @@ struct nrsense_plan_s {
 };
 
 namespace nrs {
-// Transforms per cuFFT execution of `total` BF16 coil grids of `ngrid` points:
-// cuFFT's BF16 plans hold fewer than 2^31 elements, so the batch runs as
-// consecutive sub-batches; the size is the largest divisor of total under
-// that limit (every sub-batch is full).  0 if one grid alone is too large.
-inline long long bf16_sub_batch(long long total, long long ngrid) {
-  const long long limit = ((1LL << 31) - 1) / ngrid;
-  for (long long d = std::min(total, limit); d >= 1; --d)
-    if (total % d == 0) return d;
-  return 0;
-}
-
 // RAII stage marker: records an event pair around a stage when profiling.
 struct StageMark {
   nrsense_plan_s* p;
