@@ -198,7 +198,7 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t plan, int32_t phase,
  *   flags        NRSENSE_CG_X0: x_dev holds the initial guess; NRSENSE_CG_GRAPH:
  *                iterations are captured once as a CUDA graph (per plan, x_dev,
  *                lambda) and replayed: with tol = 0 (a fixed iteration count)
- *                min(maxit, 64) iterations form one graph, otherwise 10, with
+ *                min(maxit, 64) iterations form one graph, otherwise 2, with
  *                the converged flag read between graph launches.
  *   x_dev        image (device): initial guess (with NRSENSE_CG_X0) and solution.
  *   iters_host   receives the number of iterations (may be NULL).

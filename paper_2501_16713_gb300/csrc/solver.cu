@@ -525,10 +525,11 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
   // iterations, in chunks; the converged flag is read between chunks
   const bool graph = (flags & NRSENSE_CG_GRAPH) != 0;
   // graph chunks: a fixed-count solve (tol == 0) is one graph of up to kGraphMax
-  // iterations; a tolerance-driven solve replays 10-iteration graphs and reads
-  // the converged flag between them (iterations after convergence are no-ops)
+  // iterations; a tolerance-driven solve replays 2-iteration graphs and reads
+  // the converged flag between them (an iteration after convergence changes
+  // nothing but still applies the operator, so short chunks waste at most one)
   const int chunk = rec ? 1
-                  : graph ? std::max(1, std::min<int>(maxit, tol == 0.0 ? kGraphMax : 10))
+                  : graph ? std::max(1, std::min<int>(maxit, tol == 0.0 ? kGraphMax : 2))
                           : 5;
   const int mode = flexible ? 1 : 0;
   if (graph && (w->gexec == nullptr || w->g_x != x || w->g_lambda != lambda ||

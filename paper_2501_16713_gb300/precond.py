@@ -21,23 +21,30 @@ import numpy as np
 from .nrsense import CNN_CHANNELS, Cnn, Plan
 
 
-def laplacian_params(c):
+def laplacian_params(c, stencil="central"):
     """Parameters of the symmetric form (z = u0 + N4^T (I + W5^T W5) N4 u0)
-    that make it z = u0 - c L u0, L the zero-padded Laplacian built from
-    central differences (first layer: +-sqrt(c) times the central difference
-    along each axis of each of Re, Im; hidden layers: identity on those 12
-    channels; W5 = 0).  For fixed masks the ReLU pairs cancel, so the map is
-    linear, symmetric and positive definite: a local approximation of the
-    inverse of a normal operator whose k-space weight grows as |k|^-2."""
+    that make it z = u0 + c D^T D u0 = u0 - c L u0 with D the zero-padded
+    difference along each axis (first layer: +-sqrt(c) D along each axis of
+    each of Re, Im; hidden layers: identity on those 12 channels; W5 = 0).
+    stencil "central": D u[i] = (u[i+1] - u[i-1]) / 2 (L has a null at the
+    Nyquist frequency); "forward": D u[i] = u[i+1] - u[i] (L is the 7-point
+    Laplacian).  For fixed masks the ReLU pairs cancel, so the map is linear,
+    symmetric and positive definite: a local approximation of the inverse of
+    a normal operator whose k-space weight grows as |k|^-2."""
     params = [(np.zeros((co, ci, 3, 3, 3), np.float32), np.zeros(co, np.float32))
               for ci, co in zip(CNN_CHANNELS[:-1], CNN_CHANNELS[1:])]
     w1 = params[0][0]
-    a = 0.5 * math.sqrt(c)
+    if stencil == "central":
+        a, taps = 0.5 * math.sqrt(c), (2, 0)
+    elif stencil == "forward":
+        a, taps = math.sqrt(c), (2, 1)
+    else:
+        raise ValueError(stencil)
     for ax in range(3):
         for comp in range(2):
             ch = 4 * ax + 2 * comp
             ip, im = [1, 1, 1], [1, 1, 1]
-            ip[ax], im[ax] = 2, 0
+            ip[ax], im[ax] = taps
             w1[ch, comp][tuple(ip)], w1[ch, comp][tuple(im)] = a, -a
             w1[ch + 1, comp][tuple(ip)], w1[ch + 1, comp][tuple(im)] = -a, a
     for l in (1, 2, 3):
