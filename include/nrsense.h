@@ -368,7 +368,8 @@ nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* 
  * nrsense_plan_autotune times, on the plan's own k-space point sets (first
  * phase chunk) and internal buffers, the k-space spreading kernel with
  * register accumulation and with shared-memory accumulation, and the k-space
- * interpolation with 8 and with 4 coils per CTA (reps launches each, after
+ * interpolation with 8 and with 4 coils per CTA, its tile halos staged per
+ * value or by one tensor-memory-accelerator copy (reps launches each, after
  * one warm-up launch, CUDA events on `stream`; synchronises), keeps the
  * faster of each in the plan and reports times and choices in *out (host).
  * The compensated precision always uses shared-memory accumulation; plans
@@ -382,8 +383,10 @@ nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* 
 typedef struct {
   int32_t spread_variant;  /* NRSENSE_TUNE_SPREAD_* */
   int32_t interp_coils;    /* coils per interpolation CTA: 8 or 4 */
+  int32_t interp_tma;      /* 1: tile halos loaded by the tensor memory accelerator */
   double  spread_ms[2];    /* measured: register, shared */
-  double  interp_ms[2];    /* measured: 8 coils, 4 coils */
+  double  interp_ms[2];    /* measured, per-value staging: 8 coils, 4 coils */
+  double  interp_tma_ms[2];/* measured, TMA staging: 8 coils, 4 coils (-1: not available) */
 } nrsense_tuning;
 nrsense_status nrsense_plan_autotune(nrsense_plan_t plan, int32_t reps, nrsense_tuning* out_host,
                                      void* stream);

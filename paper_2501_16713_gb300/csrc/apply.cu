@@ -98,6 +98,12 @@ nrsense_status launched() {
     p->launches += (call);                          \
   } while (0)
 
+// tensor map for the TMA-staged interpolation, or null for the per-value staging
+const CUtensorMap* interp_tmap(const nrsense_plan_s* p) {
+  if (!p->interp_tma || !p->tma_ok || p->W != 4) return nullptr;
+  return (p->interp_coils == 8 && p->C > 4) ? &p->tmap_xwork8 : &p->tmap_xwork4;
+}
+
 // Phase table of phases [j0, j1) of the k-space point sets; value/output rows
 // of phase j start at off_j - row_base.
 PhaseTable kspace_table(const nrsense_plan_s* p, int j0, int j1, bool spread, long long row_base) {
@@ -188,7 +194,7 @@ nrsense_status sense_chunk_forward(nrsense_plan_s* p, int j0, int j1, const nrse
   NRS_TRY(fft_gc(p, nph, p->b_xpad, p->b_xwork, CUFFT_FORWARD, s));
   const PhaseTable t = kspace_table(p, j0, j1, /*spread=*/false, row_base);
   STAGE(INTERP_KSPACE, launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
-                                            p->grid_bf16, y, p->interp_coils, s));
+                                            p->grid_bf16, y, p->interp_coils, interp_tmap(p), p->d_status, s));
   return launched();
 }
 
@@ -234,7 +240,7 @@ nrsense_status nrsense_kspace_forward(nrsense_plan_t p, int32_t phase, const nrs
   NRS_TRY(fft_gc(p, 1, p->b_xpad, p->b_xwork, CUFFT_FORWARD, s));
   const PhaseTable t = kspace_table(p, phase, phase + 1, false, p->off[phase]);
   STAGE(INTERP_KSPACE, launch_interp_kspace(p->geo, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
-                                            p->grid_bf16, y, p->interp_coils, s));
+                                            p->grid_bf16, y, p->interp_coils, interp_tmap(p), p->d_status, s));
   return launched();
 }
 
@@ -305,9 +311,11 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
       t->spread_variant != NRSENSE_TUNE_SPREAD_SHARED)
     return NRSENSE_ERR_ARG;
   if (t->interp_coils != 4 && t->interp_coils != 8) return NRSENSE_ERR_ARG;
+  if (t->interp_tma != 0 && t->interp_tma != 1) return NRSENSE_ERR_ARG;
   p->spread_variant = t->spread_variant == NRSENSE_TUNE_SPREAD_REGISTER ? kSpreadRegister
                                                                          : kSpreadShared;
   p->interp_coils = t->interp_coils;
+  p->interp_tma = t->interp_tma == 1 && p->tma_ok;
   return NRSENSE_OK;
 }
 
@@ -318,6 +326,7 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
   out->spread_variant = p->spread_variant == kSpreadRegister ? NRSENSE_TUNE_SPREAD_REGISTER
                                                              : NRSENSE_TUNE_SPREAD_SHARED;
   out->interp_coils = p->interp_coils;
+  out->interp_tma = p->interp_tma ? 1 : 0;
   if (p->C == 0) return NRSENSE_OK;  // nothing to choose without k space
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Geo& g = p->geo;
@@ -347,11 +356,24 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
                                    p->d_status, s);
     });
   const int chunks[2] = {8, 4};
-  for (int k = 0; k < 2; ++k)
-    out->interp_ms[k] = time_ms([&] {
-      p->launches += launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, ti, p->b_xwork,
-                                          p->grid_bf16, p->b_y, chunks[k], s);
-    });
+  const bool saved_tma = p->interp_tma;
+  for (int t = 0; t < 2; ++t) {
+    if (t == 1 && !(p->tma_ok && p->W == 4)) {
+      out->interp_tma_ms[0] = out->interp_tma_ms[1] = -1.0;
+      break;
+    }
+    for (int k = 0; k < 2; ++k) {
+      p->interp_tma = t == 1;
+      p->interp_coils = chunks[k];
+      const CUtensorMap* tm = interp_tmap(p);
+      const double ms = time_ms([&] {
+        p->launches += launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, ti, p->b_xwork,
+                                            p->grid_bf16, p->b_y, chunks[k], tm, p->d_status, s);
+      });
+      (t == 0 ? out->interp_ms : out->interp_tma_ms)[k] = ms;
+    }
+  }
+  p->interp_tma = saved_tma;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (cudaGetLastError() != cudaSuccess) return NRSENSE_ERR_CUDA;
@@ -360,10 +382,23 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
   // the compensated variant has only the shared-memory kernel: keep the default there
   if (!p->comp_spread)
     p->spread_variant = out->spread_ms[1] < out->spread_ms[0] ? kSpreadShared : kSpreadRegister;
-  p->interp_coils = out->interp_ms[1] < out->interp_ms[0] ? 4 : 8;
+  // fastest interpolation: staging (per value / TMA) x coils per CTA (8 / 4)
+  double best = out->interp_ms[0];
+  p->interp_tma = false;
+  p->interp_coils = 8;
+  for (int t = 0; t < 2; ++t)
+    for (int k = 0; k < 2; ++k) {
+      const double ms = (t == 0 ? out->interp_ms : out->interp_tma_ms)[k];
+      if (ms >= 0.0 && ms < best) {
+        best = ms;
+        p->interp_tma = t == 1;
+        p->interp_coils = chunks[k];
+      }
+    }
   out->spread_variant = p->spread_variant == kSpreadRegister ? NRSENSE_TUNE_SPREAD_REGISTER
                                                              : NRSENSE_TUNE_SPREAD_SHARED;
   out->interp_coils = p->interp_coils;
+  out->interp_tma = p->interp_tma ? 1 : 0;
   return NRSENSE_OK;
 }
 

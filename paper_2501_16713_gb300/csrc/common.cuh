@@ -150,6 +150,8 @@ __device__ __forceinline__ float2 grid_ld(const bf162* p) {
 }
 __device__ __forceinline__ void grid_st(float2* p, float2 v) { *p = v; }
 __device__ __forceinline__ void grid_st(bf162* p, float2 v) { *p = __float22bfloat162_rn(v); }
+__device__ __forceinline__ float2 grid_ld_shared(const float2* p) { return *p; }
+__device__ __forceinline__ float2 grid_ld_shared(const bf162* p) { return __bfloat1622float2(*p); }
 // two consecutive stored values (coils 2q, 2q+1) from shared memory as float4
 __device__ __forceinline__ float4 grid_ld2_shared(const float2* p) {
   return *reinterpret_cast<const float4*>(p);

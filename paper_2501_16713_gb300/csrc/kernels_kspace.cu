@@ -4,6 +4,8 @@
 // gridding G_j^H (F^H -> Z^H -> 1/c, then S^H).  Coil grids are coil-major
 // ([C][G^3]) so that cuFFT transforms contiguous batches; coil maps keep the
 // caller's (C, N^3) layout.
+#include <cudaTypedefs.h>
+
 #include "plan_internal.h"
 
 namespace nrs {
@@ -213,6 +215,183 @@ __global__ void __launch_bounds__(256) interp_tile_kernel(
   }
 }
 
+// K6 with the tile halo loaded by the tensor memory accelerator (W = 4).
+// One cp.async.bulk.tensor copy per CTA moves the (8+3)^3 halo of CC coil
+// grids (box x extent 12 for 16-byte rows) into shared memory as
+// [c][z][y][x]; an mbarrier tracks the transaction bytes and every thread
+// waits on it with a bounded poll (on expiry the CTA records
+// NRSENSE_ERR_TIMEOUT and returns without computing).  Tiles whose halo wraps
+// the periodic grid edge are staged by per-value asynchronous copies into the
+// same layout.  A group of W * CC lanes serves one sample: lane = (tap x,
+// coil), so the CC coils of one tap read distinct banks; tap-x partial sums
+// are reduced by shuffles.
+constexpr int kTmaXP = 12;                 // box x extent (12 values = 96 / 48 bytes)
+constexpr long long kTmaMaxPoll = 1LL << 24;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned mbar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+template <int CC, typename GT>
+__global__ void __launch_bounds__(256) interp_tma_kernel(
+    const __grid_constant__ CUtensorMap tmap, Geo g, KernelCoefs kc, int C, TilePlan tp,
+    PhaseTable pt, const GT* __restrict__ grids, float2* __restrict__ y,
+    int32_t* __restrict__ status) {
+  constexpr int W = 4, T = 8, H = T + W - 1, XP = kTmaXP;
+  constexpr int LPS = W * CC, SPW = 32 / LPS;  // lanes per sample, samples per warp
+  static_assert(LPS <= 32, "coil chunk");
+  constexpr unsigned kBytes = unsigned(CC * H * H * XP * sizeof(GT));
+  extern __shared__ float4 smem_raw[];
+  // the bulk tensor copy needs a 128-byte aligned destination: round up
+  // (the launch reserves 128 extra bytes)
+  const unsigned raw = smem_addr(smem_raw);
+  GT* halo = reinterpret_cast<GT*>(reinterpret_cast<unsigned char*>(smem_raw) +
+                                   ((128u - (raw & 127u)) & 127u));  // [CC][H][H][XP]
+  __shared__ float s_coef[W][kNumCoef];
+  __shared__ __align__(8) unsigned long long mbar;
+  const int jj = phase_of(pt.item0, pt.nphase, blockIdx.x);
+  const SpreadItem it = pt.items[jj][blockIdx.x - pt.item0[jj]];
+  const float4* __restrict__ qs = pt.qs[jj];
+  const int32_t* __restrict__ perm = pt.perm[jj];
+  const GT* __restrict__ grid = grids + (long long)jj * C * g.ngrid;
+  const long long row0 = pt.row0[jj];
+  const int coil0 = blockIdx.y * CC;
+  const int tz = it.tile / (tp.nt1 * tp.nt2);
+  const int rem = it.tile - tz * (tp.nt1 * tp.nt2);
+  const int ty = rem / tp.nt2;
+  const int tx = rem - ty * tp.nt2;
+  const int o0 = tz * T, o1 = ty * T, o2 = tx * T;
+  if (threadIdx.x < W * kNumCoef) s_coef[threadIdx.x / kNumCoef][threadIdx.x % kNumCoef] =
+      kc.c[threadIdx.x / kNumCoef][threadIdx.x % kNumCoef];
+  const bool use_tma = o0 + H <= g.g0 && o1 + H <= g.g1 && o2 + XP <= g.g2;
+  if (use_tma) {
+    const unsigned mb = smem_addr(&mbar);
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb),
+                   "r"(kBytes)
+                   : "memory");
+      // box origin (x, y, z, grid slot); x * sizeof(GT) is a multiple of 16
+      asm volatile(
+          "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+          " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_addr(halo)),
+          "l"(reinterpret_cast<unsigned long long>(&tmap)), "r"(o2), "r"(o1), "r"(o0),
+          "r"(jj * C + coil0), "r"(mb)
+          : "memory");
+    }
+    bool ok = false;
+    for (long long k = 0; k < kTmaMaxPoll && !ok; ++k) ok = mbar_try_wait(mb, 0);
+    if (!ok) {
+      if (status) atomicCAS(status, 0, NRSENSE_ERR_TIMEOUT);
+      // give the copy in flight a last bounded chance to land before leaving
+      for (long long k = 0; k < kTmaMaxPoll && !ok; ++k) ok = mbar_try_wait(mb, 0);
+      return;
+    }
+  } else {
+    // wrapped halo: per-value copies into the same [c][z][y][x] layout
+    for (int i = threadIdx.x; i < CC * H * H * H; i += blockDim.x) {
+      const int x = i % H;
+      const int r = i / H;
+      const int yy = r % H, z = (r / H) % H, c = r / (H * H);
+      const int gz = wrap_once(o0 + z, g.g0), gy = wrap_once(o1 + yy, g.g1),
+                gx = wrap_once(o2 + x, g.g2);
+      const bool valid = coil0 + c < C;
+      const GT* src =
+          grid + (valid ? (long long)(coil0 + c) * g.ngrid + ((long long)gz * g.g1 + gy) * g.g2 + gx
+                        : 0);
+      cp_async_grid(halo + ((c * H + z) * H + yy) * XP + x, src, valid);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPS;          // sample slot in the warp
+  const int gl = lane - grp * LPS;     // lane in the group
+  const int c = gl % CC, txl = gl / CC;
+  const int gbase = grp * LPS;
+  const bool active_lane = grp < SPW;
+  const int nwarps = blockDim.x >> 5;
+  for (int s0 = it.begin + warp * SPW; s0 < it.end; s0 += nwarps * SPW) {
+    const int s = s0 + grp;
+    const bool live = active_lane && s < it.end;
+    float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
+    int l0 = 0, l1 = 0, l2 = 0;
+    if (live) {
+      qv = __ldg(qs + s);
+      int b0, b1, b2;
+      unpack_base(__float_as_uint(qv.w), b0, b1, b2);
+      l0 = min(max(b0 - o0, 0), T - 1);  // in range for a well-formed plan
+      l1 = min(max(b1 - o1, 0), T - 1);
+      l2 = min(max(b2 - o2, 0), T - 1);
+    }
+    // this lane's tap txl on each axis
+    float w0t, w1t, w2t;
+    {
+      const float s0f = fmaf(2.f, qv.x, -1.f), s1f = fmaf(2.f, qv.y, -1.f),
+                  s2f = fmaf(2.f, qv.z, -1.f);
+      float a0 = s_coef[txl][kNumCoef - 1], a1 = a0, a2 = a0;
+#pragma unroll
+      for (int k = kNumCoef - 2; k >= 0; --k) {
+        const float ck = s_coef[txl][k];
+        a0 = fmaf(a0, s0f, ck);
+        a1 = fmaf(a1, s1f, ck);
+        a2 = fmaf(a2, s2f, ck);
+      }
+      w0t = a0;
+      w1t = a1;
+      w2t = a2;
+    }
+    float w0[W], w1[W];
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      w0[t] = __shfl_sync(0xffffffffu, w0t, gbase + t * CC);
+      w1[t] = __shfl_sync(0xffffffffu, w1t, gbase + t * CC);
+    }
+    float2 acc = make_float2(0.f, 0.f);
+    if (live) {
+      const GT* base = halo + ((c * H + l0) * H + l1) * XP + l2 + txl;
+#pragma unroll
+      for (int t0 = 0; t0 < W; ++t0) {
+#pragma unroll
+        for (int t1 = 0; t1 < W; ++t1) {
+          const float w = w0[t0] * w1[t1] * w2t;
+          const float2 v = grid_ld_shared(base + (t0 * H + t1) * XP);
+          acc.x = fmaf(w, v.x, acc.x);
+          acc.y = fmaf(w, v.y, acc.y);
+        }
+      }
+    }
+    // reduce over tap x (lanes CC apart within the group)
+#pragma unroll
+    for (int off = CC; off < LPS; off <<= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (live && txl == 0 && coil0 + c < C) y[(row0 + __ldg(perm + s)) * C + coil0 + c] = acc;
+  }
+}
+
+template <int CC, typename GT>
+constexpr size_t interp_tma_smem() {  // halo + alignment slack
+  return size_t(CC) * (8 + 3) * (8 + 3) * kTmaXP * sizeof(GT) + 128;
+}
+
 template <int W, int CC, typename GT>
 constexpr size_t interp_smem() {
   return size_t(8 + W - 1) * (8 + W - 1) * (8 + W - 1) * CC * sizeof(GT);
@@ -285,6 +464,12 @@ int launch_image_to_padded(const Geo& g, int C, const float* deapod, const nrsen
 }
 
 namespace {
+template <int CC, typename GT>
+cudaError_t set_tma_smem() {
+  return cudaFuncSetAttribute(interp_tma_kernel<CC, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(interp_tma_smem<CC, GT>()));
+}
+
 template <int W, int CC, typename GT>
 cudaError_t set_interp_smem() {
   return cudaFuncSetAttribute(interp_tile_kernel<W, CC, GT>,
@@ -317,15 +502,73 @@ cudaError_t configure_kernels() {
   if (e == cudaSuccess) e = set_interp_smem<4, 8, bf162>();
   if (e == cudaSuccess) e = set_interp_smem<4, 4, bf162>();
   if (e == cudaSuccess) e = set_interp_smem<6, 4, bf162>();
+  if (e == cudaSuccess) e = set_tma_smem<4, float2>();
+  if (e == cudaSuccess) e = set_tma_smem<8, float2>();
+  if (e == cudaSuccess) e = set_tma_smem<4, bf162>();
+  if (e == cudaSuccess) e = set_tma_smem<8, bf162>();
   return e;
+}
+
+bool make_grid_tensor_map(CUtensorMap* m, const void* base, const Geo& g, long long slots,
+                          bool bf16, int coil_chunk) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (encode == nullptr) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || fn == nullptr) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t esz = bf16 ? 4 : 8;
+  // x innermost; strides in bytes for dimensions 1..3 (multiples of 16)
+  const cuuint64_t dims[4] = {cuuint64_t(g.g2), cuuint64_t(g.g1), cuuint64_t(g.g0),
+                              cuuint64_t(slots)};
+  const cuuint64_t strides[3] = {cuuint64_t(g.g2) * esz, cuuint64_t(g.g1) * g.g2 * esz,
+                                 cuuint64_t(g.ngrid) * esz};
+  for (int k = 0; k < 3; ++k)
+    if (strides[k] % 16) return false;
+  const cuuint32_t box[4] = {cuuint32_t(kTmaXP), 11u, 11u, cuuint32_t(coil_chunk)};
+  const cuuint32_t elem[4] = {1, 1, 1, 1};
+  const CUresult r = encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64,
+                            4, const_cast<void*>(base), dims, strides, box, elem,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                          const PhaseTable& pt, const void* grids, bool bf16, nrsense_c64* y,
-                         int coil_chunk, cudaStream_t s) {
+                         int coil_chunk, const CUtensorMap* tmap, int32_t* status,
+                         cudaStream_t s) {
   const int nitems = pt.item0[pt.nphase];
   if (nitems == 0) return 0;
   auto* yp = reinterpret_cast<float2*>(y);
+  if (tmap != nullptr && W == 4) {
+    const int cc = (coil_chunk == 8 && C > 4) ? 8 : 4;
+    const dim3 gd(nitems, (C + cc - 1) / cc);
+    if (bf16) {
+      const auto* gp = static_cast<const bf162*>(grids);
+      if (cc == 8)
+        interp_tma_kernel<8, bf162><<<gd, 256, interp_tma_smem<8, bf162>(), s>>>(
+            *tmap, g, kc, C, tp, pt, gp, yp, status);
+      else
+        interp_tma_kernel<4, bf162><<<gd, 256, interp_tma_smem<4, bf162>(), s>>>(
+            *tmap, g, kc, C, tp, pt, gp, yp, status);
+    } else {
+      const auto* gp = static_cast<const float2*>(grids);
+      if (cc == 8)
+        interp_tma_kernel<8, float2><<<gd, 256, interp_tma_smem<8, float2>(), s>>>(
+            *tmap, g, kc, C, tp, pt, gp, yp, status);
+      else
+        interp_tma_kernel<4, float2><<<gd, 256, interp_tma_smem<4, float2>(), s>>>(
+            *tmap, g, kc, C, tp, pt, gp, yp, status);
+    }
+    return 1;
+  }
   if (bf16)
     interp_dispatch(g, W, kc, C, tp, pt, static_cast<const bf162*>(grids), yp, nitems, coil_chunk,
                     s);

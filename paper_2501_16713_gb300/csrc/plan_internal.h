@@ -1,6 +1,7 @@
 // Host-side plan structure and kernel launchers (internal).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cufft.h>
 
@@ -82,6 +83,9 @@ struct nrsense_plan_s {
   bool grid_bf16 = false;     // desc.precision == NRSENSE_BF16_STORE
   int spread_variant = 1;     // kSpreadRegister or kSpreadShared (autotuned)
   int interp_coils = 8;       // coils per interpolation CTA (autotuned)
+  bool interp_tma = false;    // TMA-staged interpolation (autotuned; needs tma_ok)
+  bool tma_ok = false;        // tensor maps of b_xwork built
+  CUtensorMap tmap_xwork4{}, tmap_xwork8{};  // boxes of 4 and 8 coil grids
   bool comp_spread = false;   // desc.precision == NRSENSE_FP32_COMPENSATED
   nrsense_c64* b_y = nullptr;      // Mtot * C
   nrsense_c64* b_tmp = nullptr;    // N^3 (normal operator scratch)
@@ -167,10 +171,17 @@ int launch_coil_fanout_pad(const Geo& g, int C, int nph, const float* deapod,
                            cudaStream_t s);
 int launch_image_to_padded(const Geo& g, int C, const float* deapod, const nrsense_c64* v,
                            void* xpad, bool bf16, cudaStream_t s);
-// coil_chunk: coils per CTA (8 or 4; W = 4 and C > 4 only, else ignored)
+// coil_chunk: coils per CTA (8 or 4; W = 4 and C > 4 only, else ignored);
+// tmap (may be null): tensor map of `grids` with a box of coil_chunk coils,
+// which selects the TMA-staged kernel (W = 4); status receives a timeout.
 int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                          const PhaseTable& pt, const void* grids, bool bf16, nrsense_c64* y,
-                         int coil_chunk, cudaStream_t s);
+                         int coil_chunk, const CUtensorMap* tmap, int32_t* status,
+                         cudaStream_t s);
+// Tensor map of `slots` consecutive coil grids at base ([slot][G0][G1][G2]
+// values) with a halo box of 12 x 11 x 11 values x coil_chunk grids.
+bool make_grid_tensor_map(CUtensorMap* m, const void* base, const Geo& g, long long slots,
+                          bool bf16, int coil_chunk);
 // one-time kernel attributes (large dynamic shared memory); plan time
 cudaError_t configure_kernels();
 cudaError_t configure_spread_kernels();

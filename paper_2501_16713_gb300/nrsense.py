@@ -44,7 +44,9 @@ class Desc(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("spread_variant", ctypes.c_int32), ("interp_coils", ctypes.c_int32),
-                ("spread_ms", ctypes.c_double * 2), ("interp_ms", ctypes.c_double * 2)]
+                ("interp_tma", ctypes.c_int32),
+                ("spread_ms", ctypes.c_double * 2), ("interp_ms", ctypes.c_double * 2),
+                ("interp_tma_ms", ctypes.c_double * 2)]
 
 
 class Info(ctypes.Structure):
@@ -459,6 +461,7 @@ class Plan:
             t = Tuning()
             t.spread_variant = int(store[key]["spread_variant"])
             t.interp_coils = int(store[key]["interp_coils"])
+            t.interp_tma = int(store[key].get("interp_tma", 0))
             _check(self.lib.nrsense_plan_set_tuning(self._h, ctypes.byref(t)),
                    "nrsense_plan_set_tuning")
             return dict(store[key], cached=True)
@@ -466,7 +469,8 @@ class Plan:
         _check(self.lib.nrsense_plan_autotune(self._h, int(reps), ctypes.byref(t), _stream(stream)),
                "nrsense_plan_autotune")
         res = {"spread_variant": t.spread_variant, "interp_coils": t.interp_coils,
-               "spread_ms": list(t.spread_ms), "interp_ms": list(t.interp_ms)}
+               "interp_tma": t.interp_tma, "spread_ms": list(t.spread_ms),
+               "interp_ms": list(t.interp_ms), "interp_tma_ms": list(t.interp_tma_ms)}
         if cache:
             store[key] = res
             tmp = cache + ".tmp"

@@ -258,8 +258,8 @@ def test_phase_chunking_matches_oracle(chunk):
 
 def test_autotune_choices_compute_the_same_values(tmp_path):
     # every launch choice (register / shared-memory spreading, 8 / 4 coils per
-    # interpolation CTA) computes bitwise the same operator; the cache file
-    # round-trips the choices
+    # interpolation CTA, per-value / TMA halo staging) computes bitwise the
+    # same operator; the cache file round-trips the choices
     import torch
     shape = (16, 16, 24)
     case = synth.small_case(shape, 8, 2, [2500, 1800], seed=41)
@@ -272,13 +272,17 @@ def test_autotune_choices_compute_the_same_values(tmp_path):
     assert not res["cached"] and res["spread_variant"] in (1, 2) and res["interp_coils"] in (4, 8)
     from paper_2501_16713_gb300.nrsense import Tuning
     import ctypes
+    # grid 32 x 32 x 48 with 8^3 tiles: interior tiles take the TMA-staged
+    # halo, tiles at the upper edges the wrapped per-value staging
     for sv in (1, 2):
         for ic in (8, 4):
-            t = Tuning()
-            t.spread_variant, t.interp_coils = sv, ic
-            assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == 0
-            assert torch.equal(plan.forward(x), y0)
-            assert torch.equal(plan.adjoint(y0), xa0)
+            for tma in (0, 1):
+                t = Tuning()
+                t.spread_variant, t.interp_coils, t.interp_tma = sv, ic, tma
+                assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == 0
+                assert torch.equal(plan.forward(x), y0), (sv, ic, tma)
+                assert torch.equal(plan.adjoint(y0), xa0)
+    assert plan.device_status() == 0
     res2 = plan.autotune(cache=cache)
     assert res2["cached"] and res2["spread_variant"] == res["spread_variant"]
     t = Tuning()
