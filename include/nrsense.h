@@ -367,7 +367,8 @@ nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* 
  * Autotuning of the launch choices of a plan (no counterpart in the paper).
  * nrsense_plan_autotune times, on the plan's own k-space point sets (first
  * phase chunk) and internal buffers, the k-space spreading kernel with
- * register accumulation and with shared-memory accumulation, and the k-space
+ * register accumulation (a CTA per tile or per tile plane) and with
+ * shared-memory accumulation, and the k-space
  * interpolation with 8 and with 4 coils per CTA, its tile halos staged per
  * value or by one tensor-memory-accelerator copy (reps launches each, after
  * one warm-up launch, CUDA events on `stream`; synchronises), keeps the
@@ -378,13 +379,14 @@ nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* 
  * geometry).  Both change only speed: every choice computes the same values.
  * Errors: ERR_ARG (null, reps outside 1..100, unknown choice), ERR_CUDA.
  */
-#define NRSENSE_TUNE_SPREAD_REGISTER 1
-#define NRSENSE_TUNE_SPREAD_SHARED   2
+#define NRSENSE_TUNE_SPREAD_REGISTER      1  /* register accumulation, CTA per tile */
+#define NRSENSE_TUNE_SPREAD_SHARED        2  /* shared-memory accumulation */
+#define NRSENSE_TUNE_SPREAD_REGISTER_WARP 3  /* register accumulation, CTA per tile plane */
 typedef struct {
   int32_t spread_variant;  /* NRSENSE_TUNE_SPREAD_* */
   int32_t interp_coils;    /* coils per interpolation CTA: 8 or 4 */
   int32_t interp_tma;      /* 1: tile halos loaded by the tensor memory accelerator */
-  double  spread_ms[2];    /* measured: register, shared */
+  double  spread_ms[3];    /* measured: register, shared, register per plane */
   double  interp_ms[2];    /* measured, per-value staging: 8 coils, 4 coils */
   double  interp_tma_ms[2];/* measured, TMA staging: 8 coils, 4 coils (-1: not available) */
 } nrsense_tuning;

@@ -308,12 +308,14 @@ nrsense_status nrsense_apply_normal(nrsense_plan_t p, const nrsense_c64* x, doub
 nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t) {
   if (p == nullptr || t == nullptr) return NRSENSE_ERR_ARG;
   if (t->spread_variant != NRSENSE_TUNE_SPREAD_REGISTER &&
-      t->spread_variant != NRSENSE_TUNE_SPREAD_SHARED)
+      t->spread_variant != NRSENSE_TUNE_SPREAD_SHARED &&
+      t->spread_variant != NRSENSE_TUNE_SPREAD_REGISTER_WARP)
     return NRSENSE_ERR_ARG;
   if (t->interp_coils != 4 && t->interp_coils != 8) return NRSENSE_ERR_ARG;
   if (t->interp_tma != 0 && t->interp_tma != 1) return NRSENSE_ERR_ARG;
-  p->spread_variant = t->spread_variant == NRSENSE_TUNE_SPREAD_REGISTER ? kSpreadRegister
-                                                                         : kSpreadShared;
+  p->spread_variant = t->spread_variant == NRSENSE_TUNE_SPREAD_REGISTER   ? kSpreadRegister
+                      : t->spread_variant == NRSENSE_TUNE_SPREAD_SHARED ? kSpreadShared
+                                                                        : kSpreadRegisterWarp;
   p->interp_coils = t->interp_coils;
   p->interp_tma = t->interp_tma == 1 && p->tma_ok;
   return NRSENSE_OK;
@@ -324,7 +326,8 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
   if (p == nullptr || out == nullptr || reps < 1 || reps > 100) return NRSENSE_ERR_ARG;
   std::memset(out, 0, sizeof(*out));
   out->spread_variant = p->spread_variant == kSpreadRegister ? NRSENSE_TUNE_SPREAD_REGISTER
-                                                             : NRSENSE_TUNE_SPREAD_SHARED;
+                        : p->spread_variant == kSpreadShared ? NRSENSE_TUNE_SPREAD_SHARED
+                                                             : NRSENSE_TUNE_SPREAD_REGISTER_WARP;
   out->interp_coils = p->interp_coils;
   out->interp_tma = p->interp_tma ? 1 : 0;
   if (p->C == 0) return NRSENSE_OK;  // nothing to choose without k space
@@ -348,8 +351,8 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
       return -1.0;
     return double(ms) / reps;
   };
-  const int variants[2] = {kSpreadRegister, kSpreadShared};
-  for (int k = 0; k < 2; ++k)
+  const int variants[3] = {kSpreadRegister, kSpreadShared, kSpreadRegisterWarp};
+  for (int k = 0; k < 3; ++k)
     out->spread_ms[k] = time_ms([&] {
       p->launches += launch_spread(g, p->W, p->kc, p->C, p->ktiles, ts, p->b_y, p->b_xspread,
                                    p->grid_bf16, p->comp_spread, variants[k], p->b_scratch,
@@ -377,11 +380,17 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (cudaGetLastError() != cudaSuccess) return NRSENSE_ERR_CUDA;
+  for (int k = 0; k < 3; ++k)
+    if (!(out->spread_ms[k] >= 0.0)) return NRSENSE_ERR_CUDA;
   for (int k = 0; k < 2; ++k)
-    if (!(out->spread_ms[k] >= 0.0) || !(out->interp_ms[k] >= 0.0)) return NRSENSE_ERR_CUDA;
+    if (!(out->interp_ms[k] >= 0.0)) return NRSENSE_ERR_CUDA;
   // the compensated variant has only the shared-memory kernel: keep the default there
-  if (!p->comp_spread)
-    p->spread_variant = out->spread_ms[1] < out->spread_ms[0] ? kSpreadShared : kSpreadRegister;
+  if (!p->comp_spread) {
+    int bk = 0;
+    for (int k = 1; k < 3; ++k)
+      if (out->spread_ms[k] < out->spread_ms[bk]) bk = k;
+    p->spread_variant = variants[bk];
+  }
   // fastest interpolation: staging (per value / TMA) x coils per CTA (8 / 4)
   double best = out->interp_ms[0];
   p->interp_tma = false;
@@ -396,7 +405,8 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
       }
     }
   out->spread_variant = p->spread_variant == kSpreadRegister ? NRSENSE_TUNE_SPREAD_REGISTER
-                                                             : NRSENSE_TUNE_SPREAD_SHARED;
+                        : p->spread_variant == kSpreadShared ? NRSENSE_TUNE_SPREAD_SHARED
+                                                             : NRSENSE_TUNE_SPREAD_REGISTER_WARP;
   out->interp_coils = p->interp_coils;
   out->interp_tma = p->interp_tma ? 1 : 0;
   return NRSENSE_OK;

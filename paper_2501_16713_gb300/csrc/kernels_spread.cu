@@ -141,12 +141,15 @@ struct ItemRef {
   SpreadItem it;
   int jj, local;
 };
-__device__ __forceinline__ ItemRef item_ref(const PhaseTable& pt) {
+__device__ __forceinline__ ItemRef item_ref(const PhaseTable& pt, int index) {
   ItemRef r;
-  r.jj = phase_of(pt.item0, pt.nphase, blockIdx.x);
-  r.local = blockIdx.x - pt.item0[r.jj];
+  r.jj = phase_of(pt.item0, pt.nphase, index);
+  r.local = index - pt.item0[r.jj];
   r.it = pt.items[r.jj][r.local];
   return r;
+}
+__device__ __forceinline__ ItemRef item_ref(const PhaseTable& pt) {
+  return item_ref(pt, blockIdx.x);
 }
 __device__ __forceinline__ int scratch_slot(const PhaseTable& pt, const ItemRef& r) {
   return r.it.slot < 0 ? -1 : pt.slot0[r.jj] + r.it.slot;
@@ -286,15 +289,20 @@ __global__ void __launch_bounds__(kThreads) spread_coils_kernel(
 // the plane), so nothing is read back from or written to shared memory per
 // update.  The result (and the order of every sum) is the same per grid value
 // as for the shared-memory kernel: list order within the item.
-template <int CC, typename GT>
-__global__ void __launch_bounds__(kThreads) spread_coils_reg_kernel(
+// WPC = 8: a CTA is a work item's tile, warp w its plane w.  WPC = 1: a CTA
+// is one warp, block b serves plane b % 8 of item b / 8, so a plane's warp
+// frees its resources as soon as it is done (the planes of a tile carry
+// different amounts of work).  Same summation order, same result.
+template <int CC, typename GT, int WPC>
+__global__ void __launch_bounds__(32 * WPC, WPC == 1 ? 24 : 3) spread_coils_reg_kernel(
     Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
     GT* __restrict__ grids, float2* __restrict__ scratch) {
   constexpr int W = 4, T = 8, B = 32, NB = W + T + 1;
   static_assert(CC == 2 || CC == 4 || CC == 8, "coil chunk");
-  __shared__ __align__(16) CoilStage<CC> stg[kThreads / 32][B];
+  static_assert(WPC == 1 || WPC == 8, "warps per CTA");
+  __shared__ __align__(16) CoilStage<CC> stg[WPC][B];
 
-  const ItemRef ir = item_ref(pt);
+  const ItemRef ir = item_ref(pt, WPC == 8 ? int(blockIdx.x) : int(blockIdx.x >> 3));
   const SpreadItem it = ir.it;
   const int2* __restrict__ list = pt.list[ir.jj];
   const float4* __restrict__ qs = pt.qs[ir.jj];
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(kThreads) spread_coils_reg_kernel(
   const int coil0 = blockIdx.y * CC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TileOrigin to = tile_origin(g, tp, it.tile);
-  const int lz = warp, x = lane & 7, yh = lane >> 3;
+  const int lz = WPC == 8 ? warp : int(blockIdx.x & 7), x = lane & 7, yh = lane >> 3;
 
   float2 acc[2][CC];
 #pragma unroll
@@ -652,9 +660,13 @@ int dispatch_coils(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& t
     const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2) * (COMP ? 2 : 1);
     spread_coils_kernel<CC, GT, COMP><<<grid, kThreads, smem, s>>>(g, kc, C, tp, pt, vals, grids,
                                                                    scratch);
+  } else if (variant == kSpreadRegisterWarp) {
+    const dim3 wgrid(8u * pt.item0[pt.nphase], chunks);
+    spread_coils_reg_kernel<CC, GT, 1><<<wgrid, 32, 0, s>>>(g, kc, C, tp, pt, vals, grids,
+                                                            scratch);
   } else {
-    spread_coils_reg_kernel<CC, GT><<<grid, kThreads, 0, s>>>(g, kc, C, tp, pt, vals, grids,
-                                                              scratch);
+    spread_coils_reg_kernel<CC, GT, 8><<<grid, kThreads, 0, s>>>(g, kc, C, tp, pt, vals, grids,
+                                                                 scratch);
   }
   return 1 + launch_reduce<8, CC, GT, COMP>(g, C, tp, pt, chunks, grids, scratch, s);
 }

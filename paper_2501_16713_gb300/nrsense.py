@@ -45,7 +45,7 @@ class Desc(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("spread_variant", ctypes.c_int32), ("interp_coils", ctypes.c_int32),
                 ("interp_tma", ctypes.c_int32),
-                ("spread_ms", ctypes.c_double * 2), ("interp_ms", ctypes.c_double * 2),
+                ("spread_ms", ctypes.c_double * 3), ("interp_ms", ctypes.c_double * 2),
                 ("interp_tma_ms", ctypes.c_double * 2)]
 
 
