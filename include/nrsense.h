@@ -368,13 +368,14 @@ nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* 
  * nrsense_plan_autotune times, on the plan's own k-space point sets (first
  * phase chunk) and internal buffers, the k-space spreading kernel with
  * register accumulation (a CTA per tile or per tile plane) and with
- * shared-memory accumulation, and the k-space
+ * shared-memory accumulation, the image-space spreading kernel with a CTA
+ * per tile or per plane pair, and the k-space
  * interpolation with 8 and with 4 coils per CTA, its tile halos staged per
  * value or by one tensor-memory-accelerator copy (reps launches each, after
  * one warm-up launch, CUDA events on `stream`; synchronises), keeps the
  * faster of each in the plan and reports times and choices in *out (host).
- * The compensated precision always uses shared-memory accumulation; plans
- * without coils have nothing to tune (*out holds the current choices).
+ * The compensated precision always uses shared-memory accumulation for k
+ * space; plans without coils tune only the image-space spread.
  * nrsense_plan_set_tuning applies stored choices (e.g. a cache keyed by the
  * geometry).  Both change only speed: every choice computes the same values.
  * Errors: ERR_ARG (null, reps outside 1..100, unknown choice), ERR_CUDA.
@@ -389,6 +390,8 @@ typedef struct {
   double  spread_ms[3];    /* measured: register, shared, register per plane */
   double  interp_ms[2];    /* measured, per-value staging: 8 coils, 4 coils */
   double  interp_tma_ms[2];/* measured, TMA staging: 8 coils, 4 coils (-1: not available) */
+  int32_t spread_image_warp;   /* image-space spread: 0 CTA per tile, 1 CTA per plane pair */
+  double  spread_image_ms[2];  /* measured: CTA per tile, CTA per plane pair */
 } nrsense_tuning;
 nrsense_status nrsense_plan_autotune(nrsense_plan_t plan, int32_t reps, nrsense_tuning* out_host,
                                      void* stream);

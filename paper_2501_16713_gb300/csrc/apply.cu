@@ -174,7 +174,8 @@ nrsense_status warp_adjoint(nrsense_plan_s* p, const nrsense_c64* m, nrsense_c64
   }
   const PhaseTable t = image_table(p);
   STAGE(SPREAD_IMAGE, launch_spread(g, p->W, p->kc, 1, p->itiles, t, m, p->b_ugrid, false,
-                                    p->comp_spread, p->spread_variant, p->b_scratch, p->d_status, s));
+                                    p->comp_spread, p->spread_image_variant, p->b_scratch,
+                                    p->d_status, s));
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_ugrid, p->b_ugrid, CUFFT_FORWARD));
   STAGE(CROP_DEAPOD, launch_crop_deapod(g, p->deapod, p->b_ugrid, x, s));
@@ -318,6 +319,8 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
                                                                         : kSpreadRegisterWarp;
   p->interp_coils = t->interp_coils;
   p->interp_tma = t->interp_tma == 1 && p->tma_ok;
+  if (t->spread_image_warp != 0 && t->spread_image_warp != 1) return NRSENSE_ERR_ARG;
+  p->spread_image_variant = t->spread_image_warp ? kSpreadRegisterWarp : kSpreadShared;
   return NRSENSE_OK;
 }
 
@@ -330,9 +333,41 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
                                                              : NRSENSE_TUNE_SPREAD_REGISTER_WARP;
   out->interp_coils = p->interp_coils;
   out->interp_tma = p->interp_tma ? 1 : 0;
-  if (p->C == 0) return NRSENSE_OK;  // nothing to choose without k space
+  out->spread_image_warp = p->spread_image_variant == kSpreadRegisterWarp ? 1 : 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Geo& g = p->geo;
+  if (!p->identity_warp && p->ipts.tp.t0 == 16) {
+    // image-space spread: CTA per tile or per plane pair, timed on the plan's
+    // displaced voxels (values: the internal warped-image buffer)
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+      return NRSENSE_ERR_CUDA;
+    const PhaseTable tim = image_table(p);
+    const int iv[2] = {kSpreadShared, kSpreadRegisterWarp};
+    for (int k = 0; k < 2; ++k) {
+      auto run = [&] {
+        p->launches += launch_spread(g, p->W, p->kc, 1, p->itiles, tim, p->b_m, p->b_ugrid, false,
+                                     p->comp_spread, iv[k], p->b_scratch, p->d_status, s);
+      };
+      run();
+      cudaEventRecord(a, s);
+      for (int r = 0; r < reps; ++r) run();
+      cudaEventRecord(b, s);
+      float ms = -1.f;
+      if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return NRSENSE_ERR_CUDA;
+      }
+      out->spread_image_ms[k] = double(ms) / reps;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    p->spread_image_variant =
+        out->spread_image_ms[1] < out->spread_image_ms[0] ? kSpreadRegisterWarp : kSpreadShared;
+    out->spread_image_warp = p->spread_image_variant == kSpreadRegisterWarp ? 1 : 0;
+  }
+  if (p->C == 0) return NRSENSE_OK;  // nothing more to choose without k space
   const int j1 = std::min(p->P, p->phase_chunk);
   const PhaseTable ts = kspace_table(p, 0, j1, true, 0);
   const PhaseTable ti = kspace_table(p, 0, j1, false, 0);

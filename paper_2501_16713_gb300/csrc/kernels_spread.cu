@@ -415,18 +415,24 @@ struct SingleStage {
   float2 val;
 };
 
-template <bool COMP>
-__global__ void __launch_bounds__(kThreads) spread_single_kernel(
+// WPC = 8: a CTA is a work item's tile (8 warps, 2 planes each, accumulator
+// of the whole tile); WPC = 1: a CTA is one warp with planes 2w, 2w+1 of item
+// b / 8, w = b % 8, and an accumulator of those two planes only, so each
+// plane pair frees its resources when done.  Same summation order.
+template <bool COMP, int WPC>
+__global__ void __launch_bounds__(32 * WPC) spread_single_kernel(
     Geo g, KernelCoefs kc, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
     float2* __restrict__ grids, float2* __restrict__ scratch) {
   constexpr int W = 4, T = 16, B = 32, NB = W + T + 1;
   constexpr int RS = T + 4;  // padded row stride: 4 tap rows hit disjoint banks
+  constexpr int NP = WPC == 8 ? T : 2;  // planes held in shared memory
+  static_assert(WPC == 1 || WPC == 8, "warps per CTA");
   extern __shared__ float4 smem_raw[];
-  float2* acc = reinterpret_cast<float2*>(smem_raw);  // [T][T][RS]
-  float2* comp = COMP ? acc + T * T * RS : nullptr;
-  __shared__ SingleStage stg[kThreads / 32][B];
+  float2* acc = reinterpret_cast<float2*>(smem_raw);  // [NP][T][RS]
+  float2* comp = COMP ? acc + NP * T * RS : nullptr;
+  __shared__ SingleStage stg[WPC][B];
 
-  const ItemRef ir = item_ref(pt);
+  const ItemRef ir = item_ref(pt, WPC == 8 ? int(blockIdx.x) : int(blockIdx.x >> 3));
   const SpreadItem it = ir.it;
   const int2* __restrict__ list = pt.list[ir.jj];
   const float4* __restrict__ qs = pt.qs[ir.jj];
@@ -434,10 +440,13 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
   float2* __restrict__ grid = grids + (long long)ir.jj * g.ngrid;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TileOrigin to = tile_origin(g, tp, it.tile);
-  for (int i = tid; i < T * T * RS * (COMP ? 2 : 1); i += kThreads) acc[i] = make_float2(0.f, 0.f);
+  const int pw = WPC == 8 ? warp : int(blockIdx.x & 7);  // plane pair of this warp
+  const int pbase = WPC == 8 ? 0 : 2 * pw;               // first plane held
+  for (int i = tid; i < NP * T * RS * (COMP ? 2 : 1); i += 32 * WPC)
+    acc[i] = make_float2(0.f, 0.f);
   __syncthreads();
 
-  const int z0 = 2 * warp;
+  const int z0 = 2 * pw;
   if (z0 < to.e0) {
     const int32_t* ib = pt.bins[ir.jj] + (long long)ir.local * NB;
     const int beg = it.begin + __ldg(ib + min(z0, NB - 1));
@@ -483,7 +492,7 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
         const int ly = d.r1 + ty, lx = d.r2 + tx;
         if ((unsigned)ly < (unsigned)to.e1 && (unsigned)lx < (unsigned)to.e2 && lz < to.e0) {
           const float w = d.wzy[hz][ty] * d.wx[tx];
-          const int off = (lz * T + ly) * RS + lx;
+          const int off = ((lz - pbase) * T + ly) * RS + lx;
           float2 cur = acc[off];
           if constexpr (COMP) {
             float2 cc = comp[off];
@@ -501,11 +510,11 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
     }
   }
   __syncthreads();
-  // write the tile (or partial tile), dropping the row padding
+  // write the held planes of the tile (or partial tile), dropping the row padding
   constexpr int kPts = T * T * T;
   const int slot = scratch_slot(pt, ir);
   auto value = [&](int lz, int ly, int lx) {
-    const int off = (lz * T + ly) * RS + lx;
+    const int off = ((lz - pbase) * T + ly) * RS + lx;
     float2 v = acc[off];
     if constexpr (COMP) {
       v.x += comp[off].x;
@@ -514,17 +523,17 @@ __global__ void __launch_bounds__(kThreads) spread_single_kernel(
     return v;
   };
   if (slot < 0) {
-    for (int i = tid; i < kPts; i += kThreads) {
-      const int lx = i % T, ly = (i / T) % T, lz = i / (T * T);
+    for (int i = tid; i < NP * T * T; i += 32 * WPC) {
+      const int lx = i % T, ly = (i / T) % T, lz = pbase + i / (T * T);
       if (lz < to.e0 && ly < to.e1 && lx < to.e2) {
         const long long gi = ((long long)(to.o0 + lz) * g.g1 + (to.o1 + ly)) * g.g2 + (to.o2 + lx);
         grid[gi] = value(lz, ly, lx);
       }
     }
   } else {
-    float2* dst = scratch + (long long)slot * kPts;
-    for (int i = tid; i < kPts; i += kThreads) {
-      const int lx = i % T, ly = (i / T) % T, lz = i / (T * T);
+    float2* dst = scratch + (long long)slot * kPts + pbase * T * T;
+    for (int i = tid; i < NP * T * T; i += 32 * WPC) {
+      const int lx = i % T, ly = (i / T) % T, lz = pbase + i / (T * T);
       dst[i] = value(lz, ly, lx);
     }
   }
@@ -721,10 +730,10 @@ cudaError_t configure_spread_kernels() {
   if (e == cudaSuccess) e = set_coils_smem<bf162, false>();
   if (e == cudaSuccess) e = set_coils_smem<bf162, true>();
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(spread_single_kernel<false>,
+    e = cudaFuncSetAttribute(spread_single_kernel<false, 8>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(spread_single_kernel<true>,
+    e = cudaFuncSetAttribute(spread_single_kernel<true, 8>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e;
 }
@@ -743,16 +752,26 @@ int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TileP
   const auto* v = reinterpret_cast<const float2*>(vals);
   auto* sc = reinterpret_cast<float2*>(scratch);
   if (W == 4 && C == 1 && tp.t0 == 16 && !bf16) {
-    // single channel (image space), FP32 grid
+    // single channel (image space), FP32 grid; variant == kSpreadRegisterWarp
+    // selects a CTA per plane pair
     auto* gr = static_cast<float2*>(grids);
-    const size_t smem = size_t(16 * 16 * 20) * sizeof(float2) * (comp ? 2 : 1);
+    const bool per_warp = variant == kSpreadRegisterWarp;
+    const int np = per_warp ? 2 : 16;
+    const size_t smem = size_t(np * 16 * 20) * sizeof(float2) * (comp ? 2 : 1);
+    const unsigned items = pt.item0[pt.nphase];
+    const dim3 grid(per_warp ? 8u * items : items, 1);
+    const int threads = per_warp ? 32 : kThreads;
     if (comp) {
-      spread_single_kernel<true><<<dim3(pt.item0[pt.nphase], 1), kThreads, smem, s>>>(g, kc, tp, pt,
-                                                                                       v, gr, sc);
+      if (per_warp)
+        spread_single_kernel<true, 1><<<grid, threads, smem, s>>>(g, kc, tp, pt, v, gr, sc);
+      else
+        spread_single_kernel<true, 8><<<grid, threads, smem, s>>>(g, kc, tp, pt, v, gr, sc);
       return 1 + launch_reduce<16, 1, float2, true>(g, 1, tp, pt, 1, gr, sc, s);
     }
-    spread_single_kernel<false><<<dim3(pt.item0[pt.nphase], 1), kThreads, smem, s>>>(
-        g, kc, tp, pt, v, gr, sc);
+    if (per_warp)
+      spread_single_kernel<false, 1><<<grid, threads, smem, s>>>(g, kc, tp, pt, v, gr, sc);
+    else
+      spread_single_kernel<false, 8><<<grid, threads, smem, s>>>(g, kc, tp, pt, v, gr, sc);
     return 1 + launch_reduce<16, 1, float2>(g, 1, tp, pt, 1, gr, sc, s);
   }
   if (bf16) {

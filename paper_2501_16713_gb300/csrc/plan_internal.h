@@ -83,6 +83,8 @@ struct nrsense_plan_s {
   bool grid_bf16 = false;     // desc.precision == NRSENSE_BF16_STORE
   int spread_variant = 1;     // kSpreadRegister or kSpreadShared (autotuned)
   int interp_coils = 8;       // coils per interpolation CTA (autotuned)
+  int spread_image_variant = 2;  // image-space spread: kSpreadShared (CTA per tile) or
+                                 // kSpreadRegisterWarp (CTA per plane pair) (autotuned)
   bool interp_tma = false;    // TMA-staged interpolation (autotuned; needs tma_ok)
   bool tma_ok = false;        // tensor maps of b_xwork built
   CUtensorMap tmap_xwork4{}, tmap_xwork8{};  // boxes of 4 and 8 coil grids

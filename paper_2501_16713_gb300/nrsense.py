@@ -46,7 +46,9 @@ class Tuning(ctypes.Structure):
     _fields_ = [("spread_variant", ctypes.c_int32), ("interp_coils", ctypes.c_int32),
                 ("interp_tma", ctypes.c_int32),
                 ("spread_ms", ctypes.c_double * 3), ("interp_ms", ctypes.c_double * 2),
-                ("interp_tma_ms", ctypes.c_double * 2)]
+                ("interp_tma_ms", ctypes.c_double * 2),
+                ("spread_image_warp", ctypes.c_int32),
+                ("spread_image_ms", ctypes.c_double * 2)]
 
 
 class Info(ctypes.Structure):
@@ -462,6 +464,7 @@ class Plan:
             t.spread_variant = int(store[key]["spread_variant"])
             t.interp_coils = int(store[key]["interp_coils"])
             t.interp_tma = int(store[key].get("interp_tma", 0))
+            t.spread_image_warp = int(store[key].get("spread_image_warp", 0))
             _check(self.lib.nrsense_plan_set_tuning(self._h, ctypes.byref(t)),
                    "nrsense_plan_set_tuning")
             return dict(store[key], cached=True)
@@ -470,7 +473,9 @@ class Plan:
                "nrsense_plan_autotune")
         res = {"spread_variant": t.spread_variant, "interp_coils": t.interp_coils,
                "interp_tma": t.interp_tma, "spread_ms": list(t.spread_ms),
-               "interp_ms": list(t.interp_ms), "interp_tma_ms": list(t.interp_tma_ms)}
+               "interp_ms": list(t.interp_ms), "interp_tma_ms": list(t.interp_tma_ms),
+               "spread_image_warp": t.spread_image_warp,
+               "spread_image_ms": list(t.spread_image_ms)}
         if cache:
             store[key] = res
             tmp = cache + ".tmp"

@@ -279,6 +279,7 @@ def test_autotune_choices_compute_the_same_values(tmp_path):
             for tma in (0, 1):
                 t = Tuning()
                 t.spread_variant, t.interp_coils, t.interp_tma = sv, ic, tma
+                t.spread_image_warp = tma  # both image-space spread variants too
                 assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == 0
                 assert torch.equal(plan.forward(x), y0), (sv, ic, tma)
                 assert torch.equal(plan.adjoint(y0), xa0)
