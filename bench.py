@@ -36,7 +36,7 @@ STAGE_KERNEL_SOURCE = {
     "interp_image": "kernels_image.cu", "spread_image": "kernels_spread.cu",
     "coil_fanout_pad": "kernels_kspace.cu", "crop_coilsum": "kernels_kspace.cu",
     "deapod_pad": "kernels_image.cu", "crop_deapod": "kernels_image.cu",
-    "vector": "kernels_image.cu",
+    "vector": "kernels_image.cu", "fista": "fista.cu",
 }
 FFT_STAGES = ("fft_n", "fft_g", "fft_gc")
 
@@ -441,6 +441,210 @@ def run_cg192(args):
     return line
 
 
+FISTA_LEVELS = 4
+FISTA_ITERS = 400     # the iteration count of the paper's wavelet-FISTA (Appendix 1)
+FISTA_TAU = 1e-3      # lambda / L: threshold at 1e-3 of the unit peak image intensity
+FISTA_STEP_BYTES = 48  # per voxel: read z, E0 z, b, x_{k-1}; write x_k, z_{k+1} (complex64)
+
+
+def run_fista128(args):
+    """Wavelet-FISTA on the 128^3, 8-coil, 4-phase workload (the default E
+    workload): 400 iterations of the fused FISTA step (gradient step, 4-level
+    Haar shrinkage, momentum) around the normal operator, replayed as CUDA
+    graphs of 32 iterations; lambda = 1e-3 L, L = 2.04 lambda_max (power
+    iteration).  Reports iterations/s, the per-iteration split between the
+    normal operator and the step kernel (from an eager 32-iteration profile)
+    and the step kernel's roofline."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2501_16713_gb300 import Plan, build
+
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = synth.workload("sense128")
+    spec = w["spec"]
+    shape = spec.shape
+    plan = Plan(shape, disp=torch.from_numpy(np.stack(w["disp"])).to(dev),
+                coords=[torch.from_numpy(c).to(dev) for c in w["coords"]],
+                smaps=torch.from_numpy(w["smaps"]).to(dev))
+    tuning = plan.autotune(reps=3)
+    x_true = torch.from_numpy(w["x"]).to(dev)
+    gen = torch.Generator(device=dev).manual_seed(6)
+    y = _noisy(plan, x_true, gen)
+    L = plan.lipschitz(iters=20, seed=4)
+    lam = FISTA_TAU * L
+    out = torch.empty(shape, dtype=torch.complex64, device=dev)
+    # warm-up: graph capture and caches
+    for _ in range(max(1, args.warmup - 2)):
+        plan.solve_fista(y, lam, levels=FISTA_LEVELS, L=L, maxit=64, graph=True, out=out)
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(vis.split(",")[0] if vis else "0")
+    clocks.start()
+    time.sleep(0.3)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(args.steps, 2))
+    e0.record(s)
+    for _ in range(reps):
+        x, hist, _ = plan.solve_fista(y, lam, levels=FISTA_LEVELS, L=L, maxit=FISTA_ITERS,
+                                      graph=True, out=out)
+    e1.record(s)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / reps
+    err = float(torch.linalg.norm(x - x_true) / torch.linalg.norm(x_true))
+    # eager 32-iteration profile: normal operator vs the fused step kernel
+    out2 = torch.empty_like(out)
+    plan.profile_start(max_launches=32 * 64 + 64)
+    plan.solve_fista(y, lam, levels=FISTA_LEVELS, L=L, maxit=32, graph=False, out=out2)
+    stages, own = plan.profile_stop()
+    f_ms, f_n = stages["fista"]
+    step_ms = f_ms / max(f_n, 1)
+    normal_ms = (sum(v[0] for k, v in stages.items() if k != "fista")) / 32
+    nvox = int(np.prod(shape))
+    step_bytes = FISTA_STEP_BYTES * nvox
+    achieved = step_bytes / (step_ms * 1e-3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    # end to end through the public API: data from pinned host memory, the
+    # image back to pinned host memory
+    yh = y.cpu().pin_memory()
+    xh = torch.empty(shape, dtype=torch.complex64).pin_memory()
+    yd = torch.empty_like(y)
+    te = time.perf_counter()
+    yd.copy_(yh, non_blocking=True)
+    plan.solve_fista(yd, lam, levels=FISTA_LEVELS, L=L, maxit=FISTA_ITERS, graph=True, out=out)
+    xh.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - te) * 1000.0
+    line = {"metric": "wavelet-FISTA iterations/s", "value": FISTA_ITERS * 1000.0 / ms,
+            "unit": "iterations/s", "higher_is_better": True, "n_gpus": 1, "steps": reps,
+            "warmup": args.warmup, "ms_per_step": ms, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64/f32 operator and step, f64 reductions", "data": "synthetic",
+            "config": {"workload": "fista128", "image": list(shape), "coils": spec.n_coils,
+                       "phases": len(plan.counts), "samples_per_phase": plan.counts,
+                       "iterations": FISTA_ITERS, "levels": FISTA_LEVELS,
+                       "lambda_over_L": FISTA_TAU, "L": L, "graph_chunk": 32,
+                       "tuning": tuning,
+                       "l2": "one step = one E apply (~12 GB touched) + the step kernel; no flush"},
+            "ms_per_iteration": ms / FISTA_ITERS,
+            "split_ms_per_iteration": {"normal": round(normal_ms, 4), "fista_step": round(step_ms, 4)},
+            "roofline": {"kernel": "fista_step", "bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs",
+                         "alg_bytes_per_launch": step_bytes, "ms_per_launch": step_ms,
+                         "traffic": ncu_traffic("fista", "fista128")},
+            "e2e": {"value": FISTA_ITERS * 1000.0 / e2e_ms, "unit": "iterations/s",
+                    "h2d_bytes_per_step": int(yh.numel() * 8) // FISTA_ITERS,
+                    "d2h_bytes_per_step": int(xh.numel() * 8) // FISTA_ITERS},
+            "gpu_launches": int(own),
+            "rel_error_vs_phantom": err, "last_rel_change": hist[-1],
+            "clocks": clk}
+    plan.close()
+    return line
+
+
+def run_fista_warp192(args):
+    """Appendix 1 in 3D at 192^3: recover a piecewise-constant phantom p from
+    q = T p (one nonrigid warp, image-space gridding, no coils) with 400
+    wavelet-FISTA iterations at lambda = 1e-6; the naive inversion warps q by
+    -d.  Reports iterations/s, both recovery errors and the step kernel's
+    roofline (192^3: the step moves 340 MB, more than L2)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2501_16713_gb300 import Plan, build
+
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    shape = (192, 192, 192)
+    p_img = torch.from_numpy(synth.phantom(shape, 41, n_ellipsoids=20, smooth_vox=0.0)).to(dev)
+    d = synth.bump_displacement(shape, 42, 6.0, width_range=(12.0, 30.0))
+    plan = Plan(shape, disp=torch.from_numpy(d[None]).to(dev))
+    q = plan.warp_forward(p_img)
+    neg = Plan(shape, disp=torch.from_numpy((-d)[None]).to(dev))
+    naive = neg.warp_forward(q[0])[0]
+    neg.close()
+    L = plan.lipschitz(iters=20, seed=4)
+    lam = 1e-6
+    out = torch.empty(shape, dtype=torch.complex64, device=dev)
+    for _ in range(max(1, args.warmup - 2)):
+        plan.solve_fista(q, lam, levels=FISTA_LEVELS, L=L, maxit=64, graph=True, out=out)
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(vis.split(",")[0] if vis else "0")
+    clocks.start()
+    time.sleep(0.3)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    x, hist, _ = plan.solve_fista(q, lam, levels=FISTA_LEVELS, L=L, maxit=FISTA_ITERS,
+                                  graph=True, out=out)
+    e1.record(s)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    nrm = float(torch.linalg.norm(p_img))
+    err = float(torch.linalg.norm(x - p_img)) / nrm
+    err_naive = float(torch.linalg.norm(naive - p_img)) / nrm
+    out2 = torch.empty_like(out)
+    plan.profile_start(max_launches=32 * 64 + 64)
+    plan.solve_fista(q, lam, levels=FISTA_LEVELS, L=L, maxit=32, graph=False, out=out2)
+    stages, own = plan.profile_stop()
+    f_ms, f_n = stages["fista"]
+    step_ms = f_ms / max(f_n, 1)
+    normal_ms = (sum(v[0] for k, v in stages.items() if k != "fista")) / 32
+    step_bytes = FISTA_STEP_BYTES * int(np.prod(shape))
+    achieved = step_bytes / (step_ms * 1e-3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    line = {"metric": "wavelet-FISTA iterations/s", "value": FISTA_ITERS * 1000.0 / ms,
+            "unit": "iterations/s", "higher_is_better": True, "n_gpus": 1, "steps": 1,
+            "warmup": args.warmup, "ms_per_step": ms, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64/f32 operator and step, f64 reductions", "data": "synthetic",
+            "config": {"workload": "fista_warp192", "image": list(shape), "coils": 0,
+                       "phases": 1, "max_disp_vox": 6.0, "iterations": FISTA_ITERS,
+                       "levels": FISTA_LEVELS, "lambda": lam, "L": L, "graph_chunk": 32,
+                       "l2": "step kernel moves 340 MB per launch (> L2); no flush"},
+            "ms_per_iteration": ms / FISTA_ITERS,
+            "split_ms_per_iteration": {"normal": round(normal_ms, 4), "fista_step": round(step_ms, 4)},
+            "roofline": {"kernel": "fista_step", "bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs",
+                         "alg_bytes_per_launch": step_bytes, "ms_per_launch": step_ms,
+                         "traffic": ncu_traffic("fista", "fista_warp192")},
+            "gpu_launches": int(own),
+            "rel_error": {"fista": err, "naive_minus_d": err_naive},
+            "last_rel_change": hist[-1], "clocks": clk}
+    plan.close()
+    return line
+
+
+def fista_oracle_cost(seed=0):
+    """Seconds of one oracle FISTA iteration on the 128^3 workload: the
+    modelled E apply (oracle_cost) plus the oracle's proximal step (Haar
+    transform, threshold, inverse) timed in full."""
+    import numpy as np
+
+    import synth
+    from oracle import fista as OF
+
+    w = synth.workload("sense128")
+    e, desc = oracle_cost(w, seed=seed)
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(w["spec"].shape) + 1j * rng.standard_normal(w["spec"].shape)
+    t = time.perf_counter()
+    OF.prox_wavelet_l1(v, 0.1, FISTA_LEVELS)
+    t_prox = time.perf_counter() - t
+    return e + t_prox, desc + f"; plus the FP64 Haar proximal step timed in full ({t_prox:.2f} s)"
+
+
 def run_sweep256(args):
     """Precision sweep on the 256^3, 32-coil, 8-phase workload (4 M samples per
     phase): for FP32, BF16 storage and compensated FP32 spreading, E applies/s
@@ -715,7 +919,8 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
-    special = {"precond128": run_precond, "cg192": run_cg192, "sweep256": run_sweep256}
+    special = {"precond128": run_precond, "cg192": run_cg192, "sweep256": run_sweep256,
+               "fista128": run_fista128, "fista_warp192": run_fista_warp192}
     if args.workload in special and args.impl == "ours":
         if int(os.environ.get("RANK", "0")) == 0:
             print(json.dumps(special[args.workload](args)), flush=True)
@@ -729,29 +934,35 @@ def main():
         # the oracle on the host cores; rank 0 only
         if rank != 0:
             return
-        if args.workload == "precond128":
+        if args.workload in ("precond128", "fista_warp192"):
             print(json.dumps({"impl": "reference", "unavailable":
-                              "the learned-preconditioner workload has no CPU reference arm"}))
+                              f"the {args.workload} workload has no CPU reference arm"}))
             return
         import synth
-        w = synth.workload(args.workload)
+        metric, unit = METRIC, UNIT
+        if args.workload == "fista128":
+            cost = fista_oracle_cost
+            metric, unit = "wavelet-FISTA iterations/s", "iterations/s"
+        else:
+            w = synth.workload(args.workload)
+            cost = lambda seed: oracle_cost(w, seed=seed)  # noqa: E731
         for _ in range(min(args.warmup, 1)):
-            oracle_cost(w, seed=99)
+            cost(99)
         vals = []
         desc = ""
         for k in range(args.steps):
-            e, desc = oracle_cost(w, seed=k)
+            e, desc = cost(k)
             vals.append(e)
         e_s = statistics.mean(vals)
         v = 1.0 / e_s
-        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+        line = {"impl": "reference", "metric": metric, "value": v, "unit": unit,
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": e_s * 1000.0, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": args.workload},
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle",
                                  "sample": desc},
-                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return

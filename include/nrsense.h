@@ -398,6 +398,69 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t plan, int32_t reps, nrsense_
 nrsense_status nrsense_plan_set_tuning(nrsense_plan_t plan, const nrsense_tuning* tuning_host);
 
 /*
+ * Wavelet-FISTA (reconstruction optimisation equation; wavelet-FISTA as in
+ * the in-vivo study and Appendix 1).  The problem
+ *     minimise  ||y - A x||_2^2 + lambda ||W x||_1,   A = [A_0; ...; A_{P-1}]
+ * (without coils A = [T_0; ...; T_{P-1}], the warp-only inversion of Appendix
+ * 1) is solved by Beck and Teboulle's constant-step FISTA:
+ *     x_k = W^H soft(W (z_k - (2/L)(E0 z_k - b)), lambda / L),
+ *     z_{k+1} = x_k + ((t_k - 1) / t_{k+1}) (x_k - x_{k-1}),
+ *     t_1 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,  z_1 = x_0,
+ * E0 = sum_j A_j^H A_j, b = sum_j A_j^H y_j, L >= 2 lambda_max(E0) (the
+ * Lipschitz constant of the gradient of ||y - A x||^2).  W is the orthonormal
+ * separable 3D Haar transform with `levels` levels (0 .. 4; 0 = identity)
+ * applied to real and imaginary parts; every image axis must be divisible by
+ * 2^levels (ERR_ARG otherwise).  soft(c, tau) = c max(0, 1 - tau / |c|) on
+ * every coefficient, the coarsest approximation included.
+ *
+ * nrsense_wavelet_forward - c = W x in the Mallat layout: level 1 details
+ *   fill the seven high-pass octants of the volume, level 2 details the
+ *   octants of the low-pass corner, and so on; the approximation sits in the
+ *   corner (n0, n1, n2) / 2^levels.  n_host: image shape (host, 3 values, each
+ *   >= 1).  x_dev, c_dev: (n0, n1, n2) complex device arrays; they must not
+ *   alias (ERR_ARG).
+ * nrsense_wavelet_inverse - x = W^H c (c in the Mallat layout); no aliasing.
+ * nrsense_wavelet_shrink  - u = W^H soft(W v, tau), the proximal map of
+ *   tau ||W .||_1; tau >= 0; u_dev may equal v_dev (in place).
+ *   All three are stream-ordered and need no plan.
+ *
+ * nrsense_normal_max_eig - power iteration on E0 (the plan's normal operator
+ *   with lambda = 0): v <- v / |v|, then `iters` times w = E0 v,
+ *   q = Re<v, w>, v <- w / |w|.  v_dev (plan image shape, device): the start
+ *   vector on entry (caller-chosen, e.g. random), the last normalised iterate
+ *   on exit.  *eig_host receives the last q (a lower bound of lambda_max that
+ *   converges to it).  Synchronises the call's stream.
+ *
+ * nrsense_solve_fista - `maxit` FISTA iterations (0 .. 2^20).
+ *   y_dev      data, layout of nrsense_apply_forward's output (device).
+ *   lambda     L1 weight (>= 0).
+ *   lipschitz  L (> 0); a value below 2 lambda_max(E0) may diverge.
+ *   flags      NRSENSE_CG_X0: x_dev holds x_0 (else x_0 = 0);
+ *              NRSENSE_CG_GRAPH: iterations run as a captured CUDA graph of 32
+ *              iterations, replayed (captured once per plan, x_dev, levels,
+ *              lambda and L), the remainder eagerly.
+ *   x_dev      image (device): x_0 on entry with NRSENSE_CG_X0, x_maxit on exit.
+ *   hist_host  receives ||x_k - x_{k-1}|| / ||x_k|| for k = 1 .. maxit (maxit
+ *              doubles; may be NULL).
+ *   The first call allocates the plan's FISTA workspace (three image
+ *   vectors, an internal stream).  Vectors are FP32, reductions FP64; the
+ *   call synchronises its stream at exit.
+ */
+nrsense_status nrsense_wavelet_forward(const nrsense_c64* x_dev, nrsense_c64* c_dev,
+                                       const int32_t* n_host, int32_t levels, void* stream);
+nrsense_status nrsense_wavelet_inverse(const nrsense_c64* c_dev, nrsense_c64* x_dev,
+                                       const int32_t* n_host, int32_t levels, void* stream);
+nrsense_status nrsense_wavelet_shrink(const nrsense_c64* v_dev, nrsense_c64* u_dev,
+                                      const int32_t* n_host, int32_t levels, double tau,
+                                      void* stream);
+nrsense_status nrsense_normal_max_eig(nrsense_plan_t plan, nrsense_c64* v_dev, int32_t iters,
+                                      double* eig_host, void* stream);
+nrsense_status nrsense_solve_fista(nrsense_plan_t plan, const nrsense_c64* y_dev, double lambda,
+                                   int32_t levels, double lipschitz, int32_t maxit,
+                                   uint32_t flags, nrsense_c64* x_dev, double* hist_host,
+                                   void* stream);
+
+/*
  * nrsense_device_status - read (and with clear != 0, reset) the plan's
  * latched device status word; synchronises `stream`.  *out_host receives
  * NRSENSE_OK or the first device-side error (ERR_BOUNDS, ERR_TIMEOUT).
@@ -414,7 +477,7 @@ nrsense_status nrsense_device_status(nrsense_plan_t plan, int32_t clear, int32_t
  * count_host[s]; *own_kernels_host receives the number of the library's own
  * CUDA kernels launched in the window (cuFFT kernels excluded).
  */
-#define NRSENSE_NUM_STAGES 14
+#define NRSENSE_NUM_STAGES 15
 #define NRSENSE_STAGE_FFT_N          0  /* cuFFT, N^3 */
 #define NRSENSE_STAGE_FFT_G          1  /* cuFFT, G^3 single grid */
 #define NRSENSE_STAGE_FFT_GC         2  /* cuFFT, G^3 x C batched */
@@ -429,6 +492,7 @@ nrsense_status nrsense_device_status(nrsense_plan_t plan, int32_t clear, int32_t
 #define NRSENSE_STAGE_VECTOR        11  /* elementwise vector kernels */
 #define NRSENSE_STAGE_SOLVER        12  /* CG reductions and updates */
 #define NRSENSE_STAGE_CNN           13  /* preconditioner network inside flexible CG */
+#define NRSENSE_STAGE_FISTA         14  /* wavelet FISTA steps and power iteration */
 nrsense_status nrsense_profile_start(nrsense_plan_t plan, int32_t max_launches);
 nrsense_status nrsense_profile_stop(nrsense_plan_t plan, double* ms_host, int64_t* count_host,
                                     int64_t* own_kernels_host);

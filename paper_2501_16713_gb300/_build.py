@@ -31,6 +31,7 @@ SOURCES = [
     "solver.cu",
     "noalloc.cu",
     "cnn.cu",
+    "fista.cu",
 ]
 HEADERS = ["common.cuh", "plan_internal.h", "kb_host.h"]
 

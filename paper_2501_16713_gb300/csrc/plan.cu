@@ -604,6 +604,7 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
 
 void release(nrsense_plan_s* p) {
   cg_release(p);
+  fista_release(p);
   for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
   p->prof_events.clear();
   if (p->have_fft_n) cufftDestroy(p->fft_n);
@@ -721,7 +722,7 @@ const char* nrsense_stage_name(int32_t st) {
   static const char* names[NRSENSE_NUM_STAGES] = {
       "fft_n", "fft_g", "fft_gc", "deapod_pad", "interp_image", "spread_image", "crop_deapod",
       "coil_fanout_pad", "interp_kspace", "spread_kspace", "crop_coilsum", "vector", "solver",
-      "cnn"};
+      "cnn", "fista"};
   return (st >= 0 && st < NRSENSE_NUM_STAGES) ? names[st] : "unknown";
 }
 

@@ -44,6 +44,7 @@ struct PointSet {
 }  // namespace nrs
 
 struct nrsense_cg_ws;  // CG workspace (solver.cu)
+struct nrsense_fista_ws;  // FISTA workspace (fista.cu)
 struct nrsense_cnn_s;  // preconditioner network (cnn.cu)
 
 struct nrsense_plan_s {
@@ -119,6 +120,7 @@ struct nrsense_plan_s {
   long long launches_at_start = 0;
 
   nrsense_cg_ws* cg = nullptr;  // allocated by the first nrsense_solve_cg
+  nrsense_fista_ws* fista = nullptr;  // allocated by the first FISTA or power-iteration call
 };
 
 namespace nrs {
@@ -207,6 +209,8 @@ int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TileP
 int spread_coil_chunk(int C);
 // free the CG workspace of a plan (solver.cu)
 void cg_release(nrsense_plan_s* p);
+// free the FISTA workspace of a plan (fista.cu)
+void fista_release(nrsense_plan_s* p);
 // tile edge of a point set: 16 for the single-channel W=4 spread (image
 // space) on grids of at least 16 + W - 1 points per axis, 8 otherwise
 int spread_tile_edge(int W, int C, int gmin);

@@ -107,10 +107,18 @@ _SIGS = {
     "nrsense_cnn_adam_step": [_VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, ctypes.c_uint32, _VP],
     "nrsense_cnn_launches": [_VP, ctypes.POINTER(ctypes.c_int64)],
+    "nrsense_wavelet_forward": [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _VP],
+    "nrsense_wavelet_inverse": [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _VP],
+    "nrsense_wavelet_shrink": [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                               ctypes.c_double, _VP],
+    "nrsense_normal_max_eig": [_VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _VP],
+    "nrsense_solve_fista": [_VP, _VP, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
+                            ctypes.c_int32, ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_double),
+                            _VP],
 }
 CG_X0 = 1
 CG_GRAPH = 2
-NUM_STAGES = 14
+NUM_STAGES = 15
 _STRING_RESULT = ("nrsense_status_string", "nrsense_stage_name")
 _INT64_RESULT = ("nrsense_cnn_num_params",)
 CNN_CHANNELS = (2, 16, 16, 16, 16, 2)
@@ -189,6 +197,40 @@ def dot_noalloc(x, y, out=None, stream=None):
     _check(lib.nrsense_dot_noalloc(_ptr(x), _ptr(y), int(x.numel()), _ptr(out), _stream(stream)),
            "nrsense_dot_noalloc")
     return out
+
+
+
+def _wavelet(fn, where, a, levels, out, tau=None, stream=None):
+    import torch
+    lib = load()
+    _need(a, torch.complex64, None, "input")
+    if a.dim() != 3:
+        raise ValueError("input must be a 3D image")
+    if out is None:
+        out = torch.empty_like(a)
+    _need(out, torch.complex64, tuple(a.shape), "out")
+    n = (ctypes.c_int32 * 3)(*a.shape)
+    args = [_ptr(a), _ptr(out), n, int(levels)] + ([float(tau)] if tau is not None else [])
+    _check(getattr(lib, fn)(*args, _stream(stream)), where)
+    return out
+
+
+def wavelet_forward(x, levels, out=None, stream=None):
+    """W x: orthonormal 3D Haar pyramid with `levels` levels, Mallat layout."""
+    return _wavelet("nrsense_wavelet_forward", "nrsense_wavelet_forward", x, levels, out,
+                    stream=stream)
+
+
+def wavelet_inverse(c, levels, out=None, stream=None):
+    """W^H c for Mallat-layout coefficients c."""
+    return _wavelet("nrsense_wavelet_inverse", "nrsense_wavelet_inverse", c, levels, out,
+                    stream=stream)
+
+
+def wavelet_shrink(v, tau, levels, out=None, stream=None):
+    """W^H soft(W v, tau): the proximal map of tau ||W .||_1 (out may be v)."""
+    return _wavelet("nrsense_wavelet_shrink", "nrsense_wavelet_shrink", v, levels, out, tau,
+                    stream=stream)
 
 
 class Plan:
@@ -483,6 +525,43 @@ class Plan:
                 json.dump(store, f, indent=1)
             os.replace(tmp, cache)
         return dict(res, cached=False)
+
+    def max_eig(self, v0, iters=30, stream=None):
+        """Power iteration on sum_j A_j^H A_j from v0 (overwritten with the
+        last normalised iterate).  Returns (Rayleigh quotient, v)."""
+        import torch
+        _need(v0, torch.complex64, self.shape, "v0")
+        e = ctypes.c_double()
+        _check(self.lib.nrsense_normal_max_eig(self._h, _ptr(v0), int(iters), ctypes.byref(e),
+                                               _stream(stream)), "nrsense_normal_max_eig")
+        return e.value, v0
+
+    def lipschitz(self, iters=30, seed=0, margin=1.02, stream=None):
+        """L = 2 margin lambda_max(sum_j A_j^H A_j), lambda_max by power
+        iteration from a seeded random start (the FISTA step bound)."""
+        import torch
+        g = torch.Generator(device="cuda").manual_seed(int(seed))
+        v = torch.randn(self.shape, dtype=torch.complex64, device="cuda", generator=g)
+        lam_max, _ = self.max_eig(v, iters, stream=stream)
+        return 2.0 * margin * lam_max
+
+    def solve_fista(self, y, lam, levels=3, L=None, maxit=400, x0=None, graph=True, stream=None,
+                    out=None):
+        """Wavelet-FISTA on ||y - A x||^2 + lam ||W x||_1 (W: orthonormal 3D
+        Haar with `levels` levels).  L: step bound (>= 2 lambda_max of the
+        normal operator; estimated with lipschitz() when omitted).
+        Returns (x, history of ||x_k - x_{k-1}|| / ||x_k||, L)."""
+        import torch
+        _need(y, torch.complex64, self.forward_shape(), "y")
+        x = self._x_for(x0, out)
+        if L is None:
+            L = self.lipschitz(stream=stream)
+        hist = (ctypes.c_double * max(int(maxit), 1))()
+        flags = (CG_X0 if x0 is not None else 0) | (CG_GRAPH if graph else 0)
+        _check(self.lib.nrsense_solve_fista(self._h, _ptr(y), float(lam), int(levels), float(L),
+                                            int(maxit), flags, _ptr(x), hist, _stream(stream)),
+               "nrsense_solve_fista")
+        return x, list(hist[: int(maxit)]), float(L)
 
     def phase_slice(self, y, j):
         """Rows of phase j in a stacked (sum M_j, C) k-space array."""
