@@ -461,6 +461,65 @@ nrsense_status nrsense_solve_fista(nrsense_plan_t plan, const nrsense_c64* y_dev
                                    void* stream);
 
 /*
+ * Motion capture for segmented acquisitions (section "Motion Capturing for
+ * Segmented Data Acquisitions"; phase binning in "Nonrigid Respiratory Motion
+ * Correction").  A heartbeat's low-resolution iNAV is the gridding
+ * reconstruction of its density-corrected data; translations come from
+ * correlations with a reference iNAV and are removed by linear phase shifts
+ * of the k-space data; k-means on the translations gives the respiratory
+ * phases, the least-variance cluster being the reference.
+ *
+ * nrsense_dcf - Pipe-Menon density compensation of phase `phase`'s samples:
+ *   w = 1, then `iters` times w <- w / (B P w), P the k-space spread of w onto
+ *   the oversampled grid and B the interpolation back to the samples, both
+ *   with the plan's gridding kernel (no FFT).  w_dev: M_phase floats (device,
+ *   overwritten).  Needs n_coils >= 1 and FP32 grids (ERR_STATE otherwise);
+ *   0 <= iters <= 10000.  Stream-ordered; uses the plan's k-space grid
+ *   buffers (so it must not overlap other calls on the plan).
+ * nrsense_apply_adjoint_weighted - x = sum_j A_j^H (w . y_j): the adjoint of
+ *   nrsense_apply_adjoint with every row (sample) of y scaled by w (one float
+ *   per sample, shared by the coils; rows as y).  The first call allocates a
+ *   copy of y's size in the plan.  Needs n_coils >= 1.
+ * nrsense_translation_xcorr - for b < count: c_b[t] = sum_n |ref[n]| |img_b[n + t]|
+ *   (circular), t_b = argmax (first in C order on ties) refined per axis by
+ *   the vertex of the parabola through c at t - 1, t, t + 1 (kept when that
+ *   parabola is not concave) and wrapped to (-n/2, n/2]; img_b[n] = ref[n - t]
+ *   gives t_b = t.  ref_dev: (n0, n1, n2) complex; imgs_dev: count images of
+ *   that shape, consecutive (device).  shifts_host: count x 3 doubles.  FP32
+ *   magnitudes and cuFFT real transforms; allocates its buffers and cuFFT
+ *   plans per call and synchronises the stream.  Each n >= 2, n0 n1 n2 <= 2^28.
+ * nrsense_phase_ramp - y[r][c] *= exp(+i omega_r . t_s) for every row r of
+ *   segment s, rows seg_off[s] <= r < seg_off[s + 1] (undoes a translation of
+ *   the image by +t_s).  coords_dev: rows_total x 3 float radians; y_dev:
+ *   rows_total x n_coils complex, in place (device).  seg_off_host: nseg + 1
+ *   non-decreasing int64 within [0, rows_total] (ERR_ARG otherwise);
+ *   shifts_host: nseg x 3 finite doubles (voxels).  Synchronises the stream.
+ * nrsense_kmeans - k-means (Lloyd) of n points in 3D (host memory, n x 3
+ *   doubles): start from the points at the positions (j + 1/2) n / k of the
+ *   order along the first principal axis (sign: largest-magnitude entry
+ *   positive; stable order), then assign each point to the nearest centre
+ *   (ties to the lower index) and move each centre to its members' mean (an
+ *   empty cluster keeps its centre) until the assignment repeats or max_iter
+ *   assignments.  labels_host: n int32; centres_host: k x 3; inertia_host,
+ *   iters_host, reference_host (the cluster of least mean squared distance to
+ *   its centre) may be NULL.  Host only; 1 <= k <= n.
+ */
+nrsense_status nrsense_dcf(nrsense_plan_t plan, int32_t phase, int32_t iters, float* w_dev,
+                           void* stream);
+nrsense_status nrsense_apply_adjoint_weighted(nrsense_plan_t plan, const nrsense_c64* y_dev,
+                                              const float* w_dev, nrsense_c64* x_dev,
+                                              void* stream);
+nrsense_status nrsense_translation_xcorr(const nrsense_c64* ref_dev, const nrsense_c64* imgs_dev,
+                                         const int32_t* n_host, int32_t count,
+                                         double* shifts_host, void* stream);
+nrsense_status nrsense_phase_ramp(const float* coords_dev, nrsense_c64* y_dev, int64_t rows_total,
+                                  int32_t n_coils, int32_t nseg, const int64_t* seg_off_host,
+                                  const double* shifts_host, void* stream);
+nrsense_status nrsense_kmeans(const double* points_host, int64_t n, int32_t k, int32_t max_iter,
+                              int32_t* labels_host, double* centres_host, double* inertia_host,
+                              int32_t* iters_host, int32_t* reference_host);
+
+/*
  * nrsense_device_status - read (and with clear != 0, reset) the plan's
  * latched device status word; synchronises `stream`.  *out_host receives
  * NRSENSE_OK or the first device-side error (ERR_BOUNDS, ERR_TIMEOUT).

@@ -12,7 +12,8 @@ Plan does, and raises if the library has not been built.
 """
 
 from .nrsense import (Cnn, Plan, NrsenseError, load, exported_symbols,  # noqa: F401
-                      wavelet_forward, wavelet_inverse, wavelet_shrink)
+                      wavelet_forward, wavelet_inverse, wavelet_shrink, translation_xcorr,
+                      phase_ramp, kmeans)
 
 
 def build(verbose: bool = False, force: bool = False) -> str:

@@ -32,6 +32,7 @@ SOURCES = [
     "noalloc.cu",
     "cnn.cu",
     "fista.cu",
+    "motion.cu",
 ]
 HEADERS = ["common.cuh", "plan_internal.h", "kb_host.h"]
 

@@ -216,6 +216,12 @@ nrsense_status sense_chunk_adjoint(nrsense_plan_s* p, int j0, int j1, const nrse
 
 }  // namespace
 
+namespace nrs {
+PhaseTable kspace_phase_table(const nrsense_plan_s* p, int phase, bool spread) {
+  return kspace_table(p, phase, phase + 1, spread, p->off[phase]);
+}
+}  // namespace nrs
+
 extern "C" {
 
 nrsense_status nrsense_warp_forward(nrsense_plan_t p, const nrsense_c64* x, nrsense_c64* m,

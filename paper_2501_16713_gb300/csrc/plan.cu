@@ -605,6 +605,7 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
 void release(nrsense_plan_s* p) {
   cg_release(p);
   fista_release(p);
+  motion_release(p);
   for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
   p->prof_events.clear();
   if (p->have_fft_n) cufftDestroy(p->fft_n);

@@ -45,6 +45,7 @@ struct PointSet {
 
 struct nrsense_cg_ws;  // CG workspace (solver.cu)
 struct nrsense_fista_ws;  // FISTA workspace (fista.cu)
+struct nrsense_motion_ws;  // density compensation / weighted adjoint workspace (motion.cu)
 struct nrsense_cnn_s;  // preconditioner network (cnn.cu)
 
 struct nrsense_plan_s {
@@ -121,6 +122,7 @@ struct nrsense_plan_s {
 
   nrsense_cg_ws* cg = nullptr;  // allocated by the first nrsense_solve_cg
   nrsense_fista_ws* fista = nullptr;  // allocated by the first FISTA or power-iteration call
+  nrsense_motion_ws* motion = nullptr;  // allocated by the first DCF or weighted-adjoint call
 };
 
 namespace nrs {
@@ -211,6 +213,11 @@ int spread_coil_chunk(int C);
 void cg_release(nrsense_plan_s* p);
 // free the FISTA workspace of a plan (fista.cu)
 void fista_release(nrsense_plan_s* p);
+// free the motion-capture workspace of a plan (motion.cu)
+void motion_release(nrsense_plan_s* p);
+// point table of one phase of the k-space point sets, rows relative to the
+// phase's first sample (apply.cu)
+PhaseTable kspace_phase_table(const nrsense_plan_s* p, int phase, bool spread);
 // tile edge of a point set: 16 for the single-channel W=4 spread (image
 // space) on grids of at least 16 + W - 1 points per axis, 8 otherwise
 int spread_tile_edge(int W, int C, int gmin);

@@ -112,6 +112,16 @@ _SIGS = {
     "nrsense_wavelet_shrink": [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                ctypes.c_double, _VP],
     "nrsense_normal_max_eig": [_VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _VP],
+    "nrsense_dcf": [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP],
+    "nrsense_apply_adjoint_weighted": [_VP, _VP, _VP, _VP, _VP],
+    "nrsense_translation_xcorr": [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                  ctypes.POINTER(ctypes.c_double), _VP],
+    "nrsense_phase_ramp": [_VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), _VP],
+    "nrsense_kmeans": [ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int32,
+                       ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "nrsense_solve_fista": [_VP, _VP, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
                             ctypes.c_int32, ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_double),
                             _VP],
@@ -232,6 +242,67 @@ def wavelet_shrink(v, tau, levels, out=None, stream=None):
     return _wavelet("nrsense_wavelet_shrink", "nrsense_wavelet_shrink", v, levels, out, tau,
                     stream=stream)
 
+
+
+def translation_xcorr(ref, imgs, stream=None):
+    """Translations of each image against ref by magnitude cross-correlation
+    (nrsense_translation_xcorr).  ref: (n0, n1, n2), imgs: (count, n0, n1, n2)
+    complex64 CUDA tensors.  Returns a (count, 3) float64 numpy array."""
+    import torch
+    lib = load()
+    _need(ref, torch.complex64, None, "ref")
+    if ref.dim() != 3:
+        raise ValueError("ref must be a 3D image")
+    _need(imgs, torch.complex64, None, "imgs")
+    if imgs.dim() != 4 or tuple(imgs.shape[1:]) != tuple(ref.shape):
+        raise ValueError("imgs must be (count,) + ref.shape")
+    count = int(imgs.shape[0])
+    out = np.zeros((count, 3), dtype=np.float64)
+    n = (ctypes.c_int32 * 3)(*ref.shape)
+    _check(lib.nrsense_translation_xcorr(
+        _ptr(ref), _ptr(imgs), n, count,
+        out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)),
+        "nrsense_translation_xcorr")
+    return out
+
+
+def phase_ramp(coords, y, seg_off, shifts, stream=None):
+    """In place: y[r] *= exp(+i omega_r . t_s) for the rows of segment s
+    (nrsense_phase_ramp).  coords: (rows, 3) float32, y: (rows, C) complex64
+    CUDA tensors; seg_off: nseg + 1 row offsets; shifts: (nseg, 3) voxels."""
+    import torch
+    lib = load()
+    _need(coords, torch.float32, None, "coords")
+    _need(y, torch.complex64, None, "y")
+    if y.dim() != 2 or coords.dim() != 2 or coords.shape[1] != 3 or coords.shape[0] != y.shape[0]:
+        raise ValueError("coords must be (rows, 3) and y (rows, C)")
+    off = np.ascontiguousarray(np.asarray(seg_off, dtype=np.int64))
+    sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64).reshape(-1, 3))
+    if off.size != sh.shape[0] + 1 or off[-1] > y.shape[0]:
+        raise ValueError("seg_off must hold nseg + 1 offsets within the rows")
+    _check(lib.nrsense_phase_ramp(
+        _ptr(coords), _ptr(y), int(y.shape[0]), int(y.shape[1]), int(sh.shape[0]),
+        off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)),
+        "nrsense_phase_ramp")
+    return y
+
+
+def kmeans(points, k, max_iter=100):
+    """k-means of (n, 3) points (nrsense_kmeans, host).  Returns (labels,
+    centres, inertia, iterations, reference cluster)."""
+    lib = load()
+    p = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 3))
+    n = p.shape[0]
+    labels = np.zeros(n, dtype=np.int32)
+    centres = np.zeros((max(int(k), 1), 3), dtype=np.float64)
+    inertia, iters, ref = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.nrsense_kmeans(p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n, int(k),
+                              int(max_iter), labels.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                              centres.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              ctypes.byref(inertia), ctypes.byref(iters), ctypes.byref(ref)),
+           "nrsense_kmeans")
+    return labels, centres, inertia.value, iters.value, ref.value
 
 class Plan:
     """Nonrigid SENSE operator A_j = G_j S T_j over P motion states.
@@ -525,6 +596,29 @@ class Plan:
                 json.dump(store, f, indent=1)
             os.replace(tmp, cache)
         return dict(res, cached=False)
+
+    def dcf(self, phase, iters=10, out=None, stream=None):
+        """Pipe-Menon density compensation weights of one phase's samples
+        (nrsense_dcf).  Returns a float32 CUDA tensor of M_phase values."""
+        import torch
+        m = int(self.counts[phase])
+        if out is None:
+            out = torch.empty(m, dtype=torch.float32, device="cuda")
+        _need(out, torch.float32, (m,), "out")
+        _check(self.lib.nrsense_dcf(self._h, int(phase), int(iters), _ptr(out), _stream(stream)),
+               "nrsense_dcf")
+        return out
+
+    def adjoint_weighted(self, y, w, out=None, stream=None):
+        """sum_j A_j^H (w . y_j) with one weight per sample (rows of y)."""
+        import torch
+        _need(y, torch.complex64, self.forward_shape(), "y")
+        _need(w, torch.float32, (int(y.shape[0]),), "w")
+        out = self._img() if out is None else _need(out, torch.complex64, self.shape, "out")
+        _check(self.lib.nrsense_apply_adjoint_weighted(self._h, _ptr(y), _ptr(w), _ptr(out),
+                                                       _stream(stream)),
+               "nrsense_apply_adjoint_weighted")
+        return out
 
     def max_eig(self, v0, iters=30, stream=None):
         """Power iteration on sum_j A_j^H A_j from v0 (overwritten with the
