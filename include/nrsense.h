@@ -369,9 +369,10 @@ nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* 
  * phase chunk) and internal buffers, the k-space spreading kernel with
  * register accumulation (a CTA per tile or per tile plane) and with
  * shared-memory accumulation, the image-space spreading kernel with a CTA
- * per tile or per plane pair, and the k-space
+ * per tile or per plane pair, the k-space
  * interpolation with 8 and with 4 coils per CTA, its tile halos staged per
- * value or by one tensor-memory-accelerator copy (reps launches each, after
+ * value or by one tensor-memory-accelerator copy, and the coil-grid
+ * transforms (cuFFT or the own pruned passes) (reps launches each, after
  * one warm-up launch, CUDA events on `stream`; synchronises), keeps the
  * faster of each in the plan and reports times and choices in *out (host).
  * The compensated precision always uses shared-memory accumulation for k
@@ -392,6 +393,11 @@ typedef struct {
   double  interp_tma_ms[2];/* measured, TMA staging: 8 coils, 4 coils (-1: not available) */
   int32_t spread_image_warp;   /* image-space spread: 0 CTA per tile, 1 CTA per plane pair */
   double  spread_image_ms[2];  /* measured: CTA per tile, CTA per plane pair */
+  int32_t fft_pruned;          /* 1: own pruned coil-grid transforms with the coil fan-out and
+                                  combination fused (sigma 2, power-of-two grid sizes 32..256,
+                                  FP32 grids); 0: cuFFT plus the fan-out / combination kernels */
+  double  fft_ms[2];           /* measured forward + adjoint of the first phase chunk:
+                                  cuFFT path, pruned path (-1: not available) */
 } nrsense_tuning;
 nrsense_status nrsense_plan_autotune(nrsense_plan_t plan, int32_t reps, nrsense_tuning* out_host,
                                      void* stream);
@@ -536,7 +542,7 @@ nrsense_status nrsense_device_status(nrsense_plan_t plan, int32_t clear, int32_t
  * count_host[s]; *own_kernels_host receives the number of the library's own
  * CUDA kernels launched in the window (cuFFT kernels excluded).
  */
-#define NRSENSE_NUM_STAGES 15
+#define NRSENSE_NUM_STAGES 16
 #define NRSENSE_STAGE_FFT_N          0  /* cuFFT, N^3 */
 #define NRSENSE_STAGE_FFT_G          1  /* cuFFT, G^3 single grid */
 #define NRSENSE_STAGE_FFT_GC         2  /* cuFFT, G^3 x C batched */
@@ -552,6 +558,7 @@ nrsense_status nrsense_device_status(nrsense_plan_t plan, int32_t clear, int32_t
 #define NRSENSE_STAGE_SOLVER        12  /* CG reductions and updates */
 #define NRSENSE_STAGE_CNN           13  /* preconditioner network inside flexible CG */
 #define NRSENSE_STAGE_FISTA         14  /* wavelet FISTA steps and power iteration */
+#define NRSENSE_STAGE_FFT_PRUNED    15  /* own pruned coil-grid transforms, K5 and K8 fused */
 nrsense_status nrsense_profile_start(nrsense_plan_t plan, int32_t max_launches);
 nrsense_status nrsense_profile_stop(nrsense_plan_t plan, double* ms_host, int64_t* count_host,
                                     int64_t* own_kernels_host);

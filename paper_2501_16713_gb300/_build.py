@@ -33,6 +33,7 @@ SOURCES = [
     "cnn.cu",
     "fista.cu",
     "motion.cu",
+    "fft_pruned.cu",
 ]
 HEADERS = ["common.cuh", "plan_internal.h", "kb_host.h"]
 

@@ -183,16 +183,36 @@ nrsense_status warp_adjoint(nrsense_plan_s* p, const nrsense_c64* m, nrsense_c64
   return fft(p, NRSENSE_STAGE_FFT_N, p->fft_n, s, x, x, CUFFT_INVERSE);
 }
 
+// The cuFFT forward path reads the zero padding of b_xpad and b_xmid; the
+// pruned transforms keep their intermediates there, so re-zero after them.
+nrsense_status clean_pads(nrsense_plan_s* p, cudaStream_t s) {
+  if (!p->pad_dirty) return NRSENSE_OK;
+  const size_t cgb = size_t(p->geo.ngrid) * p->C * p->phase_chunk * (p->grid_bf16 ? 4 : 8);
+  if (cudaMemsetAsync(p->b_xpad, 0, cgb, s) != cudaSuccess ||
+      cudaMemsetAsync(p->b_xmid, 0, cgb, s) != cudaSuccess)
+    return NRSENSE_ERR_CUDA;
+  p->pad_dirty = false;
+  return NRSENSE_OK;
+}
+
 // y rows of phases [j0, j1) (row off_j - row_base of y) = G_j S m_j, where m
 // holds the chunk's warped images consecutively.
 nrsense_status sense_chunk_forward(nrsense_plan_s* p, int j0, int j1, const nrsense_c64* m,
                                    nrsense_c64* y, long long row_base, cudaStream_t s) {
   const Geo& g = p->geo;
   const int nph = j1 - j0;
-  STAGE(COIL_FANOUT, launch_coil_fanout_pad(g, p->C, nph, p->deapod, p->smaps, m, p->b_xpad,
-                                            p->grid_bf16, s));
-  NRS_TRY(launched());
-  NRS_TRY(fft_gc(p, nph, p->b_xpad, p->b_xwork, CUFFT_FORWARD, s));
+  if (p->fft_pruned) {
+    STAGE(FFT_PRUNED, launch_pruned_forward(g, p->C, nph, p->deapod, p->smaps, m, p->b_xpad,
+                                            p->b_xmid, p->b_xwork, s));
+    p->pad_dirty = true;
+    NRS_TRY(launched());
+  } else {
+    NRS_TRY(clean_pads(p, s));
+    STAGE(COIL_FANOUT, launch_coil_fanout_pad(g, p->C, nph, p->deapod, p->smaps, m, p->b_xpad,
+                                              p->grid_bf16, s));
+    NRS_TRY(launched());
+    NRS_TRY(fft_gc(p, nph, p->b_xpad, p->b_xwork, CUFFT_FORWARD, s));
+  }
   const PhaseTable t = kspace_table(p, j0, j1, /*spread=*/false, row_base);
   STAGE(INTERP_KSPACE, launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
                                             p->grid_bf16, y, p->interp_coils, interp_tmap(p), p->d_status, s));
@@ -208,6 +228,12 @@ nrsense_status sense_chunk_adjoint(nrsense_plan_s* p, int j0, int j1, const nrse
   STAGE(SPREAD_KSPACE, launch_spread(g, p->W, p->kc, p->C, p->ktiles, t, y, p->b_xspread,
                                      p->grid_bf16, p->comp_spread, p->spread_variant, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
+  if (p->fft_pruned) {
+    STAGE(FFT_PRUNED, launch_pruned_inverse(g, p->C, nph, p->deapod, p->smaps, p->b_xspread,
+                                            p->b_xmid, p->b_xpad, w, s));
+    p->pad_dirty = true;
+    return launched();
+  }
   NRS_TRY(fft_gc(p, nph, p->b_xspread, p->b_xwork, CUFFT_INVERSE, s));
   STAGE(CROP_COILSUM, launch_crop_coilsum(g, p->C, nph, p->deapod, p->smaps, p->b_xwork,
                                           p->grid_bf16, w, s));
@@ -242,6 +268,7 @@ nrsense_status nrsense_kspace_forward(nrsense_plan_t p, int32_t phase, const nrs
   if (p->C == 0) return NRSENSE_ERR_STATE;
   if (phase < 0 || phase >= p->P) return NRSENSE_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  NRS_TRY(clean_pads(p, s));
   STAGE(COIL_FANOUT, launch_image_to_padded(p->geo, p->C, p->deapod, v, p->b_xpad, p->grid_bf16, s));
   NRS_TRY(launched());
   NRS_TRY(fft_gc(p, 1, p->b_xpad, p->b_xwork, CUFFT_FORWARD, s));
@@ -326,7 +353,10 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
   p->interp_coils = t->interp_coils;
   p->interp_tma = t->interp_tma == 1 && p->tma_ok;
   if (t->spread_image_warp != 0 && t->spread_image_warp != 1) return NRSENSE_ERR_ARG;
+  if (t->fft_pruned != 0 && t->fft_pruned != 1) return NRSENSE_ERR_ARG;
+  if (t->fft_pruned == 1 && !p->fft_pruned_ok) return NRSENSE_ERR_ARG;
   p->spread_image_variant = t->spread_image_warp ? kSpreadRegisterWarp : kSpreadShared;
+  p->fft_pruned = t->fft_pruned == 1;
   return NRSENSE_OK;
 }
 
@@ -340,6 +370,8 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
   out->interp_coils = p->interp_coils;
   out->interp_tma = p->interp_tma ? 1 : 0;
   out->spread_image_warp = p->spread_image_variant == kSpreadRegisterWarp ? 1 : 0;
+  out->fft_pruned = p->fft_pruned ? 1 : 0;
+  out->fft_ms[0] = out->fft_ms[1] = -1.0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Geo& g = p->geo;
   if (!p->identity_warp && p->ipts.tp.t0 == 16) {
@@ -418,6 +450,28 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
     }
   }
   p->interp_tma = saved_tma;
+  if (p->fft_pruned_ok) {
+    // coil-grid transforms: cuFFT with the K5 / K8 kernels vs the own pruned
+    // passes, timed as the first chunk's forward and adjoint (zero inputs: the
+    // same work, no growth over the repetitions)
+    const bool saved = p->fft_pruned;
+    if (cudaMemsetAsync(p->b_m, 0, size_t(j1) * g.nvox * sizeof(nrsense_c64), s) != cudaSuccess)
+      return NRSENSE_ERR_CUDA;
+    for (int k = 0; k < 2; ++k) {
+      p->fft_pruned = k == 1;
+      nrsense_status st = NRSENSE_OK;
+      out->fft_ms[k] = time_ms([&] {
+        if (st == NRSENSE_OK) st = sense_chunk_forward(p, 0, j1, p->b_m, p->b_y, 0, s);
+        if (st == NRSENSE_OK) st = sense_chunk_adjoint(p, 0, j1, p->b_y, 0, p->b_m, s);
+      });
+      if (st != NRSENSE_OK) {
+        p->fft_pruned = saved;
+        return st;
+      }
+    }
+    p->fft_pruned = out->fft_ms[1] >= 0.0 && out->fft_ms[1] < out->fft_ms[0];
+    out->fft_pruned = p->fft_pruned ? 1 : 0;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (cudaGetLastError() != cudaSuccess) return NRSENSE_ERR_CUDA;

@@ -571,6 +571,10 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     NRS_TRY(dev_alloc(p, &p->b_xspread, cgb));
     NRS_TRY(dev_alloc(p, &p->b_xmid, cgb));
     if (cudaMemsetAsync(p->b_xmid, 0, cgb, s) != cudaSuccess) return NRSENSE_ERR_CUDA;
+    // own pruned transforms where supported (chosen by default; the autotuner
+    // times both paths)
+    p->fft_pruned_ok = pruned_fft_supported(g, p->C, p->grid_bf16) && init_pruned_fft() == cudaSuccess;
+    p->fft_pruned = p->fft_pruned_ok;
     // tensor maps of the interpolation input (TMA-staged halos, W = 4)
     const long long slots = (long long)p->C * p->phase_chunk;
     p->tma_ok = p->W == 4 &&
@@ -723,7 +727,7 @@ const char* nrsense_stage_name(int32_t st) {
   static const char* names[NRSENSE_NUM_STAGES] = {
       "fft_n", "fft_g", "fft_gc", "deapod_pad", "interp_image", "spread_image", "crop_deapod",
       "coil_fanout_pad", "interp_kspace", "spread_kspace", "crop_coilsum", "vector", "solver",
-      "cnn", "fista"};
+      "cnn", "fista", "fft_pruned"};
   return (st >= 0 && st < NRSENSE_NUM_STAGES) ? names[st] : "unknown";
 }
 

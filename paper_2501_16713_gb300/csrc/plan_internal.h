@@ -120,6 +120,11 @@ struct nrsense_plan_s {
   long long launches = 0;                // own kernels launched (always counted)
   long long launches_at_start = 0;
 
+  // own pruned coil-grid transforms with the coil fan-out and combination fused
+  bool fft_pruned_ok = false;  // supported: sigma 2, power-of-two grids of 32..256, FP32 grids
+  bool fft_pruned = false;     // chosen (else cuFFT plus the K5 / K8 kernels)
+  bool pad_dirty = false;      // b_xpad / b_xmid hold the pruned transforms' intermediates
+
   nrsense_cg_ws* cg = nullptr;  // allocated by the first nrsense_solve_cg
   nrsense_fista_ws* fista = nullptr;  // allocated by the first FISTA or power-iteration call
   nrsense_motion_ws* motion = nullptr;  // allocated by the first DCF or weighted-adjoint call
@@ -209,6 +214,19 @@ int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TileP
                   bool comp, int variant, nrsense_c64* scratch, int32_t* status, cudaStream_t s);
 // coils handled by one spreading CTA
 int spread_coil_chunk(int C);
+// own pruned coil-grid transforms (fft_pruned.cu).  Forward: grid slots
+// jj * C + c of phases jj < nph = DFT3(S_c m_jj / C3 zero-padded), through the
+// intermediates t1 (slots x N0 x N1 x G2) and t2 (slots x N0 x G1 x G2).
+// Inverse: w_jj = C3^-1 sum_c conj(S_c) crop(IDFT3(grid slot jj * C + c)).
+// Each returns the number of kernels launched.
+bool pruned_fft_supported(const Geo& g, int C, bool bf16);
+cudaError_t init_pruned_fft();
+int launch_pruned_forward(const Geo& g, int C, int nph, const float* deapod,
+                          const nrsense_c64* smaps, const nrsense_c64* m, void* t1, void* t2,
+                          void* grid, cudaStream_t s);
+int launch_pruned_inverse(const Geo& g, int C, int nph, const float* deapod,
+                          const nrsense_c64* smaps, const void* grid, void* t2, void* t1,
+                          nrsense_c64* w, cudaStream_t s);
 // free the CG workspace of a plan (solver.cu)
 void cg_release(nrsense_plan_s* p);
 // free the FISTA workspace of a plan (fista.cu)

@@ -48,7 +48,8 @@ class Tuning(ctypes.Structure):
                 ("spread_ms", ctypes.c_double * 3), ("interp_ms", ctypes.c_double * 2),
                 ("interp_tma_ms", ctypes.c_double * 2),
                 ("spread_image_warp", ctypes.c_int32),
-                ("spread_image_ms", ctypes.c_double * 2)]
+                ("spread_image_ms", ctypes.c_double * 2),
+                ("fft_pruned", ctypes.c_int32), ("fft_ms", ctypes.c_double * 2)]
 
 
 class Info(ctypes.Structure):
@@ -128,7 +129,7 @@ _SIGS = {
 }
 CG_X0 = 1
 CG_GRAPH = 2
-NUM_STAGES = 15
+NUM_STAGES = 16
 _STRING_RESULT = ("nrsense_status_string", "nrsense_stage_name")
 _INT64_RESULT = ("nrsense_cnn_num_params",)
 CNN_CHANNELS = (2, 16, 16, 16, 16, 2)
@@ -578,6 +579,7 @@ class Plan:
             t.interp_coils = int(store[key]["interp_coils"])
             t.interp_tma = int(store[key].get("interp_tma", 0))
             t.spread_image_warp = int(store[key].get("spread_image_warp", 0))
+            t.fft_pruned = int(store[key].get("fft_pruned", 0))
             _check(self.lib.nrsense_plan_set_tuning(self._h, ctypes.byref(t)),
                    "nrsense_plan_set_tuning")
             return dict(store[key], cached=True)
@@ -588,7 +590,8 @@ class Plan:
                "interp_tma": t.interp_tma, "spread_ms": list(t.spread_ms),
                "interp_ms": list(t.interp_ms), "interp_tma_ms": list(t.interp_tma_ms),
                "spread_image_warp": t.spread_image_warp,
-               "spread_image_ms": list(t.spread_image_ms)}
+               "spread_image_ms": list(t.spread_image_ms),
+               "fft_pruned": t.fft_pruned, "fft_ms": list(t.fft_ms)}
         if cache:
             store[key] = res
             tmp = cache + ".tmp"

@@ -1,0 +1,118 @@
+"""Own pruned coil-grid transforms (fan-out and coil combination fused) vs
+the FP64 oracle and vs the cuFFT path.
+
+Shape 16 x 32 x 64 gives grids of 32, 64 and 128 points: every supported
+transform length but 256 in one plan (256 runs in the full-size tests and the
+benchmark).  Both paths must match the oracle within the FP32 operator bar
+and each other within 2e-6; switching between them must reproduce each
+path's values bit for bit (the cuFFT path needs the zero padding the pruned
+path overwrites); the per-coil stage call after a pruned application must
+equal a fresh plan's; an unsupported geometry refuses the pruned choice.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+from helpers import TOL_FP32, make_plan, rel_l2, to_dev
+from oracle import operators as O
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (16, 32, 64)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _set(plan, pruned):
+    from paper_2501_16713_gb300.nrsense import Tuning
+    t = Tuning()
+    t.spread_variant, t.interp_coils, t.interp_tma = 3, 8, 1
+    t.spread_image_warp, t.fft_pruned = 0, int(pruned)
+    return plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t))
+
+
+@pytest.fixture(scope="module")
+def case():
+    c = synth.small_case(SHAPE, 3, 2, [5000, 4200], seed=81, max_disp=1.5, rigid=0.5)
+    plan = make_plan(c, SHAPE)
+    yield c, plan
+    plan.close()
+
+
+def test_both_paths_match_oracle(case):
+    c, plan = case
+    geo = O.Geometry(SHAPE)
+    d64 = [d.astype(np.float64) for d in c["disp"]]
+    x = c["x"].astype(np.complex128)
+    ys_ref = O.stacked_forward(geo, x, d64, c["smaps"], c["coords"])
+    y_ref = np.concatenate(ys_ref)
+    xa_ref = O.stacked_adjoint(geo, ys_ref, d64, c["smaps"], c["coords"])
+    out = {}
+    for pruned in (0, 1):
+        assert _set(plan, pruned) == 0
+        y = plan.forward(to_dev(c["x"]))
+        xa = plan.adjoint(to_dev(y_ref.astype(np.complex64)))
+        e_f, e_a = rel_l2(y.cpu().numpy(), y_ref), rel_l2(xa.cpu().numpy(), xa_ref)
+        print(f"pruned={pruned}: forward rel L2 {e_f:.2e}, adjoint rel L2 {e_a:.2e}")
+        assert e_f < TOL_FP32 and e_a < TOL_FP32
+        out[pruned] = (y.cpu().numpy(), xa.cpu().numpy())
+    assert rel_l2(out[1][0], out[0][0]) < 2e-6
+    assert rel_l2(out[1][1], out[0][1]) < 2e-6
+    assert plan.device_status() == 0
+
+
+def test_switching_paths_is_reproducible(case):
+    import torch
+    c, plan = case
+    x = to_dev(c["x"])
+    res = {}
+    for pruned in (1, 0, 1, 0):
+        assert _set(plan, pruned) == 0
+        e = plan.normal(x, 0.5)
+        if pruned in res:
+            assert torch.equal(e, res[pruned]), pruned
+        else:
+            res[pruned] = e
+    assert rel_l2(res[1].cpu().numpy(), res[0].cpu().numpy()) < 2e-6
+
+
+def test_stage_call_after_pruned_application(case):
+    import torch
+    c, plan = case
+    rng = np.random.default_rng(82)
+    v = to_dev((rng.standard_normal((3,) + SHAPE) + 1j * rng.standard_normal((3,) + SHAPE))
+               .astype(np.complex64))
+    assert _set(plan, 1) == 0
+    plan.normal(to_dev(c["x"]), 0.0)           # leaves the intermediates in the pad buffers
+    y1 = plan.kspace_forward(0, v)
+    fresh = make_plan(c, SHAPE)
+    y2 = fresh.kspace_forward(0, v)
+    assert torch.equal(y1, y2)
+    fresh.close()
+
+
+def test_autotune_times_both_paths(case):
+    _, plan = case
+    res = plan.autotune(reps=2)
+    print(res["fft_ms"], res["fft_pruned"])
+    assert res["fft_ms"][0] > 0 and res["fft_ms"][1] > 0 and res["fft_pruned"] in (0, 1)
+
+
+def test_unsupported_geometry_refuses_pruned():
+    shape = (16, 16, 24)  # a 48-point grid
+    c = synth.small_case(shape, 2, 1, [1500], seed=83)
+    plan = make_plan(c, shape)
+    assert _set(plan, 1) == -1
+    res = plan.autotune(reps=1)
+    assert res["fft_pruned"] == 0 and res["fft_ms"] == [-1.0, -1.0]
+    plan.close()
