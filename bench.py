@@ -36,7 +36,7 @@ STAGE_KERNEL_SOURCE = {
     "interp_image": "kernels_image.cu", "spread_image": "kernels_spread.cu",
     "coil_fanout_pad": "kernels_kspace.cu", "crop_coilsum": "kernels_kspace.cu",
     "deapod_pad": "kernels_image.cu", "crop_deapod": "kernels_image.cu",
-    "vector": "kernels_image.cu", "fista": "fista.cu",
+    "vector": "kernels_image.cu", "fista": "fista.cu", "fft_pruned": "fft_pruned.cu",
 }
 FFT_STAGES = ("fft_n", "fft_g", "fft_gc")
 
@@ -52,7 +52,16 @@ def stage_bytes(info, shape, C, P, M):
     Ms = float(sum(M))
     k = 8.0 * C * rho * G3 * P + (12.0 + 8.0 * C) * Ms
     img = 8.0 * G3 + (12.0 + 8.0) * P * N3
+    # own pruned coil-grid transforms (sigma 2), per coil grid and E: forward
+    # reads S_c (and the phase image once per C grids), writes and re-reads
+    # T1 (N0 N1 G2) and T2 (N0 G1 G2), writes the grid; the adjoint mirrors it
+    G2 = float(info["grid"][2])
+    G1 = float(info["grid"][1])
+    t1 = 8.0 * shape[0] * shape[1] * G2
+    t2 = 8.0 * shape[0] * G1 * G2
+    per_grid = 2.0 * (8.0 * N3 + 8.0 * N3 / max(C, 1)) + 4.0 * t1 + 4.0 * t2 + 2.0 * 8.0 * G3
     return {
+        "fft_pruned": P * C * per_grid,
         "interp_kspace": k, "spread_kspace": k,
         "interp_image": img, "spread_image": img,
         "deapod_pad": 16.0 * N3, "crop_deapod": 16.0 * N3,
