@@ -286,8 +286,9 @@ __global__ void __launch_bounds__(kThreads) spread_coils_kernel(
 // streams its plane's range of the list with the same per-warp staging as
 // spread_coils_kernel; every lane then adds each staged point's contribution
 // to its own two points (zero weight outside the point's 4 x 4 footprint in
-// the plane), so nothing is read back from or written to shared memory per
-// update.  The result (and the order of every sum) is the same per grid value
+// the plane), one half-plane at a time so that points whose footprint misses
+// the half are skipped, and nothing is read back from or written to shared
+// memory per update.  The result (and the order of every sum) is the same per grid value
 // as for the shared-memory kernel: list order within the item.
 // WPC = 8: a CTA is a work item's tile, warp w its plane w.  WPC = 1: a CTA
 // is one warp, block b serves plane b % 8 of item b / 8, so a plane's warp
@@ -358,23 +359,25 @@ __global__ void __launch_bounds__(32 * WPC, WPC == 1 ? 24 : 3) spread_coils_reg_
           d.val[c] = (coil0 + c < C) ? __ldg(src + c) : make_float2(0.f, 0.f);
       }
       __syncwarp();
-      for (int p = 0; p < n; ++p) {
-        const CoilStage<CC>& d = st[p];
-        const int tx = x - d.r2, ty0 = yh - d.r1, ty1 = ty0 + 4;
-        const float wxv = (unsigned)tx < (unsigned)W ? d.wx[tx & (W - 1)] : 0.f;
-        const float w0 = (unsigned)ty0 < (unsigned)W ? d.wzy[ty0 & (W - 1)] * wxv : 0.f;
-        const float w1 = (unsigned)ty1 < (unsigned)W ? d.wzy[ty1 & (W - 1)] * wxv : 0.f;
+      // one pass per half-plane (rows 0-3: acc[0], rows 4-7: acc[1]); a point
+      // whose 4-row footprint (rows r1 .. r1 + 3) misses the half is skipped
+      // (a warp-uniform branch) -- it would only add zero-weight terms
 #pragma unroll
-        for (int c2 = 0; c2 < CC / 2; ++c2) {
-          const float4 v = reinterpret_cast<const float4*>(d.val)[c2];
-          acc[0][2 * c2].x = fmaf(w0, v.x, acc[0][2 * c2].x);
-          acc[0][2 * c2].y = fmaf(w0, v.y, acc[0][2 * c2].y);
-          acc[0][2 * c2 + 1].x = fmaf(w0, v.z, acc[0][2 * c2 + 1].x);
-          acc[0][2 * c2 + 1].y = fmaf(w0, v.w, acc[0][2 * c2 + 1].y);
-          acc[1][2 * c2].x = fmaf(w1, v.x, acc[1][2 * c2].x);
-          acc[1][2 * c2].y = fmaf(w1, v.y, acc[1][2 * c2].y);
-          acc[1][2 * c2 + 1].x = fmaf(w1, v.z, acc[1][2 * c2 + 1].x);
-          acc[1][2 * c2 + 1].y = fmaf(w1, v.w, acc[1][2 * c2 + 1].y);
+      for (int h = 0; h < 2; ++h) {
+        for (int p = 0; p < n; ++p) {
+          const CoilStage<CC>& d = st[p];
+          if (h == 0 ? d.r1 > 3 : d.r1 < 1) continue;
+          const int tx = x - d.r2, ty = yh + 4 * h - d.r1;
+          const float wxv = (unsigned)tx < (unsigned)W ? d.wx[tx & (W - 1)] : 0.f;
+          const float w = (unsigned)ty < (unsigned)W ? d.wzy[ty & (W - 1)] * wxv : 0.f;
+#pragma unroll
+          for (int c2 = 0; c2 < CC / 2; ++c2) {
+            const float4 v = reinterpret_cast<const float4*>(d.val)[c2];
+            acc[h][2 * c2].x = fmaf(w, v.x, acc[h][2 * c2].x);
+            acc[h][2 * c2].y = fmaf(w, v.y, acc[h][2 * c2].y);
+            acc[h][2 * c2 + 1].x = fmaf(w, v.z, acc[h][2 * c2 + 1].x);
+            acc[h][2 * c2 + 1].y = fmaf(w, v.w, acc[h][2 * c2 + 1].y);
+          }
         }
       }
       __syncwarp();
