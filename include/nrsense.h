@@ -367,8 +367,8 @@ nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* 
  * Autotuning of the launch choices of a plan (no counterpart in the paper).
  * nrsense_plan_autotune times, on the plan's own k-space point sets (first
  * phase chunk) and internal buffers, the k-space spreading kernel with
- * register accumulation (a CTA per tile or per tile plane) and with
- * shared-memory accumulation, the image-space spreading kernel with a CTA
+ * register accumulation (a CTA per tile or per tile plane), with
+ * shared-memory accumulation and with tensor-core accumulation, the image-space spreading kernel with a CTA
  * per tile or per plane pair, the k-space
  * interpolation with 8 and with 4 coils per CTA, its tile halos staged per
  * value or by one tensor-memory-accelerator copy, and the coil-grid
@@ -378,12 +378,18 @@ nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* 
  * The compensated precision always uses shared-memory accumulation for k
  * space; plans without coils tune only the image-space spread.
  * nrsense_plan_set_tuning applies stored choices (e.g. a cache keyed by the
- * geometry).  Both change only speed: every choice computes the same values.
+ * geometry).  Both change only speed: every choice computes the same values
+ * (bitwise, except the tensor-core spread and the pruned transforms, which
+ * agree to FP32 rounding).
  * Errors: ERR_ARG (null, reps outside 1..100, unknown choice), ERR_CUDA.
  */
 #define NRSENSE_TUNE_SPREAD_REGISTER      1  /* register accumulation, CTA per tile */
 #define NRSENSE_TUNE_SPREAD_SHARED        2  /* shared-memory accumulation */
 #define NRSENSE_TUNE_SPREAD_REGISTER_WARP 3  /* register accumulation, CTA per tile plane */
+#define NRSENSE_TUNE_SPREAD_MMA           4  /* tensor-core accumulation (TF32 split in three
+                                                products), CTA per tile plane, 8-coil chunks
+                                                (fewer coils: as REGISTER_WARP); within FP32
+                                                rounding of, not bitwise equal to, the others */
 typedef struct {
   int32_t spread_variant;  /* NRSENSE_TUNE_SPREAD_* */
   int32_t interp_coils;    /* coils per interpolation CTA: 8 or 4 */
@@ -398,6 +404,7 @@ typedef struct {
                                   FP32 grids); 0: cuFFT plus the fan-out / combination kernels */
   double  fft_ms[2];           /* measured forward + adjoint of the first phase chunk:
                                   cuFFT path, pruned path (-1: not available) */
+  double  spread_mma_ms;       /* measured tensor-core spread (-1: not available) */
 } nrsense_tuning;
 nrsense_status nrsense_plan_autotune(nrsense_plan_t plan, int32_t reps, nrsense_tuning* out_host,
                                      void* stream);

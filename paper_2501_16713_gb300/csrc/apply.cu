@@ -343,12 +343,14 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
   if (p == nullptr || t == nullptr) return NRSENSE_ERR_ARG;
   if (t->spread_variant != NRSENSE_TUNE_SPREAD_REGISTER &&
       t->spread_variant != NRSENSE_TUNE_SPREAD_SHARED &&
-      t->spread_variant != NRSENSE_TUNE_SPREAD_REGISTER_WARP)
+      t->spread_variant != NRSENSE_TUNE_SPREAD_REGISTER_WARP &&
+      t->spread_variant != NRSENSE_TUNE_SPREAD_MMA)
     return NRSENSE_ERR_ARG;
   if (t->interp_coils != 4 && t->interp_coils != 8) return NRSENSE_ERR_ARG;
   if (t->interp_tma != 0 && t->interp_tma != 1) return NRSENSE_ERR_ARG;
   p->spread_variant = t->spread_variant == NRSENSE_TUNE_SPREAD_REGISTER   ? kSpreadRegister
                       : t->spread_variant == NRSENSE_TUNE_SPREAD_SHARED ? kSpreadShared
+                      : t->spread_variant == NRSENSE_TUNE_SPREAD_MMA    ? kSpreadMMA
                                                                         : kSpreadRegisterWarp;
   p->interp_coils = t->interp_coils;
   p->interp_tma = t->interp_tma == 1 && p->tma_ok;
@@ -366,6 +368,7 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
   std::memset(out, 0, sizeof(*out));
   out->spread_variant = p->spread_variant == kSpreadRegister ? NRSENSE_TUNE_SPREAD_REGISTER
                         : p->spread_variant == kSpreadShared ? NRSENSE_TUNE_SPREAD_SHARED
+                        : p->spread_variant == kSpreadMMA    ? NRSENSE_TUNE_SPREAD_MMA
                                                              : NRSENSE_TUNE_SPREAD_REGISTER_WARP;
   out->interp_coils = p->interp_coils;
   out->interp_tma = p->interp_tma ? 1 : 0;
@@ -431,6 +434,13 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
                                    p->grid_bf16, p->comp_spread, variants[k], p->b_scratch,
                                    p->d_status, s);
     });
+  const bool mma_ok = p->W == 4 && p->C > 4 && !p->comp_spread;
+  out->spread_mma_ms = -1.0;
+  if (mma_ok)
+    out->spread_mma_ms = time_ms([&] {
+      p->launches += launch_spread(g, p->W, p->kc, p->C, p->ktiles, ts, p->b_y, p->b_xspread,
+                                   p->grid_bf16, false, kSpreadMMA, p->b_scratch, p->d_status, s);
+    });
   const int chunks[2] = {8, 4};
   const bool saved_tma = p->interp_tma;
   for (int t = 0; t < 2; ++t) {
@@ -485,6 +495,8 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
     for (int k = 1; k < 3; ++k)
       if (out->spread_ms[k] < out->spread_ms[bk]) bk = k;
     p->spread_variant = variants[bk];
+    if (mma_ok && out->spread_mma_ms >= 0.0 && out->spread_mma_ms < out->spread_ms[bk])
+      p->spread_variant = kSpreadMMA;
   }
   // fastest interpolation: staging (per value / TMA) x coils per CTA (8 / 4)
   double best = out->interp_ms[0];
@@ -501,6 +513,7 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
     }
   out->spread_variant = p->spread_variant == kSpreadRegister ? NRSENSE_TUNE_SPREAD_REGISTER
                         : p->spread_variant == kSpreadShared ? NRSENSE_TUNE_SPREAD_SHARED
+                        : p->spread_variant == kSpreadMMA    ? NRSENSE_TUNE_SPREAD_MMA
                                                              : NRSENSE_TUNE_SPREAD_REGISTER_WARP;
   out->interp_coils = p->interp_coils;
   out->interp_tma = p->interp_tma ? 1 : 0;

@@ -408,6 +408,182 @@ __global__ void __launch_bounds__(32 * WPC, WPC == 1 ? 24 : 3) spread_coils_reg_
 }
 
 // ---------------------------------------------------------------------------
+// W = 4, 8 coils, 8^3 tiles, tensor cores.  One warp (CTA) per tile plane with
+// the same per-warp staging of 32 points as spread_coils_reg_kernel<8, GT, 1>;
+// a staged batch updates the plane by the contraction
+//   C[m][n] += sum_k A[m][k] V[k][n],   m = ly * 8 + lx (grid point of the
+//   plane), k = point of the batch, n = 2 coil + (0: re, 1: im),
+//   A[m][k] = wz_k wy_k(ly - r1_k) wx_k(lx - r2_k)  (0 outside the footprint),
+// run as mma.sync m16n8k8 TF32 products with FP32 accumulation (4 row tiles
+// x 2 column tiles x 4 k steps per batch).  Each operand is split x = hi + lo
+// (hi = x rounded to TF32, lo = the rest rounded to TF32) and the products
+// hi.hi + hi.lo + lo.hi are accumulated, which keeps the error near FP32
+// rounding (the dropped lo.lo term is below 2^-22 relative).  The summation
+// order differs from the FMA kernels, so the result is not bitwise theirs.
+// Fragment layouts (PTX, m16n8k8 .tf32): g = lane / 4, q = lane % 4;
+// A: a0 (g, q), a1 (g + 8, q), a2 (g, q + 4), a3 (g + 8, q + 4);
+// B: b0 (k = q, n = g), b1 (k = q + 4, n = g);
+// C: c0, c1 (g, 2q, 2q + 1), c2, c3 (g + 8, 2q, 2q + 1).
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, "
+      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <typename GT>
+__global__ void __launch_bounds__(32, 16) spread_coils_mma_kernel(
+    Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
+    GT* __restrict__ grids, float2* __restrict__ scratch) {
+  constexpr int CC = 8, W = 4, T = 8, B = 32, NB = W + T + 1;
+  __shared__ __align__(16) CoilStage<CC> stg[B];
+
+  const ItemRef ir = item_ref(pt, int(blockIdx.x >> 3));
+  const SpreadItem it = ir.it;
+  const int2* __restrict__ list = pt.list[ir.jj];
+  const float4* __restrict__ qs = pt.qs[ir.jj];
+  const long long row0 = pt.row0[ir.jj];
+  GT* __restrict__ grid = grids + (long long)ir.jj * C * g.ngrid;
+  const int coil0 = blockIdx.y * CC;
+  const int lane = threadIdx.x & 31, gq = lane >> 2, q = lane & 3;
+  const TileOrigin to = tile_origin(g, tp, it.tile);
+  const int lz = int(blockIdx.x & 7);
+
+  float acc[4][2][4];
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
+
+  if (lz < to.e0) {
+    const int32_t* ib = pt.bins[ir.jj] + (long long)ir.local * NB;
+    const int beg = it.begin + __ldg(ib + min(lz, NB - 1));
+    const int end = it.begin + __ldg(ib + min(lz + W, NB - 1));
+    for (int base = beg; base < end; base += B) {
+      const int n = min(B, end - base);
+      if (lane < n) {
+        const int2 e = __ldg(list + base + lane);
+        const float4 qq = __ldg(qs + e.x);
+        int b0, b1, b2;
+        unpack_base(__float_as_uint(qq.w), b0, b1, b2);
+        int r0 = b0 - to.o0, r1 = b1 - to.o1, r2 = b2 - to.o2;
+        if (r0 < 0) r0 += g.g0;
+        if (r0 >= T) r0 -= g.g0;
+        if (r1 < 0) r1 += g.g1;
+        if (r1 >= T) r1 -= g.g1;
+        if (r2 < 0) r2 += g.g2;
+        if (r2 >= T) r2 -= g.g2;
+        float wz[W], wy[W], wx[W];
+        kernel_weights<W>(qq.x, kc, wz);
+        kernel_weights<W>(qq.y, kc, wy);
+        kernel_weights<W>(qq.z, kc, wx);
+        const int t0 = lz - r0;
+        const float wzt = ((unsigned)t0 < (unsigned)W) ? select_tap<W>(wz, t0) : 0.f;
+        CoilStage<CC>& d = stg[lane];
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+          d.wzy[t] = wzt * wy[t];
+          d.wx[t] = wx[t];
+        }
+        d.r1 = r1;
+        d.r2 = r2;
+        const float2* src = vals + (row0 + e.y) * C + coil0;
+#pragma unroll
+        for (int c = 0; c < CC; ++c)
+          d.val[c] = (coil0 + c < C) ? __ldg(src + c) : make_float2(0.f, 0.f);
+      }
+      __syncwarp();
+#pragma unroll 1
+      for (int ks = 0; ks < 4; ++ks) {
+        if (8 * ks >= n) break;  // warp-uniform
+        // this lane's A columns: points k0 (a0, a1) and k0 + 4 (a2, a3), at
+        // grid column lx = gq, every row ly
+        float wa[2][T];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int k = 8 * ks + q + 4 * j;
+          const bool live = k < n;
+          const CoilStage<CC>& d = stg[live ? k : 0];
+          const int tx = gq - d.r2;
+          const float wxv = (live && (unsigned)tx < (unsigned)W) ? d.wx[tx & (W - 1)] : 0.f;
+#pragma unroll
+          for (int ly = 0; ly < T; ++ly) {
+            const int ty = ly - d.r1;
+            wa[j][ly] = (unsigned)ty < (unsigned)W ? d.wzy[ty & (W - 1)] * wxv : 0.f;
+          }
+        }
+        // B: values of points k0 (b0) and k0 + 4 (b1), column n = 8 nt + gq:
+        // coil 4 nt + gq / 2, real part for even gq
+        uint32_t bh[2][2], bl[2][2];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const int k = 8 * ks + q + 4 * j;
+            const float2 v = k < n ? stg[k].val[4 * nt + (gq >> 1)] : make_float2(0.f, 0.f);
+            split_tf32((gq & 1) ? v.y : v.x, bh[nt][j], bl[nt][j]);
+          }
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+          uint32_t ah[4], al[4];
+          split_tf32(wa[0][2 * mt], ah[0], al[0]);
+          split_tf32(wa[0][2 * mt + 1], ah[1], al[1]);
+          split_tf32(wa[1][2 * mt], ah[2], al[2]);
+          split_tf32(wa[1][2 * mt + 1], ah[3], al[3]);
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) {
+            mma_tf32(acc[mt][nt], ah[0], ah[1], ah[2], ah[3], bh[nt][0], bh[nt][1]);
+            mma_tf32(acc[mt][nt], ah[0], ah[1], ah[2], ah[3], bl[nt][0], bl[nt][1]);
+            mma_tf32(acc[mt][nt], al[0], al[1], al[2], al[3], bh[nt][0], bh[nt][1]);
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // write out: grid column lx = gq, rows 2 mt (c0, c1) and 2 mt + 1 (c2, c3),
+  // coils 4 nt + q
+  const int slot = scratch_slot(pt, ir);
+  const int lx = gq;
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ly = 2 * mt + h;
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int c = 4 * nt + q;
+        const float2 v = make_float2(acc[mt][nt][2 * h], acc[mt][nt][2 * h + 1]);
+        if (slot < 0) {
+          if (lz < to.e0 && ly < to.e1 && lx < to.e2 && coil0 + c < C) {
+            const long long gi =
+                ((long long)(to.o0 + lz) * g.g1 + (to.o1 + ly)) * g.g2 + (to.o2 + lx);
+            grid_st(grid + (long long)(coil0 + c) * g.ngrid + gi, v);
+          }
+        } else {
+          scratch[((long long)slot * gridDim.y + blockIdx.y) * (T * T * T * CC) +
+                  ((lz * T + ly) * T + lx) * CC + c] = v;
+        }
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // W = 4, one channel (image space), 16^3 tiles.  Warp w owns planes 2w and
 // 2w+1 (one per half-warp) and streams the union of their list ranges, with
 // the same per-warp staging as above; lane = (tap x, tap y, plane).
@@ -672,7 +848,10 @@ int dispatch_coils(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& t
     const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2) * (COMP ? 2 : 1);
     spread_coils_kernel<CC, GT, COMP><<<grid, kThreads, smem, s>>>(g, kc, C, tp, pt, vals, grids,
                                                                    scratch);
-  } else if (variant == kSpreadRegisterWarp) {
+  } else if (variant == kSpreadMMA && CC == 8) {
+    const dim3 wgrid(8u * pt.item0[pt.nphase], chunks);
+    spread_coils_mma_kernel<GT><<<wgrid, 32, 0, s>>>(g, kc, C, tp, pt, vals, grids, scratch);
+  } else if (variant == kSpreadRegisterWarp || variant == kSpreadMMA) {
     const dim3 wgrid(8u * pt.item0[pt.nphase], chunks);
     spread_coils_reg_kernel<CC, GT, 1><<<wgrid, 32, 0, s>>>(g, kc, C, tp, pt, vals, grids,
                                                             scratch);

@@ -208,7 +208,7 @@ int launch_crop_to_coils(const Geo& g, int C, const float* deapod, const void* x
 // compensated accumulation (W = 4 kernels); variant selects register or
 // shared-memory accumulation for the multi-coil W = 4 kernel (register
 // accumulation with a CTA per tile, or with a CTA per tile plane).
-constexpr int kSpreadRegister = 1, kSpreadShared = 2, kSpreadRegisterWarp = 3;
+constexpr int kSpreadRegister = 1, kSpreadShared = 2, kSpreadRegisterWarp = 3, kSpreadMMA = 4;
 int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                   const PhaseTable& pt, const nrsense_c64* vals, void* grids, bool bf16,
                   bool comp, int variant, nrsense_c64* scratch, int32_t* status, cudaStream_t s);

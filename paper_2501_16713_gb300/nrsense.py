@@ -49,7 +49,8 @@ class Tuning(ctypes.Structure):
                 ("interp_tma_ms", ctypes.c_double * 2),
                 ("spread_image_warp", ctypes.c_int32),
                 ("spread_image_ms", ctypes.c_double * 2),
-                ("fft_pruned", ctypes.c_int32), ("fft_ms", ctypes.c_double * 2)]
+                ("fft_pruned", ctypes.c_int32), ("fft_ms", ctypes.c_double * 2),
+                ("spread_mma_ms", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -591,7 +592,8 @@ class Plan:
                "interp_ms": list(t.interp_ms), "interp_tma_ms": list(t.interp_tma_ms),
                "spread_image_warp": t.spread_image_warp,
                "spread_image_ms": list(t.spread_image_ms),
-               "fft_pruned": t.fft_pruned, "fft_ms": list(t.fft_ms)}
+               "fft_pruned": t.fft_pruned, "fft_ms": list(t.fft_ms),
+               "spread_mma_ms": t.spread_mma_ms}
         if cache:
             store[key] = res
             tmp = cache + ".tmp"

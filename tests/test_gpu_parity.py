@@ -257,8 +257,8 @@ def test_phase_chunking_matches_oracle(chunk):
 
 
 def test_autotune_choices_compute_the_same_values(tmp_path):
-    # every launch choice (register / shared-memory spreading, 8 / 4 coils per
-    # interpolation CTA, per-value / TMA halo staging) computes bitwise the
+    # every FMA launch choice (register / shared-memory spreading, 8 / 4 coils
+    # per interpolation CTA, per-value / TMA halo staging) computes bitwise the
     # same operator; the cache file round-trips the choices
     import torch
     shape = (16, 16, 24)
@@ -269,7 +269,10 @@ def test_autotune_choices_compute_the_same_values(tmp_path):
     xa0 = plan.adjoint(y0)
     cache = str(tmp_path / "tune.json")
     res = plan.autotune(reps=2, cache=cache)
-    assert not res["cached"] and res["spread_variant"] in (1, 2, 3) and res["interp_coils"] in (4, 8)
+    # the tensor-core spread (4) may win the timing; it is checked against the
+    # oracle in test_gpu_spread_mma.py (FP32-rounding, not bitwise, agreement)
+    assert not res["cached"] and res["spread_variant"] in (1, 2, 3, 4)
+    assert res["interp_coils"] in (4, 8)
     from paper_2501_16713_gb300.nrsense import Tuning
     import ctypes
     # grid 32 x 32 x 48 with 8^3 tiles: interior tiles take the TMA-staged
@@ -287,6 +290,6 @@ def test_autotune_choices_compute_the_same_values(tmp_path):
     res2 = plan.autotune(cache=cache)
     assert res2["cached"] and res2["spread_variant"] == res["spread_variant"]
     t = Tuning()
-    t.spread_variant, t.interp_coils = 4, 8
+    t.spread_variant, t.interp_coils = 5, 8  # no such spread variant
     assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == -1
     plan.close()
