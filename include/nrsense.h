@@ -404,7 +404,9 @@ typedef struct {
                                   FP32 grids); 0: cuFFT plus the fan-out / combination kernels */
   double  fft_ms[2];           /* measured forward + adjoint of the first phase chunk:
                                   cuFFT path, pruned path (-1: not available) */
-  double  spread_mma_ms;       /* measured tensor-core spread (-1: not available) */
+  double  spread_mma_ms;       /* measured tensor-core spread, best warps per CTA (-1: n/a) */
+  int32_t spread_mma_wpc;      /* warps (tile planes) per CTA of the tensor-core spread: 1, 2
+                                  or 4 (set_tuning: other values mean 1) */
 } nrsense_tuning;
 nrsense_status nrsense_plan_autotune(nrsense_plan_t plan, int32_t reps, nrsense_tuning* out_host,
                                      void* stream);

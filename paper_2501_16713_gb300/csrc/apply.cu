@@ -350,8 +350,11 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
   if (t->interp_tma != 0 && t->interp_tma != 1) return NRSENSE_ERR_ARG;
   p->spread_variant = t->spread_variant == NRSENSE_TUNE_SPREAD_REGISTER   ? kSpreadRegister
                       : t->spread_variant == NRSENSE_TUNE_SPREAD_SHARED ? kSpreadShared
-                      : t->spread_variant == NRSENSE_TUNE_SPREAD_MMA    ? kSpreadMMA
-                                                                        : kSpreadRegisterWarp;
+                      : t->spread_variant == NRSENSE_TUNE_SPREAD_MMA
+                          ? spread_mma_variant(t->spread_mma_wpc == 2 || t->spread_mma_wpc == 4
+                                                   ? t->spread_mma_wpc
+                                                   : 1)
+                          : kSpreadRegisterWarp;
   p->interp_coils = t->interp_coils;
   p->interp_tma = t->interp_tma == 1 && p->tma_ok;
   if (t->spread_image_warp != 0 && t->spread_image_warp != 1) return NRSENSE_ERR_ARG;
@@ -368,7 +371,7 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
   std::memset(out, 0, sizeof(*out));
   out->spread_variant = p->spread_variant == kSpreadRegister ? NRSENSE_TUNE_SPREAD_REGISTER
                         : p->spread_variant == kSpreadShared ? NRSENSE_TUNE_SPREAD_SHARED
-                        : p->spread_variant == kSpreadMMA    ? NRSENSE_TUNE_SPREAD_MMA
+                        : spread_base(p->spread_variant) == kSpreadMMA ? NRSENSE_TUNE_SPREAD_MMA
                                                              : NRSENSE_TUNE_SPREAD_REGISTER_WARP;
   out->interp_coils = p->interp_coils;
   out->interp_tma = p->interp_tma ? 1 : 0;
@@ -436,11 +439,21 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
     });
   const bool mma_ok = p->W == 4 && p->C > 4 && !p->comp_spread;
   out->spread_mma_ms = -1.0;
-  if (mma_ok)
-    out->spread_mma_ms = time_ms([&] {
-      p->launches += launch_spread(g, p->W, p->kc, p->C, p->ktiles, ts, p->b_y, p->b_xspread,
-                                   p->grid_bf16, false, kSpreadMMA, p->b_scratch, p->d_status, s);
-    });
+  out->spread_mma_wpc = 0;
+  if (mma_ok) {
+    const int wpcs[3] = {1, 2, 4};
+    for (int k = 0; k < 3; ++k) {
+      const double ms = time_ms([&] {
+        p->launches += launch_spread(g, p->W, p->kc, p->C, p->ktiles, ts, p->b_y, p->b_xspread,
+                                     p->grid_bf16, false, spread_mma_variant(wpcs[k]),
+                                     p->b_scratch, p->d_status, s);
+      });
+      if (ms >= 0.0 && (out->spread_mma_ms < 0.0 || ms < out->spread_mma_ms)) {
+        out->spread_mma_ms = ms;
+        out->spread_mma_wpc = wpcs[k];
+      }
+    }
+  }
   const int chunks[2] = {8, 4};
   const bool saved_tma = p->interp_tma;
   for (int t = 0; t < 2; ++t) {
@@ -496,7 +509,7 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
       if (out->spread_ms[k] < out->spread_ms[bk]) bk = k;
     p->spread_variant = variants[bk];
     if (mma_ok && out->spread_mma_ms >= 0.0 && out->spread_mma_ms < out->spread_ms[bk])
-      p->spread_variant = kSpreadMMA;
+      p->spread_variant = spread_mma_variant(out->spread_mma_wpc);
   }
   // fastest interpolation: staging (per value / TMA) x coils per CTA (8 / 4)
   double best = out->interp_ms[0];
@@ -513,7 +526,7 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
     }
   out->spread_variant = p->spread_variant == kSpreadRegister ? NRSENSE_TUNE_SPREAD_REGISTER
                         : p->spread_variant == kSpreadShared ? NRSENSE_TUNE_SPREAD_SHARED
-                        : p->spread_variant == kSpreadMMA    ? NRSENSE_TUNE_SPREAD_MMA
+                        : spread_base(p->spread_variant) == kSpreadMMA ? NRSENSE_TUNE_SPREAD_MMA
                                                              : NRSENSE_TUNE_SPREAD_REGISTER_WARP;
   out->interp_coils = p->interp_coils;
   out->interp_tma = p->interp_tma ? 1 : 0;

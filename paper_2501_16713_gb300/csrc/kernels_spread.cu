@@ -444,14 +444,20 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-template <typename GT>
-__global__ void __launch_bounds__(32, 16) spread_coils_mma_kernel(
+// WPC warps per CTA, warp w serving plane (blockIdx.x * WPC + w) % 8 of item
+// (blockIdx.x * WPC + w) / 8 (WPC divides 8).
+template <typename GT, int WPC>
+__global__ void __launch_bounds__(32 * WPC, 16 / WPC) spread_coils_mma_kernel(
     Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
     GT* __restrict__ grids, float2* __restrict__ scratch) {
   constexpr int CC = 8, W = 4, T = 8, B = 32, NB = W + T + 1;
-  __shared__ __align__(16) CoilStage<CC> stg[B];
+  static_assert(WPC == 1 || WPC == 2 || WPC == 4, "warps per CTA");
+  __shared__ __align__(16) CoilStage<CC> stg_all[WPC][B];
+  const int warp = int(threadIdx.x >> 5);
+  CoilStage<CC>* stg = stg_all[warp];
+  const int plane_id = int(blockIdx.x) * WPC + warp;
 
-  const ItemRef ir = item_ref(pt, int(blockIdx.x >> 3));
+  const ItemRef ir = item_ref(pt, plane_id >> 3);
   const SpreadItem it = ir.it;
   const int2* __restrict__ list = pt.list[ir.jj];
   const float4* __restrict__ qs = pt.qs[ir.jj];
@@ -460,7 +466,7 @@ __global__ void __launch_bounds__(32, 16) spread_coils_mma_kernel(
   const int coil0 = blockIdx.y * CC;
   const int lane = threadIdx.x & 31, gq = lane >> 2, q = lane & 3;
   const TileOrigin to = tile_origin(g, tp, it.tile);
-  const int lz = int(blockIdx.x & 7);
+  const int lz = plane_id & 7;
 
   float acc[4][2][4];
 #pragma unroll
@@ -844,13 +850,23 @@ int dispatch_coils(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& t
                    int variant, cudaStream_t s) {
   const int chunks = (C + CC - 1) / CC;
   const dim3 grid(pt.item0[pt.nphase], chunks);
+  const int mma_wpc = spread_mma_wpc(variant);
+  variant = spread_base(variant);
   if (COMP || variant == kSpreadShared) {
     const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2) * (COMP ? 2 : 1);
     spread_coils_kernel<CC, GT, COMP><<<grid, kThreads, smem, s>>>(g, kc, C, tp, pt, vals, grids,
                                                                    scratch);
   } else if (variant == kSpreadMMA && CC == 8) {
-    const dim3 wgrid(8u * pt.item0[pt.nphase], chunks);
-    spread_coils_mma_kernel<GT><<<wgrid, 32, 0, s>>>(g, kc, C, tp, pt, vals, grids, scratch);
+    const unsigned planes = 8u * pt.item0[pt.nphase];
+    if (mma_wpc == 4)
+      spread_coils_mma_kernel<GT, 4><<<dim3(planes / 4, chunks), 128, 0, s>>>(
+          g, kc, C, tp, pt, vals, grids, scratch);
+    else if (mma_wpc == 2)
+      spread_coils_mma_kernel<GT, 2><<<dim3(planes / 2, chunks), 64, 0, s>>>(
+          g, kc, C, tp, pt, vals, grids, scratch);
+    else
+      spread_coils_mma_kernel<GT, 1><<<dim3(planes, chunks), 32, 0, s>>>(
+          g, kc, C, tp, pt, vals, grids, scratch);
   } else if (variant == kSpreadRegisterWarp || variant == kSpreadMMA) {
     const dim3 wgrid(8u * pt.item0[pt.nphase], chunks);
     spread_coils_reg_kernel<CC, GT, 1><<<wgrid, 32, 0, s>>>(g, kc, C, tp, pt, vals, grids,

@@ -209,6 +209,11 @@ int launch_crop_to_coils(const Geo& g, int C, const float* deapod, const void* x
 // shared-memory accumulation for the multi-coil W = 4 kernel (register
 // accumulation with a CTA per tile, or with a CTA per tile plane).
 constexpr int kSpreadRegister = 1, kSpreadShared = 2, kSpreadRegisterWarp = 3, kSpreadMMA = 4;
+// a spread variant value carries, in bits 8 and up, the warps per CTA of the
+// tensor-core kernel (1, 2 or 4; 0 means 1)
+inline int spread_base(int v) { return v & 0xff; }
+inline int spread_mma_wpc(int v) { return (v >> 8) ? (v >> 8) : 1; }
+inline int spread_mma_variant(int wpc) { return kSpreadMMA | (wpc << 8); }
 int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                   const PhaseTable& pt, const nrsense_c64* vals, void* grids, bool bf16,
                   bool comp, int variant, nrsense_c64* scratch, int32_t* status, cudaStream_t s);

@@ -50,7 +50,7 @@ class Tuning(ctypes.Structure):
                 ("spread_image_warp", ctypes.c_int32),
                 ("spread_image_ms", ctypes.c_double * 2),
                 ("fft_pruned", ctypes.c_int32), ("fft_ms", ctypes.c_double * 2),
-                ("spread_mma_ms", ctypes.c_double)]
+                ("spread_mma_ms", ctypes.c_double), ("spread_mma_wpc", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -581,6 +581,7 @@ class Plan:
             t.interp_tma = int(store[key].get("interp_tma", 0))
             t.spread_image_warp = int(store[key].get("spread_image_warp", 0))
             t.fft_pruned = int(store[key].get("fft_pruned", 0))
+            t.spread_mma_wpc = int(store[key].get("spread_mma_wpc", 1))
             _check(self.lib.nrsense_plan_set_tuning(self._h, ctypes.byref(t)),
                    "nrsense_plan_set_tuning")
             return dict(store[key], cached=True)
@@ -593,7 +594,7 @@ class Plan:
                "spread_image_warp": t.spread_image_warp,
                "spread_image_ms": list(t.spread_image_ms),
                "fft_pruned": t.fft_pruned, "fft_ms": list(t.fft_ms),
-               "spread_mma_ms": t.spread_mma_ms}
+               "spread_mma_ms": t.spread_mma_ms, "spread_mma_wpc": t.spread_mma_wpc}
         if cache:
             store[key] = res
             tmp = cache + ".tmp"

@@ -32,11 +32,11 @@ def _built():
     g.build()
 
 
-def _set(plan, spread, pruned=0):
+def _set(plan, spread, pruned=0, wpc=1):
     from paper_2501_16713_gb300.nrsense import Tuning
     t = Tuning()
     t.spread_variant, t.interp_coils, t.interp_tma = spread, 8, 0
-    t.spread_image_warp, t.fft_pruned = 0, pruned
+    t.spread_image_warp, t.fft_pruned, t.spread_mma_wpc = 0, pruned, wpc
     return plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t))
 
 
@@ -75,6 +75,10 @@ def test_mma_spread_matches_oracle_and_register_kernel(case):
     d = rel_l2(out[4], out[3])
     print(f"tensor-core vs register spread: rel L2 {d:.2e}")
     assert d < 2e-6
+    # 2 or 4 tile planes per CTA: the same per-plane work, bitwise the same
+    for wpc in (2, 4):
+        assert _set(plan, 4, wpc=wpc) == 0
+        assert np.array_equal(plan.adjoint(to_dev(y)).cpu().numpy(), out[4]), wpc
     assert plan.device_status() == 0
 
 
@@ -96,5 +100,6 @@ def test_mma_spread_normal_operator(case):
 def test_autotune_reports_mma(case):
     _, plan = case
     res = plan.autotune(reps=2)
-    print(res["spread_ms"], res["spread_mma_ms"], res["spread_variant"])
+    print(res["spread_ms"], res["spread_mma_ms"], res["spread_mma_wpc"], res["spread_variant"])
     assert res["spread_mma_ms"] > 0 and res["spread_variant"] in (1, 2, 3, 4)
+    assert res["spread_mma_wpc"] in (1, 2, 4)
