@@ -270,6 +270,9 @@ def _timed_solve(fn):
     return res, e0.elapsed_time(e1)
 
 
+CIRC_LAMBDA_FACTOR = 10.0
+
+
 def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, seed=5):
     """Plain CG and flexible CG with `net` to tol on y = A x + noise,
     lambda = rel_lambda * lambda_max (power iteration); both captured as CUDA
@@ -286,11 +289,30 @@ def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, s
     (fcg, ms_f) = _timed_solve(lambda: plan.solve_fcg(y, lam, net, tol=tol, maxit=maxit,
                                                       graph=True, out=out))
     diff = float((out - x_cg).norm() / x_cg.norm())
+    # circulant preconditioner (set up once per lambda: one E application,
+    # timed apart), alone and followed by the network; built for
+    # CIRC_LAMBDA_FACTOR x lambda (a sweep on this workload: 1x 28, 3x 21,
+    # 10x 19, 30x 22, 100x 27 iterations)
+    t0 = time.perf_counter()
+    plan.set_circulant(CIRC_LAMBDA_FACTOR * lam)
+    ms_setup = (time.perf_counter() - t0) * 1000.0
+    (pc, ms_pc) = _timed_solve(lambda: plan.solve_fcg(y, lam, None, tol=tol, maxit=maxit,
+                                                      graph=True, out=out, circulant=True))
+    diff_pc = float((out - x_cg).norm() / x_cg.norm())
+    (pcn, ms_pcn) = _timed_solve(lambda: plan.solve_fcg(y, lam, net, tol=tol, maxit=maxit,
+                                                        graph=True, out=out, circulant=True))
+    diff_pcn = float((out - x_cg).norm() / x_cg.norm())
+    best = min(ms_f, ms_pc, ms_pcn)
     return {"tol": tol, "lambda": lam, "lambda_rel": rel_lambda, "lambda_max": lam_max,
             "plain": {"iters": cg[1], "ms": round(ms_cg, 2), "true_res": cg[3]},
             "fcg": {"iters": fcg[1], "ms": round(ms_f, 2), "true_res": fcg[3],
-                    "fallbacks": fcg[5]},
-            "speedup": round(ms_cg / ms_f, 3), "solution_rel_diff": diff}
+                    "fallbacks": fcg[5], "solution_rel_diff": diff},
+            "circulant": {"iters": pc[1], "ms": round(ms_pc, 2), "true_res": pc[3],
+                          "solution_rel_diff": diff_pc, "setup_ms": round(ms_setup, 2),
+                          "lambda_factor": CIRC_LAMBDA_FACTOR},
+            "circulant_net": {"iters": pcn[1], "ms": round(ms_pcn, 2), "true_res": pcn[3],
+                              "fallbacks": pcn[5], "solution_rel_diff": diff_pcn},
+            "speedup": round(ms_cg / best, 3), "speedup_fcg_net": round(ms_cg / ms_f, 3)}
 
 
 def run_precond(args):

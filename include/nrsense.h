@@ -213,6 +213,9 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t plan, int32_t phase,
  */
 #define NRSENSE_CG_X0     (1u << 0)
 #define NRSENSE_CG_GRAPH  (1u << 1)
+#define NRSENSE_CG_CIRCULANT (1u << 2)  /* nrsense_solve_fcg: precondition by the plan's
+                                            circulant preconditioner (nrsense_set_circulant),
+                                            before the network when one is given */
 nrsense_status nrsense_solve_cg(nrsense_plan_t plan, const nrsense_c64* y_dev, double lambda,
                                 double tol, int32_t maxit, uint32_t flags, nrsense_c64* x_dev,
                                 int32_t* iters_host, double* res_hist_host, double* true_res_host,
@@ -362,6 +365,25 @@ nrsense_status nrsense_cnn_launches(nrsense_cnn_t net, int64_t* out_host);
 #define NRSENSE_DOT_NOALLOC_MAX_N (16384LL * 4096LL)
 nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* y_dev, int64_t n,
                                    double* out_dev, void* stream);
+
+/*
+ * Circulant preconditioner (not in the paper; serves the Tikhonov CG solve).
+ * nrsense_set_circulant computes the point-spread function of the plan's
+ * normal operator, h = E0 delta at the image centre (E0 with lambda = 0, one
+ * application), and keeps d[k] = 1 / (max(Re DFT(h with the centre moved to
+ * the origin)[k], 0) + lambda): the inverse of the circulant (shift-invariant)
+ * approximation of E0 + lambda I, Hermitian positive definite.  enable = 0
+ * switches it off (buffers are kept).  Synchronises the stream.  Errors:
+ * ERR_ARG (lambda < 0 or not finite), ERR_OOM, ERR_CUFFT.
+ * nrsense_apply_circulant: z = IDFT(d . DFT(r)) for image-shaped device
+ * vectors (z may equal r); ERR_STATE before nrsense_set_circulant.
+ * nrsense_solve_fcg with NRSENSE_CG_CIRCULANT uses z = M(M_c r) (network
+ * given) or z = M_c r (net = NULL: preconditioned CG).
+ */
+nrsense_status nrsense_set_circulant(nrsense_plan_t plan, double lambda, int32_t enable,
+                                     void* stream);
+nrsense_status nrsense_apply_circulant(nrsense_plan_t plan, const nrsense_c64* r_dev,
+                                       nrsense_c64* z_dev, void* stream);
 
 /*
  * Autotuning of the launch choices of a plan (no counterpart in the paper).

@@ -126,6 +126,12 @@ struct nrsense_plan_s {
   bool pad_dirty = false;      // b_xpad / b_xmid hold the pruned transforms' intermediates
 
   nrsense_cg_ws* cg = nullptr;  // allocated by the first nrsense_solve_cg
+  // circulant preconditioner (nrsense_set_circulant, solver.cu)
+  float* circ_d = nullptr;          // per frequency (DFT order): 1 / (max(Re hhat, 0) + lambda)
+  nrsense_c64* circ_tmp = nullptr;  // image-sized work vector
+  cufftHandle fft_circ = 0;
+  bool have_fft_circ = false;
+  bool circ_on = false;
   nrsense_fista_ws* fista = nullptr;  // allocated by the first FISTA or power-iteration call
   nrsense_motion_ws* motion = nullptr;  // allocated by the first DCF or weighted-adjoint call
 };

@@ -307,6 +307,34 @@ __global__ void sub_kernel(float2* __restrict__ r, const float2* __restrict__ ex
   }
 }
 
+// unit impulse at linear index idx (the vector is zeroed before)
+__global__ void impulse_kernel(float2* x, long long idx) { x[idx] = make_float2(1.f, 0.f); }
+
+// d[k] = 1 / (max(Re hhat_c[k], 0) + lam), hhat_c the DFT of the PSF with the
+// image centre moved to the origin: for even N, DFT(roll(h, -N/2))[k] =
+// (-1)^(k0 + k1 + k2) DFT(h)[k].
+__global__ void circ_diag_kernel(const float2* __restrict__ hhat, float* __restrict__ d, int n0,
+                                 int n1, int n2, float lam) {
+  const long long n = (long long)n0 * n1 * n2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k2 = int(i % n2), k1 = int((i / n2) % n1), k0 = int(i / ((long long)n1 * n2));
+    const float re = ((k0 + k1 + k2) & 1) ? -hhat[i].x : hhat[i].x;
+    d[i] = 1.0f / (fmaxf(re, 0.0f) + lam);
+  }
+}
+
+// t *= d / N (the inverse DFT's 1/N)
+__global__ void circ_scale_kernel(float2* __restrict__ t, const float* __restrict__ d, long long n,
+                                  float inv_n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float k = d[i] * inv_n;
+    const float2 v = t[i];
+    t[i] = make_float2(v.x * k, v.y * k);
+  }
+}
+
 #define NRS_TRY(expr)                  \
   do {                                 \
     nrsense_status _st = (expr);       \
@@ -324,6 +352,7 @@ nrsense_status launched() {
 struct nrsense_cg_ws {
   nrsense_c64 *r = nullptr, *p = nullptr, *Ep = nullptr, *b = nullptr;
   nrsense_c64* z = nullptr;    // flexible CG only (allocated on first use)
+  nrsense_c64* zc = nullptr;   // circulant-preconditioned residual (allocated on first use)
   double* partial = nullptr;   // 2 * kRedBlocks
   CgState* st = nullptr;
   double* hist = nullptr;
@@ -342,6 +371,13 @@ struct nrsense_cg_ws {
 namespace nrs {
 
 void cg_release(nrsense_plan_s* p) {
+  if (p->have_fft_circ) cufftDestroy(p->fft_circ);
+  p->have_fft_circ = false;
+  cudaFree(p->circ_d);
+  cudaFree(p->circ_tmp);
+  p->circ_d = nullptr;
+  p->circ_tmp = nullptr;
+  p->circ_on = false;
   nrsense_cg_ws* w = p->cg;
   if (!w) return;
   if (w->gexec) cudaGraphExecDestroy(w->gexec);
@@ -353,6 +389,7 @@ void cg_release(nrsense_plan_s* p) {
   cudaFree(w->Ep);
   cudaFree(w->b);
   cudaFree(w->z);
+  cudaFree(w->zc);
   cudaFree(w->partial);
   cudaFree(w->st);
   cudaFree(w->hist);
@@ -364,7 +401,7 @@ void cg_release(nrsense_plan_s* p) {
 
 namespace {
 
-nrsense_status cg_workspace(nrsense_plan_s* p, int maxit, bool flexible) {
+nrsense_status cg_workspace(nrsense_plan_s* p, int maxit, bool flexible, bool circ = false) {
   const size_t vb = size_t(p->geo.nvox) * sizeof(nrsense_c64);
   if (!p->cg) {
     p->cg = new (std::nothrow) nrsense_cg_ws();
@@ -388,6 +425,11 @@ nrsense_status cg_workspace(nrsense_plan_s* p, int maxit, bool flexible) {
     w->z = nullptr;
     return NRSENSE_ERR_OOM;
   }
+  if (circ && !w->zc && cudaMalloc(&w->zc, vb) != cudaSuccess) {
+    cudaGetLastError();
+    w->zc = nullptr;
+    return NRSENSE_ERR_OOM;
+  }
   if (w->hist_cap < maxit + 1) {
     cudaFree(w->hist);
     w->hist = nullptr;
@@ -401,16 +443,41 @@ nrsense_status cg_workspace(nrsense_plan_s* p, int maxit, bool flexible) {
   return NRSENSE_OK;
 }
 
-// z = M(r) (the network) or z = r (no network), then the flexible CG
-// coefficient and direction.  start: first direction.
-nrsense_status fcg_direction(nrsense_plan_s* p, nrsense_cnn_s* net, bool start, cudaStream_t s) {
+// z = M_c r = IDFT(d . DFT(r)) (circulant preconditioner; z may equal r)
+nrsense_status circ_apply(nrsense_plan_s* p, const nrsense_c64* r, nrsense_c64* z, cudaStream_t s) {
+  StageMark m(p, NRSENSE_STAGE_SOLVER, s);
+  const long long n = p->geo.nvox;
+  if (cufftSetStream(p->fft_circ, s) != CUFFT_SUCCESS ||
+      cufftExecC2C(p->fft_circ, reinterpret_cast<cufftComplex*>(const_cast<nrsense_c64*>(r)),
+                   reinterpret_cast<cufftComplex*>(p->circ_tmp), CUFFT_FORWARD) != CUFFT_SUCCESS)
+    return NRSENSE_ERR_CUFFT;
+  circ_scale_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(reinterpret_cast<float2*>(p->circ_tmp),
+                                                       p->circ_d, n, 1.0f / float(n));
+  p->launches += 1;
+  if (cufftExecC2C(p->fft_circ, reinterpret_cast<cufftComplex*>(p->circ_tmp),
+                   reinterpret_cast<cufftComplex*>(z), CUFFT_INVERSE) != CUFFT_SUCCESS)
+    return NRSENSE_ERR_CUFFT;
+  return launched();
+}
+
+// z = M(r) (the network), z = M_c r (circulant), z = M(M_c r) (both) or
+// z = r (neither), then the flexible CG coefficient and direction.  start:
+// first direction.
+nrsense_status fcg_direction(nrsense_plan_s* p, nrsense_cnn_s* net, bool circ, bool start,
+                             cudaStream_t s) {
   nrsense_cg_ws* w = p->cg;
   const long long n = p->geo.nvox;
   const float2* r = reinterpret_cast<const float2*>(w->r);
   const float2* z = r;
+  const double* sumsq = &w->st->rr;  // |r|^2 of the network input, when it is r
+  if (circ) {
+    NRS_TRY(circ_apply(p, w->r, w->zc, s));
+    z = reinterpret_cast<const float2*>(w->zc);
+    sumsq = nullptr;
+  }
   if (net) {
     StageMark m(p, NRSENSE_STAGE_CNN, s);
-    p->launches += cnn_apply_async(net, r, &w->st->rr, reinterpret_cast<float2*>(w->z), s);
+    p->launches += cnn_apply_async(net, z, sumsq, reinterpret_cast<float2*>(w->z), s);
     z = reinterpret_cast<const float2*>(w->z);
   }
   StageMark m(p, NRSENSE_STAGE_SOLVER, s);
@@ -426,7 +493,7 @@ nrsense_status fcg_direction(nrsense_plan_s* p, nrsense_cnn_s* net, bool start, 
 // One CG (net == nullptr, flexible == false) or flexible CG iteration on
 // stream s, without host synchronisation.
 nrsense_status cg_iteration(nrsense_plan_s* p, nrsense_c64* x, double lambda, bool flexible,
-                            nrsense_cnn_s* net, cudaStream_t s) {
+                            nrsense_cnn_s* net, bool circ, cudaStream_t s) {
   nrsense_cg_ws* w = p->cg;
   const long long n = p->geo.nvox;
   NRS_TRY(nrsense_apply_normal(p, w->p, lambda, w->Ep, s));
@@ -450,7 +517,7 @@ nrsense_status cg_iteration(nrsense_plan_s* p, nrsense_c64* x, double lambda, bo
     }
     p->launches += 5;
   }
-  if (flexible) NRS_TRY(fcg_direction(p, net, false, s));
+  if (flexible) NRS_TRY(fcg_direction(p, net, circ, false, s));
   return launched();
 }
 
@@ -479,7 +546,9 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
                           const nrsense_c64* y, double lambda, double tol, int32_t maxit,
                           uint32_t flags, nrsense_c64* x, const SolveOut& out, Record* rec,
                           cudaStream_t us) {
-  NRS_TRY(cg_workspace(p, maxit, flexible));
+  const bool circ = flexible && (flags & NRSENSE_CG_CIRCULANT) != 0;
+  if (circ && !p->circ_on) return NRSENSE_ERR_STATE;
+  NRS_TRY(cg_workspace(p, maxit, flexible, circ));
   nrsense_cg_ws* w = p->cg;
   const long long n = p->geo.nvox;
   const size_t vb = size_t(n) * sizeof(nrsense_c64);
@@ -517,7 +586,7 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
   p->launches += 1;
   NRS_TRY(launched());
   if (flexible) {
-    NRS_TRY(fcg_direction(p, net, true, s));
+    NRS_TRY(fcg_direction(p, net, circ, true, s));
   } else if (cudaMemcpyAsync(w->p, w->r, vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
     return NRSENSE_ERR_CUDA;
   }
@@ -531,7 +600,7 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
   const int chunk = rec ? 1
                   : graph ? std::max(1, std::min<int>(maxit, tol == 0.0 ? kGraphMax : 2))
                           : 5;
-  const int mode = flexible ? 1 : 0;
+  const int mode = flexible ? (circ ? 2 : 1) : 0;
   if (graph && (w->gexec == nullptr || w->g_x != x || w->g_lambda != lambda ||
                 w->g_chunk != chunk || w->g_mode != mode || w->g_net != net)) {
     if (w->gexec) {
@@ -543,7 +612,7 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
       return NRSENSE_ERR_CUDA;
     nrsense_status cst = NRSENSE_OK;
     for (int k = 0; k < chunk && cst == NRSENSE_OK; ++k)
-      cst = cg_iteration(p, x, lambda, flexible, net, s);
+      cst = cg_iteration(p, x, lambda, flexible, net, circ, s);
     const cudaError_t e = cudaStreamEndCapture(s, &gph);
     if (cst != NRSENSE_OK) {
       if (gph) cudaGraphDestroy(gph);
@@ -579,7 +648,7 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
       p->launches += 5LL * chunk;  // approximate: kernels of the captured operator not recounted
     } else {
       for (int k = 0; k < chunk && it + k < maxit; ++k)
-        NRS_TRY(cg_iteration(p, x, lambda, flexible, net, s));
+        NRS_TRY(cg_iteration(p, x, lambda, flexible, net, circ, s));
     }
   }
   if (rec) {
@@ -669,6 +738,73 @@ nrsense_status nrsense_solve_fcg(nrsense_plan_t p, nrsense_cnn_t net, const nrse
   const SolveOut out{iters, res_hist, true_res, fallbacks};
   return solve_impl(p, true, net, y, lambda, tol, maxit, flags, x, out, nullptr,
                     static_cast<cudaStream_t>(stream));
+}
+
+nrsense_status nrsense_set_circulant(nrsense_plan_t p, double lambda, int32_t enable,
+                                     void* stream) {
+  if (p == nullptr || !(lambda >= 0.0) || !std::isfinite(lambda)) return NRSENSE_ERR_ARG;
+  if (!enable) {
+    p->circ_on = false;
+    return NRSENSE_OK;
+  }
+  const Geo& g = p->geo;
+  const long long n = g.nvox;
+  const size_t vb = size_t(n) * sizeof(nrsense_c64);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->circ_d) {
+    if (cudaMalloc(&p->circ_d, size_t(n) * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&p->circ_tmp, vb) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(p->circ_d);
+      cudaFree(p->circ_tmp);
+      p->circ_d = nullptr;
+      p->circ_tmp = nullptr;
+      return NRSENSE_ERR_OOM;
+    }
+  }
+  if (!p->have_fft_circ) {
+    if (cufftPlan3d(&p->fft_circ, g.n0, g.n1, g.n2, CUFFT_C2C) != CUFFT_SUCCESS)
+      return NRSENSE_ERR_CUFFT;
+    p->have_fft_circ = true;
+  }
+  // h = E0 delta at the image centre, hhat = DFT(h), d from hhat
+  nrsense_c64* h = nullptr;
+  if (cudaMalloc(&h, vb) != cudaSuccess) {
+    cudaGetLastError();
+    return NRSENSE_ERR_OOM;
+  }
+  nrsense_status st = NRSENSE_OK;
+  const long long centre = ((long long)(g.n0 / 2) * g.n1 + g.n1 / 2) * g.n2 + g.n2 / 2;
+  if (cudaMemsetAsync(p->circ_tmp, 0, vb, s) != cudaSuccess) st = NRSENSE_ERR_CUDA;
+  if (st == NRSENSE_OK) {
+    impulse_kernel<<<1, 1, 0, s>>>(reinterpret_cast<float2*>(p->circ_tmp), centre);
+    p->launches += 1;
+    st = launched();
+  }
+  if (st == NRSENSE_OK) st = nrsense_apply_normal(p, p->circ_tmp, 0.0, h, s);
+  if (st == NRSENSE_OK &&
+      (cufftSetStream(p->fft_circ, s) != CUFFT_SUCCESS ||
+       cufftExecC2C(p->fft_circ, reinterpret_cast<cufftComplex*>(h),
+                    reinterpret_cast<cufftComplex*>(p->circ_tmp), CUFFT_FORWARD) != CUFFT_SUCCESS))
+    st = NRSENSE_ERR_CUFFT;
+  if (st == NRSENSE_OK) {
+    circ_diag_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(reinterpret_cast<const float2*>(p->circ_tmp),
+                                                        p->circ_d, g.n0, g.n1, g.n2,
+                                                        float(lambda));
+    p->launches += 1;
+    st = launched();
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess && st == NRSENSE_OK) st = NRSENSE_ERR_CUDA;
+  cudaFree(h);
+  p->circ_on = st == NRSENSE_OK;
+  return st;
+}
+
+nrsense_status nrsense_apply_circulant(nrsense_plan_t p, const nrsense_c64* r, nrsense_c64* z,
+                                       void* stream) {
+  if (p == nullptr || r == nullptr || z == nullptr) return NRSENSE_ERR_ARG;
+  if (!p->circ_on) return NRSENSE_ERR_STATE;
+  return circ_apply(p, r, z, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

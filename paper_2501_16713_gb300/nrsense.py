@@ -115,6 +115,8 @@ _SIGS = {
                                ctypes.c_double, _VP],
     "nrsense_normal_max_eig": [_VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _VP],
     "nrsense_dcf": [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP],
+    "nrsense_set_circulant": [_VP, ctypes.c_double, ctypes.c_int32, _VP],
+    "nrsense_apply_circulant": [_VP, _VP, _VP, _VP],
     "nrsense_apply_adjoint_weighted": [_VP, _VP, _VP, _VP, _VP],
     "nrsense_translation_xcorr": [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                   ctypes.POINTER(ctypes.c_double), _VP],
@@ -130,6 +132,7 @@ _SIGS = {
 }
 CG_X0 = 1
 CG_GRAPH = 2
+CG_CIRCULANT = 4
 NUM_STAGES = 16
 _STRING_RESULT = ("nrsense_status_string", "nrsense_stage_name")
 _INT64_RESULT = ("nrsense_cnn_num_params",)
@@ -534,9 +537,26 @@ class Plan:
         k = cnt.value
         return (x, it.value, list(hist[: it.value + 1]), tres.value, code, rec_r[:k], rec_e[:k])
 
+    def set_circulant(self, lam, enable=True, stream=None):
+        """Build (or switch off) the circulant preconditioner for lambda
+        (nrsense_set_circulant): one normal-operator application."""
+        _check(self.lib.nrsense_set_circulant(self._h, float(lam), int(bool(enable)),
+                                              _stream(stream)), "nrsense_set_circulant")
+
+    def apply_circulant(self, r, out=None, stream=None):
+        """z = M_c r with the circulant preconditioner (nrsense_apply_circulant)."""
+        import torch
+        _need(r, torch.complex64, self.shape, "r")
+        out = self._img() if out is None else _need(out, torch.complex64, self.shape, "out")
+        _check(self.lib.nrsense_apply_circulant(self._h, _ptr(r), _ptr(out), _stream(stream)),
+               "nrsense_apply_circulant")
+        return out
+
     def solve_fcg(self, y, lam, net=None, tol=1e-4, maxit=100, x0=None, graph=False, stream=None,
-                  check=True, out=None):
-        """Flexible CG preconditioned by the network `net` (a Cnn, or None).
+                  check=True, out=None, circulant=False):
+        """Flexible CG preconditioned by the network `net` (a Cnn, or None)
+        and, with circulant=True, by the circulant preconditioner first
+        (set_circulant must have been called).
 
         Returns (x, iterations, residual history, true relative residual,
         status code, fallbacks)."""
@@ -546,7 +566,8 @@ class Plan:
         it, fb = ctypes.c_int32(), ctypes.c_int32()
         hist = (ctypes.c_double * (int(maxit) + 1))()
         tres = ctypes.c_double()
-        flags = (CG_X0 if x0 is not None else 0) | (CG_GRAPH if graph else 0)
+        flags = ((CG_X0 if x0 is not None else 0) | (CG_GRAPH if graph else 0)
+                 | (CG_CIRCULANT if circulant else 0))
         code = self.lib.nrsense_solve_fcg(
             self._h, None if net is None else net._h, _ptr(y), float(lam), float(tol), int(maxit),
             flags, _ptr(x), ctypes.byref(it), hist, ctypes.byref(tres), ctypes.byref(fb),
