@@ -447,7 +447,7 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1
 // WPC warps per CTA, warp w serving plane (blockIdx.x * WPC + w) % 8 of item
 // (blockIdx.x * WPC + w) / 8 (WPC divides 8).
 template <typename GT, int WPC>
-__global__ void __launch_bounds__(32 * WPC, 16 / WPC) spread_coils_mma_kernel(
+__global__ void __launch_bounds__(32 * WPC, WPC == 4 ? 5 : 16 / WPC) spread_coils_mma_kernel(
     Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
     GT* __restrict__ grids, float2* __restrict__ scratch) {
   constexpr int CC = 8, W = 4, T = 8, B = 32, NB = W + T + 1;
