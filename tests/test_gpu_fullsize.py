@@ -1,11 +1,13 @@
 """Full-size checks on the 128^3, 8-coil, 4-phase workload that bench.py times.
 
-The same plan configuration as the benchmark (automatic phase chunking).  The
-FP64 oracle cannot run the whole operator at this size in test time, so the
-checks are (a) sampled outputs the oracle computes one by one from its own
-step-by-step intermediates (the warped image at sampled voxels; k-space
-samples of one phase and two coils), and (b) properties that hold at any
-size: adjointness of A, symmetry and positivity of the normal operator.
+The same plan configuration as the benchmark (automatic phase chunking, the
+autotuned kernel choices).  The FP64 oracle cannot run the whole operator at
+this size in test time, so the checks are (a) sampled outputs the oracle
+computes one by one from its own step-by-step intermediates (the warped image
+at sampled voxels; k-space samples of one phase and two coils), (b) the
+adjoint of data that are nonzero on 300 samples of one phase in two coils,
+which the oracle computes exactly, and (c) properties that hold at any size:
+adjointness of A, symmetry and positivity of the normal operator.
 """
 
 import numpy as np
@@ -27,6 +29,9 @@ def full():
     g.build()
     w = synth.workload("sense128")
     plan = make_plan(w, w["spec"].shape)
+    # the benchmark's launch configuration: the autotuned choices
+    tuning = plan.autotune(reps=2)
+    print("tuning", tuning)
     yield w, plan
     plan.close()
 
@@ -95,3 +100,27 @@ def test_full_adjointness_and_normal_operator(full):
     # E x equals A^H (A x) at full size
     AhAx = plan.adjoint(Ax)
     assert float(torch.linalg.norm(d(AhAx) - d(Ex)) / torch.linalg.norm(d(Ex))) < 1e-6
+
+
+def test_full_adjoint_sparse_data(full):
+    w, plan = full
+    geo = O.Geometry(w["spec"].shape)
+    rng = np.random.default_rng(3)
+    j, coils = 1, (0, 5)
+    M = [c.shape[0] for c in w["coords"]]
+    sel = rng.choice(M[j], 300, replace=False)
+    y = np.zeros((sum(M), 8), np.complex64)
+    off = int(np.sum(M[:j]))
+    vals = (rng.standard_normal((300, 2)) + 1j * rng.standard_normal((300, 2))).astype(np.complex64)
+    for k, c in enumerate(coils):
+        y[off + sel, c] = vals[:, k]
+    got = plan.adjoint(to_dev(y)).cpu().numpy()
+    # oracle: T_j^H sum_c conj(S_c) G_j^H y_c over the 300 samples
+    v = np.zeros(geo.shape, np.complex128)
+    for k, c in enumerate(coils):
+        g = O.kspace_adjoint(geo, vals[:, k].astype(np.complex128), w["coords"][j][sel])
+        v += np.conj(w["smaps"][c]) * g
+    ref = O.warp_adjoint(geo, v, w["disp"][j].astype(np.float64))
+    e = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print(f"full-size adjoint of sparse data: rel L2 {e:.2e}")
+    assert e < TOL_FP32
