@@ -409,7 +409,8 @@ nrsense_status nrsense_apply_circulant(nrsense_plan_t plan, const nrsense_c64* r
 #define NRSENSE_TUNE_SPREAD_SHARED        2  /* shared-memory accumulation */
 #define NRSENSE_TUNE_SPREAD_REGISTER_WARP 3  /* register accumulation, CTA per tile plane */
 #define NRSENSE_TUNE_SPREAD_MMA           4  /* tensor-core accumulation (TF32 split in three
-                                                products), CTA per tile plane, 8-coil chunks
+                                                products), a warp per tile plane or per 4^3
+                                                sub-block, 8-coil chunks
                                                 (fewer coils: as REGISTER_WARP); within FP32
                                                 rounding of, not bitwise equal to, the others */
 typedef struct {
@@ -426,9 +427,15 @@ typedef struct {
                                   FP32 grids); 0: cuFFT plus the fan-out / combination kernels */
   double  fft_ms[2];           /* measured forward + adjoint of the first phase chunk:
                                   cuFFT path, pruned path (-1: not available) */
-  double  spread_mma_ms;       /* measured tensor-core spread, best warps per CTA (-1: n/a) */
-  int32_t spread_mma_wpc;      /* warps (tile planes) per CTA of the tensor-core spread: 1, 2
-                                  or 4 (set_tuning: other values mean 1) */
+  double  spread_mma_ms;       /* measured tensor-core spread, best geometry and warps per CTA
+                                  (-1: n/a) */
+  int32_t spread_mma_wpc;      /* warps per CTA of the tensor-core spread: 1, 2 or 4
+                                  (set_tuning: other values mean 1) */
+  int32_t spread_mma_cube;     /* tensor-core spread geometry: 0 a warp per tile plane (1 x 8 x 8
+                                  grid points), 1 a warp per 4 x 4 x 4 sub-block of the tile
+                                  (points staged once per sub-block they meet: 5.4 times on
+                                  average against 7.6 tile planes) */
+  double  spread_mma_geo_ms[2];/* measured, best warps per CTA: planes, sub-blocks (-1: n/a) */
 } nrsense_tuning;
 nrsense_status nrsense_plan_autotune(nrsense_plan_t plan, int32_t reps, nrsense_tuning* out_host,
                                      void* stream);

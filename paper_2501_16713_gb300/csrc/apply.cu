@@ -117,6 +117,8 @@ PhaseTable kspace_table(const nrsense_plan_s* p, int j0, int j1, bool spread, lo
     t.perm[jj] = ps.perm;
     t.list[jj] = ps.list;
     t.bins[jj] = ps.bins;
+    t.clist[jj] = ps.clist;
+    t.cbins[jj] = ps.cbins;
     t.items[jj] = spread ? ps.items : ps.iitems;
     t.reduces[jj] = ps.reduces;
     t.row0[jj] = p->off[j0 + jj] - row_base;
@@ -348,12 +350,14 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
     return NRSENSE_ERR_ARG;
   if (t->interp_coils != 4 && t->interp_coils != 8) return NRSENSE_ERR_ARG;
   if (t->interp_tma != 0 && t->interp_tma != 1) return NRSENSE_ERR_ARG;
+  if (t->spread_mma_cube != 0 && t->spread_mma_cube != 1) return NRSENSE_ERR_ARG;
   p->spread_variant = t->spread_variant == NRSENSE_TUNE_SPREAD_REGISTER   ? kSpreadRegister
                       : t->spread_variant == NRSENSE_TUNE_SPREAD_SHARED ? kSpreadShared
                       : t->spread_variant == NRSENSE_TUNE_SPREAD_MMA
                           ? spread_mma_variant(t->spread_mma_wpc == 2 || t->spread_mma_wpc == 4
                                                    ? t->spread_mma_wpc
-                                                   : 1)
+                                                   : 1,
+                                               t->spread_mma_cube == 1)
                           : kSpreadRegisterWarp;
   p->interp_coils = t->interp_coils;
   p->interp_tma = t->interp_tma == 1 && p->tma_ok;
@@ -440,17 +444,27 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
   const bool mma_ok = p->W == 4 && p->C > 4 && !p->comp_spread;
   out->spread_mma_ms = -1.0;
   out->spread_mma_wpc = 0;
+  out->spread_mma_cube = 0;
+  out->spread_mma_geo_ms[0] = out->spread_mma_geo_ms[1] = -1.0;
   if (mma_ok) {
     const int wpcs[3] = {1, 2, 4};
-    for (int k = 0; k < 3; ++k) {
-      const double ms = time_ms([&] {
-        p->launches += launch_spread(g, p->W, p->kc, p->C, p->ktiles, ts, p->b_y, p->b_xspread,
-                                     p->grid_bf16, false, spread_mma_variant(wpcs[k]),
-                                     p->b_scratch, p->d_status, s);
-      });
-      if (ms >= 0.0 && (out->spread_mma_ms < 0.0 || ms < out->spread_mma_ms)) {
-        out->spread_mma_ms = ms;
-        out->spread_mma_wpc = wpcs[k];
+    for (int cube = 0; cube < 2; ++cube) {
+      if (cube == 1 && ts.clist[0] == nullptr) break;
+      for (int k = 0; k < 3; ++k) {
+        const double ms = time_ms([&] {
+          p->launches += launch_spread(g, p->W, p->kc, p->C, p->ktiles, ts, p->b_y,
+                                       p->b_xspread, p->grid_bf16, false,
+                                       spread_mma_variant(wpcs[k], cube == 1), p->b_scratch,
+                                       p->d_status, s);
+        });
+        if (ms < 0.0) continue;
+        double& geo_ms = out->spread_mma_geo_ms[cube];
+        if (geo_ms < 0.0 || ms < geo_ms) geo_ms = ms;
+        if (out->spread_mma_ms < 0.0 || ms < out->spread_mma_ms) {
+          out->spread_mma_ms = ms;
+          out->spread_mma_wpc = wpcs[k];
+          out->spread_mma_cube = cube;
+        }
       }
     }
   }
@@ -509,7 +523,7 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
       if (out->spread_ms[k] < out->spread_ms[bk]) bk = k;
     p->spread_variant = variants[bk];
     if (mma_ok && out->spread_mma_ms >= 0.0 && out->spread_mma_ms < out->spread_ms[bk])
-      p->spread_variant = spread_mma_variant(out->spread_mma_wpc);
+      p->spread_variant = spread_mma_variant(out->spread_mma_wpc, out->spread_mma_cube == 1);
   }
   // fastest interpolation: staging (per value / TMA) x coils per CTA (8 / 4)
   double best = out->interp_ms[0];

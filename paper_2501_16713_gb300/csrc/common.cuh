@@ -61,6 +61,9 @@ constexpr int kMaxBins = kMaxWidth + 16;
 // per-phase point data stay in their own arrays; a launch receives this table
 // by value and finds the phase of a CTA from the item prefix sums.
 constexpr int kMaxChunkPhases = 16;
+// Footprint classes of a point in an 8^3 tile (3 per axis: low half only, both
+// halves, high half only) and the per-item offsets that delimit them.
+constexpr int kCubeBins = 27 + 1;
 struct SpreadItem;
 struct ReduceItem;
 struct PhaseTable {
@@ -68,6 +71,8 @@ struct PhaseTable {
   const int32_t* perm[kMaxChunkPhases];
   const int2* list[kMaxChunkPhases];
   const int32_t* bins[kMaxChunkPhases];
+  const int2* clist[kMaxChunkPhases];     // class-ordered lists (8^3 tiles, W = 4), or null
+  const int32_t* cbins[kMaxChunkPhases];  // kCubeBins class starts per item
   const SpreadItem* items[kMaxChunkPhases];
   const ReduceItem* reduces[kMaxChunkPhases];
   long long row0[kMaxChunkPhases];    // first value/output row of the phase

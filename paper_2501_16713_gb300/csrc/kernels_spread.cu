@@ -590,6 +590,197 @@ __global__ void __launch_bounds__(32 * WPC, WPC == 4 ? 5 : 16 / WPC) spread_coil
 }
 
 // ---------------------------------------------------------------------------
+// The same contraction over 4^3 sub-blocks of an 8^3 tile instead of tile
+// planes.  Warp w serves sub-block sb = (blockIdx.x * WPC + w) % 8 (bits z, y,
+// x from high to low) of item (blockIdx.x * WPC + w) / 8 and streams the
+// points whose footprint meets it: in the item's class-ordered list, per axis
+// the classes "low half only" and "both halves" for a low sub-block, "both"
+// and "high half only" for a high one, i.e. four runs of two adjacent
+// classes.  A point meets (7/4)^3 = 5.4 sub-blocks on average against
+// 4 x (11/8)^2 = 7.6 tile planes, so staging, operand building and products
+// fall by 29 %.  Rows m = 16 z + 4 y + x of the sub-block (z, y, x in 0..3):
+// lane (g, q) holds x = g % 4 with y = g / 4 (row g) and y + 2 (row g + 8) for
+// every m-tile z.  Columns and the TF32 split are those of the plane kernel.
+struct CubeStage {
+  float wz[4], wy[4], wx[4];
+  int r0, r1, r2, pad0;  // first tap relative to the sub-block origin, in [-3, 3]
+  float2 val[8];
+  float pad1[4];  // 144-byte records: the four points a k-step reads sit on disjoint banks
+};
+static_assert(sizeof(CubeStage) == 144, "staging record");
+
+template <typename GT, int WPC>
+__global__ void __launch_bounds__(32 * WPC, WPC == 4 ? 5 : 16 / WPC) spread_coils_cube_kernel(
+    Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
+    GT* __restrict__ grids, float2* __restrict__ scratch) {
+  constexpr int CC = 8, W = 4, T = 8, B = 32;
+  static_assert(WPC == 1 || WPC == 2 || WPC == 4, "warps per CTA");
+  __shared__ __align__(16) CubeStage stg_all[WPC][B];
+  const int warp = int(threadIdx.x >> 5);
+  CubeStage* stg = stg_all[warp];
+  const int block_id = int(blockIdx.x) * WPC + warp;
+
+  const ItemRef ir = item_ref(pt, block_id >> 3);
+  const SpreadItem it = ir.it;
+  const int2* __restrict__ list = pt.clist[ir.jj];
+  const float4* __restrict__ qs = pt.qs[ir.jj];
+  const long long row0 = pt.row0[ir.jj];
+  GT* __restrict__ grid = grids + (long long)ir.jj * C * g.ngrid;
+  const int coil0 = blockIdx.y * CC;
+  const int lane = threadIdx.x & 31, gq = lane >> 2, q = lane & 3;
+  const TileOrigin to = tile_origin(g, tp, it.tile);
+  const int sb = block_id & 7, bz = sb >> 2, by = (sb >> 1) & 1, bx = sb & 1;
+  const int sz = 4 * bz, sy = 4 * by, sx = 4 * bx;  // sub-block origin in the tile
+
+  float acc[4][2][4];
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
+
+  if (sz < to.e0 && sy < to.e1 && sx < to.e2) {
+    // the four runs (classes 9 cz + 3 cy + {bx, bx + 1}, cz in {bz, bz + 1},
+    // cy in {by, by + 1}) and their prefix sums
+    const int32_t* cb = pt.cbins[ir.jj] + (long long)ir.local * kCubeBins;
+    int rs[4], pre[5];
+    pre[0] = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int c = 9 * (bz + (r >> 1)) + 3 * (by + (r & 1)) + bx;
+      rs[r] = __ldg(cb + c);
+      pre[r + 1] = pre[r] + (__ldg(cb + c + 2) - rs[r]);
+    }
+    const int total = pre[4];
+    // 16-byte value loads when every staged row segment is 16-byte aligned
+    const bool vec_vals = (C & 1) == 0 && coil0 + CC <= C &&
+                          (reinterpret_cast<uintptr_t>(vals) & 15) == 0;
+    for (int base = 0; base < total; base += B) {
+      const int n = min(B, total - base);
+      if (lane < n) {
+        const int i = base + lane;
+        const int r = (i >= pre[1]) + (i >= pre[2]) + (i >= pre[3]);
+        const int rsr = r == 0 ? rs[0] : r == 1 ? rs[1] : r == 2 ? rs[2] : rs[3];
+        const int prr = r == 0 ? pre[0] : r == 1 ? pre[1] : r == 2 ? pre[2] : pre[3];
+        const int2 e = __ldg(list + it.begin + rsr + (i - prr));
+        const float4 qq = __ldg(qs + e.x);
+        int b0, b1, b2;
+        unpack_base(__float_as_uint(qq.w), b0, b1, b2);
+        int r0 = b0 - to.o0, r1 = b1 - to.o1, r2 = b2 - to.o2;
+        if (r0 < 0) r0 += g.g0;
+        if (r0 >= T) r0 -= g.g0;
+        if (r1 < 0) r1 += g.g1;
+        if (r1 >= T) r1 -= g.g1;
+        if (r2 < 0) r2 += g.g2;
+        if (r2 >= T) r2 -= g.g2;
+        float wz[W], wy[W], wx[W];
+        kernel_weights<W>(qq.x, kc, wz);
+        kernel_weights<W>(qq.y, kc, wy);
+        kernel_weights<W>(qq.z, kc, wx);
+        CubeStage& d = stg[lane];
+        reinterpret_cast<float4*>(d.wz)[0] = make_float4(wz[0], wz[1], wz[2], wz[3]);
+        reinterpret_cast<float4*>(d.wy)[0] = make_float4(wy[0], wy[1], wy[2], wy[3]);
+        reinterpret_cast<float4*>(d.wx)[0] = make_float4(wx[0], wx[1], wx[2], wx[3]);
+        reinterpret_cast<int4*>(&d.r0)[0] = make_int4(r0 - sz, r1 - sy, r2 - sx, 0);
+        const float2* src = vals + (row0 + e.y) * C + coil0;
+        if (vec_vals) {
+#pragma unroll
+          for (int c2 = 0; c2 < CC / 2; ++c2)
+            reinterpret_cast<float4*>(d.val)[c2] = __ldg(reinterpret_cast<const float4*>(src) + c2);
+        } else {
+#pragma unroll
+          for (int c = 0; c < CC; ++c)
+            d.val[c] = (coil0 + c < C) ? __ldg(src + c) : make_float2(0.f, 0.f);
+        }
+      }
+      __syncwarp();
+#pragma unroll 1
+      for (int ks = 0; ks < 4; ++ks) {
+        if (8 * ks >= n) break;  // warp-uniform
+        // this lane's A entries: points k0 (a0, a1) and k0 + 4 (a2, a3) at
+        // column x = g % 4, rows y = g / 4 and y + 2, factor wy wx here, wz
+        // per m-tile below
+        float pyx[2][2];
+        int rz[2];
+        const CubeStage* dj[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int k = 8 * ks + q + 4 * j;
+          const bool live = k < n;
+          const CubeStage& d = stg[live ? k : 0];
+          dj[j] = &d;
+          const int4 rr = *reinterpret_cast<const int4*>(&d.r0);
+          rz[j] = rr.x;
+          const int tx = (gq & 3) - rr.z;
+          const float wxv = (live && (unsigned)tx < (unsigned)W) ? d.wx[tx & (W - 1)] : 0.f;
+          const int ty0 = (gq >> 2) - rr.y, ty1 = ty0 + 2;
+          pyx[j][0] = (unsigned)ty0 < (unsigned)W ? d.wy[ty0 & (W - 1)] * wxv : 0.f;
+          pyx[j][1] = (unsigned)ty1 < (unsigned)W ? d.wy[ty1 & (W - 1)] * wxv : 0.f;
+        }
+        uint32_t bh[2][2], bl[2][2];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const int k = 8 * ks + q + 4 * j;
+            const float2 v = k < n ? stg[k].val[4 * nt + (gq >> 1)] : make_float2(0.f, 0.f);
+            split_tf32((gq & 1) ? v.y : v.x, bh[nt][j], bl[nt][j]);
+          }
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+          float a[2][2];
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const int tz = mt - rz[j];
+            const float wzv = (unsigned)tz < (unsigned)W ? dj[j]->wz[tz & (W - 1)] : 0.f;
+            a[j][0] = wzv * pyx[j][0];
+            a[j][1] = wzv * pyx[j][1];
+          }
+          uint32_t ah[4], al[4];
+          split_tf32(a[0][0], ah[0], al[0]);
+          split_tf32(a[0][1], ah[1], al[1]);
+          split_tf32(a[1][0], ah[2], al[2]);
+          split_tf32(a[1][1], ah[3], al[3]);
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) {
+            mma_tf32(acc[mt][nt], ah[0], ah[1], ah[2], ah[3], bh[nt][0], bh[nt][1]);
+            mma_tf32(acc[mt][nt], ah[0], ah[1], ah[2], ah[3], bl[nt][0], bl[nt][1]);
+            mma_tf32(acc[mt][nt], al[0], al[1], al[2], al[3], bh[nt][0], bh[nt][1]);
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // write out: m-tile mt is tile plane sz + mt; rows y = g / 4 (c0, c1) and
+  // y + 2 (c2, c3), column x = g % 4; coils 4 nt + q
+  const int slot = scratch_slot(pt, ir);
+  const int lx = sx + (gq & 3);
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int lz = sz + mt, ly = sy + (gq >> 2) + 2 * h;
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int c = 4 * nt + q;
+        const float2 v = make_float2(acc[mt][nt][2 * h], acc[mt][nt][2 * h + 1]);
+        if (slot < 0) {
+          if (lz < to.e0 && ly < to.e1 && lx < to.e2 && coil0 + c < C) {
+            const long long gi =
+                ((long long)(to.o0 + lz) * g.g1 + (to.o1 + ly)) * g.g2 + (to.o2 + lx);
+            grid_st(grid + (long long)(coil0 + c) * g.ngrid + gi, v);
+          }
+        } else {
+          scratch[((long long)slot * gridDim.y + blockIdx.y) * (T * T * T * CC) +
+                  ((lz * T + ly) * T + lx) * CC + c] = v;
+        }
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // W = 4, one channel (image space), 16^3 tiles.  Warp w owns planes 2w and
 // 2w+1 (one per half-warp) and streams the union of their list ranges, with
 // the same per-warp staging as above; lane = (tap x, tap y, plane).
@@ -851,11 +1042,23 @@ int dispatch_coils(const Geo& g, const KernelCoefs& kc, int C, const TilePlan& t
   const int chunks = (C + CC - 1) / CC;
   const dim3 grid(pt.item0[pt.nphase], chunks);
   const int mma_wpc = spread_mma_wpc(variant);
+  const bool mma_cube = spread_mma_cube(variant);
   variant = spread_base(variant);
   if (COMP || variant == kSpreadShared) {
     const size_t smem = size_t(8 * 8 * 8) * CC * sizeof(float2) * (COMP ? 2 : 1);
     spread_coils_kernel<CC, GT, COMP><<<grid, kThreads, smem, s>>>(g, kc, C, tp, pt, vals, grids,
                                                                    scratch);
+  } else if (variant == kSpreadMMA && CC == 8 && mma_cube && pt.clist[0] != nullptr) {
+    const unsigned blocks = 8u * pt.item0[pt.nphase];
+    if (mma_wpc == 4)
+      spread_coils_cube_kernel<GT, 4><<<dim3(blocks / 4, chunks), 128, 0, s>>>(
+          g, kc, C, tp, pt, vals, grids, scratch);
+    else if (mma_wpc == 2)
+      spread_coils_cube_kernel<GT, 2><<<dim3(blocks / 2, chunks), 64, 0, s>>>(
+          g, kc, C, tp, pt, vals, grids, scratch);
+    else
+      spread_coils_cube_kernel<GT, 1><<<dim3(blocks, chunks), 32, 0, s>>>(
+          g, kc, C, tp, pt, vals, grids, scratch);
   } else if (variant == kSpreadMMA && CC == 8) {
     const unsigned planes = 8u * pt.item0[pt.nphase];
     if (mma_wpc == 4)

@@ -322,6 +322,46 @@ nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, Po
     }
     bk[nb - 1] = itm.end - itm.begin;
   }
+  // class-ordered copy for the tensor-core spread over 4^3 sub-blocks (8^3
+  // tiles, W = 4): along each axis the first-tap offset r in [-3, 7] puts a
+  // footprint in the low half of the tile only (r <= 0), in both halves
+  // (1 <= r <= 3) or in the high half only (r >= 4); the entries of every item
+  // are ordered by class 9 c0 + 3 c1 + c2 (stable), with 28 offsets per item
+  const bool cube = W == 4 && tp.t0 == 8 && tp.t1 == 8 && tp.t2 == 8;
+  std::vector<int2> clist2;
+  std::vector<int32_t> cbins;
+  if (cube) {
+    clist2.resize(list_len);
+    cbins.assign(items.size() * kCubeBins, 0);
+    std::vector<int32_t> cls;
+    for (size_t k = 0; k < items.size(); ++k) {
+      const SpreadItem& itm = items[k];
+      const long long t = itm.tile;
+      const int o[3] = {int(t / ((long long)tp.nt1 * tp.nt2)) * 8, int((t / tp.nt2) % tp.nt1) * 8,
+                        int(t % tp.nt2) * 8};
+      const int n = itm.end - itm.begin;
+      cls.resize(n);
+      int32_t* cb = cbins.data() + k * kCubeBins;
+      for (int i = 0; i < n; ++i) {
+        const HostPoint& h = pts[order[list[itm.begin + i]]];
+        int c = 0;
+        for (int a = 0; a < 3; ++a) {
+          int r = h.b[a] - o[a];
+          if (r < 0) r += gsz[a];
+          if (r >= 8) r -= gsz[a];
+          c = 3 * c + (r <= 0 ? 0 : r < 4 ? 1 : 2);
+        }
+        cls[i] = c;
+        cb[c + 1]++;
+      }
+      for (int c = 0; c < kCubeBins - 1; ++c) cb[c + 1] += cb[c];
+      std::vector<int32_t> at(cb, cb + kCubeBins - 1);
+      for (int i = 0; i < n; ++i) {
+        const int32_t si = list[itm.begin + i];
+        clist2[itm.begin + at[cls[i]]++] = make_int2(si, perm[si]);
+      }
+    }
+  }
   std::vector<int2> list2(list_len);
   for (long long i = 0; i < list_len; ++i) list2[i] = make_int2(list[i], perm[list[i]]);
   std::vector<int32_t>().swap(list);
@@ -340,6 +380,12 @@ nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, Po
   NRS_TRY(upload(ps->bins, bins, s));
   NRS_TRY(upload(ps->reduces, reds, s));
   NRS_TRY(upload(ps->iitems, iitems, s));
+  if (cube) {
+    NRS_TRY(dev_alloc_n(p, &ps->clist, std::max<long long>(list_len, 1)));
+    NRS_TRY(dev_alloc_n(p, &ps->cbins, std::max<long long>((long long)cbins.size(), 1)));
+    NRS_TRY(upload(ps->clist, clist2, s));
+    NRS_TRY(upload(ps->cbins, cbins, s));
+  }
   return NRSENSE_OK;
 }
 

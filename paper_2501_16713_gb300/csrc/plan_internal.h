@@ -30,6 +30,10 @@ struct PointSet {
   int2* list = nullptr;
   SpreadItem* items = nullptr;  // heaviest first
   int32_t* bins = nullptr;      // per item: W + T + 1 plane-offset bin starts (relative)
+  // 8^3 tiles, W = 4: the list with every item's entries ordered by footprint
+  // class (4^3 sub-blocks touched), and kCubeBins class starts per item
+  int2* clist = nullptr;
+  int32_t* cbins = nullptr;
   int n_items = 0;
   ReduceItem* reduces = nullptr;
   int n_reduces = 0;
@@ -215,11 +219,15 @@ int launch_crop_to_coils(const Geo& g, int C, const float* deapod, const void* x
 // shared-memory accumulation for the multi-coil W = 4 kernel (register
 // accumulation with a CTA per tile, or with a CTA per tile plane).
 constexpr int kSpreadRegister = 1, kSpreadShared = 2, kSpreadRegisterWarp = 3, kSpreadMMA = 4;
-// a spread variant value carries, in bits 8 and up, the warps per CTA of the
-// tensor-core kernel (1, 2 or 4; 0 means 1)
+// a spread variant value carries, in bits 8-15, the warps per CTA of the
+// tensor-core kernel (1, 2 or 4; 0 means 1) and, in bit 16, its geometry
+// (0: a warp per tile plane, 1: a warp per 4^3 sub-block)
 inline int spread_base(int v) { return v & 0xff; }
-inline int spread_mma_wpc(int v) { return (v >> 8) ? (v >> 8) : 1; }
-inline int spread_mma_variant(int wpc) { return kSpreadMMA | (wpc << 8); }
+inline int spread_mma_wpc(int v) { return ((v >> 8) & 0xff) ? ((v >> 8) & 0xff) : 1; }
+inline bool spread_mma_cube(int v) { return ((v >> 16) & 1) != 0; }
+inline int spread_mma_variant(int wpc, bool cube = false) {
+  return kSpreadMMA | (wpc << 8) | (cube ? 1 << 16 : 0);
+}
 int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                   const PhaseTable& pt, const nrsense_c64* vals, void* grids, bool bf16,
                   bool comp, int variant, nrsense_c64* scratch, int32_t* status, cudaStream_t s);

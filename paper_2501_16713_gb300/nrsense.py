@@ -50,7 +50,8 @@ class Tuning(ctypes.Structure):
                 ("spread_image_warp", ctypes.c_int32),
                 ("spread_image_ms", ctypes.c_double * 2),
                 ("fft_pruned", ctypes.c_int32), ("fft_ms", ctypes.c_double * 2),
-                ("spread_mma_ms", ctypes.c_double), ("spread_mma_wpc", ctypes.c_int32)]
+                ("spread_mma_ms", ctypes.c_double), ("spread_mma_wpc", ctypes.c_int32),
+                ("spread_mma_cube", ctypes.c_int32), ("spread_mma_geo_ms", ctypes.c_double * 2)]
 
 
 class Info(ctypes.Structure):
@@ -603,6 +604,7 @@ class Plan:
             t.spread_image_warp = int(store[key].get("spread_image_warp", 0))
             t.fft_pruned = int(store[key].get("fft_pruned", 0))
             t.spread_mma_wpc = int(store[key].get("spread_mma_wpc", 1))
+            t.spread_mma_cube = int(store[key].get("spread_mma_cube", 0))
             _check(self.lib.nrsense_plan_set_tuning(self._h, ctypes.byref(t)),
                    "nrsense_plan_set_tuning")
             return dict(store[key], cached=True)
@@ -615,7 +617,9 @@ class Plan:
                "spread_image_warp": t.spread_image_warp,
                "spread_image_ms": list(t.spread_image_ms),
                "fft_pruned": t.fft_pruned, "fft_ms": list(t.fft_ms),
-               "spread_mma_ms": t.spread_mma_ms, "spread_mma_wpc": t.spread_mma_wpc}
+               "spread_mma_ms": t.spread_mma_ms, "spread_mma_wpc": t.spread_mma_wpc,
+               "spread_mma_cube": t.spread_mma_cube,
+               "spread_mma_geo_ms": list(t.spread_mma_geo_ms)}
         if cache:
             store[key] = res
             tmp = cache + ".tmp"
