@@ -54,12 +54,18 @@ def stage_bytes(info, shape, C, P, M):
     img = 8.0 * G3 + (12.0 + 8.0) * P * N3
     # own pruned coil-grid transforms (sigma 2), per coil grid and E: forward
     # reads S_c (and the phase image once per C grids), writes and re-reads
-    # T1 (N0 N1 G2) and T2 (N0 G1 G2), writes the grid; the adjoint mirrors it
+    # T1 (N0 N1 G2) and T2 (N0 G1 G2), writes the grid; the adjoint mirrors it.
+    # The axis-0 passes touch only the tiles of the union over phases (fu of
+    # the grid; the rest is never read forward and is zero in the adjoint) and
+    # the forward one reads T2 only for tile columns holding such tiles (fc)
     G2 = float(info["grid"][2])
     G1 = float(info["grid"][1])
+    fu = info.get("union_fraction", 1.0)
+    fc = info.get("union_columns", 1.0)
     t1 = 8.0 * shape[0] * shape[1] * G2
     t2 = 8.0 * shape[0] * G1 * G2
-    per_grid = 2.0 * (8.0 * N3 + 8.0 * N3 / max(C, 1)) + 4.0 * t1 + 4.0 * t2 + 2.0 * 8.0 * G3
+    per_grid = (2.0 * (8.0 * N3 + 8.0 * N3 / max(C, 1)) + 4.0 * t1 + (3.0 + fc) * t2 +
+                2.0 * 8.0 * fu * G3)
     return {
         "fft_pruned": P * C * per_grid,
         "interp_kspace": k, "spread_kspace": k,

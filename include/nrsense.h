@@ -106,6 +106,10 @@ typedef struct {
   int64_t split_tiles;       /* tiles split across several work items */
   int64_t device_bytes;      /* device memory held by the plan (excl. cuFFT work) */
   int32_t phase_chunk;       /* phases per launch actually used */
+  double  union_fraction;    /* fraction of tiles in the union over phases (the tiles the
+                                k-space spread writes; the rest of a coil grid stays zero) */
+  double  union_columns;     /* fraction of (axis 1, axis 2) tile columns holding a union tile:
+                                the pruned transforms' axis-0 passes touch only those */
 } nrsense_info;
 
 /*

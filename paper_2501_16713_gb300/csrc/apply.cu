@@ -204,7 +204,7 @@ nrsense_status sense_chunk_forward(nrsense_plan_s* p, int j0, int j1, const nrse
   const Geo& g = p->geo;
   const int nph = j1 - j0;
   if (p->fft_pruned) {
-    STAGE(FFT_PRUNED, launch_pruned_forward(g, p->C, nph, p->deapod, p->smaps, m, p->b_xpad,
+    STAGE(FFT_PRUNED, launch_pruned_forward(g, p->C, nph, p->kcolmask, p->deapod, p->smaps, m, p->b_xpad,
                                             p->b_xmid, p->b_xwork, s));
     p->pad_dirty = true;
     NRS_TRY(launched());
@@ -231,7 +231,7 @@ nrsense_status sense_chunk_adjoint(nrsense_plan_s* p, int j0, int j1, const nrse
                                      p->grid_bf16, p->comp_spread, p->spread_variant, p->b_scratch, p->d_status, s));
   NRS_TRY(launched());
   if (p->fft_pruned) {
-    STAGE(FFT_PRUNED, launch_pruned_inverse(g, p->C, nph, p->deapod, p->smaps, p->b_xspread,
+    STAGE(FFT_PRUNED, launch_pruned_inverse(g, p->C, nph, p->kcolmask, p->deapod, p->smaps, p->b_xspread,
                                             p->b_xmid, p->b_xpad, w, s));
     p->pad_dirty = true;
     return launched();

@@ -270,14 +270,24 @@ __global__ void __launch_bounds__(Shape<R1, R2>::threads) fwd_y_kernel(
 }
 
 // F3: grid[slot][:][y][x] = DFT_z of T2[slot][data planes][y][x].
-// CTA: (block of 16 x, y, slot).
+// CTA: (block of 16 x, y, slot).  colmask (or null): per (y, x) 8^3-tile
+// column a bit per z tile that is ever read; other tiles are not stored, and
+// a CTA whose two tile columns have none returns at once.
 template <int R1, int R2>
 __global__ void __launch_bounds__(Shape<R1, R2>::threads) fwd_z_kernel(
-    PassGeo g, const float2* __restrict__ t2, float2* __restrict__ grid) {
+    PassGeo g, const uint32_t* __restrict__ colmask, const float2* __restrict__ t2,
+    float2* __restrict__ grid) {
   __shared__ float2 sy[Shape<R1, R2>::smem];
   __shared__ float2 tw[R1 * R2];
-  fill_twiddles<R1 * R2>(tw);
   const int xb = blockIdx.x, y = blockIdx.y;
+  uint32_t m0 = ~0u, m1 = ~0u;  // tile columns of x in [16 xb, 16 xb + 8) and [.. + 8, .. + 16)
+  if (colmask != nullptr) {
+    const uint32_t* cm = colmask + (y >> 3) * (g.g2 >> 3) + 2 * xb;
+    m0 = __ldg(cm);
+    m1 = __ldg(cm + 1);
+    if ((m0 | m1) == 0u) return;  // CTA-uniform
+  }
+  fill_twiddles<R1 * R2>(tw);
   const long long slot = blockIdx.z;
   const long long plane = (long long)g.g1 * g.g2;
   const float2* src = t2 + slot * g.n0 * plane + (long long)y * g.g2 + xb * kCols;
@@ -287,24 +297,37 @@ __global__ void __launch_bounds__(Shape<R1, R2>::threads) fwd_z_kernel(
   };
   auto st = [&](int col, int k1, auto k2c, float2 v) {
     constexpr int k2 = decltype(k2c)::value;
-    dst[(k1 + R1 * k2) * plane + col] = v;
+    const int z = k1 + R1 * k2;
+    if (((col < 8 ? m0 : m1) >> (z >> 3)) & 1u) dst[z * plane + col] = v;
   };
   fft16<R1, R2, false, false, true, false>(sy, tw, ld, st);
 }
 
 // I3: T2[slot][i0][y][x] = (inverse DFT_z of grid[slot][:][y][x]) at the data planes.
+// colmask (or null): z tiles outside it are zero in the grid and not loaded.
 template <int R1, int R2>
 __global__ void __launch_bounds__(Shape<R1, R2>::threads) inv_z_kernel(
-    PassGeo g, const float2* __restrict__ grid, float2* __restrict__ t2) {
+    PassGeo g, const uint32_t* __restrict__ colmask, const float2* __restrict__ grid,
+    float2* __restrict__ t2) {
   __shared__ float2 sy[Shape<R1, R2>::smem];
   __shared__ float2 tw[R1 * R2];
   fill_twiddles<R1 * R2>(tw);
   const int xb = blockIdx.x, y = blockIdx.y;
+  uint32_t m0 = ~0u, m1 = ~0u;
+  if (colmask != nullptr) {
+    const uint32_t* cm = colmask + (y >> 3) * (g.g2 >> 3) + 2 * xb;
+    m0 = __ldg(cm);
+    m1 = __ldg(cm + 1);
+  }
   const long long slot = blockIdx.z;
   const long long plane = (long long)g.g1 * g.g2;
   const float2* src = grid + slot * g.g0 * plane + (long long)y * g.g2 + xb * kCols;
   float2* dst = t2 + slot * g.n0 * plane + (long long)y * g.g2 + xb * kCols;
-  auto ld = [&](int col, int n1, int t) -> float2 { return src[(R2 * n1 + t) * plane + col]; };
+  auto ld = [&](int col, int n1, int t) -> float2 {
+    const int z = R2 * n1 + t;
+    return (((col < 8 ? m0 : m1) >> (z >> 3)) & 1u) ? src[z * plane + col]
+                                                    : make_float2(0.f, 0.f);
+  };
   auto st = [&](int col, int k1, auto k2c, float2 v) {
     constexpr int k2 = decltype(k2c)::value;
     dst[img_out<R1, R2>(k1, k2) * plane + col] = v;
@@ -419,7 +442,8 @@ bool pruned_fft_supported(const Geo& g, int C, bool bf16) {
 
 cudaError_t init_pruned_fft() { return cudaSuccess; }  // no tables to upload
 
-int launch_pruned_forward(const Geo& g, int C, int nph, const float* deapod,
+int launch_pruned_forward(const Geo& g, int C, int nph, const uint32_t* colmask,
+                          const float* deapod,
                           const nrsense_c64* smaps, const nrsense_c64* m, void* t1, void* t2,
                           void* grid, cudaStream_t s) {
   const PassGeo pg = pass_geo(g, C, nph);
@@ -430,11 +454,12 @@ int launch_pruned_forward(const Geo& g, int C, int nph, const float* deapod,
   NRS_LAUNCH_L(fwd_x_kernel, g.g2, dim3((g.n1 + kCols - 1) / kCols, g.n0, nph), s, pg, deapod,
                reinterpret_cast<const float2*>(smaps), reinterpret_cast<const float2*>(m), T1);
   NRS_LAUNCH_L(fwd_y_kernel, g.g1, dim3(g.g2 / kCols, g.n0, slots), s, pg, T1, T2);
-  NRS_LAUNCH_L(fwd_z_kernel, g.g0, dim3(g.g2 / kCols, g.g1, slots), s, pg, T2, Gd);
+  NRS_LAUNCH_L(fwd_z_kernel, g.g0, dim3(g.g2 / kCols, g.g1, slots), s, pg, colmask, T2, Gd);
   return 3;
 }
 
-int launch_pruned_inverse(const Geo& g, int C, int nph, const float* deapod,
+int launch_pruned_inverse(const Geo& g, int C, int nph, const uint32_t* colmask,
+                          const float* deapod,
                           const nrsense_c64* smaps, const void* grid, void* t2, void* t1,
                           nrsense_c64* w, cudaStream_t s) {
   const PassGeo pg = pass_geo(g, C, nph);
@@ -442,7 +467,7 @@ int launch_pruned_inverse(const Geo& g, int C, int nph, const float* deapod,
   auto* T2 = static_cast<float2*>(t2);
   const auto* Gd = static_cast<const float2*>(grid);
   const unsigned slots = unsigned(C * nph);
-  NRS_LAUNCH_L(inv_z_kernel, g.g0, dim3(g.g2 / kCols, g.g1, slots), s, pg, Gd, T2);
+  NRS_LAUNCH_L(inv_z_kernel, g.g0, dim3(g.g2 / kCols, g.g1, slots), s, pg, colmask, Gd, T2);
   NRS_LAUNCH_L(inv_y_kernel, g.g1, dim3(g.g2 / kCols, g.n0, slots), s, pg, T2, T1);
   NRS_LAUNCH_L(inv_x_kernel, g.g2, dim3((g.n1 + kCols - 1) / kCols, g.n0, nph), s, pg, deapod,
                reinterpret_cast<const float2*>(smaps), T1, reinterpret_cast<float2*>(w));

@@ -538,6 +538,24 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     // any phase occupies (zeros where it has no points), the rest stay zero
     std::vector<char> uni((size_t)ktiles.ntiles, 0);
     for (int j = 0; j < p->P; ++j) mark_touched_tiles(p, ktiles, all[(size_t)j], uni);
+    long long nuni = 0;
+    for (char u : uni) nuni += u != 0;
+    p->kuni_fraction = double(nuni) / double(uni.size());
+    // per (y, x) tile column, a bit per z tile of the union: the pruned
+    // transforms store (forward) and load (adjoint) only those tiles
+    if (ktiles.nt0 <= 32) {
+      std::vector<uint32_t> cm((size_t)ktiles.nt1 * ktiles.nt2, 0u);
+      long long ncol = 0;
+      for (long long t = 0; t < ktiles.ntiles; ++t)
+        if (uni[(size_t)t]) {
+          const long long col = t % ((long long)ktiles.nt1 * ktiles.nt2);
+          cm[(size_t)col] |= 1u << int(t / ((long long)ktiles.nt1 * ktiles.nt2));
+        }
+      for (uint32_t v : cm) ncol += v != 0u;
+      p->kcol_fraction = double(ncol) / double(cm.size());
+      NRS_TRY(dev_alloc_n(p, &p->kcolmask, (long long)cm.size()));
+      NRS_TRY(upload(p->kcolmask, cm, s));
+    }
     for (int j = 0; j < p->P; ++j) {
       NRS_TRY(build_pointset(p, all[(size_t)j], &p->kpts[j], ktiles, &uni, /*interp=*/true, s));
       std::vector<HostPoint>().swap(all[(size_t)j]);
@@ -733,6 +751,8 @@ nrsense_status nrsense_plan_info(nrsense_plan_t p, nrsense_info* out) {
   out->split_tiles = split;
   out->device_bytes = p->device_bytes;
   out->phase_chunk = p->phase_chunk;
+  out->union_fraction = p->kuni_fraction;
+  out->union_columns = p->kcol_fraction;
   return NRSENSE_OK;
 }
 

@@ -128,6 +128,13 @@ struct nrsense_plan_s {
   bool fft_pruned_ok = false;  // supported: sigma 2, power-of-two grids of 32..256, FP32 grids
   bool fft_pruned = false;     // chosen (else cuFFT plus the K5 / K8 kernels)
   bool pad_dirty = false;      // b_xpad / b_xmid hold the pruned transforms' intermediates
+  // k-space tiles written by the spread (the union over phases), as one
+  // 32-bit mask over axis-0 tiles per (axis-1, axis-2) tile column; null when
+  // axis 0 has more than 32 tiles.  Tiles outside it are zero in the spread
+  // target and never read by the interpolation.
+  uint32_t* kcolmask = nullptr;
+  double kcol_fraction = 1.0;  // tile columns with at least one such tile
+  double kuni_fraction = 1.0;  // tiles of the union
 
   nrsense_cg_ws* cg = nullptr;  // allocated by the first nrsense_solve_cg
   // circulant preconditioner (nrsense_set_circulant, solver.cu)
@@ -240,10 +247,12 @@ int spread_coil_chunk(int C);
 // Each returns the number of kernels launched.
 bool pruned_fft_supported(const Geo& g, int C, bool bf16);
 cudaError_t init_pruned_fft();
-int launch_pruned_forward(const Geo& g, int C, int nph, const float* deapod,
+int launch_pruned_forward(const Geo& g, int C, int nph, const uint32_t* colmask,
+                          const float* deapod,
                           const nrsense_c64* smaps, const nrsense_c64* m, void* t1, void* t2,
                           void* grid, cudaStream_t s);
-int launch_pruned_inverse(const Geo& g, int C, int nph, const float* deapod,
+int launch_pruned_inverse(const Geo& g, int C, int nph, const uint32_t* colmask,
+                          const float* deapod,
                           const nrsense_c64* smaps, const void* grid, void* t2, void* t1,
                           nrsense_c64* w, cudaStream_t s);
 // free the CG workspace of a plan (solver.cu)

@@ -60,7 +60,8 @@ class Info(ctypes.Structure):
                 ("tile", ctypes.c_int32 * 3), ("n_tiles", ctypes.c_int64),
                 ("occupied_fraction", ctypes.c_double), ("spread_items", ctypes.c_int64),
                 ("split_tiles", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("phase_chunk", ctypes.c_int32)]
+                ("phase_chunk", ctypes.c_int32), ("union_fraction", ctypes.c_double),
+                ("union_columns", ctypes.c_double)]
 
 
 _VP = ctypes.c_void_p

@@ -116,3 +116,38 @@ def test_unsupported_geometry_refuses_pruned():
     res = plan.autotune(reps=1)
     assert res["fft_pruned"] == 0 and res["fft_ms"] == [-1.0, -1.0]
     plan.close()
+
+
+def test_pruned_skips_tiles_outside_the_union():
+    """Samples confined to |omega| < 0.35 pi: most tiles of the 32 x 64 x 128
+    grids are outside the union over phases, so the axis-0 passes skip them.
+    The cuFFT path runs first and leaves values in every tile of the
+    interpolation input; the pruned path then stores only union tiles, the
+    interpolation reads only taps inside them, and the adjoint's axis-0 pass
+    takes the other tiles as the zeros the spread target holds there."""
+    c = synth.small_case(SHAPE, 3, 2, [3000, 2600], seed=82, max_disp=1.0, rigid=0.5)
+    c["coords"] = [(0.35 * w).astype(np.float32) for w in c["coords"]]
+    plan = make_plan(c, SHAPE)
+    info = plan.info()
+    fu, fc = info["union_fraction"], info["union_columns"]
+    print(f"union: {fu:.3f} of the tiles, {fc:.3f} of the tile columns")
+    assert 0.0 < fu <= fc < 0.5
+    geo = O.Geometry(SHAPE)
+    d64 = [d.astype(np.float64) for d in c["disp"]]
+    x = c["x"].astype(np.complex128)
+    ys_ref = O.stacked_forward(geo, x, d64, c["smaps"], c["coords"])
+    xa_ref = O.stacked_adjoint(geo, ys_ref, d64, c["smaps"], c["coords"])
+    e_ref = O.normal(geo, x, d64, c["smaps"], c["coords"], 0.5)
+    assert _set(plan, False) == 0
+    plan.forward(to_dev(c["x"]))
+    y0 = to_dev(np.concatenate(ys_ref).astype(np.complex64))
+    plan.adjoint(y0)
+    assert _set(plan, True) == 0
+    y = plan.forward(to_dev(c["x"])).cpu().numpy()
+    xa = plan.adjoint(y0).cpu().numpy()
+    e = plan.normal(to_dev(c["x"]), 0.5).cpu().numpy()
+    errs = (rel_l2(y, np.concatenate(ys_ref)), rel_l2(xa, xa_ref), rel_l2(e, e_ref))
+    print("pruned with skipped tiles: forward %.2e, adjoint %.2e, normal %.2e" % errs)
+    assert max(errs) < TOL_FP32
+    assert plan.device_status() == 0
+    plan.close()
