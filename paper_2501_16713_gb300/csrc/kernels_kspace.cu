@@ -128,6 +128,10 @@ __global__ void __launch_bounds__(256) interp_tile_kernel(
   const int gbase = grp * LPS;
   const bool active_lane = grp < SPW;
   const int nwarps = blockDim.x >> 5;
+  // polynomial coefficients of this lane's tap (fixed per lane)
+  float cf[kNumCoef];
+#pragma unroll
+  for (int k = 0; k < kNumCoef; ++k) cf[k] = s_coef[txl][k];
   for (int s0 = it.begin + warp * SPW; s0 < it.end; s0 += nwarps * SPW) {
     const int s = s0 + grp;
     const bool live = active_lane && s < it.end;
@@ -146,10 +150,10 @@ __global__ void __launch_bounds__(256) interp_tile_kernel(
     {
       const float s0f = fmaf(2.f, qv.x, -1.f), s1f = fmaf(2.f, qv.y, -1.f),
                   s2f = fmaf(2.f, qv.z, -1.f);
-      float a0 = s_coef[txl][kNumCoef - 1], a1 = a0, a2 = a0;
+      float a0 = cf[kNumCoef - 1], a1 = a0, a2 = a0;
 #pragma unroll
       for (int k = kNumCoef - 2; k >= 0; --k) {
-        const float ck = s_coef[txl][k];
+        const float ck = cf[k];
         a0 = fmaf(a0, s0f, ck);
         a1 = fmaf(a1, s1f, ck);
         a2 = fmaf(a2, s2f, ck);
@@ -169,9 +173,10 @@ __global__ void __launch_bounds__(256) interp_tile_kernel(
       const GT* base = halo + ((l0 * H + l1) * H + l2 + txl) * CC + 2 * q;
 #pragma unroll
       for (int t0 = 0; t0 < W; ++t0) {
+        const float w02 = w0[t0] * w2t;
 #pragma unroll
         for (int t1 = 0; t1 < W; ++t1) {
-          const float w = w0[t0] * w1[t1] * w2t;
+          const float w = w02 * w1[t1];
           const float4 v = grid_ld2_shared(base + ((t0 * H + t1) * H) * CC);
           acc.x = fmaf(w, v.x, acc.x);
           acc.y = fmaf(w, v.y, acc.y);
@@ -327,6 +332,10 @@ __global__ void __launch_bounds__(256) interp_tma_kernel(
   const int gbase = grp * LPS;
   const bool active_lane = grp < SPW;
   const int nwarps = blockDim.x >> 5;
+  // polynomial coefficients of this lane's tap (fixed per lane)
+  float cf[kNumCoef];
+#pragma unroll
+  for (int k = 0; k < kNumCoef; ++k) cf[k] = s_coef[txl][k];
   for (int s0 = it.begin + warp * SPW; s0 < it.end; s0 += nwarps * SPW) {
     const int s = s0 + grp;
     const bool live = active_lane && s < it.end;
@@ -345,10 +354,10 @@ __global__ void __launch_bounds__(256) interp_tma_kernel(
     {
       const float s0f = fmaf(2.f, qv.x, -1.f), s1f = fmaf(2.f, qv.y, -1.f),
                   s2f = fmaf(2.f, qv.z, -1.f);
-      float a0 = s_coef[txl][kNumCoef - 1], a1 = a0, a2 = a0;
+      float a0 = cf[kNumCoef - 1], a1 = a0, a2 = a0;
 #pragma unroll
       for (int k = kNumCoef - 2; k >= 0; --k) {
-        const float ck = s_coef[txl][k];
+        const float ck = cf[k];
         a0 = fmaf(a0, s0f, ck);
         a1 = fmaf(a1, s1f, ck);
         a2 = fmaf(a2, s2f, ck);
@@ -368,9 +377,10 @@ __global__ void __launch_bounds__(256) interp_tma_kernel(
       const GT* base = halo + ((c * H + l0) * H + l1) * XP + l2 + txl;
 #pragma unroll
       for (int t0 = 0; t0 < W; ++t0) {
+        const float w02 = w0[t0] * w2t;
 #pragma unroll
         for (int t1 = 0; t1 < W; ++t1) {
-          const float w = w0[t0] * w1[t1] * w2t;
+          const float w = w02 * w1[t1];
           const float2 v = grid_ld_shared(base + (t0 * H + t1) * XP);
           acc.x = fmaf(w, v.x, acc.x);
           acc.y = fmaf(w, v.y, acc.y);
