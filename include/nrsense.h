@@ -419,7 +419,8 @@ nrsense_status nrsense_apply_circulant(nrsense_plan_t plan, const nrsense_c64* r
                                                 rounding of, not bitwise equal to, the others */
 typedef struct {
   int32_t spread_variant;  /* NRSENSE_TUNE_SPREAD_* */
-  int32_t interp_coils;    /* coils per interpolation CTA: 8 or 4 */
+  int32_t interp_coils;    /* coils per interpolation CTA: 8, 4 or 2 (2 with TMA staging; the
+                              per-value staging then takes 4) */
   int32_t interp_tma;      /* 1: tile halos loaded by the tensor memory accelerator */
   double  spread_ms[3];    /* measured: register, shared, register per plane */
   double  interp_ms[2];    /* measured, per-value staging: 8 coils, 4 coils */
@@ -440,6 +441,7 @@ typedef struct {
                                   (points staged once per sub-block they meet: 5.4 times on
                                   average against 7.6 tile planes) */
   double  spread_mma_geo_ms[2];/* measured, best warps per CTA: planes, sub-blocks (-1: n/a) */
+  double  interp_tma2_ms;      /* measured, TMA staging with 2 coils per CTA (-1: n/a) */
 } nrsense_tuning;
 nrsense_status nrsense_plan_autotune(nrsense_plan_t plan, int32_t reps, nrsense_tuning* out_host,
                                      void* stream);

@@ -101,6 +101,7 @@ nrsense_status launched() {
 // tensor map for the TMA-staged interpolation, or null for the per-value staging
 const CUtensorMap* interp_tmap(const nrsense_plan_s* p) {
   if (!p->interp_tma || !p->tma_ok || p->W != 4) return nullptr;
+  if (p->interp_coils == 2) return &p->tmap_xwork2;
   return (p->interp_coils == 8 && p->C > 4) ? &p->tmap_xwork8 : &p->tmap_xwork4;
 }
 
@@ -348,7 +349,7 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
       t->spread_variant != NRSENSE_TUNE_SPREAD_REGISTER_WARP &&
       t->spread_variant != NRSENSE_TUNE_SPREAD_MMA)
     return NRSENSE_ERR_ARG;
-  if (t->interp_coils != 4 && t->interp_coils != 8) return NRSENSE_ERR_ARG;
+  if (t->interp_coils != 2 && t->interp_coils != 4 && t->interp_coils != 8) return NRSENSE_ERR_ARG;
   if (t->interp_tma != 0 && t->interp_tma != 1) return NRSENSE_ERR_ARG;
   if (t->spread_mma_cube != 0 && t->spread_mma_cube != 1) return NRSENSE_ERR_ARG;
   p->spread_variant = t->spread_variant == NRSENSE_TUNE_SPREAD_REGISTER   ? kSpreadRegister
@@ -486,6 +487,17 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
       (t == 0 ? out->interp_ms : out->interp_tma_ms)[k] = ms;
     }
   }
+  // TMA staging with 2 coils per CTA (halo of 23 KB: more CTAs per SM)
+  out->interp_tma2_ms = -1.0;
+  if (p->tma_ok && p->W == 4) {
+    p->interp_tma = true;
+    p->interp_coils = 2;
+    const CUtensorMap* tm = interp_tmap(p);
+    out->interp_tma2_ms = time_ms([&] {
+      p->launches += launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, ti, p->b_xwork,
+                                          p->grid_bf16, p->b_y, 2, tm, p->d_status, s);
+    });
+  }
   p->interp_tma = saved_tma;
   if (p->fft_pruned_ok) {
     // coil-grid transforms: cuFFT with the K5 / K8 kernels vs the own pruned
@@ -525,7 +537,7 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
     if (mma_ok && out->spread_mma_ms >= 0.0 && out->spread_mma_ms < out->spread_ms[bk])
       p->spread_variant = spread_mma_variant(out->spread_mma_wpc, out->spread_mma_cube == 1);
   }
-  // fastest interpolation: staging (per value / TMA) x coils per CTA (8 / 4)
+  // fastest interpolation: staging (per value / TMA) x coils per CTA (8 / 4; TMA also 2)
   double best = out->interp_ms[0];
   p->interp_tma = false;
   p->interp_coils = 8;
@@ -538,6 +550,10 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
         p->interp_coils = chunks[k];
       }
     }
+  if (out->interp_tma2_ms >= 0.0 && out->interp_tma2_ms < best) {
+    p->interp_tma = true;
+    p->interp_coils = 2;
+  }
   out->spread_variant = p->spread_variant == kSpreadRegister ? NRSENSE_TUNE_SPREAD_REGISTER
                         : p->spread_variant == kSpreadShared ? NRSENSE_TUNE_SPREAD_SHARED
                         : spread_base(p->spread_variant) == kSpreadMMA ? NRSENSE_TUNE_SPREAD_MMA

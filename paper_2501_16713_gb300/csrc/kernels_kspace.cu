@@ -249,7 +249,7 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned mbar, unsigned parity) {
 }
 
 template <int CC, typename GT>
-__global__ void __launch_bounds__(256) interp_tma_kernel(
+__global__ void __launch_bounds__(256, CC == 2 ? 6 : 1) interp_tma_kernel(
     const __grid_constant__ CUtensorMap tmap, Geo g, KernelCoefs kc, int C, TilePlan tp,
     PhaseTable pt, const GT* __restrict__ grids, float2* __restrict__ y,
     int32_t* __restrict__ status) {
@@ -491,7 +491,7 @@ template <typename GT>
 void interp_dispatch(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                      const PhaseTable& pt, const GT* gp, float2* yp, int nitems, int coil_chunk,
                      cudaStream_t s) {
-  if (W == 4 && C > 4 && coil_chunk != 4) {
+  if (W == 4 && C > 4 && coil_chunk == 8) {  // per-value staging: 8 or 4 coils
     const dim3 gd(nitems, (C + 7) / 8);
     interp_tile_kernel<4, 8, GT><<<gd, 256, interp_smem<4, 8, GT>(), s>>>(g, kc, C, tp, pt, gp, yp);
   } else if (W == 4) {
@@ -516,6 +516,8 @@ cudaError_t configure_kernels() {
   if (e == cudaSuccess) e = set_tma_smem<8, float2>();
   if (e == cudaSuccess) e = set_tma_smem<4, bf162>();
   if (e == cudaSuccess) e = set_tma_smem<8, bf162>();
+  if (e == cudaSuccess) e = set_tma_smem<2, float2>();
+  if (e == cudaSuccess) e = set_tma_smem<2, bf162>();
   return e;
 }
 
@@ -558,12 +560,16 @@ int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, cons
   if (nitems == 0) return 0;
   auto* yp = reinterpret_cast<float2*>(y);
   if (tmap != nullptr && W == 4) {
-    const int cc = (coil_chunk == 8 && C > 4) ? 8 : 4;
+    // the tensor map's coil box must match: 8 (C > 4), 2, else 4
+    const int cc = (coil_chunk == 8 && C > 4) ? 8 : coil_chunk == 2 ? 2 : 4;
     const dim3 gd(nitems, (C + cc - 1) / cc);
     if (bf16) {
       const auto* gp = static_cast<const bf162*>(grids);
       if (cc == 8)
         interp_tma_kernel<8, bf162><<<gd, 256, interp_tma_smem<8, bf162>(), s>>>(
+            *tmap, g, kc, C, tp, pt, gp, yp, status);
+      else if (cc == 2)
+        interp_tma_kernel<2, bf162><<<gd, 256, interp_tma_smem<2, bf162>(), s>>>(
             *tmap, g, kc, C, tp, pt, gp, yp, status);
       else
         interp_tma_kernel<4, bf162><<<gd, 256, interp_tma_smem<4, bf162>(), s>>>(
@@ -572,6 +578,9 @@ int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, cons
       const auto* gp = static_cast<const float2*>(grids);
       if (cc == 8)
         interp_tma_kernel<8, float2><<<gd, 256, interp_tma_smem<8, float2>(), s>>>(
+            *tmap, g, kc, C, tp, pt, gp, yp, status);
+      else if (cc == 2)
+        interp_tma_kernel<2, float2><<<gd, 256, interp_tma_smem<2, float2>(), s>>>(
             *tmap, g, kc, C, tp, pt, gp, yp, status);
       else
         interp_tma_kernel<4, float2><<<gd, 256, interp_tma_smem<4, float2>(), s>>>(

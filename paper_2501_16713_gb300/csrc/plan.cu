@@ -643,7 +643,8 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     const long long slots = (long long)p->C * p->phase_chunk;
     p->tma_ok = p->W == 4 &&
                 make_grid_tensor_map(&p->tmap_xwork4, p->b_xwork, g, slots, p->grid_bf16, 4) &&
-                make_grid_tensor_map(&p->tmap_xwork8, p->b_xwork, g, slots, p->grid_bf16, 8);
+                make_grid_tensor_map(&p->tmap_xwork8, p->b_xwork, g, slots, p->grid_bf16, 8) &&
+                make_grid_tensor_map(&p->tmap_xwork2, p->b_xwork, g, slots, p->grid_bf16, 2);
     // empty tiles of the spread target are never written: zero them once
     if (cudaMemsetAsync(p->b_xspread, 0, cgb, s) != cudaSuccess) return NRSENSE_ERR_CUDA;
     NRS_TRY(dev_alloc_n(p, &p->b_y, std::max<long long>(p->Mtot * p->C, 1)));

@@ -93,7 +93,7 @@ struct nrsense_plan_s {
                                  // kSpreadRegisterWarp (CTA per plane pair) (autotuned)
   bool interp_tma = false;    // TMA-staged interpolation (autotuned; needs tma_ok)
   bool tma_ok = false;        // tensor maps of b_xwork built
-  CUtensorMap tmap_xwork4{}, tmap_xwork8{};  // boxes of 4 and 8 coil grids
+  CUtensorMap tmap_xwork4{}, tmap_xwork8{}, tmap_xwork2{};  // boxes of 4, 8, 2 coil grids
   bool comp_spread = false;   // desc.precision == NRSENSE_FP32_COMPENSATED
   nrsense_c64* b_y = nullptr;      // Mtot * C
   nrsense_c64* b_tmp = nullptr;    // N^3 (normal operator scratch)

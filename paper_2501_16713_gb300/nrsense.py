@@ -51,7 +51,8 @@ class Tuning(ctypes.Structure):
                 ("spread_image_ms", ctypes.c_double * 2),
                 ("fft_pruned", ctypes.c_int32), ("fft_ms", ctypes.c_double * 2),
                 ("spread_mma_ms", ctypes.c_double), ("spread_mma_wpc", ctypes.c_int32),
-                ("spread_mma_cube", ctypes.c_int32), ("spread_mma_geo_ms", ctypes.c_double * 2)]
+                ("spread_mma_cube", ctypes.c_int32), ("spread_mma_geo_ms", ctypes.c_double * 2),
+                ("interp_tma2_ms", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -620,7 +621,8 @@ class Plan:
                "fft_pruned": t.fft_pruned, "fft_ms": list(t.fft_ms),
                "spread_mma_ms": t.spread_mma_ms, "spread_mma_wpc": t.spread_mma_wpc,
                "spread_mma_cube": t.spread_mma_cube,
-               "spread_mma_geo_ms": list(t.spread_mma_geo_ms)}
+               "spread_mma_geo_ms": list(t.spread_mma_geo_ms),
+               "interp_tma2_ms": t.interp_tma2_ms}
         if cache:
             store[key] = res
             tmp = cache + ".tmp"
