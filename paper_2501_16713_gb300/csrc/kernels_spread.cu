@@ -789,7 +789,9 @@ struct SingleStage {
   float wx[4];
   int r1, r2;
   float2 val;
+  float pad[4];  // 80-byte records: a quarter-warp's 16-byte stores hit disjoint banks
 };
+static_assert(sizeof(SingleStage) == 80, "staging record");
 
 // WPC = 8: a CTA is a work item's tile (8 warps, 2 planes each, accumulator
 // of the whole tile); WPC = 1: a CTA is one warp with planes 2w, 2w+1 of item
@@ -806,7 +808,7 @@ __global__ void __launch_bounds__(32 * WPC) spread_single_kernel(
   extern __shared__ float4 smem_raw[];
   float2* acc = reinterpret_cast<float2*>(smem_raw);  // [NP][T][RS]
   float2* comp = COMP ? acc + NP * T * RS : nullptr;
-  __shared__ SingleStage stg[WPC][B];
+  __shared__ __align__(16) SingleStage stg[WPC][B];
 
   const ItemRef ir = item_ref(pt, WPC == 8 ? int(blockIdx.x) : int(blockIdx.x >> 3));
   const SpreadItem it = ir.it;
@@ -852,32 +854,30 @@ __global__ void __launch_bounds__(32 * WPC) spread_single_kernel(
         const float wa = ((unsigned)ta < (unsigned)W) ? select_tap<W>(wz, ta) : 0.f;
         const float wb = ((unsigned)tb < (unsigned)W && z0 + 1 < to.e0) ? select_tap<W>(wz, tb) : 0.f;
         SingleStage& d = st[lane];
-#pragma unroll
-        for (int t = 0; t < W; ++t) {
-          d.wzy[0][t] = wa * wy[t];
-          d.wzy[1][t] = wb * wy[t];
-          d.wx[t] = wx[t];
-        }
-        d.r1 = r1;
-        d.r2 = r2;
-        d.val = __ldg(vals + row0 + e.y);
+        const float2 v = __ldg(vals + row0 + e.y);
+        float4* d4 = reinterpret_cast<float4*>(&d);
+        d4[0] = make_float4(wa * wy[0], wa * wy[1], wa * wy[2], wa * wy[3]);
+        d4[1] = make_float4(wb * wy[0], wb * wy[1], wb * wy[2], wb * wy[3]);
+        d4[2] = make_float4(wx[0], wx[1], wx[2], wx[3]);
+        d4[3] = make_float4(__int_as_float(r1), __int_as_float(r2), v.x, v.y);
       }
       __syncwarp();
       for (int p = 0; p < n; ++p) {
         const SingleStage& d = st[p];
-        const int ly = d.r1 + ty, lx = d.r2 + tx;
+        const float4 rv = reinterpret_cast<const float4*>(&d)[3];  // r1, r2, value
+        const int ly = __float_as_int(rv.x) + ty, lx = __float_as_int(rv.y) + tx;
         if ((unsigned)ly < (unsigned)to.e1 && (unsigned)lx < (unsigned)to.e2 && lz < to.e0) {
           const float w = d.wzy[hz][ty] * d.wx[tx];
           const int off = ((lz - pbase) * T + ly) * RS + lx;
           float2 cur = acc[off];
           if constexpr (COMP) {
             float2 cc = comp[off];
-            comp_fma(w, d.val.x, cur.x, cc.x);
-            comp_fma(w, d.val.y, cur.y, cc.y);
+            comp_fma(w, rv.z, cur.x, cc.x);
+            comp_fma(w, rv.w, cur.y, cc.y);
             comp[off] = cc;
           } else {
-            cur.x = fmaf(w, d.val.x, cur.x);
-            cur.y = fmaf(w, d.val.y, cur.y);
+            cur.x = fmaf(w, rv.z, cur.x);
+            cur.y = fmaf(w, rv.w, cur.y);
           }
           acc[off] = cur;
         }
