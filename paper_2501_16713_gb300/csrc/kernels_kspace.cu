@@ -279,6 +279,25 @@ __global__ void __launch_bounds__(256, CC == 2 ? 6 : 1) interp_tma_kernel(
   const int o0 = tz * T, o1 = ty * T, o2 = tx * T;
   if (threadIdx.x < W * kNumCoef) s_coef[threadIdx.x / kNumCoef][threadIdx.x % kNumCoef] =
       kc.c[threadIdx.x / kNumCoef][threadIdx.x % kNumCoef];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / LPS;          // sample slot in the warp
+  const int gl = lane - grp * LPS;     // lane in the group
+  const int c = gl % CC, txl = gl / CC;
+  const int gbase = grp * LPS;
+  const bool active_lane = grp < SPW;
+  const int nwarps = blockDim.x >> 5;
+  const int stride = nwarps * SPW;
+  // the first sample's position record and output row, loaded while the
+  // halo is in flight; each iteration then loads the next one's
+  float4 q_next = make_float4(0.f, 0.f, 0.f, 0.f);
+  int row_next = 0;
+  {
+    const int s = it.begin + warp * SPW + grp;
+    if (active_lane && s < it.end) {
+      q_next = __ldg(qs + s);
+      row_next = __ldg(perm + s);
+    }
+  }
   const bool use_tma = o0 + H <= g.g0 && o1 + H <= g.g1 && o2 + XP <= g.g2;
   if (use_tma) {
     const unsigned mb = smem_addr(&mbar);
@@ -325,24 +344,21 @@ __global__ void __launch_bounds__(256, CC == 2 ? 6 : 1) interp_tma_kernel(
     __syncthreads();
   }
 
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int grp = lane / LPS;          // sample slot in the warp
-  const int gl = lane - grp * LPS;     // lane in the group
-  const int c = gl % CC, txl = gl / CC;
-  const int gbase = grp * LPS;
-  const bool active_lane = grp < SPW;
-  const int nwarps = blockDim.x >> 5;
   // polynomial coefficients of this lane's tap (fixed per lane)
   float cf[kNumCoef];
 #pragma unroll
   for (int k = 0; k < kNumCoef; ++k) cf[k] = s_coef[txl][k];
-  for (int s0 = it.begin + warp * SPW; s0 < it.end; s0 += nwarps * SPW) {
+  for (int s0 = it.begin + warp * SPW; s0 < it.end; s0 += stride) {
     const int s = s0 + grp;
     const bool live = active_lane && s < it.end;
-    float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 qv = q_next;
+    const int row = row_next;
+    if (active_lane && s + stride < it.end) {
+      q_next = __ldg(qs + s + stride);
+      row_next = __ldg(perm + s + stride);
+    }
     int l0 = 0, l1 = 0, l2 = 0;
     if (live) {
-      qv = __ldg(qs + s);
       int b0, b1, b2;
       unpack_base(__float_as_uint(qv.w), b0, b1, b2);
       l0 = min(max(b0 - o0, 0), T - 1);  // in range for a well-formed plan
@@ -393,7 +409,7 @@ __global__ void __launch_bounds__(256, CC == 2 ? 6 : 1) interp_tma_kernel(
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
     }
-    if (live && txl == 0 && coil0 + c < C) y[(row0 + __ldg(perm + s)) * C + coil0 + c] = acc;
+    if (live && txl == 0 && coil0 + c < C) y[(row0 + row) * C + coil0 + c] = acc;
   }
 }
 
