@@ -832,10 +832,14 @@ __global__ void __launch_bounds__(32 * WPC) spread_single_kernel(
     const int tx = lane & 3, ty = (lane >> 2) & 3, hz = lane >> 4;
     const int lz = z0 + hz;
     SingleStage* st = stg[warp];
+    // each batch loads the next batch's list entries
+    int2 e_next = make_int2(0, 0);
+    if (beg + lane < end) e_next = __ldg(list + beg + lane);
     for (int base = beg; base < end; base += B) {
       const int n = min(B, end - base);
+      const int2 e = e_next;
+      if (base + B + lane < end) e_next = __ldg(list + base + B + lane);
       if (lane < n) {
-        const int2 e = __ldg(list + base + lane);
         const float4 q = __ldg(qs + e.x);
         int b0, b1, b2;
         unpack_base(__float_as_uint(q.w), b0, b1, b2);
