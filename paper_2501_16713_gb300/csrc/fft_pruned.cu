@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(Shape<R1, R2>::threads, 4) fwd_x_kernel(
 // F2: T2[slot][i0][:][x] = DFT_y of T1[slot][i0][data rows][x].
 // CTA: (block of 16 x, i0, slot).
 template <int R1, int R2>
-__global__ void __launch_bounds__(Shape<R1, R2>::threads) fwd_y_kernel(
+__global__ void __launch_bounds__(Shape<R1, R2>::threads, 5) fwd_y_kernel(
     PassGeo g, const float2* __restrict__ t1, float2* __restrict__ t2) {
   __shared__ float2 sy[Shape<R1, R2>::smem];
   __shared__ float2 tw[R1 * R2];
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(Shape<R1, R2>::threads) fwd_y_kernel(
 // column a bit per z tile that is ever read; other tiles are not stored, and
 // a CTA whose two tile columns have none returns at once.
 template <int R1, int R2>
-__global__ void __launch_bounds__(Shape<R1, R2>::threads) fwd_z_kernel(
+__global__ void __launch_bounds__(Shape<R1, R2>::threads, 5) fwd_z_kernel(
     PassGeo g, const uint32_t* __restrict__ colmask, const float2* __restrict__ t2,
     float2* __restrict__ grid) {
   __shared__ float2 sy[Shape<R1, R2>::smem];
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(Shape<R1, R2>::threads) fwd_z_kernel(
 // I3: T2[slot][i0][y][x] = (inverse DFT_z of grid[slot][:][y][x]) at the data planes.
 // colmask (or null): z tiles outside it are zero in the grid and not loaded.
 template <int R1, int R2>
-__global__ void __launch_bounds__(Shape<R1, R2>::threads) inv_z_kernel(
+__global__ void __launch_bounds__(Shape<R1, R2>::threads, 5) inv_z_kernel(
     PassGeo g, const uint32_t* __restrict__ colmask, const float2* __restrict__ grid,
     float2* __restrict__ t2) {
   __shared__ float2 sy[Shape<R1, R2>::smem];
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(Shape<R1, R2>::threads) inv_z_kernel(
 
 // I2: T1[slot][i0][i1][x] = (inverse DFT_y of T2[slot][i0][:][x]) at the data rows.
 template <int R1, int R2>
-__global__ void __launch_bounds__(Shape<R1, R2>::threads) inv_y_kernel(
+__global__ void __launch_bounds__(Shape<R1, R2>::threads, 5) inv_y_kernel(
     PassGeo g, const float2* __restrict__ t2, float2* __restrict__ t1) {
   __shared__ float2 sy[Shape<R1, R2>::smem];
   __shared__ float2 tw[R1 * R2];
