@@ -249,7 +249,7 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned mbar, unsigned parity) {
 }
 
 template <int CC, typename GT>
-__global__ void __launch_bounds__(256, CC == 2 ? 6 : 1) interp_tma_kernel(
+__global__ void __launch_bounds__(256, CC == 2 ? 6 : CC == 4 ? 4 : 1) interp_tma_kernel(
     const __grid_constant__ CUtensorMap tmap, Geo g, KernelCoefs kc, int C, TilePlan tp,
     PhaseTable pt, const GT* __restrict__ grids, float2* __restrict__ y,
     int32_t* __restrict__ status) {
@@ -365,9 +365,24 @@ __global__ void __launch_bounds__(256, CC == 2 ? 6 : 1) interp_tma_kernel(
       l1 = min(max(b1 - o1, 0), T - 1);
       l2 = min(max(b2 - o2, 0), T - 1);
     }
-    // this lane's tap txl on each axis
-    float w0t, w1t, w2t;
-    {
+    // kernel weights of the sample: axis a at tap t
+    float w0[W], w1[W], w2t;
+    if constexpr (CC >= 4) {
+      // lane (txl, c) evaluates axis min(c, 2) at tap txl; the others take
+      // it by shuffle (the same values as evaluating all three here)
+      const float f = c == 0 ? qv.x : (c == 1 ? qv.y : qv.z);
+      const float sf = fmaf(2.f, f, -1.f);
+      float a = cf[kNumCoef - 1];
+#pragma unroll
+      for (int k = kNumCoef - 2; k >= 0; --k) a = fmaf(a, sf, cf[k]);
+#pragma unroll
+      for (int t = 0; t < W; ++t) {
+        w0[t] = __shfl_sync(0xffffffffu, a, gbase + t * CC);
+        w1[t] = __shfl_sync(0xffffffffu, a, gbase + t * CC + 1);
+      }
+      w2t = __shfl_sync(0xffffffffu, a, gbase + txl * CC + 2);
+    } else {
+      // this lane's tap txl on each axis
       const float s0f = fmaf(2.f, qv.x, -1.f), s1f = fmaf(2.f, qv.y, -1.f),
                   s2f = fmaf(2.f, qv.z, -1.f);
       float a0 = cf[kNumCoef - 1], a1 = a0, a2 = a0;
@@ -378,15 +393,12 @@ __global__ void __launch_bounds__(256, CC == 2 ? 6 : 1) interp_tma_kernel(
         a1 = fmaf(a1, s1f, ck);
         a2 = fmaf(a2, s2f, ck);
       }
-      w0t = a0;
-      w1t = a1;
       w2t = a2;
-    }
-    float w0[W], w1[W];
 #pragma unroll
-    for (int t = 0; t < W; ++t) {
-      w0[t] = __shfl_sync(0xffffffffu, w0t, gbase + t * CC);
-      w1[t] = __shfl_sync(0xffffffffu, w1t, gbase + t * CC);
+      for (int t = 0; t < W; ++t) {
+        w0[t] = __shfl_sync(0xffffffffu, a0, gbase + t * CC);
+        w1[t] = __shfl_sync(0xffffffffu, a1, gbase + t * CC);
+      }
     }
     float2 acc = make_float2(0.f, 0.f);
     if (live) {
