@@ -87,8 +87,10 @@ __device__ __forceinline__ float2 twiddle16(float2 a) {
 }
 
 // In-register radix-2 DFT of length R (R <= 16): a[k] = sum_n a[n] W_R^(+-nk)
-// (bit-reversed input order, then log2 R butterfly stages).
-template <int R, bool INV>
+// (bit-reversed input order, then log2 R butterfly stages).  ZMID: the inputs
+// n in [R/4, 3R/4) are zero, so the first stage, which pairs n and n + R/2,
+// is a copy (u, u) or a copy and a negation (v, -v).
+template <int R, bool INV, bool ZMID = false>
 __device__ __forceinline__ void dft(float2 (&a)[R]) {
   static_for<0, R>([&](auto ic) {
     constexpr int i = decltype(ic)::value, j = bitrev(i, R);
@@ -105,10 +107,21 @@ __device__ __forceinline__ void dft(float2 (&a)[R]) {
         constexpr int i = decltype(gc)::value * len;
         static_for<0, half>([&](auto kc) {
           constexpr int k = decltype(kc)::value;
-          const float2 u = a[i + k];
-          const float2 v = twiddle16<INV, (16 / len) * k>(a[i + k + half]);
-          a[i + k] = make_float2(u.x + v.x, u.y + v.y);
-          a[i + k + half] = make_float2(u.x - v.x, u.y - v.y);
+          if constexpr (ZMID && len == 2) {
+            // original indices bitrev(i) < R/2 and bitrev(i) + R/2
+            constexpr int n = bitrev(i, R);
+            if constexpr (n < R / 4) {
+              a[i + 1] = a[i];
+            } else {
+              a[i] = a[i + 1];
+              a[i + 1] = make_float2(-a[i].x, -a[i].y);
+            }
+          } else {
+            const float2 u = a[i + k];
+            const float2 v = twiddle16<INV, (16 / len) * k>(a[i + k + half]);
+            a[i + k] = make_float2(u.x + v.x, u.y + v.y);
+            a[i + k + half] = make_float2(u.x - v.x, u.y - v.y);
+          }
         });
       });
     }
@@ -180,7 +193,7 @@ __device__ __forceinline__ void fft16(float2* sy, const float2* tw, const Ld& ld
       else
         a[n1] = make_float2(0.f, 0.f);
     });
-    dft<R1, INV>(a);
+    dft<R1, INV, PIN>(a);
     static_for<0, R1>([&](auto kc) {
       constexpr int k1 = decltype(kc)::value;
       float2 v = a[k1];
