@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "nonrigid-SENSE A^H.A applies/s"
 UNIT = "applies/s"
 
-# stage -> algorithmic bytes per step
+# stage -> CUDA source file of its kernels (the key of the committed ncu traffic records)
 STAGE_KERNEL_SOURCE = {
     "interp_kspace": "kernels_kspace.cu", "spread_kspace": "kernels_spread.cu",
     "interp_image": "kernels_image.cu", "spread_image": "kernels_spread.cu",
