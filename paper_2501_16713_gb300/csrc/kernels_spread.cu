@@ -757,6 +757,22 @@ __global__ void __launch_bounds__(32 * WPC, WPC == 4 ? 6 : 16 / WPC) spread_coil
   // y + 2 (c2, c3), column x = g % 4; coils 4 nt + q
   const int slot = scratch_slot(pt, ir);
   const int lx = sx + (gq & 3);
+  if (slot < 0 && sz + 4 <= to.e0 && sy + 4 <= to.e1 && sx + 4 <= to.e2 && coil0 + CC <= C) {
+    // the whole sub-block and coil chunk lie in the grid: one base address,
+    // constant strides (plane, two rows, four coils)
+    const long long plane = (long long)g.g1 * g.g2;
+    GT* base = grid + (long long)(coil0 + q) * g.ngrid +
+               ((long long)(to.o0 + sz) * g.g1 + (to.o1 + sy + (gq >> 2))) * g.g2 + (to.o2 + lx);
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+          grid_st(base + mt * plane + 2 * h * g.g2 + 4LL * nt * g.ngrid,
+                  make_float2(acc[mt][nt][2 * h], acc[mt][nt][2 * h + 1]));
+    return;
+  }
 #pragma unroll
   for (int mt = 0; mt < 4; ++mt)
 #pragma unroll
