@@ -83,3 +83,31 @@ int main(void) {{
     assert i == [ctypes.sizeof(I), I.kb_beta.offset, I.tile.offset, I.n_tiles.offset,
                  I.device_bytes.offset, I.phase_chunk.offset]
     assert int(out[2]) == D.phase_chunk.offset
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc not available")
+def test_every_mirrored_field_matches_header(tmp_path):
+    """Each ctypes mirror of a header struct: size and the offset of every
+    field, as the C compiler lays them out (fields appended to the header
+    structs must be appended to the mirrors in the same order)."""
+    from paper_2501_16713_gb300 import nrsense
+    pairs = [("nrsense_desc", nrsense.Desc), ("nrsense_info", nrsense.Info),
+             ("nrsense_tuning", nrsense.Tuning)]
+    lines = []
+    for cname, cls in pairs:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f}));')
+    src = tmp_path / "fields.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n"
+                   f'#include "{HEADER}"\nint main(void) {{\n' + "\n".join(lines) +
+                   "\n  return 0;\n}\n")
+    exe = tmp_path / "fields"
+    subprocess.run(["gcc", "-std=c99", "-o", str(exe), str(src)], check=True)
+    got = [int(v) for v in
+           subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for _, cls in pairs:
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, f).offset for f, _ in cls._fields_]
+    assert got == want
