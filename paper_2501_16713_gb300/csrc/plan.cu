@@ -145,7 +145,7 @@ void mark_touched_tiles(const nrsense_plan_s* p, const TilePlan& tp,
 // points (NULL = every tile); interp: also build interpolation work items.
 nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, PointSet* ps,
                               const TilePlan& tp, const std::vector<char>* write_mask,
-                              bool interp, cudaStream_t s) {
+                              bool interp, int max_item, cudaStream_t s) {
   const Geo& g = p->geo;
   ps->tp = tp;
   const int W = p->W;
@@ -273,12 +273,12 @@ nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, Po
     const long long L = e - b;
     if (L > 0) occupied++;
     if (L == 0 && write_mask != nullptr && !(*write_mask)[t]) continue;
-    if (L <= kSpreadMaxItem) {
+    if (L <= max_item) {
       items.push_back({int32_t(t), int32_t(b), int32_t(e), -1});
     } else {
       // deal the (r0-sorted) entries round-robin into chunks, so every chunk
       // spans all planes of the tile and keeps the r0 order
-      const int nchunk = int((L + kSpreadMaxItem - 1) / kSpreadMaxItem);
+      const int nchunk = int((L + max_item - 1) / max_item);
       std::vector<int32_t> seg(list.begin() + b, list.begin() + e);
       long long w = b;
       ReduceItem r{int32_t(t), slots, nchunk, 0};
@@ -489,7 +489,8 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
         h.row = int32_t(j * g.nvox + v);
       }
     }
-    NRS_TRY(build_pointset(p, pts, &p->ipts, itiles, nullptr, /*interp=*/false, s));
+    NRS_TRY(build_pointset(p, pts, &p->ipts, itiles, nullptr, /*interp=*/false,
+                           kSpreadMaxItemImage, s));
   }
 
   // coils and k-space
@@ -557,7 +558,8 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
       NRS_TRY(upload(p->kcolmask, cm, s));
     }
     for (int j = 0; j < p->P; ++j) {
-      NRS_TRY(build_pointset(p, all[(size_t)j], &p->kpts[j], ktiles, &uni, /*interp=*/true, s));
+      NRS_TRY(build_pointset(p, all[(size_t)j], &p->kpts[j], ktiles, &uni, /*interp=*/true,
+                             kSpreadMaxItem, s));
       std::vector<HostPoint>().swap(all[(size_t)j]);
     }
   }

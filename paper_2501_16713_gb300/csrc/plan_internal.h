@@ -268,8 +268,12 @@ PhaseTable kspace_phase_table(const nrsense_plan_s* p, int phase, bool spread);
 // space) on grids of at least 16 + W - 1 points per axis, 8 otherwise
 int spread_tile_edge(int W, int C, int gmin);
 constexpr int kSpreadTile = 8;
-// largest number of list entries one spreading CTA processes
+// largest number of list entries one spreading work item processes (heavier
+// tiles are split and their partial tiles summed): k space, and the image
+// space, whose 16^3 tiles hold a few thousand entries each and whose
+// single-channel partial sums cost more than the longer items (measured)
 constexpr int kSpreadMaxItem = 1024;
+constexpr int kSpreadMaxItemImage = 4096;
 // largest number of points one interpolation CTA processes
 constexpr int kInterpMaxItem = 1024;
 

@@ -293,3 +293,33 @@ def test_autotune_choices_compute_the_same_values(tmp_path):
     t.spread_variant, t.interp_coils = 5, 8  # no such spread variant
     assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == -1
     plan.close()
+
+
+def test_image_heavy_tiles_are_split():
+    # displacements pulling every voxel toward the centre: the displaced
+    # positions 2 (n + d) = 0.2 n + 14.4 fill grid cells 13..20 of every axis,
+    # across the boundary of the two 16-point tiles per axis, so each of the
+    # 2^3 image-space tiles lists 2197 to 4096 voxels per phase, 6591 to
+    # 12288 entries for three phases: every tile is split into work items
+    # and the partial tiles are summed
+    shape = (16, 16, 16)
+    n = np.indices(shape).astype(np.float32)
+    d = 0.9 * (8.0 - n)
+    disp = [d, d + np.float32(0.05), d - np.float32(0.05)]
+    plan = make_plan({"disp": disp}, shape)
+    geo = O.Geometry(shape)
+    rng = np.random.default_rng(12)
+    w = crandn(rng, (3,) + shape)
+    ref = sum(O.warp_adjoint(geo, w[j], disp[j].astype(np.float64)) for j in range(3))
+    from paper_2501_16713_gb300.nrsense import Tuning
+    import ctypes
+    for warp_variant in (0, 1):  # CTA per tile, CTA per plane pair
+        t = Tuning()
+        t.spread_variant, t.interp_coils, t.spread_image_warp = 3, 8, warp_variant
+        assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == 0
+        xa = plan.warp_adjoint(to_dev(w)).cpu().numpy()
+        e = rel_l2(xa, ref)
+        print(f"image-space adjoint with split tiles, variant {warp_variant}: rel L2 {e:.2e}")
+        assert e < TOL_FP32
+    assert plan.device_status() == 0
+    plan.close()
