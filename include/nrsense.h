@@ -363,8 +363,12 @@ nrsense_status nrsense_cnn_launches(nrsense_cnn_t net, int64_t* out_host);
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.  All calls
  * on a device share the one array: calls that overlap on the GPU (different
- * streams, no ordering) race and must not be issued.  Returns NRSENSE_ERR_CUDA
- * if the address lookup or a launch fails.
+ * streams, no ordering) race and must not be issued.  The looked-up address
+ * is cached per device for the life of the process; after a cudaDeviceReset
+ * of that device the cache is stale and the call must not be used again in
+ * that process.  Returns NRSENSE_ERR_CUDA if a CUDA error from earlier work is
+ * pending when it is called (nothing is launched then), or if the address
+ * lookup or a launch fails.
  */
 #define NRSENSE_DOT_NOALLOC_MAX_N (16384LL * 4096LL)
 nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* y_dev, int64_t n,
@@ -481,6 +485,14 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t plan, const nrsense_tuning
  *   on exit.  *eig_host receives the last q (a lower bound of lambda_max that
  *   converges to it).  Synchronises the call's stream.
  *
+ * nrsense_fista_lipschitz - the step bound L = 2 margin q of the FISTA
+ *   iteration, q from nrsense_normal_max_eig(plan, v_dev, iters) (same
+ *   arguments and behaviour, v_dev overwritten).  The gradient of
+ *   ||y - A x||^2 is 2 (E0 x - b), so its Lipschitz constant is 2 lambda_max(E0);
+ *   q approaches lambda_max from below and margin >= 1 (e.g. 1.02) covers the
+ *   rest.  *lipschitz_host receives L.  ERR_ARG: margin < 1 or not finite,
+ *   or an argument nrsense_normal_max_eig rejects.
+ *
  * nrsense_solve_fista - `maxit` FISTA iterations (0 .. 2^20).
  *   y_dev      data, layout of nrsense_apply_forward's output (device).
  *   lambda     L1 weight (>= 0).
@@ -505,6 +517,8 @@ nrsense_status nrsense_wavelet_shrink(const nrsense_c64* v_dev, nrsense_c64* u_d
                                       void* stream);
 nrsense_status nrsense_normal_max_eig(nrsense_plan_t plan, nrsense_c64* v_dev, int32_t iters,
                                       double* eig_host, void* stream);
+nrsense_status nrsense_fista_lipschitz(nrsense_plan_t plan, nrsense_c64* v_dev, int32_t iters,
+                                      double margin, double* lipschitz_host, void* stream);
 nrsense_status nrsense_solve_fista(nrsense_plan_t plan, const nrsense_c64* y_dev, double lambda,
                                    int32_t levels, double lipschitz, int32_t maxit,
                                    uint32_t flags, nrsense_c64* x_dev, double* hist_host,

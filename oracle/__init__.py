@@ -25,8 +25,7 @@ Gridding for Nonrigid Motion-Corrected MR Image Reconstruction"
 * solvers.py    - conjugate gradients on the normal equations of the stacked
                   model with a Tikhonov term.
 
-Readings of the paper where it is silent are stated where they are used and
-collected in DESIGN.md.
+Readings of the paper where it is silent are stated where they are used.
 """
 
 from .kernel import bessel_i0, bessel_i0m1, beatty_beta, kb_kernel, kb_kernel_ft  # noqa: F401

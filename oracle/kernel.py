@@ -6,7 +6,7 @@ Cores and its Fourier transform C for deapodization (Notations table;
 of the interpolation kernel).  The kernel family is Kaiser-Bessel, the kernel
 of Beatty et al. whose notation the paper adapts.
 
-Reading (stated in the design doc): the Kaiser-Bessel shape minus its edge value,
+Reading (the paper names the family, not its exact form): the Kaiser-Bessel shape minus its edge value,
 
     c(u) = I0(beta * sqrt(1 - (2u/W)^2)) - 1   for |u| <= W/2,   0 otherwise,
 

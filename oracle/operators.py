@@ -18,7 +18,7 @@ Image-space gridding (section "Image-space Gridding"):
     transpose of the above, i.e. spread, forward DFT of size G scaled by 1/N,
     crop to K_N, divide by C(k/G), unnormalised inverse DFT of size N.
 
-Readings (collected in the design doc): forward DFT uses exp(-2 pi i ...); the
+Readings of the paper where it is silent: forward DFT uses exp(-2 pi i ...); the
 inverse DFT of size G is scaled by 1/N so that T_j with zero displacement is
 the identity up to the kernel's aliasing error; the -N/2 bin of K_N maps to
 frequency -N/2 of the G grid; boundaries are periodic (positions mod N, taps

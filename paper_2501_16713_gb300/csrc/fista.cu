@@ -768,6 +768,17 @@ nrsense_status nrsense_normal_max_eig(nrsense_plan_t p, nrsense_c64* v, int32_t 
   return NRSENSE_OK;
 }
 
+nrsense_status nrsense_fista_lipschitz(nrsense_plan_t p, nrsense_c64* v, int32_t iters,
+                                      double margin, double* lipschitz, void* stream) {
+  if (lipschitz == nullptr || !(margin >= 1.0) || !std::isfinite(margin)) return NRSENSE_ERR_ARG;
+  double q = 0.0;
+  NRS_TRY(nrsense_normal_max_eig(p, v, iters, &q, stream));
+  // the gradient of ||y - A x||^2 is 2 (E0 x - b): its Lipschitz constant is
+  // 2 lambda_max(E0); q approaches lambda_max from below, hence the margin
+  *lipschitz = 2.0 * margin * q;
+  return NRSENSE_OK;
+}
+
 nrsense_status nrsense_solve_fista(nrsense_plan_t p, const nrsense_c64* y, double lambda,
                                    int32_t levels, double lipschitz, int32_t maxit, uint32_t flags,
                                    nrsense_c64* x, double* hist_host, void* stream) {

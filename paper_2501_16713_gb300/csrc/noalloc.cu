@@ -103,7 +103,9 @@ __global__ void __launch_bounds__(kNaThreads) noalloc_dot_final(const double* __
 }
 
 // Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached for the life of the
+// process.  The cache does not survive a cudaDeviceReset of that device: the
+// module is loaded again afterwards and the array may move.
 nrsense_status partials_address(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return NRSENSE_ERR_CUDA;
@@ -127,6 +129,9 @@ extern "C" nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nr
                                               int64_t n, double* out_dev, void* stream) {
   if (x_dev == nullptr || y_dev == nullptr || out_dev == nullptr || n < 0) return NRSENSE_ERR_ARG;
   if (n > NRSENSE_DOT_NOALLOC_MAX_N) return NRSENSE_ERR_ARG;  // beyond the fixed scratch
+  // an error left by earlier, unrelated work is reported as such, before
+  // anything is launched, instead of being taken for a failure of this call
+  if (cudaPeekAtLastError() != cudaSuccess) return NRSENSE_ERR_CUDA;
   double* partials = nullptr;
   const nrsense_status st = partials_address(&partials);
   if (st != NRSENSE_OK) return st;

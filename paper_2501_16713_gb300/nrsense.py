@@ -117,6 +117,8 @@ _SIGS = {
     "nrsense_wavelet_shrink": [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                ctypes.c_double, _VP],
     "nrsense_normal_max_eig": [_VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _VP],
+    "nrsense_fista_lipschitz": [_VP, _VP, ctypes.c_int32, ctypes.c_double,
+                                ctypes.POINTER(ctypes.c_double), _VP],
     "nrsense_dcf": [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP],
     "nrsense_set_circulant": [_VP, ctypes.c_double, ctypes.c_int32, _VP],
     "nrsense_apply_circulant": [_VP, _VP, _VP, _VP],
@@ -202,18 +204,28 @@ DOT_NOALLOC_MAX_N = 16384 * 4096
 
 def dot_noalloc(x, y, out=None, stream=None):
     """<x, y> in FP64 through nrsense_dot_noalloc (no plan, no allocation by
-    the library).  x, y: contiguous complex64 CUDA tensors of equal size;
-    out: a float64 CUDA tensor of 2 elements (allocated here if omitted -- the
-    library call itself allocates nothing).  Returns out."""
+    the library).  x, y: contiguous complex64 CUDA tensors of equal size on
+    one device; out: a float64 CUDA tensor of 2 elements on that device
+    (allocated here if omitted -- the library call itself allocates nothing).
+    The call runs with x's device current (on that device's current stream
+    unless `stream` is given).  Returns out."""
     import torch
     lib = load()
     _need(x, torch.complex64, None, "x")
     _need(y, torch.complex64, tuple(x.shape), "y")
+    if y.device != x.device:
+        raise ValueError(f"y is on {y.device}, x on {x.device}")
     if out is None:
         out = torch.empty(2, dtype=torch.float64, device=x.device)
     _need(out, torch.float64, (2,), "out")
-    _check(lib.nrsense_dot_noalloc(_ptr(x), _ptr(y), int(x.numel()), _ptr(out), _stream(stream)),
-           "nrsense_dot_noalloc")
+    if out.device != x.device:
+        raise ValueError(f"out is on {out.device}, x on {x.device}")
+    with torch.cuda.device(x.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        _check(lib.nrsense_dot_noalloc(_ptr(x), _ptr(y), int(x.numel()), _ptr(out),
+                                       _stream(stream)),
+               "nrsense_dot_noalloc")
     return out
 
 
@@ -665,13 +677,16 @@ class Plan:
         return e.value, v0
 
     def lipschitz(self, iters=30, seed=0, margin=1.02, stream=None):
-        """L = 2 margin lambda_max(sum_j A_j^H A_j), lambda_max by power
-        iteration from a seeded random start (the FISTA step bound)."""
+        """The FISTA step bound L = 2 margin lambda_max(sum_j A_j^H A_j)
+        (nrsense_fista_lipschitz), power iteration from a seeded random start."""
         import torch
         g = torch.Generator(device="cuda").manual_seed(int(seed))
         v = torch.randn(self.shape, dtype=torch.complex64, device="cuda", generator=g)
-        lam_max, _ = self.max_eig(v, iters, stream=stream)
-        return 2.0 * margin * lam_max
+        L = ctypes.c_double()
+        _check(self.lib.nrsense_fista_lipschitz(self._h, _ptr(v), int(iters), float(margin),
+                                                ctypes.byref(L), _stream(stream)),
+               "nrsense_fista_lipschitz")
+        return L.value
 
     def solve_fista(self, y, lam, levels=3, L=None, maxit=400, x0=None, graph=True, stream=None,
                     out=None):

@@ -53,7 +53,8 @@ def test_circulant_matches_oracle():
     z_ref = Pc.apply_circulant(d, r.astype(np.complex128))
     e = rel_l2(z, z_ref)
     print(f"circulant rel L2 {e:.2e}")
-    assert e < 2e-3
+    # FP32 operator, FFTs and PSF against FP64: measured 1.4e-6
+    assert e < 1e-5
     plan.close()
 
 

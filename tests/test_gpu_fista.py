@@ -121,6 +121,23 @@ def test_power_iteration_matches_oracle(sense_prob):
     assert abs(est - p["lam_max"]) < 1e-5 * p["lam_max"]
 
 
+def test_lipschitz_bound_matches_oracle(sense_prob):
+    # the library forms the step bound L = 2 margin lambda_max itself
+    import ctypes
+    from paper_2501_16713_gb300 import nrsense
+    p = sense_prob
+    v = to_dev(p["v0"])
+    lib = nrsense.load()
+    L = ctypes.c_double()
+    st = lib.nrsense_fista_lipschitz(p["plan"]._h, ctypes.c_void_p(v.data_ptr()), 20,
+                                     ctypes.c_double(1.05), ctypes.byref(L), None)
+    assert st == 0
+    assert abs(L.value - 2.0 * 1.05 * p["lam_max"]) < 1e-5 * L.value
+    # a margin below 1 would give a bound under 2 lambda_max: rejected
+    assert lib.nrsense_fista_lipschitz(p["plan"]._h, ctypes.c_void_p(v.data_ptr()), 20,
+                                       ctypes.c_double(0.9), ctypes.byref(L), None) == -1
+
+
 @pytest.mark.parametrize("levels", [2, 3])
 def test_fista_matches_oracle(sense_prob, levels):
     p = sense_prob

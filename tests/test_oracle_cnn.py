@@ -102,6 +102,41 @@ def test_adam_first_step_textbook():
     assert new[0][1].item() == pytest.approx(0.5 + 0.01, abs=1e-9)
 
 
+def test_adam_three_steps_textbook_values():
+    # Kingma & Ba's Algorithm 1 worked by hand (decimal arithmetic) for one
+    # scalar weight, lr 0.01, betas 0.9 / 0.999, eps 1e-8, gradients 0.3, -0.1, 0.2:
+    #   t=1: m=0.03,   v=0.00009,     m^=0.3,        v^=0.09
+    #   t=2: m=0.017,  v=0.00009991,  m^=0.017/0.19, v^=0.00009991/0.001999
+    #   t=3: m=0.0353, v=0.00013981009, m^=0.0353/0.271, v^=0.00013981009/0.002997001
+    # A bias correction that ignores t, or one applied to the wrong moment,
+    # changes steps 2 and 3.
+    expect = [(0.03, 0.00009, 0.9900000003333333222),
+              (0.017, 0.00009991, 0.9859978147928080520),
+              (0.0353, 0.00013981009, 0.9799669501576138839)]
+    params = [(np.array([[[[[1.0]]]]]), np.array([0.0]))]
+    state = cnn.adam_init(params)
+    for g, (m, v, w) in zip((0.3, -0.1, 0.2), expect):
+        grads = [(np.array([[[[[g]]]]]), np.array([0.0]))]
+        params, state = cnn.adam_step(params, grads, state, lr=0.01)
+        assert state[1][0][0].item() == pytest.approx(m, rel=1e-12)
+        assert state[2][0][0].item() == pytest.approx(v, rel=1e-12)
+        assert params[0][0].item() == pytest.approx(w, abs=1e-15)
+    assert state[0] == 3
+
+
+def test_adam_constant_gradient_moves_by_lr_every_step():
+    # with a constant gradient g the bias-corrected moments are exactly g and
+    # g^2 at every t, so each step moves by lr * sign(g) (up to eps)
+    params = [(np.array([[[[[0.2, -0.4]]]]]), np.array([1.5]))]
+    grads = [(np.array([[[[[2.5, -0.8]]]]]), np.array([-7.0]))]
+    state = cnn.adam_init(params)
+    for t in range(1, 6):
+        params, state = cnn.adam_step(params, grads, state, lr=0.05)
+        w, b = params[0]
+        assert w.ravel() == pytest.approx([0.2 - 0.05 * t, -0.4 + 0.05 * t], abs=1e-8)
+        assert b.item() == pytest.approx(1.5 + 0.05 * t, abs=1e-8)
+
+
 def test_bf16_round_matches_torch():
     torch = pytest.importorskip("torch")
     rng = _rng(7)

@@ -7,8 +7,13 @@ fixed array inside the library.  Here it is called through the C ABI and
 compared with the existing entry point that runs the same FP64 inner-product
 kernel on plan-owned scratch: the true residual ||b - E x|| / ||b|| that
 nrsense_solve_cg reports must equal sqrt(<r, r> / <b, b>) computed by two
-calls in a row.  This file is collected last so that a run stopping at the
-first failure has already run every other test.
+calls in a row.  Lengths that span several 4096-element blocks and end in a
+partial block exercise the shared array across blocks; a long call followed
+by a short one would expose stale partial sums.  The inputs are exact in
+FP64, so each result is compared with a complex128 reduction of the same
+vectors to FP64 rounding (1e-12 of sum |x_i| |y_i|).  This file is collected
+last so that a run stopping at the first failure has already run every
+other test.
 """
 
 import ctypes
@@ -64,15 +69,11 @@ def test_noalloc_dot_matches_cg_true_residual():
     assert abs(np.sqrt(rr[0] / bb[0]) - tres) <= TOL_FP32 * tres
     # each call against a plain FP64 reduction of the same vectors
     for v, o in ((r, rr), (b, bb)):
-        ref = torch.vdot(v.flatten().to(torch.complex128), v.flatten().to(torch.complex128))
-        assert abs(o[0] - ref.real.item()) <= TOL_FP32 * abs(ref.real.item())
-        assert abs(o[1]) <= TOL_FP32 * abs(ref.real.item())
+        _check_fp64(o, v.flatten(), v.flatten())
     # two more calls in a row, on a complex-valued product, leave no stale state
     for a, c in ((x, b), (b, x)):
         assert _dot(lib, a, c, out_r) == 0
-        ref = torch.vdot(a.flatten().to(torch.complex128), c.flatten().to(torch.complex128))
-        got = out_r.cpu().numpy()
-        assert abs(complex(got[0], got[1]) - complex(ref.item())) <= TOL_FP32 * abs(ref.item())
+        _check_fp64(out_r.cpu().numpy(), a.flatten(), c.flatten())
     plan.close()
 
 
@@ -92,3 +93,45 @@ def test_noalloc_dot_limits():
                                    ctypes.c_int64(0), ctypes.c_void_p(out.data_ptr()), s) == 0
     torch.cuda.synchronize()
     assert out.cpu().tolist() == [0.0, 0.0]
+
+
+def _rand(n, seed):
+    import torch
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    return torch.randn(n, dtype=torch.complex64, device="cuda", generator=gen)
+
+
+def _check_fp64(got, a, c):
+    import torch
+    a64, c64_ = a.to(torch.complex128), c.to(torch.complex128)
+    ref = complex(torch.vdot(a64, c64_).item())
+    scale = float((a64.abs() * c64_.abs()).sum().item())
+    assert abs(complex(got[0], got[1]) - ref) <= 1e-12 * scale, (got, ref, scale)
+
+
+def test_noalloc_dot_many_blocks_and_partial_tail():
+    import torch
+    from paper_2501_16713_gb300 import nrsense
+    lib = nrsense.load()
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    # long before short: the short call's final sum must not see the long
+    # call's partial sums left in the array
+    for n, seed in ((2 ** 20 + 5, 1), (3 * 4096 + 17, 2), (4096 + 1, 3), (4095, 4), (1, 5),
+                    (2 ** 20 + 5, 6), (4 * 4096, 7)):
+        a, c = _rand(n, seed), _rand(n, seed + 100)
+        assert _dot(lib, a, c, out) == 0
+        _check_fp64(out.cpu().numpy(), a, c)
+
+
+def test_noalloc_dot_python_wrapper_matches_abi():
+    import torch
+    from paper_2501_16713_gb300 import nrsense
+    lib = nrsense.load()
+    a, c = _rand(3 * 4096 + 17, 11), _rand(3 * 4096 + 17, 12)
+    raw = torch.empty(2, dtype=torch.float64, device="cuda")
+    assert _dot(lib, a, c, raw) == 0
+    got = nrsense.dot_noalloc(a, c)
+    torch.cuda.synchronize()
+    assert torch.equal(got, raw)
+    with pytest.raises(ValueError):
+        nrsense.dot_noalloc(a, c[:-1])
