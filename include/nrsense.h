@@ -429,8 +429,13 @@ typedef struct {
   double  spread_ms[3];    /* measured: register, shared, register per plane */
   double  interp_ms[2];    /* measured, per-value staging: 8 coils, 4 coils */
   double  interp_tma_ms[2];/* measured, TMA staging: 8 coils, 4 coils (-1: not available) */
-  int32_t spread_image_warp;   /* image-space spread: 0 CTA per tile, 1 CTA per plane pair */
-  double  spread_image_ms[2];  /* measured: CTA per tile, CTA per plane pair */
+  int32_t spread_image_warp;   /* image-space spread: 0 CTA per tile, 1 CTA per plane pair
+                                  (both over per-tile halo lists), 2 home tiles (every displaced
+                                  voxel spread once by the warp of the 8^3 tile holding its first
+                                  tap, super-tile rims summed by a second kernel; W = 4 and not
+                                  compensated; set_tuning rejects 2 elsewhere) */
+  double  spread_image_ms[3];  /* measured: CTA per tile, CTA per plane pair, home tiles
+                                  (-1: n/a) */
   int32_t fft_pruned;          /* 1: own pruned coil-grid transforms with the coil fan-out and
                                   combination fused (sigma 2, power-of-two grid sizes 32..256,
                                   FP32 grids); 0: cuFFT plus the fan-out / combination kernels */

@@ -34,6 +34,7 @@ SOURCES = [
     "fista.cu",
     "motion.cu",
     "fft_pruned.cu",
+    "spread_home.cu",
 ]
 HEADERS = ["common.cuh", "plan_internal.h", "kb_host.h"]
 

@@ -21,6 +21,15 @@ using namespace nrs;
 
 namespace {
 
+// image-space spread variant <-> nrsense_tuning.spread_image_warp (0 CTA per
+// tile, 1 CTA per plane pair, 2 home tiles)
+int image_variant_of(int tuning) {
+  return tuning == 2 ? kSpreadHome : tuning == 1 ? kSpreadRegisterWarp : kSpreadShared;
+}
+int image_tuning_of(int variant) {
+  return variant == kSpreadHome ? 2 : variant == kSpreadRegisterWarp ? 1 : 0;
+}
+
 #define NRS_TRY(expr)                  \
   do {                                 \
     nrsense_status _st = (expr);       \
@@ -175,10 +184,14 @@ nrsense_status warp_adjoint(nrsense_plan_s* p, const nrsense_c64* m, nrsense_c64
     STAGE(VECTOR, launch_sum_phases(g, p->P, m, x, s));
     return launched();
   }
-  const PhaseTable t = image_table(p);
-  STAGE(SPREAD_IMAGE, launch_spread(g, p->W, p->kc, 1, p->itiles, t, m, p->b_ugrid, false,
-                                    p->comp_spread, p->spread_image_variant, p->b_scratch,
-                                    p->d_status, s));
+  if (p->spread_image_variant == kSpreadHome && p->home_ok) {
+    STAGE(SPREAD_IMAGE, launch_spread_home(g, p->kc, p->ihome, m, p->b_ugrid, p->home_scratch, s));
+  } else {
+    const PhaseTable t = image_table(p);
+    STAGE(SPREAD_IMAGE, launch_spread(g, p->W, p->kc, 1, p->itiles, t, m, p->b_ugrid, false,
+                                      p->comp_spread, p->spread_image_variant, p->b_scratch,
+                                      p->d_status, s));
+  }
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_ugrid, p->b_ugrid, CUFFT_FORWARD));
   STAGE(CROP_DEAPOD, launch_crop_deapod(g, p->deapod, p->b_ugrid, x, s));
@@ -362,10 +375,11 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
                           : kSpreadRegisterWarp;
   p->interp_coils = t->interp_coils;
   p->interp_tma = t->interp_tma == 1 && p->tma_ok;
-  if (t->spread_image_warp != 0 && t->spread_image_warp != 1) return NRSENSE_ERR_ARG;
+  if (t->spread_image_warp < 0 || t->spread_image_warp > 2) return NRSENSE_ERR_ARG;
+  if (t->spread_image_warp == 2 && !p->home_ok) return NRSENSE_ERR_ARG;
   if (t->fft_pruned != 0 && t->fft_pruned != 1) return NRSENSE_ERR_ARG;
   if (t->fft_pruned == 1 && !p->fft_pruned_ok) return NRSENSE_ERR_ARG;
-  p->spread_image_variant = t->spread_image_warp ? kSpreadRegisterWarp : kSpreadShared;
+  p->spread_image_variant = image_variant_of(t->spread_image_warp);
   p->fft_pruned = t->fft_pruned == 1;
   return NRSENSE_OK;
 }
@@ -380,7 +394,8 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
                                                              : NRSENSE_TUNE_SPREAD_REGISTER_WARP;
   out->interp_coils = p->interp_coils;
   out->interp_tma = p->interp_tma ? 1 : 0;
-  out->spread_image_warp = p->spread_image_variant == kSpreadRegisterWarp ? 1 : 0;
+  out->spread_image_warp = image_tuning_of(p->spread_image_variant);
+  out->spread_image_ms[2] = -1.0;
   out->fft_pruned = p->fft_pruned ? 1 : 0;
   out->fft_ms[0] = out->fft_ms[1] = -1.0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -392,11 +407,16 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
       return NRSENSE_ERR_CUDA;
     const PhaseTable tim = image_table(p);
-    const int iv[2] = {kSpreadShared, kSpreadRegisterWarp};
-    for (int k = 0; k < 2; ++k) {
+    const int iv[3] = {kSpreadShared, kSpreadRegisterWarp, kSpreadHome};
+    for (int k = 0; k < 3; ++k) {
+      if (iv[k] == kSpreadHome && !p->home_ok) break;
       auto run = [&] {
-        p->launches += launch_spread(g, p->W, p->kc, 1, p->itiles, tim, p->b_m, p->b_ugrid, false,
-                                     p->comp_spread, iv[k], p->b_scratch, p->d_status, s);
+        if (iv[k] == kSpreadHome)
+          p->launches += launch_spread_home(g, p->kc, p->ihome, p->b_m, p->b_ugrid,
+                                            p->home_scratch, s);
+        else
+          p->launches += launch_spread(g, p->W, p->kc, 1, p->itiles, tim, p->b_m, p->b_ugrid,
+                                       false, p->comp_spread, iv[k], p->b_scratch, p->d_status, s);
       };
       run();
       cudaEventRecord(a, s);
@@ -412,9 +432,10 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    p->spread_image_variant =
-        out->spread_image_ms[1] < out->spread_image_ms[0] ? kSpreadRegisterWarp : kSpreadShared;
-    out->spread_image_warp = p->spread_image_variant == kSpreadRegisterWarp ? 1 : 0;
+    int bi = out->spread_image_ms[1] < out->spread_image_ms[0] ? 1 : 0;
+    if (out->spread_image_ms[2] >= 0.0 && out->spread_image_ms[2] < out->spread_image_ms[bi]) bi = 2;
+    p->spread_image_variant = iv[bi];
+    out->spread_image_warp = image_tuning_of(p->spread_image_variant);
   }
   if (p->C == 0) return NRSENSE_OK;  // nothing more to choose without k space
   const int j1 = std::min(p->P, p->phase_chunk);

@@ -82,6 +82,22 @@ struct PhaseTable {
   int nphase;
 };
 
+// Image-space points (the displaced voxels of all phases) sorted by the 8^3
+// home tile of their first tap, then by cell; home tiles are grouped 2 x 2 x 2
+// into 16^3 super-tiles (spread_home.cu).
+struct HomeSet {
+  const float4* qs;       // sorted: (f0, f1, f2, packed first tap)
+  const int32_t* perm;    // sorted index -> value row
+  const int32_t* tstart;  // per home tile: first sorted index (nt0 nt1 nt2 + 1 entries)
+  int nt0, nt1, nt2;      // home tiles per axis (ceil(G / 8))
+  int ns0, ns1, ns2;      // super-tiles per axis (ceil(G / 16))
+  // per grid coordinate of each axis: (count, covers...) with every cover
+  // packed as super-tile * 32 + position in its 19-point padded extent
+  const int4* cover0;
+  const int4* cover1;
+  const int4* cover2;
+};
+
 // Phase slot of work item `i` of a launch (linear search; nphase is small).
 __device__ __forceinline__ int phase_of(const int* prefix, int nphase, int i) {
   int jj = 0;

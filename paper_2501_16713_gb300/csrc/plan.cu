@@ -389,6 +389,87 @@ nrsense_status build_pointset(nrsense_plan_s* p, std::vector<HostPoint>& pts, Po
   return NRSENSE_OK;
 }
 
+// Image-space points sorted by the 8^3 home tile of their first tap, then by
+// cell (the order of the home-tile spread, spread_home.cu), with the first
+// sorted index of every home tile, and the super-tile scratch.
+nrsense_status build_home_set(nrsense_plan_s* p, const std::vector<HostPoint>& pts,
+                              cudaStream_t s) {
+  const Geo& g = p->geo;
+  HomeSet& hs = p->ihome;
+  hs.nt0 = (g.g0 + 7) / 8;
+  hs.nt1 = (g.g1 + 7) / 8;
+  hs.nt2 = (g.g2 + 7) / 8;
+  hs.ns0 = (g.g0 + 15) / 16;
+  hs.ns1 = (g.g1 + 15) / 16;
+  hs.ns2 = (g.g2 + 15) / 16;
+  const long long ntl = (long long)hs.nt0 * hs.nt1 * hs.nt2;
+  const long long npts = (long long)pts.size();
+  // (key << 32 | index): sorting by it is stable in the input order
+  std::vector<uint64_t> ko(npts);
+  std::vector<int32_t> tstart(ntl + 1, 0);
+  for (long long i = 0; i < npts; ++i) {
+    const HostPoint& h = pts[i];
+    const long long t = ((long long)(h.b[0] >> 3) * hs.nt1 + (h.b[1] >> 3)) * hs.nt2 + (h.b[2] >> 3);
+    const int cell = (((h.b[0] & 7) * 8) + (h.b[1] & 7)) * 8 + (h.b[2] & 7);
+    ko[i] = (uint64_t(t * 512 + cell) << 32) | uint64_t(i);
+    tstart[t + 1]++;
+  }
+  std::sort(ko.begin(), ko.end());
+  for (long long t = 0; t < ntl; ++t) tstart[t + 1] += tstart[t];
+  std::vector<float4> qs(std::max<long long>(npts, 1));
+  std::vector<int32_t> perm(std::max<long long>(npts, 1));
+  for (long long k = 0; k < npts; ++k) {
+    const HostPoint& h = pts[ko[k] & 0xffffffffu];
+    const uint32_t packed = pack_base(h.b[0], h.b[1], h.b[2]);
+    float w;
+    std::memcpy(&w, &packed, sizeof(w));
+    qs[k] = make_float4(h.f[0], h.f[1], h.f[2], w);
+    perm[k] = h.row;
+  }
+  std::vector<uint64_t>().swap(ko);
+  float4* dq = nullptr;
+  int32_t *dp = nullptr, *dt = nullptr;
+  NRS_TRY(dev_alloc_n(p, &dq, (long long)qs.size()));
+  NRS_TRY(dev_alloc_n(p, &dp, (long long)perm.size()));
+  NRS_TRY(dev_alloc_n(p, &dt, ntl + 1));
+  NRS_TRY(upload(dq, qs, s));
+  NRS_TRY(upload(dp, perm, s));
+  NRS_TRY(upload(dt, tstart, s));
+  hs.qs = dq;
+  hs.perm = dp;
+  hs.tstart = dt;
+  // per axis and coordinate: the super-tiles whose 3-point-padded extents
+  // cover it (directly or wrapped around the periodic grid), increasing
+  const int gsz[3] = {g.g0, g.g1, g.g2}, nsz[3] = {hs.ns0, hs.ns1, hs.ns2};
+  const int4** cov[3] = {&hs.cover0, &hs.cover1, &hs.cover2};
+  for (int a = 0; a < 3; ++a) {
+    std::vector<int4> tab(gsz[a]);
+    for (int x = 0; x < gsz[a]; ++x) {
+      int e[3] = {0, 0, 0}, n = 0;
+      for (int c = 0; c < nsz[a]; ++c) {
+        const int o = 16 * c, ext = std::min(16, gsz[a] - o);
+        for (int u : {x, x + gsz[a]})
+          if (u >= o && u < o + ext + 3) {
+            if (n == 3) return NRSENSE_ERR_ARG;  // cannot happen for grids >= 11 points
+            e[n++] = c * 32 + (u - o);
+          }
+      }
+      tab[x] = make_int4(n, e[0], e[1], e[2]);
+    }
+    int4* dtab = nullptr;
+    NRS_TRY(dev_alloc_n(p, &dtab, (long long)tab.size()));
+    NRS_TRY(upload(dtab, tab, s));
+    if (cudaStreamSynchronize(s) != cudaSuccess) return NRSENSE_ERR_CUDA;
+    *cov[a] = dtab;
+  }
+  NRS_TRY(dev_alloc_n(p, &p->home_scratch, home_scratch_elems(hs)));
+  if (configure_home_kernels() != cudaSuccess) return NRSENSE_ERR_CUDA;
+  p->home_ok = true;
+  // host vectors are freed on return: wait for the uploads
+  if (cudaStreamSynchronize(s) != cudaSuccess) return NRSENSE_ERR_CUDA;
+  return NRSENSE_OK;
+}
+
 nrsense_status cufft_check(cufftResult r) {
   return r == CUFFT_SUCCESS ? NRSENSE_OK : NRSENSE_ERR_CUFFT;
 }
@@ -491,6 +572,11 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     }
     NRS_TRY(build_pointset(p, pts, &p->ipts, itiles, nullptr, /*interp=*/false,
                            kSpreadMaxItemImage, s));
+    // home-tile spread (W = 4, plain FP32 accumulation); the default where built
+    if (p->W == 4 && !p->comp_spread) {
+      NRS_TRY(build_home_set(p, pts, s));
+      p->spread_image_variant = kSpreadHome;
+    }
   }
 
   // coils and k-space

@@ -71,6 +71,9 @@ struct nrsense_plan_s {
   long long Mtot = 0;
   std::vector<nrs::PointSet> kpts;  // per phase
   nrs::PointSet ipts;               // displaced voxels of all phases
+  nrs::HomeSet ihome{};             // the same, sorted by 8^3 home tile (home-tile spread)
+  bool home_ok = false;             // ihome built (W = 4, not compensated)
+  nrsense_c64* home_scratch = nullptr;  // super-tile rims of the home-tile spread
   nrs::TilePlan ktiles{}, itiles{};  // k-space and image-space tiles
   int phase_chunk = 1;              // phases per launch
 
@@ -89,8 +92,9 @@ struct nrsense_plan_s {
   bool grid_bf16 = false;     // desc.precision == NRSENSE_BF16_STORE
   int spread_variant = 1;     // kSpreadRegister or kSpreadShared (autotuned)
   int interp_coils = 8;       // coils per interpolation CTA (autotuned)
-  int spread_image_variant = 2;  // image-space spread: kSpreadShared (CTA per tile) or
-                                 // kSpreadRegisterWarp (CTA per plane pair) (autotuned)
+  int spread_image_variant = 2;  // image-space spread: kSpreadShared (CTA per tile),
+                                 // kSpreadRegisterWarp (CTA per plane pair) or kSpreadHome
+                                 // (home tiles, spread_home.cu) (autotuned)
   bool interp_tma = false;    // TMA-staged interpolation (autotuned; needs tma_ok)
   bool tma_ok = false;        // tensor maps of b_xwork built
   CUtensorMap tmap_xwork4{}, tmap_xwork8{}, tmap_xwork2{};  // boxes of 4, 8, 2 coil grids
@@ -225,7 +229,8 @@ int launch_crop_to_coils(const Geo& g, int C, const float* deapod, const void* x
 // compensated accumulation (W = 4 kernels); variant selects register or
 // shared-memory accumulation for the multi-coil W = 4 kernel (register
 // accumulation with a CTA per tile, or with a CTA per tile plane).
-constexpr int kSpreadRegister = 1, kSpreadShared = 2, kSpreadRegisterWarp = 3, kSpreadMMA = 4;
+constexpr int kSpreadRegister = 1, kSpreadShared = 2, kSpreadRegisterWarp = 3, kSpreadMMA = 4,
+              kSpreadHome = 5;
 // a spread variant value carries, in bits 8-15, the warps per CTA of the
 // tensor-core kernel (1, 2 or 4; 0 means 1) and, in bit 16, its geometry
 // (0: a warp per tile plane, 1: a warp per 4^3 sub-block)
@@ -240,6 +245,14 @@ int launch_spread(const Geo& g, int W, const KernelCoefs& kc, int C, const TileP
                   bool comp, int variant, nrsense_c64* scratch, int32_t* status, cudaStream_t s);
 // coils handled by one spreading CTA
 int spread_coil_chunk(int C);
+// home-tile image-space spread (spread_home.cu): all points of `hs` (values at
+// rows perm of vals) into grid; scratch holds home_scratch_elems(hs) values.
+// Returns the kernels launched.
+int launch_spread_home(const Geo& g, const KernelCoefs& kc, const HomeSet& hs,
+                       const nrsense_c64* vals, nrsense_c64* grid, nrsense_c64* scratch,
+                       cudaStream_t s);
+long long home_scratch_elems(const HomeSet& hs);
+cudaError_t configure_home_kernels();
 // own pruned coil-grid transforms (fft_pruned.cu).  Forward: grid slots
 // jj * C + c of phases jj < nph = DFT3(S_c m_jj / C3 zero-padded), through the
 // intermediates t1 (slots x N0 x N1 x G2) and t2 (slots x N0 x G1 x G2).

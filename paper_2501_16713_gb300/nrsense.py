@@ -48,7 +48,7 @@ class Tuning(ctypes.Structure):
                 ("spread_ms", ctypes.c_double * 3), ("interp_ms", ctypes.c_double * 2),
                 ("interp_tma_ms", ctypes.c_double * 2),
                 ("spread_image_warp", ctypes.c_int32),
-                ("spread_image_ms", ctypes.c_double * 2),
+                ("spread_image_ms", ctypes.c_double * 3),
                 ("fft_pruned", ctypes.c_int32), ("fft_ms", ctypes.c_double * 2),
                 ("spread_mma_ms", ctypes.c_double), ("spread_mma_wpc", ctypes.c_int32),
                 ("spread_mma_cube", ctypes.c_int32), ("spread_mma_geo_ms", ctypes.c_double * 2),

@@ -264,17 +264,28 @@ def test_autotune_choices_compute_the_same_values(tmp_path):
     shape = (16, 16, 24)
     case = synth.small_case(shape, 8, 2, [2500, 1800], seed=41)
     plan = make_plan(case, shape)
+    from paper_2501_16713_gb300.nrsense import Tuning
+    import ctypes
+    t = Tuning()
+    t.spread_variant, t.interp_coils, t.interp_tma, t.spread_image_warp = 1, 8, 0, 0
+    assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == 0
     x = to_dev(case["x"])
     y0 = plan.forward(x)
     xa0 = plan.adjoint(y0)
+    # the home-tile image-space spread sums in another order: FP32 agreement,
+    # and bitwise the same result on every call
+    t.spread_image_warp = 2
+    assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == 0
+    xh = plan.adjoint(y0)
+    assert torch.equal(plan.adjoint(y0), xh)
+    assert rel_l2(xh.cpu().numpy(), xa0.cpu().numpy()) < TOL_FP32
     cache = str(tmp_path / "tune.json")
     res = plan.autotune(reps=2, cache=cache)
     # the tensor-core spread (4) may win the timing; it is checked against the
     # oracle in test_gpu_spread_mma.py (FP32-rounding, not bitwise, agreement)
     assert not res["cached"] and res["spread_variant"] in (1, 2, 3, 4)
     assert res["interp_coils"] in (2, 4, 8)
-    from paper_2501_16713_gb300.nrsense import Tuning
-    import ctypes
+    assert res["spread_image_warp"] in (0, 1, 2) and len(res["spread_image_ms"]) == 3
     # grid 32 x 32 x 48 with 8^3 tiles: interior tiles take the TMA-staged
     # halo, tiles at the upper edges the wrapped per-value staging
     for sv in (1, 2, 3):
@@ -313,7 +324,7 @@ def test_image_heavy_tiles_are_split():
     ref = sum(O.warp_adjoint(geo, w[j], disp[j].astype(np.float64)) for j in range(3))
     from paper_2501_16713_gb300.nrsense import Tuning
     import ctypes
-    for warp_variant in (0, 1):  # CTA per tile, CTA per plane pair
+    for warp_variant in (0, 1, 2):  # CTA per tile, CTA per plane pair, home tiles
         t = Tuning()
         t.spread_variant, t.interp_coils, t.spread_image_warp = 3, 8, warp_variant
         assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == 0
@@ -322,4 +333,28 @@ def test_image_heavy_tiles_are_split():
         print(f"image-space adjoint with split tiles, variant {warp_variant}: rel L2 {e:.2e}")
         assert e < TOL_FP32
     assert plan.device_status() == 0
+    plan.close()
+
+
+@pytest.mark.parametrize("shape", [(6, 10, 18), (12, 14, 16), (20, 6, 34)])
+def test_home_tile_spread_ragged_and_wrapped(shape):
+    # grids of 12..68 points per axis: super-tiles of 16 with ragged last
+    # ones (extents 2..12), a single super-tile along an axis, and home-tile
+    # footprints that wrap around the periodic grid (displacements up to 3
+    # voxels plus a rigid shift push points across the faces)
+    from paper_2501_16713_gb300.nrsense import Tuning
+    import ctypes
+    case = synth.small_case(shape, 0, 3, None, seed=131, max_disp=3.0, rigid=2.0)
+    plan = make_plan({"disp": case["disp"]}, shape)
+    geo = O.Geometry(shape)
+    rng = np.random.default_rng(132)
+    w = crandn(rng, (3,) + shape)
+    ref = sum(O.warp_adjoint(geo, w[j], case["disp"][j].astype(np.float64)) for j in range(3))
+    t = Tuning()
+    t.spread_variant, t.interp_coils, t.spread_image_warp = 3, 8, 2
+    assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == 0
+    xa = plan.warp_adjoint(to_dev(w)).cpu().numpy()
+    e = rel_l2(xa, ref)
+    print(f"home-tile image-space adjoint {shape}: rel L2 {e:.2e}")
+    assert e < TOL_FP32
     plan.close()
