@@ -59,7 +59,7 @@ typedef int32_t nrsense_status;
 #define NRSENSE_ERR_BREAKDOWN     -5  /* CG: non-positive curvature or non-finite scalar */
 #define NRSENSE_ERR_NOT_CONVERGED -6  /* CG: maxit reached above tolerance */
 #define NRSENSE_ERR_TIMEOUT       -7  /* a bounded device wait expired */
-#define NRSENSE_ERR_BOUNDS        -8  /* a device bounds check fired */
+/* -8 is not used */
 #define NRSENSE_ERR_STATE         -9  /* call not valid for this plan (e.g. no coils) */
 
 typedef struct { float re, im; } nrsense_c64;
@@ -127,7 +127,14 @@ typedef struct {
  * afterwards), computes the kernel and deapodization tables in FP64 on the
  * host, sorts each phase's samples into spreading tiles and creates cuFFT
  * plans.  Errors: ERR_ARG (bad descriptor, NaN/Inf coordinates or
- * displacements), ERR_OOM, ERR_CUFFT, ERR_CUDA.
+ * displacements), ERR_OOM, ERR_CUFFT, ERR_CUDA; on any error every resource
+ * the call had taken is released.
+ * Test-only environment variables, read at plan creation: NRSENSE_FAULT =
+ * alloc | cufft | upload makes the first device allocation, cuFFT plan
+ * creation or host-to-device upload fail (ERR_OOM, ERR_CUFFT, ERR_CUDA);
+ * NRSENSE_TMA_POLL_LIMIT = n bounds the TMA halo wait of the k-space
+ * interpolation to n polls (0: every TMA-staged CTA records ERR_TIMEOUT,
+ * waits for its copy to land and returns without computing).
  */
 nrsense_status nrsense_plan_create(const nrsense_desc* desc,
                                    const int64_t* n_samples_host,
@@ -591,7 +598,8 @@ nrsense_status nrsense_kmeans(const double* points_host, int64_t n, int32_t k, i
 /*
  * nrsense_device_status - read (and with clear != 0, reset) the plan's
  * latched device status word; synchronises `stream`.  *out_host receives
- * NRSENSE_OK or the first device-side error (ERR_BOUNDS, ERR_TIMEOUT).
+ * NRSENSE_OK or the first device-side error (ERR_TIMEOUT: a bounded wait of
+ * the TMA-staged k-space interpolation expired).
  */
 nrsense_status nrsense_device_status(nrsense_plan_t plan, int32_t clear, int32_t* out_host,
                                      void* stream);

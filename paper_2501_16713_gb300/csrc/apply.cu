@@ -231,7 +231,8 @@ nrsense_status sense_chunk_forward(nrsense_plan_s* p, int j0, int j1, const nrse
   }
   const PhaseTable t = kspace_table(p, j0, j1, /*spread=*/false, row_base);
   STAGE(INTERP_KSPACE, launch_interp_kspace(g, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
-                                            p->grid_bf16, y, p->interp_coils, interp_tmap(p), p->d_status, s));
+                                            p->grid_bf16, y, p->interp_coils, interp_tmap(p), p->d_status, s,
+                                            p->tma_poll_limit));
   return launched();
 }
 
@@ -290,7 +291,8 @@ nrsense_status nrsense_kspace_forward(nrsense_plan_t p, int32_t phase, const nrs
   NRS_TRY(fft_gc(p, 1, p->b_xpad, p->b_xwork, CUFFT_FORWARD, s));
   const PhaseTable t = kspace_table(p, phase, phase + 1, false, p->off[phase]);
   STAGE(INTERP_KSPACE, launch_interp_kspace(p->geo, p->W, p->kc, p->C, p->ktiles, t, p->b_xwork,
-                                            p->grid_bf16, y, p->interp_coils, interp_tmap(p), p->d_status, s));
+                                            p->grid_bf16, y, p->interp_coils, interp_tmap(p), p->d_status, s,
+                                            p->tma_poll_limit));
   return launched();
 }
 

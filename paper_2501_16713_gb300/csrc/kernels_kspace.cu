@@ -6,6 +6,8 @@
 // caller's (C, N^3) layout.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "plan_internal.h"
 
 namespace nrs {
@@ -225,7 +227,9 @@ __global__ void __launch_bounds__(256) interp_tile_kernel(
 // grids (box x extent 12 for 16-byte rows) into shared memory as
 // [c][z][y][x]; an mbarrier tracks the transaction bytes and every thread
 // waits on it with a bounded poll (on expiry the CTA records
-// NRSENSE_ERR_TIMEOUT and returns without computing).  Tiles whose halo wraps
+// NRSENSE_ERR_TIMEOUT, waits again, bounded, for its copy in flight to land
+// in shared memory, and returns without computing).  The first limit is the
+// caller's (at most kTmaMaxPoll polls; a test sets 0 to make it expire).  Tiles whose halo wraps
 // the periodic grid edge are staged by per-value asynchronous copies into the
 // same layout.  A group of W * CC lanes serves one sample: lane = (tap x,
 // coil), so the CC coils of one tap read distinct banks; tap-x partial sums
@@ -252,7 +256,7 @@ template <int CC, typename GT>
 __global__ void __launch_bounds__(256, CC == 2 ? 6 : CC == 4 ? 4 : 1) interp_tma_kernel(
     const __grid_constant__ CUtensorMap tmap, Geo g, KernelCoefs kc, int C, TilePlan tp,
     PhaseTable pt, const GT* __restrict__ grids, float2* __restrict__ y,
-    int32_t* __restrict__ status) {
+    int32_t* __restrict__ status, long long poll_limit) {
   constexpr int W = 4, T = 8, H = T + W - 1, XP = kTmaXP;
   constexpr int LPS = W * CC, SPW = 32 / LPS;  // lanes per sample, samples per warp
   static_assert(LPS <= 32, "coil chunk");
@@ -319,9 +323,10 @@ __global__ void __launch_bounds__(256, CC == 2 ? 6 : CC == 4 ? 4 : 1) interp_tma
           : "memory");
     }
     bool ok = false;
-    for (long long k = 0; k < kTmaMaxPoll && !ok; ++k) ok = mbar_try_wait(mb, 0);
-    if (!ok) {
-      if (status) atomicCAS(status, 0, NRSENSE_ERR_TIMEOUT);
+    for (long long k = 0; k < poll_limit && !ok; ++k) ok = mbar_try_wait(mb, 0);
+    // one decision for the whole CTA: the warps below use full-warp shuffles
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0 && status) atomicCAS(status, 0, NRSENSE_ERR_TIMEOUT);
       // give the copy in flight a last bounded chance to land before leaving
       for (long long k = 0; k < kTmaMaxPoll && !ok; ++k) ok = mbar_try_wait(mb, 0);
       return;
@@ -583,10 +588,11 @@ bool make_grid_tensor_map(CUtensorMap* m, const void* base, const Geo& g, long l
 int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                          const PhaseTable& pt, const void* grids, bool bf16, nrsense_c64* y,
                          int coil_chunk, const CUtensorMap* tmap, int32_t* status,
-                         cudaStream_t s) {
+                         cudaStream_t s, long long poll_limit) {
   const int nitems = pt.item0[pt.nphase];
   if (nitems == 0) return 0;
   auto* yp = reinterpret_cast<float2*>(y);
+  const long long lim = poll_limit < 0 ? kTmaMaxPoll : std::min(poll_limit, kTmaMaxPoll);
   if (tmap != nullptr && W == 4) {
     // the tensor map's coil box must match: 8 (C > 4), 2, else 4
     const int cc = (coil_chunk == 8 && C > 4) ? 8 : coil_chunk == 2 ? 2 : 4;
@@ -595,24 +601,24 @@ int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, cons
       const auto* gp = static_cast<const bf162*>(grids);
       if (cc == 8)
         interp_tma_kernel<8, bf162><<<gd, 256, interp_tma_smem<8, bf162>(), s>>>(
-            *tmap, g, kc, C, tp, pt, gp, yp, status);
+            *tmap, g, kc, C, tp, pt, gp, yp, status, lim);
       else if (cc == 2)
         interp_tma_kernel<2, bf162><<<gd, 256, interp_tma_smem<2, bf162>(), s>>>(
-            *tmap, g, kc, C, tp, pt, gp, yp, status);
+            *tmap, g, kc, C, tp, pt, gp, yp, status, lim);
       else
         interp_tma_kernel<4, bf162><<<gd, 256, interp_tma_smem<4, bf162>(), s>>>(
-            *tmap, g, kc, C, tp, pt, gp, yp, status);
+            *tmap, g, kc, C, tp, pt, gp, yp, status, lim);
     } else {
       const auto* gp = static_cast<const float2*>(grids);
       if (cc == 8)
         interp_tma_kernel<8, float2><<<gd, 256, interp_tma_smem<8, float2>(), s>>>(
-            *tmap, g, kc, C, tp, pt, gp, yp, status);
+            *tmap, g, kc, C, tp, pt, gp, yp, status, lim);
       else if (cc == 2)
         interp_tma_kernel<2, float2><<<gd, 256, interp_tma_smem<2, float2>(), s>>>(
-            *tmap, g, kc, C, tp, pt, gp, yp, status);
+            *tmap, g, kc, C, tp, pt, gp, yp, status, lim);
       else
         interp_tma_kernel<4, float2><<<gd, 256, interp_tma_smem<4, float2>(), s>>>(
-            *tmap, g, kc, C, tp, pt, gp, yp, status);
+            *tmap, g, kc, C, tp, pt, gp, yp, status, lim);
     }
     return 1;
   }

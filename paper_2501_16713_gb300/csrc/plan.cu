@@ -729,6 +729,8 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     p->fft_pruned = p->fft_pruned_ok;
     // tensor maps of the interpolation input (TMA-staged halos, W = 4)
     const long long slots = (long long)p->C * p->phase_chunk;
+    // a test-only limit on the halo wait (0 makes every TMA-staged CTA time out)
+    if (const char* lim = std::getenv("NRSENSE_TMA_POLL_LIMIT")) p->tma_poll_limit = std::atoll(lim);
     p->tma_ok = p->W == 4 &&
                 make_grid_tensor_map(&p->tmap_xwork4, p->b_xwork, g, slots, p->grid_bf16, 4) &&
                 make_grid_tensor_map(&p->tmap_xwork8, p->b_xwork, g, slots, p->grid_bf16, 8) &&
@@ -896,7 +898,6 @@ const char* nrsense_status_string(nrsense_status s) {
     case NRSENSE_ERR_BREAKDOWN: return "CG breakdown";
     case NRSENSE_ERR_NOT_CONVERGED: return "CG not converged";
     case NRSENSE_ERR_TIMEOUT: return "device wait timed out";
-    case NRSENSE_ERR_BOUNDS: return "device bounds check fired";
     case NRSENSE_ERR_STATE: return "call not valid for this plan";
     default: return "unknown status";
   }

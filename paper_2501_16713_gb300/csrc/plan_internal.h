@@ -97,6 +97,8 @@ struct nrsense_plan_s {
                                  // (home tiles, spread_home.cu) (autotuned)
   bool interp_tma = false;    // TMA-staged interpolation (autotuned; needs tma_ok)
   bool tma_ok = false;        // tensor maps of b_xwork built
+  long long tma_poll_limit = -1;  // polls of the halo wait before ERR_TIMEOUT (-1: the
+                                  // kernel's own limit; NRSENSE_TMA_POLL_LIMIT at plan time)
   CUtensorMap tmap_xwork4{}, tmap_xwork8{}, tmap_xwork2{};  // boxes of 4, 8, 2 coil grids
   bool comp_spread = false;   // desc.precision == NRSENSE_FP32_COMPENSATED
   nrsense_c64* b_y = nullptr;      // Mtot * C
@@ -209,7 +211,7 @@ int launch_image_to_padded(const Geo& g, int C, const float* deapod, const nrsen
 int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, const TilePlan& tp,
                          const PhaseTable& pt, const void* grids, bool bf16, nrsense_c64* y,
                          int coil_chunk, const CUtensorMap* tmap, int32_t* status,
-                         cudaStream_t s);
+                         cudaStream_t s, long long poll_limit = -1);
 // Tensor map of `slots` consecutive coil grids at base ([slot][G0][G1][G2]
 // values) with a halo box of 12 x 11 x 11 values x coil_chunk grids.
 bool make_grid_tensor_map(CUtensorMap* m, const void* base, const Geo& g, long long slots,

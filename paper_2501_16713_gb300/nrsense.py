@@ -19,8 +19,7 @@ OK = 0
 STATUS = {
     0: "ok", -1: "invalid argument", -2: "out of memory", -3: "cuFFT failure",
     -4: "CUDA runtime failure", -5: "CG breakdown", -6: "CG not converged",
-    -7: "device wait timed out", -8: "device bounds check fired",
-    -9: "call not valid for this plan",
+    -7: "device wait timed out", -9: "call not valid for this plan",
 }
 FP32 = 0
 BF16_STORE = 1
