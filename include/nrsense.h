@@ -382,6 +382,35 @@ nrsense_status nrsense_dot_noalloc(const nrsense_c64* x_dev, const nrsense_c64* 
                                    double* out_dev, void* stream);
 
 /*
+ * Phase sharding over several GPUs (one process per GPU).  The stacked SENSE
+ * equation sums the motion states ("Nonrigid SENSE Operators": A^H y =
+ * sum_j A_j^H y_j, E = sum_j A_j^H A_j + lambda I), so a rank can hold a plan
+ * of its own states j in J_r only and the ranks' partial sums add up to the
+ * whole.  nrsense_plan_set_reduce registers the step that adds them: the
+ * library calls fn(user, image_dev, n, stream) right after it has formed this
+ * plan's phase sum of an adjoint (nrsense_apply_adjoint, and so every solver's
+ * right-hand side) or of a normal-operator application (nrsense_apply_normal,
+ * before lambda x is added), with image_dev the n = n0 n1 n2 complex values
+ * (device) and `stream` the stream the sum was formed on.  fn must replace the
+ * image, in stream order, by the sum of every rank's image (an all-reduce, e.g.
+ * ncclAllReduce on `stream`) and return NRSENSE_OK; any other return makes the
+ * calling entry point fail with ERR_CUDA.  Every rank then holds the same
+ * vectors, so the CG, flexible-CG and FISTA iterations and their FP64
+ * reductions run unchanged and identically on every rank; only images are
+ * exchanged.  fn = NULL removes the hook.  With a hook, graph capture of a
+ * solve (NRSENSE_CG_GRAPH) requires fn's work to be capturable on `stream`.
+ * As for every call of this library, the calling thread must have the plan's
+ * device current (cudaSetDevice) before it calls in.
+ * nrsense_copy_c64 copies n complex values device to device on `stream` (for
+ * reduction hooks that stage the image in their own buffer).
+ */
+typedef nrsense_status (*nrsense_reduce_fn)(void* user, nrsense_c64* image_dev, int64_t n,
+                                            void* stream);
+nrsense_status nrsense_plan_set_reduce(nrsense_plan_t plan, nrsense_reduce_fn fn, void* user);
+nrsense_status nrsense_copy_c64(nrsense_c64* dst_dev, const nrsense_c64* src_dev, int64_t n,
+                                void* stream);
+
+/*
  * Circulant preconditioner (not in the paper; serves the Tikhonov CG solve).
  * nrsense_set_circulant computes the point-spread function of the plan's
  * normal operator, h = E0 delta at the image centre (E0 with lambda = 0, one
@@ -458,6 +487,14 @@ typedef struct {
                                   average against 7.6 tile planes) */
   double  spread_mma_geo_ms[2];/* measured, best warps per CTA: planes, sub-blocks (-1: n/a) */
   double  interp_tma2_ms;      /* measured, TMA staging with 2 coils per CTA (-1: n/a) */
+  int32_t spread_max_item;     /* list entries per k-space spreading work item: heavier tiles
+                                  are split into items this long whose partial tiles are summed
+                                  in a fixed order (512, 1024 or 2048; longer items lengthen the
+                                  FP32 accumulation chains past the 1e-5 bound on dense
+                                  trajectories; set_tuning: 0 keeps the plan's, another value
+                                  re-tiles the plan, synchronising) */
+  double  spread_item_ms[3];   /* measured k-space spread with the chosen kernel at 512, 1024,
+                                  2048 entries per item (-1: n/a) */
 } nrsense_tuning;
 nrsense_status nrsense_plan_autotune(nrsense_plan_t plan, int32_t reps, nrsense_tuning* out_host,
                                      void* stream);

@@ -30,6 +30,14 @@ int image_tuning_of(int variant) {
   return variant == kSpreadHome ? 2 : variant == kSpreadRegisterWarp ? 1 : 0;
 }
 
+// The phase sum of this plan's motion states is complete only with the other
+// ranks' states: hand the image to the caller's reduction (an all-reduce)
+nrsense_status reduce_phases(nrsense_plan_s* p, nrsense_c64* img, cudaStream_t s) {
+  if (p->reduce_fn == nullptr) return NRSENSE_OK;
+  const nrsense_status st = p->reduce_fn(p->reduce_user, img, p->geo.nvox, s);
+  return st == NRSENSE_OK ? NRSENSE_OK : NRSENSE_ERR_CUDA;
+}
+
 #define NRS_TRY(expr)                  \
   do {                                 \
     nrsense_status _st = (expr);       \
@@ -328,12 +336,16 @@ nrsense_status nrsense_apply_adjoint(nrsense_plan_t p, const nrsense_c64* y, nrs
                                      void* stream) {
   if (p == nullptr || x == nullptr || y == nullptr) return NRSENSE_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (p->C == 0) return warp_adjoint(p, y, x, s);
+  if (p->C == 0) {
+    NRS_TRY(warp_adjoint(p, y, x, s));
+    return reduce_phases(p, x, s);
+  }
   for (int j0 = 0; j0 < p->P; j0 += p->phase_chunk) {
     const int j1 = std::min(p->P, j0 + p->phase_chunk);
     NRS_TRY(sense_chunk_adjoint(p, j0, j1, y, 0, p->b_m + (long long)j0 * p->geo.nvox, s));
   }
-  return warp_adjoint(p, p->b_m, x, s);
+  NRS_TRY(warp_adjoint(p, p->b_m, x, s));
+  return reduce_phases(p, x, s);
 }
 
 nrsense_status nrsense_apply_normal(nrsense_plan_t p, const nrsense_c64* x, double lambda,
@@ -350,6 +362,7 @@ nrsense_status nrsense_apply_normal(nrsense_plan_t p, const nrsense_c64* x, doub
     }
   }
   NRS_TRY(warp_adjoint(p, p->b_m, out, s));
+  NRS_TRY(reduce_phases(p, out, s));
   if (lambda != 0.0) {
     STAGE(VECTOR, launch_axpby(p->geo.nvox, x, float(lambda), out, 1.0f, s));
     NRS_TRY(launched());
@@ -383,6 +396,11 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
   if (t->fft_pruned == 1 && !p->fft_pruned_ok) return NRSENSE_ERR_ARG;
   p->spread_image_variant = image_variant_of(t->spread_image_warp);
   p->fft_pruned = t->fft_pruned == 1;
+  if (t->spread_max_item != 0) {
+    const int m = t->spread_max_item;
+    if (m != 512 && m != 1024 && m != 2048) return NRSENSE_ERR_ARG;
+    NRS_TRY(retile_kspace(p, m, nullptr));
+  }
   return NRSENSE_OK;
 }
 
@@ -398,6 +416,8 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
   out->interp_tma = p->interp_tma ? 1 : 0;
   out->spread_image_warp = image_tuning_of(p->spread_image_variant);
   out->spread_image_ms[2] = -1.0;
+  out->spread_max_item = p->spread_max_item;
+  for (int k = 0; k < 3; ++k) out->spread_item_ms[k] = -1.0;
   out->fft_pruned = p->fft_pruned ? 1 : 0;
   out->fft_ms[0] = out->fft_ms[1] = -1.0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -443,7 +463,14 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
   const int j1 = std::min(p->P, p->phase_chunk);
   const PhaseTable ts = kspace_table(p, 0, j1, true, 0);
   const PhaseTable ti = kspace_table(p, 0, j1, false, 0);
-  cudaEvent_t e0, e1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  struct EventPair {
+    cudaEvent_t &a, &b;
+    ~EventPair() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } event_guard{e0, e1};
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return NRSENSE_ERR_CUDA;
   // times the candidates on the plan's own point sets and internal buffers
@@ -544,8 +571,6 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
     p->fft_pruned = out->fft_ms[1] >= 0.0 && out->fft_ms[1] < out->fft_ms[0];
     out->fft_pruned = p->fft_pruned ? 1 : 0;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (cudaGetLastError() != cudaSuccess) return NRSENSE_ERR_CUDA;
   for (int k = 0; k < 3; ++k)
     if (!(out->spread_ms[k] >= 0.0)) return NRSENSE_ERR_CUDA;
@@ -583,7 +608,47 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
                                                              : NRSENSE_TUNE_SPREAD_REGISTER_WARP;
   out->interp_coils = p->interp_coils;
   out->interp_tma = p->interp_tma ? 1 : 0;
+  // work-item split of the k-space spread, timed with the chosen kernel: each
+  // size re-tiles the plan (host work, outside the timed launches)
+  {
+    const int sizes[3] = {512, 1024, 2048};
+    int best_m = p->spread_max_item;
+    double best_ms = -1.0;
+    for (int k = 0; k < 3; ++k) {
+      NRS_TRY(retile_kspace(p, sizes[k], s));
+      const PhaseTable tk = kspace_table(p, 0, j1, true, 0);
+      const double ms = time_ms([&] {
+        p->launches += launch_spread(g, p->W, p->kc, p->C, p->ktiles, tk, p->b_y, p->b_xspread,
+                                     p->grid_bf16, p->comp_spread, p->spread_variant,
+                                     p->b_scratch, p->d_status, s);
+      });
+      out->spread_item_ms[k] = ms;
+      if (ms >= 0.0 && (best_ms < 0.0 || ms < best_ms)) {
+        best_ms = ms;
+        best_m = sizes[k];
+      }
+    }
+    NRS_TRY(retile_kspace(p, best_m, s));
+    out->spread_max_item = p->spread_max_item;
+  }
   return NRSENSE_OK;
+}
+
+nrsense_status nrsense_plan_set_reduce(nrsense_plan_t p, nrsense_reduce_fn fn, void* user) {
+  if (p == nullptr) return NRSENSE_ERR_ARG;
+  p->reduce_fn = fn;
+  p->reduce_user = user;
+  return NRSENSE_OK;
+}
+
+nrsense_status nrsense_copy_c64(nrsense_c64* dst_dev, const nrsense_c64* src_dev, int64_t n,
+                                void* stream) {
+  if (n < 0 || (n > 0 && (dst_dev == nullptr || src_dev == nullptr))) return NRSENSE_ERR_ARG;
+  if (n == 0) return NRSENSE_OK;
+  return cudaMemcpyAsync(dst_dev, src_dev, size_t(n) * sizeof(nrsense_c64),
+                         cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? NRSENSE_OK
+             : NRSENSE_ERR_CUDA;
 }
 
 }  // extern "C"

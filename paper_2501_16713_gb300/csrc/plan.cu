@@ -41,8 +41,29 @@ nrsense_status dev_alloc(nrsense_plan_s* p, void** ptr, size_t bytes) {
     return NRSENSE_ERR_OOM;
   }
   p->allocations.push_back(*ptr);
+  p->allocation_bytes.push_back(bytes);
   p->device_bytes += (long long)bytes;
   return NRSENSE_OK;
+}
+
+// free one tracked allocation (null: no-op)
+void dev_free(nrsense_plan_s* p, void* ptr) {
+  if (ptr == nullptr) return;
+  for (size_t i = 0; i < p->allocations.size(); ++i)
+    if (p->allocations[i] == ptr) {
+      cudaFree(ptr);
+      p->device_bytes -= (long long)p->allocation_bytes[i];
+      p->allocations.erase(p->allocations.begin() + long(i));
+      p->allocation_bytes.erase(p->allocation_bytes.begin() + long(i));
+      return;
+    }
+}
+
+void free_pointset(nrsense_plan_s* p, PointSet* ps) {
+  void* arrs[] = {ps->qs, ps->perm, ps->list, ps->items, ps->bins, ps->reduces, ps->iitems,
+                  ps->clist, ps->cbins};
+  for (void* a : arrs) dev_free(p, a);
+  *ps = PointSet{};
 }
 
 template <typename T>
@@ -470,6 +491,32 @@ nrsense_status build_home_set(nrsense_plan_s* p, const std::vector<HostPoint>& p
   return NRSENSE_OK;
 }
 
+// scratch for split tiles: slots x coil chunks x tile x chunk coils (grown,
+// never shrunk)
+nrsense_status ensure_scratch(nrsense_plan_s* p) {
+  long long need = 0;
+  auto tile_pts = [](const PointSet& ps) {
+    return (long long)ps.tp.t0 * ps.tp.t1 * ps.tp.t2;
+  };
+  if (!p->identity_warp) need = std::max(need, (long long)p->ipts.n_slots * tile_pts(p->ipts));
+  if (p->C > 0) {
+    const int cc = spread_coil_chunk(p->C);
+    const int chunks = (p->C + cc - 1) / cc;
+    for (int j0 = 0; j0 < p->P; j0 += p->phase_chunk) {
+      long long slots = 0;
+      for (int j = j0; j < std::min(p->P, j0 + p->phase_chunk); ++j) slots += p->kpts[j].n_slots;
+      need = std::max(need, slots * chunks * tile_pts(p->kpts[j0]) * cc);
+    }
+  }
+  if (need <= p->scratch_elems) return NRSENSE_OK;
+  dev_free(p, p->b_scratch);
+  p->b_scratch = nullptr;
+  p->scratch_elems = 0;
+  NRS_TRY(dev_alloc_n(p, &p->b_scratch, need));
+  p->scratch_elems = need;
+  return NRSENSE_OK;
+}
+
 nrsense_status cufft_check(cufftResult r) {
   return r == CUFFT_SUCCESS ? NRSENSE_OK : NRSENSE_ERR_CUFFT;
 }
@@ -645,9 +692,10 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     }
     for (int j = 0; j < p->P; ++j) {
       NRS_TRY(build_pointset(p, all[(size_t)j], &p->kpts[j], ktiles, &uni, /*interp=*/true,
-                             kSpreadMaxItem, s));
+                             p->spread_max_item, s));
       std::vector<HostPoint>().swap(all[(size_t)j]);
     }
+    p->kunion.swap(uni);
   }
 
   // cuFFT plans
@@ -740,23 +788,7 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     NRS_TRY(dev_alloc_n(p, &p->b_y, std::max<long long>(p->Mtot * p->C, 1)));
     if (cudaMemsetAsync(p->b_xpad, 0, cgb, s) != cudaSuccess) return NRSENSE_ERR_CUDA;
   }
-  // scratch for split tiles: slots x coil chunks x tile x chunk coils
-  long long need = 0;
-  auto tile_pts = [](const PointSet& ps) {
-    return (long long)ps.tp.t0 * ps.tp.t1 * ps.tp.t2;
-  };
-  if (!p->identity_warp) need = std::max(need, (long long)p->ipts.n_slots * tile_pts(p->ipts));
-  if (p->C > 0) {
-    const int cc = spread_coil_chunk(p->C);
-    const int chunks = (p->C + cc - 1) / cc;
-    for (int j0 = 0; j0 < p->P; j0 += p->phase_chunk) {
-      long long slots = 0;
-      for (int j = j0; j < std::min(p->P, j0 + p->phase_chunk); ++j) slots += p->kpts[j].n_slots;
-      need = std::max(need, slots * chunks * tile_pts(p->kpts[j0]) * cc);
-    }
-  }
-  p->scratch_elems = need;
-  if (need > 0) NRS_TRY(dev_alloc_n(p, &p->b_scratch, need));
+  NRS_TRY(ensure_scratch(p));
   if (cudaStreamSynchronize(s) != cudaSuccess) return NRSENSE_ERR_CUDA;
   return NRSENSE_OK;
 }
@@ -777,9 +809,54 @@ void release(nrsense_plan_s* p) {
   }
   for (void* a : p->allocations) cudaFree(a);
   p->allocations.clear();
+  p->allocation_bytes.clear();
 }
 
 }  // namespace
+
+namespace nrs {
+
+nrsense_status retile_kspace(nrsense_plan_s* p, int max_item, cudaStream_t s) {
+  if (max_item < 64 || max_item > (1 << 16)) return NRSENSE_ERR_ARG;
+  if (p->C == 0 || max_item == p->spread_max_item) {
+    p->spread_max_item = p->C == 0 ? p->spread_max_item : max_item;
+    return NRSENSE_OK;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return NRSENSE_ERR_CUDA;
+  for (int j = 0; j < p->P; ++j) {
+    PointSet& ps = p->kpts[j];
+    // the sorted points, back to host records (their order is kept by the
+    // stable sort of build_pointset)
+    std::vector<float4> qs((size_t)ps.npts);
+    std::vector<int32_t> perm((size_t)ps.npts);
+    if (ps.npts > 0 &&
+        (cudaMemcpyAsync(qs.data(), ps.qs, qs.size() * sizeof(float4), cudaMemcpyDeviceToHost,
+                         s) != cudaSuccess ||
+         cudaMemcpyAsync(perm.data(), ps.perm, perm.size() * sizeof(int32_t),
+                         cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess))
+      return NRSENSE_ERR_CUDA;
+    std::vector<HostPoint> pts((size_t)ps.npts);
+    for (size_t i = 0; i < pts.size(); ++i) {
+      uint32_t packed;
+      std::memcpy(&packed, &qs[i].w, sizeof(packed));
+      unpack_base(packed, pts[i].b[0], pts[i].b[1], pts[i].b[2]);
+      pts[i].f[0] = qs[i].x;
+      pts[i].f[1] = qs[i].y;
+      pts[i].f[2] = qs[i].z;
+      pts[i].row = perm[i];
+    }
+    PointSet fresh;
+    NRS_TRY(build_pointset(p, pts, &fresh, ps.tp, &p->kunion, /*interp=*/true, max_item, s));
+    free_pointset(p, &ps);
+    ps = fresh;
+  }
+  p->spread_max_item = max_item;
+  NRS_TRY(ensure_scratch(p));
+  return cudaStreamSynchronize(s) == cudaSuccess ? NRSENSE_OK : NRSENSE_ERR_CUDA;
+}
+
+}  // namespace nrs
 
 extern "C" {
 

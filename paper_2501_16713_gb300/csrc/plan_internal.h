@@ -122,6 +122,9 @@ struct nrsense_plan_s {
 
   long long device_bytes = 0;
   std::vector<void*> allocations;
+  std::vector<size_t> allocation_bytes;  // size of each entry of allocations
+  std::vector<char> kunion;              // k-space tiles written by the spread (plan time)
+  int spread_max_item = 1024;            // list entries per k-space spreading work item
 
   // stage profiling (nrsense_profile_start/stop)
   bool prof_on = false;
@@ -142,6 +145,10 @@ struct nrsense_plan_s {
   double kcol_fraction = 1.0;  // tile columns with at least one such tile
   double kuni_fraction = 1.0;  // tiles of the union
 
+  // reduction of the phase sum over ranks that hold the other motion states
+  // (nrsense_plan_set_reduce); null: this plan holds every state
+  nrsense_reduce_fn reduce_fn = nullptr;
+  void* reduce_user = nullptr;
   nrsense_cg_ws* cg = nullptr;  // allocated by the first nrsense_solve_cg
   // circulant preconditioner (nrsense_set_circulant, solver.cu)
   float* circ_d = nullptr;          // per frequency (DFT order): 1 / (max(Re hhat, 0) + lambda)
@@ -270,6 +277,10 @@ int launch_pruned_inverse(const Geo& g, int C, int nph, const uint32_t* colmask,
                           const float* deapod,
                           const nrsense_c64* smaps, const void* grid, void* t2, void* t1,
                           nrsense_c64* w, cudaStream_t s);
+// rebuild the k-space spreading work items of every phase with at most
+// max_item list entries per item (plan.cu; the lists of split tiles are
+// re-dealt, the sorted points stay) and grow the split-tile scratch if needed
+nrsense_status retile_kspace(nrsense_plan_s* p, int max_item, cudaStream_t s);
 // free the CG workspace of a plan (solver.cu)
 void cg_release(nrsense_plan_s* p);
 // free the FISTA workspace of a plan (fista.cu)

@@ -16,6 +16,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libnrsense.so")
 
 OK = 0
+ERR_ARG = -1
+ERR_CUDA = -4
 STATUS = {
     0: "ok", -1: "invalid argument", -2: "out of memory", -3: "cuFFT failure",
     -4: "CUDA runtime failure", -5: "CG breakdown", -6: "CG not converged",
@@ -51,7 +53,8 @@ class Tuning(ctypes.Structure):
                 ("fft_pruned", ctypes.c_int32), ("fft_ms", ctypes.c_double * 2),
                 ("spread_mma_ms", ctypes.c_double), ("spread_mma_wpc", ctypes.c_int32),
                 ("spread_mma_cube", ctypes.c_int32), ("spread_mma_geo_ms", ctypes.c_double * 2),
-                ("interp_tma2_ms", ctypes.c_double)]
+                ("interp_tma2_ms", ctypes.c_double), ("spread_max_item", ctypes.c_int32),
+                ("spread_item_ms", ctypes.c_double * 3)]
 
 
 class Info(ctypes.Structure):
@@ -133,7 +136,12 @@ _SIGS = {
     "nrsense_solve_fista": [_VP, _VP, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
                             ctypes.c_int32, ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_double),
                             _VP],
+    "nrsense_plan_set_reduce": [_VP, _VP, _VP],
+    "nrsense_copy_c64": [_VP, _VP, ctypes.c_int64, _VP],
 }
+# nrsense_reduce_fn: (user, image_dev, n, stream) -> status
+REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                             ctypes.c_void_p)
 CG_X0 = 1
 CG_GRAPH = 2
 CG_CIRCULANT = 4
@@ -618,6 +626,7 @@ class Plan:
             t.fft_pruned = int(store[key].get("fft_pruned", 0))
             t.spread_mma_wpc = int(store[key].get("spread_mma_wpc", 1))
             t.spread_mma_cube = int(store[key].get("spread_mma_cube", 0))
+            t.spread_max_item = int(store[key].get("spread_max_item", 0))
             _check(self.lib.nrsense_plan_set_tuning(self._h, ctypes.byref(t)),
                    "nrsense_plan_set_tuning")
             return dict(store[key], cached=True)
@@ -633,7 +642,8 @@ class Plan:
                "spread_mma_ms": t.spread_mma_ms, "spread_mma_wpc": t.spread_mma_wpc,
                "spread_mma_cube": t.spread_mma_cube,
                "spread_mma_geo_ms": list(t.spread_mma_geo_ms),
-               "interp_tma2_ms": t.interp_tma2_ms}
+               "interp_tma2_ms": t.interp_tma2_ms, "spread_max_item": t.spread_max_item,
+               "spread_item_ms": list(t.spread_item_ms)}
         if cache:
             store[key] = res
             tmp = cache + ".tmp"
@@ -664,6 +674,40 @@ class Plan:
                                                        _stream(stream)),
                "nrsense_apply_adjoint_weighted")
         return out
+
+    def set_reduce(self, fn):
+        """Register the reduction of this plan's phase sums over ranks
+        (nrsense_plan_set_reduce).  fn(buf, stream) must replace the complex64
+        image tensor `buf` by the sum of every rank's image, in stream order on
+        `stream` (a torch.cuda.ExternalStream of the library's stream); the
+        image is staged in `buf` and copied back by the library's own copy.
+        fn = None removes the hook."""
+        import torch
+        if fn is None:
+            _check(self.lib.nrsense_plan_set_reduce(self._h, None, None), "nrsense_plan_set_reduce")
+            self._reduce = None
+            return
+        buf = torch.empty(self.shape, dtype=torch.complex64, device="cuda")
+        lib = self.lib
+
+        def tramp(user, ptr, n, stream):
+            try:
+                if n != buf.numel():
+                    return ERR_ARG
+                s = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+                sp = ctypes.c_void_p(stream)
+                if lib.nrsense_copy_c64(_ptr(buf), ctypes.c_void_p(ptr), n, sp) != OK:
+                    return ERR_CUDA
+                with torch.cuda.stream(s):
+                    fn(buf, s)
+                return lib.nrsense_copy_c64(ctypes.c_void_p(ptr), _ptr(buf), n, sp)
+            except Exception:  # noqa: BLE001 - a failure must reach the C caller as a status
+                return ERR_CUDA
+
+        cb = REDUCE_FN(tramp)
+        _check(self.lib.nrsense_plan_set_reduce(self._h, ctypes.cast(cb, ctypes.c_void_p), None),
+               "nrsense_plan_set_reduce")
+        self._reduce = (cb, buf)  # kept alive while registered
 
     def max_eig(self, v0, iters=30, stream=None):
         """Power iteration on sum_j A_j^H A_j from v0 (overwritten with the

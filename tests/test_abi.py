@@ -17,7 +17,9 @@ HEADER = os.path.join(ROOT, "include", "nrsense.h")
 def _declared():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(nrsense_[a-z_]+)\s*\(", txt)))
+    # function-pointer typedefs declare types, not entry points
+    txt = re.sub(r"typedef\s+nrsense_status\s*\(\*\s*\w+\)\s*\([^)]*\)\s*;", "", txt)
+    return sorted(set(re.findall(r"\b(nrsense_[a-z_0-9]+)\s*\(", txt)))
 
 
 @pytest.fixture(scope="module")

@@ -286,6 +286,7 @@ def test_autotune_choices_compute_the_same_values(tmp_path):
     assert not res["cached"] and res["spread_variant"] in (1, 2, 3, 4)
     assert res["interp_coils"] in (2, 4, 8)
     assert res["spread_image_warp"] in (0, 1, 2) and len(res["spread_image_ms"]) == 3
+    assert res["spread_max_item"] in (512, 1024, 2048)
     # grid 32 x 32 x 48 with 8^3 tiles: interior tiles take the TMA-staged
     # halo, tiles at the upper edges the wrapped per-value staging
     for sv in (1, 2, 3):
@@ -357,4 +358,42 @@ def test_home_tile_spread_ragged_and_wrapped(shape):
     e = rel_l2(xa, ref)
     print(f"home-tile image-space adjoint {shape}: rel L2 {e:.2e}")
     assert e < TOL_FP32
+    plan.close()
+
+
+def test_kspace_split_sizes_agree_with_oracle():
+    # the k-space work-item split (512, 1024, 2048 list entries) re-tiles the
+    # plan; the dense centre of a cone trajectory makes tiles of several
+    # thousand entries, split differently by each size: every size computes
+    # the adjoint within FP32 rounding of the oracle, deterministically (4096
+    # is refused: on this case it let the tensor-core kernel's accumulation
+    # chains reach 1.7e-5)
+    import ctypes
+    import torch
+    from paper_2501_16713_gb300.nrsense import Tuning
+    shape = (16, 16, 16)
+    case = synth.small_case(shape, 8, 2, [30000, 24000], seed=171)
+    plan = make_plan(case, shape)
+    geo = O.Geometry(shape)
+    d64 = [d.astype(np.float64) for d in case["disp"]]
+    ys = O.stacked_forward(geo, case["x"], d64, case["smaps"], case["coords"])
+    yin = to_dev(c64(np.concatenate(ys)))
+    ref = O.stacked_adjoint(geo, [c64(y).astype(np.complex128) for y in ys], d64, case["smaps"],
+                            case["coords"])
+    for spread in (3, 4):  # register spread per plane, tensor-core sub-blocks
+        for m in (512, 1024, 2048):
+            t = Tuning()
+            t.spread_variant, t.interp_coils, t.spread_max_item = spread, 8, m
+            t.spread_mma_wpc, t.spread_mma_cube = 4, 1
+            assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == 0
+            assert plan.info()["split_tiles"] > 0
+            xa = plan.adjoint(yin)
+            assert torch.equal(plan.adjoint(yin), xa)
+            e = rel_l2(xa.cpu().numpy(), ref)
+            assert e < TOL_FP32, (spread, m, e)
+    t = Tuning()
+    for bad in (300, 4096):  # not supported sizes
+        t.spread_variant, t.interp_coils, t.spread_max_item = 3, 8, bad
+        assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == -1
+    assert plan.device_status() == 0
     plan.close()
