@@ -43,7 +43,8 @@ constexpr int kHB = 32;                 // points staged per batch
 static_assert(kHAX >= kHA, "accumulator rows");
 
 // one staged point: weights (z in the order 0, 2, 1, 3 so that a lane's two
-// z taps are one 8-byte load), accumulator offset of the first tap, value
+// z taps are one 8-byte load), accumulator offset of the first tap, value;
+// 80-byte records: the 16-byte stores of a quarter-warp hit disjoint banks
 struct HomeStage {
   float wz[4];
   float wy[4];
@@ -51,8 +52,9 @@ struct HomeStage {
   int off;
   float vx, vy;
   int pad;
+  float pad2[4];
 };
-static_assert(sizeof(HomeStage) == 64, "staging record");
+static_assert(sizeof(HomeStage) == 80, "staging record");
 
 __device__ __forceinline__ int home_extent(int G, int o) { return min(kHS, G - o); }
 
