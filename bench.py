@@ -372,7 +372,8 @@ def _timed_solve(fn):
 CIRC_LAMBDA_FACTOR = 10.0
 
 
-def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, seed=5):
+def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, seed=5,
+               train_runs=0):
     """Plain CG and flexible CG with `net` to tol on y = A x + noise,
     lambda = rel_lambda * lambda_max (power iteration); both captured as CUDA
     graphs (10 iterations per graph launch)."""
@@ -401,6 +402,33 @@ def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, s
     (pcn, ms_pcn) = _timed_solve(lambda: plan.solve_fcg(y, lam, net, tol=tol, maxit=maxit,
                                                         graph=True, out=out, circulant=True))
     diff_pcn = float((out - x_cg).norm() / x_cg.norm())
+    # a network trained here from its random start (symmetric form, cosine
+    # loss on pairs of plain-CG runs, blocks kept by the flexible-CG iterations
+    # of a held-out problem), against the same network untrained
+    trained = None
+    if train_runs > 0:
+        from paper_2501_16713_gb300 import Cnn, precond
+        t0 = time.perf_counter()
+        tgen = torch.Generator(device=dev).manual_seed(seed + 100)
+        rhs = [_noisy(plan, torch.randn(shape, dtype=torch.complex64, device=dev,
+                                        generator=tgen), tgen) for _ in range(train_runs + 1)]
+        r, e, runs = precond.generate_pairs(plan, rhs[:-1], lam, tol=1e-5, maxit=maxit,
+                                            per_run=40)
+        tnet = Cnn(shape, seed=1)
+        (fu, ms_fu) = _timed_solve(lambda: plan.solve_fcg(y, lam, tnet, tol=tol, maxit=maxit,
+                                                          graph=True, out=out))
+        score = lambda n_: precond.fcg_iterations(plan, rhs[-1], lam, n_)  # noqa: E731
+        hist = precond.train_select(tnet, r, e, [(300, 1e-3, 3e-4), (300, 3e-4, 1e-4)], score)
+        t_train = time.perf_counter() - t0
+        (ft, ms_ft) = _timed_solve(lambda: plan.solve_fcg(y, lam, tnet, tol=tol, maxit=maxit,
+                                                          graph=True, out=out))
+        trained = {"iters": ft[1], "ms": round(ms_ft, 2), "true_res": ft[3], "fallbacks": ft[5],
+                   "untrained_iters": fu[1], "untrained_ms": round(ms_fu, 2),
+                   "speedup_vs_plain": round(ms_cg / ms_ft, 3),
+                   "pairs": int(r.shape[0]), "pair_runs": len(runs), "train_s": round(t_train, 1),
+                   "selection": [(b, sc) for b, _, sc in hist]}
+        tnet.close()
+        del r, e
     best = min(ms_f, ms_pc, ms_pcn)
     return {"tol": tol, "lambda": lam, "lambda_rel": rel_lambda, "lambda_max": lam_max,
             "plain": {"iters": cg[1], "ms": round(ms_cg, 2), "true_res": cg[3]},
@@ -411,6 +439,7 @@ def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, s
                           "lambda_factor": CIRC_LAMBDA_FACTOR},
             "circulant_net": {"iters": pcn[1], "ms": round(ms_pcn, 2), "true_res": pcn[3],
                               "fallbacks": pcn[5], "solution_rel_diff": diff_pcn},
+            "fcg_trained": trained, "target_speedup": 3.0,
             "speedup": round(ms_cg / best, 3), "speedup_fcg_net": round(ms_cg / ms_f, 3)}
 
 
@@ -1045,9 +1074,10 @@ def run_gpu(args, rank, world, local_rank):
         from paper_2501_16713_gb300 import Cnn, precond
         net = Cnn(shape)
         net.set_params(precond.laplacian_params(args.lap_c))
-        cg = cg_compare(plan, x, shape, dev, net)
-        cg["network"] = (f"symmetric form, Laplacian construction c={args.lap_c}, untrained "
-                         "(bench.py --workload precond128 trains)")
+        cg = cg_compare(plan, x, shape, dev, net, train_runs=8)
+        cg["network"] = (f"fcg: symmetric form, Laplacian construction c={args.lap_c}, untrained; "
+                         "fcg_trained: the same form trained from random weights on the pairs of "
+                         "8 plain-CG runs (bench.py --workload precond128 trains on 70)")
         net.close()
 
     # end to end through the public API with host buffers

@@ -110,16 +110,19 @@ def test_trained_network_reduces_iterations(prob):
     plan, lam, y, gen = prob
     r, e, iters = precond.generate_pairs(plan, _rhs(plan, gen, 12), lam, tol=1e-5, maxit=400)
     net = Cnn(SHAPE, seed=1)
+    # the same network before training: what the training gains
+    _, it_u, _, _, code_u, _ = plan.solve_fcg(y, lam, net, tol=TOL, maxit=400, check=False)
     losses = precond.train(net, r, e, steps=1000, lr=1e-3, lr_final=3e-5, batch=4, seed=0,
                            log_every=100)
     _, it_cg, _, tr_cg, _ = plan.solve_cg(y, lam, tol=TOL, maxit=400)
     x_f, it_f, _, tr_f, code, fb = plan.solve_fcg(y, lam, net, tol=TOL, maxit=400)
     print(f"pairs {r.shape[0]} from runs {iters}; loss {[round(l, 4) for l in losses if l == l]}")
     print(f"plain CG {it_cg} it, true res {tr_cg:.2e}; FCG+net {it_f} it, true res {tr_f:.2e}, "
-          f"fallbacks {fb}")
+          f"fallbacks {fb}; untrained network {it_u} it")
     assert code == 0
     assert tr_f < 2 * TOL
     assert it_f < it_cg
+    assert it_f < it_u
     net.close()
 
 
