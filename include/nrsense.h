@@ -495,6 +495,10 @@ typedef struct {
                                   re-tiles the plan, synchronising) */
   double  spread_item_ms[3];   /* measured k-space spread with the chosen kernel at 512, 1024,
                                   2048 entries per item (-1: n/a) */
+  int32_t interp_image_home;   /* image-space interpolation: 0 a thread per displaced voxel
+                                  gathering from global memory, 1 super-tiles of the upsampled
+                                  image staged in shared memory (W = 4, not compensated) */
+  double  interp_image_ms[2];  /* measured: per voxel, super-tiles (-1: n/a) */
 } nrsense_tuning;
 nrsense_status nrsense_plan_autotune(nrsense_plan_t plan, int32_t reps, nrsense_tuning* out_host,
                                      void* stream);

@@ -180,7 +180,11 @@ nrsense_status warp_forward(nrsense_plan_s* p, const nrsense_c64* x, nrsense_c64
   STAGE(DEAPOD_PAD, launch_deapod_pad(g, p->deapod, p->b_xhat, p->b_upad, s));
   NRS_TRY(launched());
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_upad, p->b_ugrid, CUFFT_INVERSE));
-  STAGE(INTERP_IMAGE, launch_interp_image(g, p->W, p->kc, p->P, p->disp, p->b_ugrid, m, s));
+  if (p->interp_home && p->home_ok) {
+    STAGE(INTERP_IMAGE, launch_interp_home(g, p->kc, p->ihome, p->b_ugrid, m, s));
+  } else {
+    STAGE(INTERP_IMAGE, launch_interp_image(g, p->W, p->kc, p->P, p->disp, p->b_ugrid, m, s));
+  }
   return launched();
 }
 
@@ -392,6 +396,9 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
   p->interp_tma = t->interp_tma == 1 && p->tma_ok;
   if (t->spread_image_warp < 0 || t->spread_image_warp > 2) return NRSENSE_ERR_ARG;
   if (t->spread_image_warp == 2 && !p->home_ok) return NRSENSE_ERR_ARG;
+  if (t->interp_image_home != 0 && t->interp_image_home != 1) return NRSENSE_ERR_ARG;
+  if (t->interp_image_home == 1 && !p->home_ok) return NRSENSE_ERR_ARG;
+  p->interp_home = t->interp_image_home == 1;
   if (t->fft_pruned != 0 && t->fft_pruned != 1) return NRSENSE_ERR_ARG;
   if (t->fft_pruned == 1 && !p->fft_pruned_ok) return NRSENSE_ERR_ARG;
   p->spread_image_variant = image_variant_of(t->spread_image_warp);
@@ -416,6 +423,8 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
   out->interp_tma = p->interp_tma ? 1 : 0;
   out->spread_image_warp = image_tuning_of(p->spread_image_variant);
   out->spread_image_ms[2] = -1.0;
+  out->interp_image_home = p->interp_home ? 1 : 0;
+  out->interp_image_ms[0] = out->interp_image_ms[1] = -1.0;
   out->spread_max_item = p->spread_max_item;
   for (int k = 0; k < 3; ++k) out->spread_item_ms[k] = -1.0;
   out->fft_pruned = p->fft_pruned ? 1 : 0;
@@ -452,6 +461,30 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
       }
       out->spread_image_ms[k] = double(ms) / reps;
     }
+    // image-space interpolation: thread per voxel, or super-tiles staged in
+    // shared memory (input: the plan's upsampled-image buffer)
+    for (int k = 0; k < 2 && (k == 0 || p->home_ok); ++k) {
+      auto run = [&] {
+        if (k == 1)
+          p->launches += launch_interp_home(g, p->kc, p->ihome, p->b_ugrid, p->b_m, s);
+        else
+          p->launches += launch_interp_image(g, p->W, p->kc, p->P, p->disp, p->b_ugrid, p->b_m, s);
+      };
+      run();
+      cudaEventRecord(a, s);
+      for (int r = 0; r < reps; ++r) run();
+      cudaEventRecord(b, s);
+      float ms = -1.f;
+      if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return NRSENSE_ERR_CUDA;
+      }
+      out->interp_image_ms[k] = double(ms) / reps;
+    }
+    p->interp_home = out->interp_image_ms[1] >= 0.0 &&
+                     out->interp_image_ms[1] < out->interp_image_ms[0];
+    out->interp_image_home = p->interp_home ? 1 : 0;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     int bi = out->spread_image_ms[1] < out->spread_image_ms[0] ? 1 : 0;

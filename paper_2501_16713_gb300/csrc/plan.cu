@@ -623,6 +623,7 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     if (p->W == 4 && !p->comp_spread) {
       NRS_TRY(build_home_set(p, pts, s));
       p->spread_image_variant = kSpreadHome;
+      p->interp_home = true;
     }
   }
 

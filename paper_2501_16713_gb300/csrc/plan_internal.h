@@ -73,6 +73,7 @@ struct nrsense_plan_s {
   nrs::PointSet ipts;               // displaced voxels of all phases
   nrs::HomeSet ihome{};             // the same, sorted by 8^3 home tile (home-tile spread)
   bool home_ok = false;             // ihome built (W = 4, not compensated)
+  bool interp_home = false;         // image-space interpolation over super-tiles (autotuned)
   nrsense_c64* home_scratch = nullptr;  // super-tile rims of the home-tile spread
   nrs::TilePlan ktiles{}, itiles{};  // k-space and image-space tiles
   int phase_chunk = 1;              // phases per launch
@@ -261,6 +262,10 @@ int launch_spread_home(const Geo& g, const KernelCoefs& kc, const HomeSet& hs,
                        const nrsense_c64* vals, nrsense_c64* grid, nrsense_c64* scratch,
                        cudaStream_t s);
 long long home_scratch_elems(const HomeSet& hs);
+// image-space interpolation over the same super-tiles (spread_home.cu): m rows
+// perm of the home set's points, all phases
+int launch_interp_home(const Geo& g, const KernelCoefs& kc, const HomeSet& hs,
+                       const nrsense_c64* u, nrsense_c64* m, cudaStream_t s);
 cudaError_t configure_home_kernels();
 // own pruned coil-grid transforms (fft_pruned.cu).  Forward: grid slots
 // jj * C + c of phases jj < nph = DFT3(S_c m_jj / C3 zero-padded), through the

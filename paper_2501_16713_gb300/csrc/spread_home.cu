@@ -206,9 +206,30 @@ __global__ void __launch_bounds__(256) home_rim_kernel(Geo g, HomeSet hs,
   const int r0 = min(3, e0), r1 = min(3, e1), r2 = min(3, e2);
   // the rim as three slabs: P0 < 3; P0 >= 3 and P1 < 3; P0, P1 >= 3 and P2 < 3
   const int na = r0 * e1 * e2, nb = (e0 - r0) * r1 * e2, nc = (e0 - r0) * (e1 - r1) * r2;
+  const bool full = e0 == kHS && e1 == kHS && e2 == kHS;
   int t = blockIdx.y * blockDim.x + threadIdx.x;
   int P0, P1, P2;
-  if (t < na) {
+  if (full && t < na + nb + nc) {
+    // 16^3 super-tile: slabs of 768, 624 and 507 points, rows of 16 or 3
+    if (t < 768) {
+      P2 = t & 15;
+      P1 = (t >> 4) & 15;
+      P0 = t >> 8;
+    } else if ((t -= 768) < 624) {
+      P2 = t & 15;
+      const int r = t >> 4;  // (P0 - 3) * 3 + P1
+      P0 = 3 + r / 3;
+      P1 = r - (P0 - 3) * 3;
+    } else {
+      t -= 624;
+      const int r = t / 3;  // (P0 - 3) * 13 + (P1 - 3)
+      P2 = t - 3 * r;
+      P0 = 3 + r / 13;
+      P1 = 3 + (r - (P0 - 3) * 13);
+    }
+  } else if (full) {
+    return;
+  } else if (t < na) {
     P2 = t % e2;
     P1 = (t / e2) % e1;
     P0 = t / (e2 * e1);
@@ -248,6 +269,105 @@ __global__ void __launch_bounds__(256) home_rim_kernel(Geo g, HomeSet hs,
   grid[((long long)x0 * g.g1 + x1) * g.g2 + x2] = sum;
 }
 
+// Backprojection Core B_j^(i) (section "Image-space Gridding", forward
+// diagram) on the same super-tiles: m_j[n] = sum_taps c3(q - g) u[g mod G],
+// q = sigma (n + d_j[n]).  A CTA copies the 19^3 padded region of its
+// super-tile (16^3 plus the 3 points footprints reach past it, wrapped around
+// the periodic grid) from u into shared memory with per-value asynchronous
+// copies, then every thread takes displaced voxels of the super-tile's eight
+// home tiles (all phases) and sums its 64 taps from shared memory: the gathers
+// never leave the SM.  Taps are summed as the per-voxel kernel does (x taps
+// weighted first, then the (z, y) weight), the result goes to the voxel's row.
+constexpr int kHR = kHP;  // staged region extent per axis (19)
+
+__global__ void __launch_bounds__(256) interp_home_kernel(Geo g, KernelCoefs kc, HomeSet hs,
+                                                          const float2* __restrict__ u,
+                                                          float2* __restrict__ m) {
+  extern __shared__ float4 smem_ih[];
+  float2* reg = reinterpret_cast<float2*>(smem_ih);  // [kHR][kHR][kHR]
+  __shared__ int s_beg[kHWarps + 1], s_start[kHWarps];
+  const int s = blockIdx.x;
+  const int s2 = s % hs.ns2, s1 = (s / hs.ns2) % hs.ns1, s0 = s / (hs.ns2 * hs.ns1);
+  const int o0 = kHS * s0, o1 = kHS * s1, o2 = kHS * s2;
+  const int e0 = home_extent(g.g0, o0), e1 = home_extent(g.g1, o1), e2 = home_extent(g.g2, o2);
+  const int p0n = e0 + 3, p1n = e1 + 3, p2n = e2 + 3;
+  {
+    // a warp copies (z, y) rows, lane = x (at most 19 of the 32 lanes)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int gx = wrap_once(o2 + lane, g.g2);
+    for (int z = 0; z < p0n; ++z) {
+      const long long zoff = (long long)wrap_once(o0 + z, g.g0) * g.g1;
+      for (int y = warp; y < p1n; y += nw)
+        if (lane < p2n)
+          cp_async_8(reg + (z * kHR + y) * kHR + lane,
+                     u + (zoff + wrap_once(o1 + y, g.g1)) * g.g2 + gx, true);
+    }
+  }
+  if (threadIdx.x == 0) {
+    // the points of the eight home tiles, as one flat range
+    int acc = 0;
+    for (int w = 0; w < kHWarps; ++w) {
+      const int w0 = (w >> 2) & 1, w1 = (w >> 1) & 1, w2 = w & 1;
+      int b = 0, n = 0;
+      if (kHT * w0 < e0 && kHT * w1 < e1 && kHT * w2 < e2) {
+        const int t = ((2 * s0 + w0) * hs.nt1 + (2 * s1 + w1)) * hs.nt2 + (2 * s2 + w2);
+        b = __ldg(hs.tstart + t);
+        n = __ldg(hs.tstart + t + 1) - b;
+      }
+      s_beg[w] = acc;
+      s_start[w] = b;
+      acc += n;
+    }
+    s_beg[kHWarps] = acc;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int total = s_beg[kHWarps];
+  for (int f = threadIdx.x; f < total; f += blockDim.x) {
+    int w = 0;
+#pragma unroll
+    for (int k = 1; k < kHWarps; ++k) w += f >= s_beg[k] ? 1 : 0;
+    const int i = s_start[w] + (f - s_beg[w]);
+    const float4 q = __ldg(hs.qs + i);
+    const int row = __ldg(hs.perm + i);
+    int b0, b1, b2;
+    unpack_base(__float_as_uint(q.w), b0, b1, b2);
+    float w0[4], w1[4], w2[4];
+    kernel_weights<4>(q.x, kc, w0);
+    kernel_weights<4>(q.y, kc, w1);
+    kernel_weights<4>(q.z, kc, w2);
+    const float2* base = reg + ((b0 - o0) * kHR + (b1 - o1)) * kHR + (b2 - o2);
+    float ar = 0.f, ai = 0.f;
+#pragma unroll
+    for (int t0 = 0; t0 < 4; ++t0)
+#pragma unroll
+      for (int t1 = 0; t1 < 4; ++t1) {
+        const float w01 = w0[t0] * w1[t1];
+        const float2* rowp = base + (t0 * kHR + t1) * kHR;
+        float rr = 0.f, ri = 0.f;
+#pragma unroll
+        for (int t2 = 0; t2 < 4; ++t2) {
+          const float2 v = rowp[t2];
+          rr = fmaf(w2[t2], v.x, rr);
+          ri = fmaf(w2[t2], v.y, ri);
+        }
+        ar = fmaf(w01, rr, ar);
+        ai = fmaf(w01, ri, ai);
+      }
+    m[row] = make_float2(ar, ai);
+  }
+}
+
+size_t interp_home_smem_bytes() { return size_t(kHR) * kHR * kHR * sizeof(float2); }
+
+int launch_interp_home(const Geo& g, const KernelCoefs& kc, const HomeSet& hs,
+                       const nrsense_c64* u, nrsense_c64* m, cudaStream_t s) {
+  const unsigned nsuper = unsigned(hs.ns0 * hs.ns1 * hs.ns2);
+  interp_home_kernel<<<nsuper, 256, interp_home_smem_bytes(), s>>>(
+      g, kc, hs, reinterpret_cast<const float2*>(u), reinterpret_cast<float2*>(m));
+  return 1;
+}
+
 size_t home_smem_bytes() { return size_t(kHWarps) * kHAcc * sizeof(float2); }
 
 long long home_scratch_elems(const HomeSet& hs) {
@@ -255,8 +375,11 @@ long long home_scratch_elems(const HomeSet& hs) {
 }
 
 cudaError_t configure_home_kernels() {
-  return cudaFuncSetAttribute(spread_home_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(home_smem_bytes()));
+  const cudaError_t e = cudaFuncSetAttribute(
+      spread_home_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(home_smem_bytes()));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(interp_home_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(interp_home_smem_bytes()));
 }
 
 int launch_spread_home(const Geo& g, const KernelCoefs& kc, const HomeSet& hs,

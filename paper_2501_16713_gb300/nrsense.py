@@ -54,7 +54,8 @@ class Tuning(ctypes.Structure):
                 ("spread_mma_ms", ctypes.c_double), ("spread_mma_wpc", ctypes.c_int32),
                 ("spread_mma_cube", ctypes.c_int32), ("spread_mma_geo_ms", ctypes.c_double * 2),
                 ("interp_tma2_ms", ctypes.c_double), ("spread_max_item", ctypes.c_int32),
-                ("spread_item_ms", ctypes.c_double * 3)]
+                ("spread_item_ms", ctypes.c_double * 3),
+                ("interp_image_home", ctypes.c_int32), ("interp_image_ms", ctypes.c_double * 2)]
 
 
 class Info(ctypes.Structure):
@@ -627,6 +628,7 @@ class Plan:
             t.spread_mma_wpc = int(store[key].get("spread_mma_wpc", 1))
             t.spread_mma_cube = int(store[key].get("spread_mma_cube", 0))
             t.spread_max_item = int(store[key].get("spread_max_item", 0))
+            t.interp_image_home = int(store[key].get("interp_image_home", 0))
             _check(self.lib.nrsense_plan_set_tuning(self._h, ctypes.byref(t)),
                    "nrsense_plan_set_tuning")
             return dict(store[key], cached=True)
@@ -643,7 +645,9 @@ class Plan:
                "spread_mma_cube": t.spread_mma_cube,
                "spread_mma_geo_ms": list(t.spread_mma_geo_ms),
                "interp_tma2_ms": t.interp_tma2_ms, "spread_max_item": t.spread_max_item,
-               "spread_item_ms": list(t.spread_item_ms)}
+               "spread_item_ms": list(t.spread_item_ms),
+               "interp_image_home": t.interp_image_home,
+               "interp_image_ms": list(t.interp_image_ms)}
         if cache:
             store[key] = res
             tmp = cache + ".tmp"

@@ -353,11 +353,23 @@ def test_home_tile_spread_ragged_and_wrapped(shape):
     ref = sum(O.warp_adjoint(geo, w[j], case["disp"][j].astype(np.float64)) for j in range(3))
     t = Tuning()
     t.spread_variant, t.interp_coils, t.spread_image_warp = 3, 8, 2
+    t.interp_image_home = 1
     assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == 0
     xa = plan.warp_adjoint(to_dev(w)).cpu().numpy()
     e = rel_l2(xa, ref)
     print(f"home-tile image-space adjoint {shape}: rel L2 {e:.2e}")
     assert e < TOL_FP32
+    # the forward warp gathered from super-tiles staged in shared memory
+    x = case["x"]
+    m = plan.warp_forward(to_dev(x)).cpu().numpy()
+    mref = np.stack([O.warp_forward(geo, x, case["disp"][j].astype(np.float64)) for j in range(3)])
+    ef = rel_l2(m, mref)
+    print(f"super-tile image-space forward {shape}: rel L2 {ef:.2e}")
+    assert ef < TOL_FP32
+    t.interp_image_home = 0
+    assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == 0
+    m0 = plan.warp_forward(to_dev(x)).cpu().numpy()
+    assert rel_l2(m, m0) < 1e-6
     plan.close()
 
 
