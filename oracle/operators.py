@@ -55,14 +55,19 @@ FFT_WORKERS = 1
 class Geometry:
     """Image size, oversampling and kernel parameters of one operator."""
 
-    def __init__(self, shape, osf: int = 2, width: int = 4, beta: float | None = None):
+    def __init__(self, shape, osf: float = 2, width: int = 4, beta: float | None = None):
         self.shape = tuple(int(s) for s in shape)
         if len(self.shape) != 3 or any(s % 2 for s in self.shape):
             raise ValueError("image dimensions must be three even integers")
-        self.osf = int(osf)
+        # sigma need not be an integer (the oversampled grid G = sigma N only
+        # has to be a whole number of points per axis)
+        self.osf = int(osf) if float(osf).is_integer() else float(osf)
         self.width = int(width)
-        self.beta = float(beta_or_default(beta, width, osf))
-        self.grid = tuple(self.osf * s for s in self.shape)
+        self.beta = float(beta_or_default(beta, width, self.osf))
+        grid = [self.osf * s for s in self.shape]
+        if any(abs(gv - round(gv)) > 1e-9 for gv in grid):
+            raise ValueError("sigma * N must be an integer on every axis")
+        self.grid = tuple(int(round(gv)) for gv in grid)
 
     def kspace_freqs(self, axis):
         """k in K_N, in numpy FFT order, as integers."""

@@ -124,3 +124,33 @@ def test_full_adjoint_sparse_data(full):
     e = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     print(f"full-size adjoint of sparse data: rel L2 {e:.2e}")
     assert e < TOL_FP32
+
+
+def test_full_phase_one_coil_every_value(full):
+    # G_0 and G_0^H of the benchmark plan (its autotuned kernels) for one coil,
+    # every output value against the oracle: all 1.5 M samples of the
+    # forward, all 2.1 M voxels of the adjoint; the other coils' inputs are
+    # zero and so must be their outputs
+    from helpers import rel_l2
+    w, plan = full
+    shape = w["spec"].shape
+    geo = O.Geometry(shape)
+    C = w["spec"].n_coils
+    om = w["coords"][0]
+    v = np.zeros((C,) + shape, np.complex64)
+    v[0] = (w["x"] * w["smaps"][0]).astype(np.complex64)
+    y = plan.kspace_forward(0, to_dev(v)).cpu().numpy()
+    yref = O.kspace_forward(geo, v[0].astype(np.complex128), om)
+    e = rel_l2(y[:, 0], yref)
+    print(f"G_0, coil 0, {yref.size} samples: rel L2 {e:.2e}")
+    assert e < TOL_FP32
+    assert not np.any(y[:, 1:])
+    rng = np.random.default_rng(8)
+    yin = np.zeros((om.shape[0], C), np.complex64)
+    yin[:, 0] = (rng.standard_normal(om.shape[0]) + 1j * rng.standard_normal(om.shape[0]))
+    xa = plan.kspace_adjoint(0, to_dev(yin)).cpu().numpy()
+    xref = O.kspace_adjoint(geo, yin[:, 0].astype(np.complex128), om)
+    ea = rel_l2(xa[0], xref)
+    print(f"G_0^H, coil 0, {xref.size} voxels: rel L2 {ea:.2e}")
+    assert ea < TOL_FP32
+    assert not np.any(xa[1:])

@@ -279,3 +279,57 @@ def test_appendix_iterative_inversion_beats_negated_field():
     err_naive = _rel(naive, p)
     err_cg = _rel(x.reshape(shape), p)
     assert err_cg < 0.5 * err_naive
+
+
+# --------------------------------------------------------------------------
+# Smaller oversampling, sigma = 1.5 with W = 6 (G = 1.5 N need not be a
+# multiple of N): the displaced positions 1.5 (n + d) no longer sit on a
+# sub-lattice of the grid, so the circulant and shift closed forms above do
+# not apply; the dense factor matrices and the rigorous aliasing bound do.
+# --------------------------------------------------------------------------
+
+def test_sigma_one_and_a_half_geometry():
+    geo = O.Geometry((8, 10, 12), 1.5, 6)
+    assert geo.grid == (12, 15, 18) and geo.osf == 1.5
+    assert geo.beta == pytest.approx(K.beatty_beta(6, 1.5))
+    with pytest.raises(ValueError):
+        O.Geometry((6, 6, 6), 1.25, 6)  # 7.5 grid points
+
+
+def test_sigma_one_and_a_half_matches_dense_factors(rng):
+    shape = (8, 6, 8)
+    geo = O.Geometry(shape, 1.5, 6)
+    d = _small_disp(rng, shape)
+    T = R.dense_warp(geo, d)
+    x = _crandn(rng, shape)
+    w = _crandn(rng, shape)
+    assert _rel(O.warp_forward(geo, x, d).ravel(), T @ x.ravel()) < 1e-12
+    assert _rel(O.warp_adjoint(geo, w, d).ravel(), T.conj().T @ w.ravel()) < 1e-12
+    om = rng.uniform(-np.pi, np.pi, (150, 3))
+    Gm = R.dense_kspace(geo, om)
+    v = _crandn(rng, shape)
+    y = _crandn(rng, (150,))
+    assert _rel(O.kspace_forward(geo, v, om), Gm @ v.ravel()) < 1e-12
+    assert _rel(O.kspace_adjoint(geo, y, om).ravel(), Gm.conj().T @ y) < 1e-12
+
+
+def test_sigma_one_and_a_half_within_bound_of_exact(rng):
+    import synth
+    shape = (16, 12, 14)
+    geo = O.Geometry(shape, 1.5, 6)
+    eps1, eps3 = R.alias_eps(geo)
+    # W = 6 at sigma 1.5 keeps the aliasing error near that of W = 4 at sigma 2
+    eps_ref = R.alias_eps(O.Geometry(shape, 2, 4))[0]
+    assert 0.1 * eps_ref < eps1 < 3 * eps_ref
+    x = synth.small_case(shape, 0, 1, 0, seed=3)["x"].astype(np.complex128)
+    x = x + 0.1 * _crandn(rng, shape)
+    d = synth.bump_displacement(shape, 9, 2.7, width_range=(2.0, 4.0)).astype(np.float64)
+    got = O.warp_forward(geo, x, d)
+    bound = eps3 * np.sum(np.abs(np.fft.fftn(x))) / np.prod(shape)
+    assert np.max(np.abs(got - R.warp_exact(geo, x, d))) <= bound
+    assert np.max(np.abs(got - R.warp_exact(geo, x, -d))) > bound
+    v = _crandn(rng, shape)
+    om = rng.uniform(-np.pi, np.pi, (400, 3))
+    gk = O.kspace_forward(geo, v, om)
+    assert np.max(np.abs(gk - R.nudft(geo, v, om))) <= eps3 * np.sum(np.abs(v))
+    assert np.max(np.abs(gk - R.nudft(geo, v, -om))) > eps3 * np.sum(np.abs(v))
