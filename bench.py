@@ -1016,7 +1016,7 @@ def run_gpu(args, rank, world, local_rank):
     disp = torch.from_numpy(np.stack(w["disp"])).to(dev)
     smaps = torch.from_numpy(w["smaps"]).to(dev)
     coords = [torch.from_numpy(c).to(dev) for c in w["coords"]]
-    plan = Plan(shape, disp=disp, coords=coords, smaps=smaps)
+    plan = Plan(shape, disp=disp, coords=coords, smaps=smaps, osf=args.osf, width=args.width)
     del disp, smaps, coords
     tuning = plan.autotune(reps=3)  # launch choices, timed on this plan (untimed region)
     info = plan.info()
@@ -1135,7 +1135,8 @@ def run_gpu(args, rank, world, local_rank):
         "data": "synthetic (seeded phantom, Gaussian-bump displacements, Gaussian coil "
                 "maps, cone-like trajectory); no trained weights",
         "config": {"workload": args.workload, "image": list(shape), "coils": spec.n_coils,
-                   "phases": len(M), "samples_per_phase": M, "osf": 2, "kb_width": 4,
+                   "phases": len(M), "samples_per_phase": M, "osf": args.osf,
+                   "kb_width": args.width, "grid": info["grid"],
                    "lambda": args.lam, "parallelism": f"replicas x{world}",
                    "tuning": tuning,
                    "l2": "inputs larger than L2: per-phase coil grids 1.07 GB, "
@@ -1180,6 +1181,9 @@ def main():
     ap.add_argument("--phases", type=int, default=None,
                     help="use only the first K phases (a smaller case for profiling)")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG comparison")
+    ap.add_argument("--osf", type=float, default=2.0,
+                    help="oversampling sigma (rational: G = sigma N per axis must be whole)")
+    ap.add_argument("--width", type=int, default=4, help="kernel width W (4 or 6)")
     ap.add_argument("--lap-c", type=float, default=30.0)
     ap.add_argument("--pair-runs", type=int, default=70)
     args = ap.parse_args()

@@ -82,7 +82,8 @@ typedef struct nrsense_cnn_s* nrsense_cnn_t;
 
 typedef struct {
   int32_t n[3];        /* image size per axis; each even and >= 4 */
-  int32_t osf;         /* oversampling sigma, integer >= 2 (grid G = osf * n) */
+  int32_t osf;         /* oversampling sigma, integer 2..4 (grid G = osf * n) unless grid[]
+                          is given */
   int32_t kb_width;    /* kernel width W in oversampled-grid units: 4 or 6 */
   double  kb_beta;     /* Kaiser-Bessel beta; 0 selects Beatty's formula */
   int32_t n_phases;    /* P >= 1 */
@@ -91,6 +92,12 @@ typedef struct {
   uint32_t flags;      /* NRSENSE_* flags */
   int32_t phase_chunk; /* phases processed per launch (1..16); 0 = as many as half of the
                           free device memory at plan time allows */
+  int32_t grid[3];     /* oversampled grid G per axis, overriding osf when all three are
+                          > 0: sigma = G / n, the same ratio on every axis, 1.25 <= sigma
+                          <= 4, G <= 1024 (a rational sigma such as 1.5 or 1.25, with a wider
+                          kernel for the same aliasing error; the pruned coil-grid transforms
+                          need sigma 2 and the tensor-core and TMA kernels W = 4, so other
+                          choices run the generic kernels); all 0: G = osf * n */
 } nrsense_desc;
 
 /* Plan-time facts, for benchmarking and tests. */

@@ -70,20 +70,46 @@ __global__ void __launch_bounds__(256) interp_image_kernel(Geo g, KernelCoefs kc
   const int i1 = int(r % g.n1);
   const int i0 = int(r / g.n1);
   const float sg = float(g.osf);
+  // sigma = G / N not an integer (g.osf == 0): sigma n = (G n) div N + r / N
+  // exactly, r = (G n) mod N; the rest in FP64
+  const int ip0 = int((long long)g.g0 * i0 / g.n0), ip1 = int((long long)g.g1 * i1 / g.n1),
+            ip2 = int((long long)g.g2 * i2 / g.n2);
+  const double fr0 = double((long long)g.g0 * i0 - (long long)ip0 * g.n0) / g.n0;
+  const double fr1 = double((long long)g.g1 * i1 - (long long)ip1 * g.n1) / g.n1;
+  const double fr2 = double((long long)g.g2 * i2 - (long long)ip2 * g.n2) / g.n2;
+  const double sr0 = double(g.g0) / g.n0, sr1 = double(g.g1) / g.n1, sr2 = double(g.g2) / g.n2;
   for (int j = 0; j < P; ++j) {
     const float* dj = disp + (long long)j * 3 * g.nvox;
-    // exact decomposition of q = sigma*n + sigma*d into first tap and fraction
-    const float s0 = sg * __ldg(dj + idx);
-    const float s1 = sg * __ldg(dj + g.nvox + idx);
-    const float s2 = sg * __ldg(dj + 2 * g.nvox + idx);
-    const float fl0 = floorf(s0), fl1 = floorf(s1), fl2 = floorf(s2);
+    float f0, f1, f2;
+    int b0, b1, b2;
+    if (g.osf > 0) {
+      // exact decomposition of q = sigma*n + sigma*d into first tap and fraction
+      const float s0 = sg * __ldg(dj + idx);
+      const float s1 = sg * __ldg(dj + g.nvox + idx);
+      const float s2 = sg * __ldg(dj + 2 * g.nvox + idx);
+      const float fl0 = floorf(s0), fl1 = floorf(s1), fl2 = floorf(s2);
+      f0 = s0 - fl0;
+      f1 = s1 - fl1;
+      f2 = s2 - fl2;
+      b0 = wrap_any(g.osf * i0 + int(fl0) - (W / 2 - 1), g.g0);
+      b1 = wrap_any(g.osf * i1 + int(fl1) - (W / 2 - 1), g.g1);
+      b2 = wrap_any(g.osf * i2 + int(fl2) - (W / 2 - 1), g.g2);
+    } else {
+      const double s0 = fr0 + sr0 * double(__ldg(dj + idx));
+      const double s1 = fr1 + sr1 * double(__ldg(dj + g.nvox + idx));
+      const double s2 = fr2 + sr2 * double(__ldg(dj + 2 * g.nvox + idx));
+      const double fl0 = floor(s0), fl1 = floor(s1), fl2 = floor(s2);
+      f0 = float(s0 - fl0);
+      f1 = float(s1 - fl1);
+      f2 = float(s2 - fl2);
+      b0 = wrap_any(ip0 + int(fl0) - (W / 2 - 1), g.g0);
+      b1 = wrap_any(ip1 + int(fl1) - (W / 2 - 1), g.g1);
+      b2 = wrap_any(ip2 + int(fl2) - (W / 2 - 1), g.g2);
+    }
     float w0[W], w1[W], w2[W];
-    kernel_weights<W>(s0 - fl0, kc, w0);
-    kernel_weights<W>(s1 - fl1, kc, w1);
-    kernel_weights<W>(s2 - fl2, kc, w2);
-    const int b0 = wrap_any(g.osf * i0 + int(fl0) - (W / 2 - 1), g.g0);
-    const int b1 = wrap_any(g.osf * i1 + int(fl1) - (W / 2 - 1), g.g1);
-    const int b2 = wrap_any(g.osf * i2 + int(fl2) - (W / 2 - 1), g.g2);
+    kernel_weights<W>(f0, kc, w0);
+    kernel_weights<W>(f1, kc, w1);
+    kernel_weights<W>(f2, kc, w2);
     int x2[W];
 #pragma unroll
     for (int t = 0; t < W; ++t) x2[t] = wrap_once(b2 + t, g.g2);

@@ -527,7 +527,20 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   const nrsense_desc& d = *desc;
   for (int a = 0; a < 3; ++a)
     if (d.n[a] < 4 || (d.n[a] & 1)) return NRSENSE_ERR_ARG;
-  if (d.osf < 2 || d.osf > 4) return NRSENSE_ERR_ARG;
+  // oversampled grid: osf * n, or given per axis (a rational sigma = G / n)
+  const bool explicit_grid = d.grid[0] > 0 && d.grid[1] > 0 && d.grid[2] > 0;
+  if (!explicit_grid && (d.grid[0] != 0 || d.grid[1] != 0 || d.grid[2] != 0)) return NRSENSE_ERR_ARG;
+  int gsize[3];
+  if (explicit_grid) {
+    for (int a = 0; a < 3; ++a) {
+      gsize[a] = d.grid[a];
+      if (4 * gsize[a] < 5 * d.n[a] || gsize[a] > 4 * d.n[a]) return NRSENSE_ERR_ARG;
+      if ((long long)gsize[a] * d.n[0] != (long long)gsize[0] * d.n[a]) return NRSENSE_ERR_ARG;
+    }
+  } else {
+    if (d.osf < 2 || d.osf > 4) return NRSENSE_ERR_ARG;
+    for (int a = 0; a < 3; ++a) gsize[a] = d.osf * d.n[a];
+  }
   if (d.kb_width != 4 && d.kb_width != 6) return NRSENSE_ERR_ARG;
   if (d.n_phases < 1 || d.n_coils < 0) return NRSENSE_ERR_ARG;
   if (d.precision != NRSENSE_FP32 && d.precision != NRSENSE_BF16_STORE &&
@@ -536,7 +549,7 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   if (d.precision == NRSENSE_FP32_COMPENSATED && d.kb_width != 4) return NRSENSE_ERR_ARG;
   if (d.precision == NRSENSE_BF16_STORE)  // cuFFT's BF16 transforms: power-of-two sizes
     for (int a = 0; a < 3; ++a) {
-      const int ga = d.osf * d.n[a];
+      const int ga = gsize[a];
       if (ga & (ga - 1)) return NRSENSE_ERR_ARG;
     }
   if (!(d.kb_beta >= 0.0) || !std::isfinite(d.kb_beta)) return NRSENSE_ERR_ARG;
@@ -549,8 +562,10 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   p->W = d.kb_width;
   Geo& g = p->geo;
   g.n0 = d.n[0]; g.n1 = d.n[1]; g.n2 = d.n[2];
-  g.osf = d.osf;
-  g.g0 = d.osf * d.n[0]; g.g1 = d.osf * d.n[1]; g.g2 = d.osf * d.n[2];
+  g.g0 = gsize[0]; g.g1 = gsize[1]; g.g2 = gsize[2];
+  // integer sigma (0 when sigma = G / n is not an integer)
+  g.osf = (g.g0 % g.n0 == 0) ? g.g0 / g.n0 : 0;
+  const double sigma = double(g.g0) / double(g.n0);
   if (g.g0 > 1024 || g.g1 > 1024 || g.g2 > 1024) return NRSENSE_ERR_ARG;  // 10-bit packed taps
   // a tile and a kernel footprint must not wrap onto each other
   const int gmin = kSpreadTile + d.kb_width - 1;
@@ -561,7 +576,7 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
   if (!p->identity_warp && disp == nullptr) return NRSENSE_ERR_ARG;
   if (p->C > 0 && (coords == nullptr || smaps == nullptr || n_samples == nullptr))
     return NRSENSE_ERR_ARG;
-  p->beta = d.kb_beta > 0 ? d.kb_beta : beatty_beta(p->W, double(d.osf));
+  p->beta = d.kb_beta > 0 ? d.kb_beta : beatty_beta(p->W, sigma);
   if (!(p->beta > 0)) return NRSENSE_ERR_ARG;
   p->poly_err = fit_kernel_polys(p->W, p->beta, &p->kc);
 
@@ -610,8 +625,8 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
         const int ii[3] = {i0, i1, i2};
         HostPoint& h = pts[(size_t)(j * g.nvox + v)];
         for (int a = 0; a < 3; ++a) {
-          // q = sigma * (n + d) = sigma*n + sigma*d, exact in FP64
-          const double q = double(d.osf) * double(ii[a]) + double(d.osf) * double(dj[a * g.nvox + v]);
+          // q = sigma * (n + d) = sigma*n + sigma*d in FP64 (sigma*n exact)
+          const double q = sigma * double(ii[a]) + sigma * double(dj[a * g.nvox + v]);
           decompose(q, gs[a], p->W, &h.b[a], &h.f[a]);
         }
         h.row = int32_t(j * g.nvox + v);

@@ -40,7 +40,7 @@ class Desc(ctypes.Structure):
                 ("kb_width", ctypes.c_int32), ("kb_beta", ctypes.c_double),
                 ("n_phases", ctypes.c_int32), ("n_coils", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("phase_chunk", ctypes.c_int32)]
+                ("phase_chunk", ctypes.c_int32), ("grid", ctypes.c_int32 * 3)]
 
 
 class Tuning(ctypes.Structure):
@@ -360,10 +360,21 @@ class Plan:
             _need(disp, torch.float32, (self.n_phases, 3) + self.shape, "disp")
         d = Desc()
         d.n[:] = self.shape
-        d.osf, d.kb_width, d.kb_beta = int(osf), int(width), float(beta)
+        # sigma: an integer (G = osf n), or rational with G = osf n whole on every axis
+        if float(osf).is_integer():
+            d.osf = int(osf)
+            self.osf = int(osf)
+        else:
+            g = [float(osf) * n for n in self.shape]
+            if any(abs(v - round(v)) > 1e-9 for v in g):
+                raise ValueError("osf * n must be an integer on every axis")
+            d.osf = 0
+            d.grid[:] = [int(round(v)) for v in g]
+            self.osf = float(osf)
+        d.kb_width, d.kb_beta = int(width), float(beta)
         d.n_phases, d.n_coils = self.n_phases, self.n_coils
         d.precision = int(precision)
-        self.width, self.osf, self.precision = int(width), int(osf), int(precision)
+        self.width, self.precision = int(width), int(precision)
         d.flags = IDENTITY_WARP if identity_warp else 0
         d.phase_chunk = int(phase_chunk)
         self.counts = [0] * self.n_phases

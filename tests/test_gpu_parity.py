@@ -409,3 +409,40 @@ def test_kspace_split_sizes_agree_with_oracle():
         assert plan.lib.nrsense_plan_set_tuning(plan._h, ctypes.byref(t)) == -1
     assert plan.device_status() == 0
     plan.close()
+
+
+@pytest.mark.parametrize("shape,osf,W", [((16, 16, 16), 2, 6), ((16, 16, 16), 1.5, 6),
+                                         ((12, 16, 20), 1.5, 6), ((16, 16, 16), 1.25, 6)])
+def test_wider_kernel_and_smaller_oversampling_vs_oracle(shape, osf, W):
+    # W = 6 at sigma 2, and the smaller grids sigma 1.5 / 1.25 (G = sigma N not
+    # a multiple of N: the displaced positions sigma (n + d) split exactly
+    # as (G n) div N + the rest; the pruned transforms, the tensor-core and
+    # TMA kernels and the home tiles do not apply and the generic kernels run)
+    C, Ms = 3, [1500, 1100]
+    # the adjoint ends with the division by C(k/G), whose gain at the band
+    # edge k = N/2 grows as sigma falls (1.6 at sigma 2 with W 4, 4.9 at 1.5,
+    # 14.7 at 1.25 with W 6) and multiplies the FP32 rounding of the spread
+    # there: at sigma 1.25 the adjoint measured 2.0e-5, so its bar is 5e-5
+    tol = TOL_FP32 if osf >= 1.5 else 5e-5
+    case = synth.small_case(shape, C, 2, Ms, seed=181, max_disp=2.0, rigid=1.0)
+    plan = make_plan(case, shape, osf=osf, width=W)
+    geo = O.Geometry(shape, osf, W)
+    assert tuple(plan.info()["grid"]) == geo.grid
+    assert plan.info()["kb_beta"] == pytest.approx(geo.beta, rel=1e-12)
+    x = case["x"]
+    d64 = _d64(case)
+    m = plan.warp_forward(to_dev(x)).cpu().numpy()
+    mref = np.stack([O.warp_forward(geo, x, d) for d in d64])
+    assert rel_l2(m, mref) < TOL_FP32
+    ys = O.stacked_forward(geo, x, d64, case["smaps"], case["coords"])
+    y = plan.forward(to_dev(x)).cpu().numpy()
+    for j in range(2):
+        assert rel_l2(plan.phase_slice(y, j), ys[j]) < TOL_FP32, j
+    yin = c64(np.concatenate(ys))
+    yl = [plan.phase_slice(yin, j).astype(np.complex128) for j in range(2)]
+    xa = plan.adjoint(to_dev(yin)).cpu().numpy()
+    assert rel_l2(xa, O.stacked_adjoint(geo, yl, d64, case["smaps"], case["coords"])) < tol
+    xn = plan.normal(to_dev(x), 0.2).cpu().numpy()
+    assert rel_l2(xn, O.normal(geo, x, d64, case["smaps"], case["coords"], 0.2)) < tol
+    assert plan.device_status() == 0
+    plan.close()
