@@ -506,6 +506,14 @@ typedef struct {
                                   gathering from global memory, 1 super-tiles of the upsampled
                                   image staged in shared memory (W = 4, not compensated) */
   double  interp_image_ms[2];  /* measured: per voxel, super-tiles (-1: n/a) */
+  int32_t image_fft_pruned;    /* image-space G^3 transforms of T and T^H: 1 own pruned passes
+                                  (data half of every axis loaded or stored, deapodization and
+                                  zero-padding / cropping fused into the x passes; sigma 2,
+                                  power-of-two grid sizes 32..256, not with the compensated
+                                  precision; set_tuning rejects 1 elsewhere), 0 cuFFT plus the
+                                  deapodization kernels */
+  double  image_fft_ms[2];     /* measured forward + adjoint G^3 transforms with their
+                                  deapodization: cuFFT path, pruned path (-1: n/a) */
 } nrsense_tuning;
 nrsense_status nrsense_plan_autotune(nrsense_plan_t plan, int32_t reps, nrsense_tuning* out_host,
                                      void* stream);

@@ -168,6 +168,43 @@ PhaseTable image_table(const nrsense_plan_s* p) {
   return t;
 }
 
+// The G^3 half of T: u = F_G^-1 of the deapodized, zero-padded spectrum in
+// b_xhat, into b_ugrid.
+nrsense_status image_grid_forward(nrsense_plan_s* p, cudaStream_t s) {
+  const Geo& g = p->geo;
+  if (p->image_fft_pruned) {
+    nrsense_c64* t1 = p->b_upad;
+    nrsense_c64* t2 = p->b_upad + (long long)g.n0 * g.n1 * g.g2;
+    STAGE(FFT_G, launch_pruned_image_forward(g, p->deapod, p->b_xhat, t1, t2, p->b_ugrid, s));
+    p->upad_dirty = true;
+    return launched();
+  }
+  if (p->upad_dirty) {
+    if (cudaMemsetAsync(p->b_upad, 0, size_t(g.ngrid) * sizeof(nrsense_c64), s) != cudaSuccess)
+      return NRSENSE_ERR_CUDA;
+    p->upad_dirty = false;
+  }
+  STAGE(DEAPOD_PAD, launch_deapod_pad(g, p->deapod, p->b_xhat, p->b_upad, s));
+  NRS_TRY(launched());
+  return fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_upad, p->b_ugrid, CUFFT_INVERSE);
+}
+
+// The G^3 half of T^H: xhat = deapodized crop of F_G of the spread grid in
+// b_ugrid (which the cuFFT path overwrites).
+nrsense_status image_grid_adjoint(nrsense_plan_s* p, nrsense_c64* xhat, cudaStream_t s) {
+  const Geo& g = p->geo;
+  if (p->image_fft_pruned) {
+    nrsense_c64* t1 = p->b_upad;
+    nrsense_c64* t2 = p->b_upad + (long long)g.n0 * g.n1 * g.g2;
+    STAGE(FFT_G, launch_pruned_image_adjoint(g, p->deapod, p->b_ugrid, t2, t1, xhat, s));
+    p->upad_dirty = true;
+    return launched();
+  }
+  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_ugrid, p->b_ugrid, CUFFT_FORWARD));
+  STAGE(CROP_DEAPOD, launch_crop_deapod(g, p->deapod, p->b_ugrid, xhat, s));
+  return launched();
+}
+
 // m (P x nvox) = T_j x for all phases
 nrsense_status warp_forward(nrsense_plan_s* p, const nrsense_c64* x, nrsense_c64* m,
                             cudaStream_t s) {
@@ -177,9 +214,7 @@ nrsense_status warp_forward(nrsense_plan_s* p, const nrsense_c64* x, nrsense_c64
     return launched();
   }
   NRS_TRY(fft(p, NRSENSE_STAGE_FFT_N, p->fft_n, s, const_cast<nrsense_c64*>(x), p->b_xhat, CUFFT_FORWARD));
-  STAGE(DEAPOD_PAD, launch_deapod_pad(g, p->deapod, p->b_xhat, p->b_upad, s));
-  NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_upad, p->b_ugrid, CUFFT_INVERSE));
+  NRS_TRY(image_grid_forward(p, s));
   if (p->interp_home && p->home_ok) {
     STAGE(INTERP_IMAGE, launch_interp_home(g, p->kc, p->ihome, p->b_ugrid, m, s));
   } else {
@@ -205,9 +240,7 @@ nrsense_status warp_adjoint(nrsense_plan_s* p, const nrsense_c64* m, nrsense_c64
                                       p->d_status, s));
   }
   NRS_TRY(launched());
-  NRS_TRY(fft(p, NRSENSE_STAGE_FFT_G, p->fft_g, s, p->b_ugrid, p->b_ugrid, CUFFT_FORWARD));
-  STAGE(CROP_DEAPOD, launch_crop_deapod(g, p->deapod, p->b_ugrid, x, s));
-  NRS_TRY(launched());
+  NRS_TRY(image_grid_adjoint(p, x, s));
   return fft(p, NRSENSE_STAGE_FFT_N, p->fft_n, s, x, x, CUFFT_INVERSE);
 }
 
@@ -376,6 +409,8 @@ nrsense_status nrsense_apply_normal(nrsense_plan_t p, const nrsense_c64* x, doub
 
 nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t) {
   if (p == nullptr || t == nullptr) return NRSENSE_ERR_ARG;
+  // every field is checked before any is applied: a rejected call leaves the
+  // plan's choices as they were
   if (t->spread_variant != NRSENSE_TUNE_SPREAD_REGISTER &&
       t->spread_variant != NRSENSE_TUNE_SPREAD_SHARED &&
       t->spread_variant != NRSENSE_TUNE_SPREAD_REGISTER_WARP &&
@@ -384,6 +419,18 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
   if (t->interp_coils != 2 && t->interp_coils != 4 && t->interp_coils != 8) return NRSENSE_ERR_ARG;
   if (t->interp_tma != 0 && t->interp_tma != 1) return NRSENSE_ERR_ARG;
   if (t->spread_mma_cube != 0 && t->spread_mma_cube != 1) return NRSENSE_ERR_ARG;
+  if (t->spread_image_warp < 0 || t->spread_image_warp > 2) return NRSENSE_ERR_ARG;
+  if (t->spread_image_warp == 2 && !p->home_ok) return NRSENSE_ERR_ARG;
+  if (t->interp_image_home != 0 && t->interp_image_home != 1) return NRSENSE_ERR_ARG;
+  if (t->interp_image_home == 1 && !p->home_ok) return NRSENSE_ERR_ARG;
+  if (t->fft_pruned != 0 && t->fft_pruned != 1) return NRSENSE_ERR_ARG;
+  if (t->fft_pruned == 1 && !p->fft_pruned_ok) return NRSENSE_ERR_ARG;
+  const int m = t->spread_max_item;
+  if (m != 0 && m != 512 && m != 1024 && m != 2048) return NRSENSE_ERR_ARG;
+  if (t->image_fft_pruned != 0 && t->image_fft_pruned != 1) return NRSENSE_ERR_ARG;
+  if (t->image_fft_pruned == 1 && !p->image_fft_ok) return NRSENSE_ERR_ARG;
+  // the one step that can fail for want of memory comes first
+  if (m != 0) NRS_TRY(retile_kspace(p, m, nullptr));
   p->spread_variant = t->spread_variant == NRSENSE_TUNE_SPREAD_REGISTER   ? kSpreadRegister
                       : t->spread_variant == NRSENSE_TUNE_SPREAD_SHARED ? kSpreadShared
                       : t->spread_variant == NRSENSE_TUNE_SPREAD_MMA
@@ -394,20 +441,10 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
                           : kSpreadRegisterWarp;
   p->interp_coils = t->interp_coils;
   p->interp_tma = t->interp_tma == 1 && p->tma_ok;
-  if (t->spread_image_warp < 0 || t->spread_image_warp > 2) return NRSENSE_ERR_ARG;
-  if (t->spread_image_warp == 2 && !p->home_ok) return NRSENSE_ERR_ARG;
-  if (t->interp_image_home != 0 && t->interp_image_home != 1) return NRSENSE_ERR_ARG;
-  if (t->interp_image_home == 1 && !p->home_ok) return NRSENSE_ERR_ARG;
   p->interp_home = t->interp_image_home == 1;
-  if (t->fft_pruned != 0 && t->fft_pruned != 1) return NRSENSE_ERR_ARG;
-  if (t->fft_pruned == 1 && !p->fft_pruned_ok) return NRSENSE_ERR_ARG;
   p->spread_image_variant = image_variant_of(t->spread_image_warp);
   p->fft_pruned = t->fft_pruned == 1;
-  if (t->spread_max_item != 0) {
-    const int m = t->spread_max_item;
-    if (m != 512 && m != 1024 && m != 2048) return NRSENSE_ERR_ARG;
-    NRS_TRY(retile_kspace(p, m, nullptr));
-  }
+  p->image_fft_pruned = t->image_fft_pruned == 1;
   return NRSENSE_OK;
 }
 
@@ -429,6 +466,8 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
   for (int k = 0; k < 3; ++k) out->spread_item_ms[k] = -1.0;
   out->fft_pruned = p->fft_pruned ? 1 : 0;
   out->fft_ms[0] = out->fft_ms[1] = -1.0;
+  out->image_fft_pruned = p->image_fft_pruned ? 1 : 0;
+  out->image_fft_ms[0] = out->image_fft_ms[1] = -1.0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Geo& g = p->geo;
   if (!p->identity_warp && p->ipts.tp.t0 == 16) {
@@ -485,6 +524,31 @@ nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tun
     p->interp_home = out->interp_image_ms[1] >= 0.0 &&
                      out->interp_image_ms[1] < out->interp_image_ms[0];
     out->interp_image_home = p->interp_home ? 1 : 0;
+    // image-space G^3 transforms with their deapodization, forward and
+    // adjoint: cuFFT path vs the pruned passes (inputs: the plan's buffers)
+    for (int k = 0; k < 2 && p->image_fft_ok; ++k) {
+      p->image_fft_pruned = k == 1;
+      nrsense_status st = NRSENSE_OK;
+      auto run = [&] {
+        if (st == NRSENSE_OK) st = image_grid_forward(p, s);
+        if (st == NRSENSE_OK) st = image_grid_adjoint(p, p->b_tmp, s);
+      };
+      run();
+      cudaEventRecord(a, s);
+      for (int r = 0; r < reps; ++r) run();
+      cudaEventRecord(b, s);
+      float ms = -1.f;
+      if (st != NRSENSE_OK || cudaEventSynchronize(b) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return st != NRSENSE_OK ? st : NRSENSE_ERR_CUDA;
+      }
+      out->image_fft_ms[k] = double(ms) / reps;
+    }
+    p->image_fft_pruned = p->image_fft_ok && out->image_fft_ms[1] >= 0.0 &&
+                          out->image_fft_ms[1] < out->image_fft_ms[0];
+    out->image_fft_pruned = p->image_fft_pruned ? 1 : 0;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     int bi = out->spread_image_ms[1] < out->spread_image_ms[0] ? 1 : 0;

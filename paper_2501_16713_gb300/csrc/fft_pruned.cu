@@ -260,9 +260,10 @@ __global__ void __launch_bounds__(Shape<R1, R2>::threads, 4) fwd_x_kernel(
   }
 }
 
-// F2: T2[slot][i0][:][x] = DFT_y of T1[slot][i0][data rows][x].
+// F2: T2[slot][i0][:][x] = DFT_y of T1[slot][i0][data rows][x] (exponent sign
+// + for INV).
 // CTA: (block of 16 x, i0, slot).
-template <int R1, int R2>
+template <int R1, int R2, bool INV>
 __global__ void __launch_bounds__(Shape<R1, R2>::threads, 5) fwd_y_kernel(
     PassGeo g, const float2* __restrict__ t1, float2* __restrict__ t2) {
   __shared__ float2 sy[Shape<R1, R2>::smem];
@@ -279,14 +280,14 @@ __global__ void __launch_bounds__(Shape<R1, R2>::threads, 5) fwd_y_kernel(
     constexpr int k2 = decltype(k2c)::value;
     dst[(k1 + R1 * k2) * g.g2 + xb * kCols + col] = v;
   };
-  fft16<R1, R2, false, false, true, false>(sy, tw, ld, st);
+  fft16<R1, R2, INV, false, true, false>(sy, tw, ld, st);
 }
 
-// F3: grid[slot][:][y][x] = DFT_z of T2[slot][data planes][y][x].
+// F3: grid[slot][:][y][x] = DFT_z of T2[slot][data planes][y][x] (sign + for INV).
 // CTA: (block of 16 x, y, slot).  colmask (or null): per (y, x) 8^3-tile
 // column a bit per z tile that is ever read; other tiles are not stored, and
 // a CTA whose two tile columns have none returns at once.
-template <int R1, int R2>
+template <int R1, int R2, bool INV>
 __global__ void __launch_bounds__(Shape<R1, R2>::threads, 5) fwd_z_kernel(
     PassGeo g, const uint32_t* __restrict__ colmask, const float2* __restrict__ t2,
     float2* __restrict__ grid) {
@@ -313,12 +314,13 @@ __global__ void __launch_bounds__(Shape<R1, R2>::threads, 5) fwd_z_kernel(
     const int z = k1 + R1 * k2;
     if (((col < 8 ? m0 : m1) >> (z >> 3)) & 1u) dst[z * plane + col] = v;
   };
-  fft16<R1, R2, false, false, true, false>(sy, tw, ld, st);
+  fft16<R1, R2, INV, false, true, false>(sy, tw, ld, st);
 }
 
-// I3: T2[slot][i0][y][x] = (inverse DFT_z of grid[slot][:][y][x]) at the data planes.
+// I3: T2[slot][i0][y][x] = (DFT_z of grid[slot][:][y][x], sign + for INV) at the
+// data planes.
 // colmask (or null): z tiles outside it are zero in the grid and not loaded.
-template <int R1, int R2>
+template <int R1, int R2, bool INV>
 __global__ void __launch_bounds__(Shape<R1, R2>::threads, 5) inv_z_kernel(
     PassGeo g, const uint32_t* __restrict__ colmask, const float2* __restrict__ grid,
     float2* __restrict__ t2) {
@@ -345,11 +347,12 @@ __global__ void __launch_bounds__(Shape<R1, R2>::threads, 5) inv_z_kernel(
     constexpr int k2 = decltype(k2c)::value;
     dst[img_out<R1, R2>(k1, k2) * plane + col] = v;
   };
-  fft16<R1, R2, true, false, false, true>(sy, tw, ld, st);
+  fft16<R1, R2, INV, false, false, true>(sy, tw, ld, st);
 }
 
-// I2: T1[slot][i0][i1][x] = (inverse DFT_y of T2[slot][i0][:][x]) at the data rows.
-template <int R1, int R2>
+// I2: T1[slot][i0][i1][x] = (DFT_y of T2[slot][i0][:][x], sign + for INV) at the
+// data rows.
+template <int R1, int R2, bool INV>
 __global__ void __launch_bounds__(Shape<R1, R2>::threads, 5) inv_y_kernel(
     PassGeo g, const float2* __restrict__ t2, float2* __restrict__ t1) {
   __shared__ float2 sy[Shape<R1, R2>::smem];
@@ -366,7 +369,7 @@ __global__ void __launch_bounds__(Shape<R1, R2>::threads, 5) inv_y_kernel(
     constexpr int k2 = decltype(k2c)::value;
     dst[img_out<R1, R2>(k1, k2) * g.g2 + xb * kCols + col] = v;
   };
-  fft16<R1, R2, true, false, false, true>(sy, tw, ld, st);
+  fft16<R1, R2, INV, false, false, true>(sy, tw, ld, st);
 }
 
 // I1: w[jj][i0][i1][i2] = C3^-1 sum_c conj(S_c) (inverse DFT_x of T1[slot][i0][i1][:])
@@ -421,6 +424,75 @@ __global__ void __launch_bounds__(Shape<R1, R2>::threads, 3) inv_x_kernel(
   }
 }
 
+// The image-space transforms of T_j (forward diagram F -> 1/C* -> Z -> F^H)
+// and T_j^H (F -> Z^H -> 1/C -> F^H) over the one G^3 grid.  Frequency k of
+// an axis sits at grid position k mod G: with the centred index i = k + N/2
+// that is the same placement as the coil images' (data at [0, G/4) and
+// [3G/4, G)), so the y and z passes above serve unchanged; only the x passes
+// differ: they read (write) the N^3 spectrum in FFT order, index
+// f = (i + N/2) mod N, and apply 1/(N^3 C3(k/G)) on the way.
+
+__device__ __forceinline__ int fft_index(int i, int n) { return i < (n >> 1) ? i + (n >> 1) : i - (n >> 1); }
+
+// T forward, x pass: T1[i0][i1][:] = inverse DFT_x of U on the data row
+// (i0, i1), U[k] = Xhat[k] / (N^3 C3(k/G)) (steps 1/C* and Z fused into the
+// loads).  CTA: (block of 16 rows i1, i0).
+template <int R1, int R2>
+__global__ void __launch_bounds__(Shape<R1, R2>::threads, 4) timg_fwd_x_kernel(
+    PassGeo g, const float* __restrict__ dtab, float scale, const float2* __restrict__ xhat,
+    float2* __restrict__ t1) {
+  __shared__ float2 sy[Shape<R1, R2>::smem];
+  __shared__ float2 tw[R1 * R2];
+  fill_twiddles<R1 * R2>(tw);
+  const int rb = blockIdx.x, i0 = blockIdx.y;
+  const int f0 = fft_index(i0, g.n0);
+  const float d0 = __ldg(dtab + i0);
+  auto ld = [&](int col, int n1, int t) -> float2 {
+    const int i1 = rb * kCols + col;
+    if (i1 >= g.n1) return make_float2(0.f, 0.f);
+    const int i2 = img_in<R1, R2>(n1, t);
+    const float2 v = __ldg(xhat + ((long long)f0 * g.n1 + fft_index(i1, g.n1)) * g.n2 +
+                           fft_index(i2, g.n2));
+    const float w = d0 * __ldg(dtab + g.n0 + i1) * __ldg(dtab + g.n0 + g.n1 + i2) * scale;
+    return make_float2(v.x * w, v.y * w);
+  };
+  auto st = [&](int col, int k1, auto k2c, float2 v) {
+    constexpr int k2 = decltype(k2c)::value;
+    const int i1 = rb * kCols + col;
+    if (i1 < g.n1) t1[((long long)i0 * g.n1 + i1) * g.g2 + k1 + R1 * k2] = v;
+  };
+  fft16<R1, R2, true, true, true, false>(sy, tw, ld, st);
+}
+
+// T adjoint, x pass: Xhat[k] = (DFT_x of T1[i0][i1][:]) at the data
+// positions / (N^3 C3(k/G)) (steps Z^H and 1/C fused into the stores).
+template <int R1, int R2>
+__global__ void __launch_bounds__(Shape<R1, R2>::threads, 4) timg_inv_x_kernel(
+    PassGeo g, const float* __restrict__ dtab, float scale, const float2* __restrict__ t1,
+    float2* __restrict__ xhat) {
+  __shared__ float2 sy[Shape<R1, R2>::smem];
+  __shared__ float2 tw[R1 * R2];
+  fill_twiddles<R1 * R2>(tw);
+  const int rb = blockIdx.x, i0 = blockIdx.y;
+  const int f0 = fft_index(i0, g.n0);
+  const float d0 = __ldg(dtab + i0);
+  const float2* src = t1 + (long long)i0 * g.n1 * g.g2;
+  auto ld = [&](int col, int n1, int t) -> float2 {
+    const int i1 = rb * kCols + col;
+    return i1 < g.n1 ? src[(long long)i1 * g.g2 + R2 * n1 + t] : make_float2(0.f, 0.f);
+  };
+  auto st = [&](int col, int k1, auto k2c, float2 v) {
+    constexpr int k2 = decltype(k2c)::value;
+    const int i1 = rb * kCols + col;
+    if (i1 >= g.n1) return;
+    const int i2 = img_out<R1, R2>(k1, k2);
+    const float w = d0 * __ldg(dtab + g.n0 + i1) * __ldg(dtab + g.n0 + g.n1 + i2) * scale;
+    xhat[((long long)f0 * g.n1 + fft_index(i1, g.n1)) * g.n2 + fft_index(i2, g.n2)] =
+        make_float2(v.x * w, v.y * w);
+  };
+  fft16<R1, R2, false, true, false, true>(sy, tw, ld, st);
+}
+
 bool radix_of(int L, int* r1, int* r2) {
   switch (L) {
     case 32: *r1 = 8; *r2 = 4; return true;
@@ -441,6 +513,16 @@ bool radix_of(int L, int* r1, int* r2) {
     }                                                                              \
   } while (0)
 
+#define NRS_LAUNCH_LS(KER, INV, L, GRID, S, ...)                                               \
+  do {                                                                                          \
+    switch (L) {                                                                                \
+      case 32: KER<8, 4, INV><<<GRID, Shape<8, 4>::threads, 0, S>>>(__VA_ARGS__); break;         \
+      case 64: KER<8, 8, INV><<<GRID, Shape<8, 8>::threads, 0, S>>>(__VA_ARGS__); break;         \
+      case 128: KER<16, 8, INV><<<GRID, Shape<16, 8>::threads, 0, S>>>(__VA_ARGS__); break;      \
+      default: KER<16, 16, INV><<<GRID, Shape<16, 16>::threads, 0, S>>>(__VA_ARGS__); break;     \
+    }                                                                                           \
+  } while (0)
+
 PassGeo pass_geo(const Geo& g, int C, int nph) {
   return PassGeo{g.n0, g.n1, g.n2, g.g0, g.g1, g.g2, C, nph};
 }
@@ -451,6 +533,12 @@ bool pruned_fft_supported(const Geo& g, int C, bool bf16) {
   if (bf16 || C < 1 || g.osf != 2) return false;
   int r1, r2;
   return radix_of(g.g0, &r1, &r2) && radix_of(g.g1, &r1, &r2) && radix_of(g.g2, &r1, &r2);
+}
+
+bool pruned_image_fft_supported(const Geo& g) {
+  int r1, r2;
+  return g.osf == 2 && radix_of(g.g0, &r1, &r2) && radix_of(g.g1, &r1, &r2) &&
+         radix_of(g.g2, &r1, &r2);
 }
 
 cudaError_t init_pruned_fft() { return cudaSuccess; }  // no tables to upload
@@ -466,8 +554,9 @@ int launch_pruned_forward(const Geo& g, int C, int nph, const uint32_t* colmask,
   const unsigned slots = unsigned(C * nph);
   NRS_LAUNCH_L(fwd_x_kernel, g.g2, dim3((g.n1 + kCols - 1) / kCols, g.n0, nph), s, pg, deapod,
                reinterpret_cast<const float2*>(smaps), reinterpret_cast<const float2*>(m), T1);
-  NRS_LAUNCH_L(fwd_y_kernel, g.g1, dim3(g.g2 / kCols, g.n0, slots), s, pg, T1, T2);
-  NRS_LAUNCH_L(fwd_z_kernel, g.g0, dim3(g.g2 / kCols, g.g1, slots), s, pg, colmask, T2, Gd);
+  NRS_LAUNCH_LS(fwd_y_kernel, false, g.g1, dim3(g.g2 / kCols, g.n0, slots), s, pg, T1, T2);
+  NRS_LAUNCH_LS(fwd_z_kernel, false, g.g0, dim3(g.g2 / kCols, g.g1, slots), s, pg, colmask, T2,
+                Gd);
   return 3;
 }
 
@@ -480,10 +569,42 @@ int launch_pruned_inverse(const Geo& g, int C, int nph, const uint32_t* colmask,
   auto* T2 = static_cast<float2*>(t2);
   const auto* Gd = static_cast<const float2*>(grid);
   const unsigned slots = unsigned(C * nph);
-  NRS_LAUNCH_L(inv_z_kernel, g.g0, dim3(g.g2 / kCols, g.g1, slots), s, pg, colmask, Gd, T2);
-  NRS_LAUNCH_L(inv_y_kernel, g.g1, dim3(g.g2 / kCols, g.n0, slots), s, pg, T2, T1);
+  NRS_LAUNCH_LS(inv_z_kernel, true, g.g0, dim3(g.g2 / kCols, g.g1, slots), s, pg, colmask, Gd,
+                T2);
+  NRS_LAUNCH_LS(inv_y_kernel, true, g.g1, dim3(g.g2 / kCols, g.n0, slots), s, pg, T2, T1);
   NRS_LAUNCH_L(inv_x_kernel, g.g2, dim3((g.n1 + kCols - 1) / kCols, g.n0, nph), s, pg, deapod,
                reinterpret_cast<const float2*>(smaps), T1, reinterpret_cast<float2*>(w));
+  return 3;
+}
+
+// u = F_G^-1 of the deapodized, zero-padded spectrum of xhat (scratch: T1,
+// N0 N1 G2 values; T2, N0 G1 G2 values)
+int launch_pruned_image_forward(const Geo& g, const float* deapod, const nrsense_c64* xhat,
+                                void* t1, void* t2, nrsense_c64* ugrid, cudaStream_t s) {
+  const PassGeo pg = pass_geo(g, 1, 1);
+  auto* T1 = static_cast<float2*>(t1);
+  auto* T2 = static_cast<float2*>(t2);
+  const float scale = float(1.0 / double(g.nvox));
+  NRS_LAUNCH_L(timg_fwd_x_kernel, g.g2, dim3((g.n1 + kCols - 1) / kCols, g.n0, 1), s, pg, deapod,
+               scale, reinterpret_cast<const float2*>(xhat), T1);
+  NRS_LAUNCH_LS(fwd_y_kernel, true, g.g1, dim3(g.g2 / kCols, g.n0, 1), s, pg, T1, T2);
+  NRS_LAUNCH_LS(fwd_z_kernel, true, g.g0, dim3(g.g2 / kCols, g.g1, 1), s, pg, nullptr, T2,
+                reinterpret_cast<float2*>(ugrid));
+  return 3;
+}
+
+// xhat = deapodized crop of F_G of the spread grid u
+int launch_pruned_image_adjoint(const Geo& g, const float* deapod, const nrsense_c64* ugrid,
+                                void* t2, void* t1, nrsense_c64* xhat, cudaStream_t s) {
+  const PassGeo pg = pass_geo(g, 1, 1);
+  auto* T1 = static_cast<float2*>(t1);
+  auto* T2 = static_cast<float2*>(t2);
+  const float scale = float(1.0 / double(g.nvox));
+  NRS_LAUNCH_LS(inv_z_kernel, false, g.g0, dim3(g.g2 / kCols, g.g1, 1), s, pg, nullptr,
+                reinterpret_cast<const float2*>(ugrid), T2);
+  NRS_LAUNCH_LS(inv_y_kernel, false, g.g1, dim3(g.g2 / kCols, g.n0, 1), s, pg, T2, T1);
+  NRS_LAUNCH_L(timg_inv_x_kernel, g.g2, dim3((g.n1 + kCols - 1) / kCols, g.n0, 1), s, pg, deapod,
+               scale, T1, reinterpret_cast<float2*>(xhat));
   return 3;
 }
 

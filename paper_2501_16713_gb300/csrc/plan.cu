@@ -779,6 +779,9 @@ nrsense_status create_impl(nrsense_plan_s* p, const nrsense_desc* desc, const in
     NRS_TRY(dev_alloc_n(p, &p->b_ugrid, g.ngrid));
     if (cudaMemsetAsync(p->b_upad, 0, size_t(g.ngrid) * sizeof(nrsense_c64), s) != cudaSuccess)
       return NRSENSE_ERR_CUDA;
+    // the pruned image-space passes: their T1 and T2 (6 N^3 values) fit in b_upad (8 N^3)
+    p->image_fft_ok = pruned_image_fft_supported(g) && !p->comp_spread;
+    p->image_fft_pruned = p->image_fft_ok;
   }
   if (p->C > 0) {
     const size_t cgb = size_t(g.ngrid) * p->C * p->phase_chunk * (p->grid_bf16 ? 4 : 8);

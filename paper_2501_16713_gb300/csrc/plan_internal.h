@@ -137,6 +137,11 @@ struct nrsense_plan_s {
   // own pruned coil-grid transforms with the coil fan-out and combination fused
   bool fft_pruned_ok = false;  // supported: sigma 2, power-of-two grids of 32..256, FP32 grids
   bool fft_pruned = false;     // chosen (else cuFFT plus the K5 / K8 kernels)
+  // image-space G^3 transforms of T / T^H by the pruned passes (scratch in
+  // b_upad, whose zero padding the cuFFT path then has to restore)
+  bool image_fft_ok = false;
+  bool image_fft_pruned = false;
+  bool upad_dirty = false;
   bool pad_dirty = false;      // b_xpad / b_xmid hold the pruned transforms' intermediates
   // k-space tiles written by the spread (the union over phases), as one
   // 32-bit mask over axis-0 tiles per (axis-1, axis-2) tile column; null when
@@ -273,6 +278,11 @@ cudaError_t configure_home_kernels();
 // Inverse: w_jj = C3^-1 sum_c conj(S_c) crop(IDFT3(grid slot jj * C + c)).
 // Each returns the number of kernels launched.
 bool pruned_fft_supported(const Geo& g, int C, bool bf16);
+bool pruned_image_fft_supported(const Geo& g);
+int launch_pruned_image_forward(const Geo& g, const float* deapod, const nrsense_c64* xhat,
+                                void* t1, void* t2, nrsense_c64* ugrid, cudaStream_t s);
+int launch_pruned_image_adjoint(const Geo& g, const float* deapod, const nrsense_c64* ugrid,
+                                void* t2, void* t1, nrsense_c64* xhat, cudaStream_t s);
 cudaError_t init_pruned_fft();
 int launch_pruned_forward(const Geo& g, int C, int nph, const uint32_t* colmask,
                           const float* deapod,

@@ -55,7 +55,8 @@ class Tuning(ctypes.Structure):
                 ("spread_mma_cube", ctypes.c_int32), ("spread_mma_geo_ms", ctypes.c_double * 2),
                 ("interp_tma2_ms", ctypes.c_double), ("spread_max_item", ctypes.c_int32),
                 ("spread_item_ms", ctypes.c_double * 3),
-                ("interp_image_home", ctypes.c_int32), ("interp_image_ms", ctypes.c_double * 2)]
+                ("interp_image_home", ctypes.c_int32), ("interp_image_ms", ctypes.c_double * 2),
+                ("image_fft_pruned", ctypes.c_int32), ("image_fft_ms", ctypes.c_double * 2)]
 
 
 class Info(ctypes.Structure):
@@ -640,6 +641,7 @@ class Plan:
             t.spread_mma_cube = int(store[key].get("spread_mma_cube", 0))
             t.spread_max_item = int(store[key].get("spread_max_item", 0))
             t.interp_image_home = int(store[key].get("interp_image_home", 0))
+            t.image_fft_pruned = int(store[key].get("image_fft_pruned", 0))
             _check(self.lib.nrsense_plan_set_tuning(self._h, ctypes.byref(t)),
                    "nrsense_plan_set_tuning")
             return dict(store[key], cached=True)
@@ -658,7 +660,8 @@ class Plan:
                "interp_tma2_ms": t.interp_tma2_ms, "spread_max_item": t.spread_max_item,
                "spread_item_ms": list(t.spread_item_ms),
                "interp_image_home": t.interp_image_home,
-               "interp_image_ms": list(t.interp_image_ms)}
+               "interp_image_ms": list(t.interp_image_ms),
+               "image_fft_pruned": t.image_fft_pruned, "image_fft_ms": list(t.image_fft_ms)}
         if cache:
             store[key] = res
             tmp = cache + ".tmp"
