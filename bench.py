@@ -370,6 +370,12 @@ def _timed_solve(fn):
 
 
 CIRC_LAMBDA_FACTOR = 10.0
+# recycled deflation space: Ritz vectors of the k largest Ritz values of a
+# DEFL_STEPS-iteration circulant-CG run on another right-hand side (the low
+# end of the circulant-preconditioned spectrum is a large cluster near
+# lambda / (CIRC_LAMBDA_FACTOR lambda); the outliers sit at the top)
+DEFL_STEPS = 30
+DEFL_KS = (16, 24)
 
 
 def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, seed=5,
@@ -402,6 +408,28 @@ def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, s
     (pcn, ms_pcn) = _timed_solve(lambda: plan.solve_fcg(y, lam, net, tol=tol, maxit=maxit,
                                                         graph=True, out=out, circulant=True))
     diff_pcn = float((out - x_cg).norm() / x_cg.norm())
+    # circulant plus a deflation space recycled from an earlier solve with
+    # another right-hand side (built once per operator, timed apart)
+    deflated = {}
+    dgen = torch.Generator(device=dev).manual_seed(seed + 200)
+    y_tr = _noisy(plan, torch.randn(shape, dtype=torch.complex64, device=dev, generator=dgen), dgen)
+    for k in DEFL_KS:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ritz, kept = plan.deflation_from_solve(y_tr, lam, steps=DEFL_STEPS, k=k, circulant=True,
+                                               largest=True)
+        torch.cuda.synchronize()
+        ms_ds = (time.perf_counter() - t0) * 1000.0
+        (pd, ms_pd) = _timed_solve(lambda: plan.solve_fcg(y, lam, None, tol=tol, maxit=maxit,
+                                                          graph=True, out=out, circulant=True,
+                                                          deflate=True))
+        deflated[k] = {"iters": pd[1], "ms": round(ms_pd, 2), "true_res": pd[3],
+                       "solution_rel_diff": float((out - x_cg).norm() / x_cg.norm()),
+                       "setup_ms": round(ms_ds, 1), "ritz_largest": float(ritz[0]),
+                       "ritz_kth": float(ritz[-1]), "kept": kept, "steps": DEFL_STEPS,
+                       "speedup_vs_plain": round(ms_cg / ms_pd, 3)}
+    plan.set_deflation(None)
+    ms_defl = min(v["ms"] for v in deflated.values())
     # a network trained here from its random start (symmetric form, cosine
     # loss on pairs of plain-CG runs, blocks kept by the flexible-CG iterations
     # of a held-out problem), against the same network untrained
@@ -429,7 +457,7 @@ def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, s
                    "selection": [(b, sc) for b, _, sc in hist]}
         tnet.close()
         del r, e
-    best = min(ms_f, ms_pc, ms_pcn)
+    best = min(ms_f, ms_pc, ms_pcn, ms_defl)
     return {"tol": tol, "lambda": lam, "lambda_rel": rel_lambda, "lambda_max": lam_max,
             "plain": {"iters": cg[1], "ms": round(ms_cg, 2), "true_res": cg[3]},
             "fcg": {"iters": fcg[1], "ms": round(ms_f, 2), "true_res": fcg[3],
@@ -439,6 +467,7 @@ def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, s
                           "lambda_factor": CIRC_LAMBDA_FACTOR},
             "circulant_net": {"iters": pcn[1], "ms": round(ms_pcn, 2), "true_res": pcn[3],
                               "fallbacks": pcn[5], "solution_rel_diff": diff_pcn},
+            "circulant_deflated": {str(k): v for k, v in deflated.items()},
             "fcg_trained": trained, "target_speedup": 3.0,
             "speedup": round(ms_cg / best, 3), "speedup_fcg_net": round(ms_cg / ms_f, 3)}
 

@@ -234,6 +234,10 @@ nrsense_status nrsense_kspace_adjoint(nrsense_plan_t plan, int32_t phase,
 #define NRSENSE_CG_CIRCULANT (1u << 2)  /* nrsense_solve_fcg: precondition by the plan's
                                             circulant preconditioner (nrsense_set_circulant),
                                             before the network when one is given */
+#define NRSENSE_CG_DEFLATE   (1u << 3)  /* nrsense_solve_fcg: deflate the plan's recycled
+                                            subspace (nrsense_set_deflation) */
+#define NRSENSE_DEFLATE_LARGEST (1u << 4)  /* nrsense_deflation_from_solve: the Ritz vectors
+                                               of the k largest Ritz values, not the smallest */
 nrsense_status nrsense_solve_cg(nrsense_plan_t plan, const nrsense_c64* y_dev, double lambda,
                                 double tol, int32_t maxit, uint32_t flags, nrsense_c64* x_dev,
                                 int32_t* iters_host, double* res_hist_host, double* true_res_host,
@@ -435,6 +439,76 @@ nrsense_status nrsense_set_circulant(nrsense_plan_t plan, double lambda, int32_t
                                      void* stream);
 nrsense_status nrsense_apply_circulant(nrsense_plan_t plan, const nrsense_c64* r_dev,
                                        nrsense_c64* z_dev, void* stream);
+
+/*
+ * Deflation with a recycled subspace (not in the paper; serves the Tikhonov CG
+ * solve of its reconstruction problem when the same operator is solved for
+ * several right-hand sides).  The method is the A-DEF2 deflated preconditioned
+ * CG of Tang, Nabben and Vuik (J. Sci. Comput. 39, 2009) with a basis W of k
+ * image vectors: E_c = W^H E W, x_0 = x_init + W E_c^-1 W^H r_init, and every
+ * search direction is projected by P^T z = z - W E_c^-1 (E W)^H z, so each
+ * residual stays orthogonal to W and the iteration runs on the spectrum of
+ * M E without W's part.
+ *
+ * nrsense_set_deflation copies W (w_dev: k consecutive image-shaped device
+ * vectors), orthonormalises it (modified Gram-Schmidt, twice per vector, FP64
+ * inner products; a vector with less than 1 % of its norm outside the span of
+ * the earlier kept ones is dropped, so the space depends only on span(W) and
+ * repeated vectors cost nothing), applies E0 (lambda = 0) to each kept vector
+ * and keeps W^H E0 W and W^H W in FP64 on the host; kept_host (may be NULL)
+ * receives the number of kept vectors.  A solve with lambda forms
+ * E W = E0 W + lambda W and inverts E_c = W^H E0 W + lambda W^H W (FP64, on the
+ * host; a pseudo-inverse that drops eigenvalues below 1e-10 of the largest, so
+ * nearly dependent basis vectors do not amplify rounding) when lambda changes.
+ * k = 0 switches deflation off and frees the space.
+ * Memory: 3 k image vectors.  Synchronises the stream.  Errors: ERR_ARG (k < 0,
+ * k > 64, w_dev NULL with k > 0), ERR_BREAKDOWN (no vector kept: W zero or
+ * not finite), ERR_OOM, ERR_CUDA.
+ *
+ * nrsense_deflation_from_solve builds W from a solve: `steps` iterations of CG
+ * (preconditioned by the circulant preconditioner with NRSENSE_CG_CIRCULANT,
+ * else none) from x = 0 on E x = sum_j A_j^H y_j, recording z_j / sqrt(rho_j)
+ * (z_j the preconditioned residual, rho_j = Re<r_j, z_j>) and the step sizes;
+ * the CG-Lanczos tridiagonal T (T[j][j] = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+ * T[j][j+1] = -sqrt(beta_j)/alpha_j, beta_j = rho_{j+1}/rho_j) is
+ * diagonalised on the host (FP64 Jacobi rotations); the Ritz vectors of the k
+ * smallest Ritz values (estimates of the smallest eigenvalues of M E), or with
+ * NRSENSE_DEFLATE_LARGEST of the k largest, become W as by
+ * nrsense_set_deflation.  ritz_host receives those k Ritz values in the order
+ * taken (ascending, or descending with NRSENSE_DEFLATE_LARGEST; may be NULL)
+ * and kept_host (may be NULL) the number of basis vectors kept (repeated Ritz
+ * vectors, which a long run in finite precision produces, are dropped).
+ * Which end pays depends on the spectrum: with the circulant preconditioner
+ * built for a larger lambda than the solve's, the low end of M E is a large
+ * cluster (every poorly sampled frequency) that k vectors cannot remove, and
+ * the high end holds the outliers.  A run that converges before `steps` uses
+ * the iterations it made (k is then clipped to them).  Temporary memory:
+ * `steps` image vectors.  Errors: ERR_ARG (steps < 1 or > 256, k < 1,
+ * k > min(steps, 64), flags other than NRSENSE_CG_CIRCULANT and
+ * NRSENSE_DEFLATE_LARGEST), ERR_STATE (circulant flag before
+ * nrsense_set_circulant), ERR_BREAKDOWN, ERR_OOM, ERR_CUDA.
+ *
+ * nrsense_solve_fcg with NRSENSE_CG_DEFLATE runs the deflated iteration
+ * (circulant and network preconditioning as without it; a network step that
+ * falls back to z = r is not projected); ERR_STATE without a space.
+ */
+nrsense_status nrsense_set_deflation(nrsense_plan_t plan, const nrsense_c64* w_dev, int32_t k,
+                                     int32_t* kept_host, void* stream);
+nrsense_status nrsense_deflation_from_solve(nrsense_plan_t plan, const nrsense_c64* y_dev,
+                                            double lambda, int32_t steps, int32_t k,
+                                            uint32_t flags, double* ritz_host,
+                                            int32_t* kept_host, void* stream);
+
+/*
+ * nrsense_symmetric_eigen - the host eigen-solver nrsense_deflation_from_solve
+ * uses: eigenvalues (ascending, vals_host[m]) and eigenvectors (column i of
+ * the row-major m x m vecs_host belongs to vals_host[i]) of the real
+ * symmetric m x m matrix a_host (row-major; only its symmetric part is
+ * meaningful), by cyclic Jacobi rotations in FP64.  Host only: needs no
+ * device.  Errors: ERR_ARG (m < 1 or > 256, NULL pointers).
+ */
+nrsense_status nrsense_symmetric_eigen(int32_t m, const double* a_host, double* vals_host,
+                                       double* vecs_host);
 
 /*
  * Autotuning of the launch choices of a plan (no counterpart in the paper).

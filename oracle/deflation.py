@@ -24,7 +24,8 @@ Hermitian positive definite.  Published methods restated here:
   * Deflation (Tang, Nabben and Vuik, "Comparison of two-level preconditioners
     derived from deflation, domain decomposition and multigrid methods",
     J. Sci. Comput. 39 (2009), the A-DEF2 variant): with a basis W of k
-    vectors, E_c = W^H E W, Q = W E_c^-1 W^H and P^T = I - Q E,
+    vectors, E_c = W^H E W, Q = W E_c^-1 W^H and P^T = I - Q E (E_c^-1 read as
+    the Moore-Penrose inverse, so a nearly dependent W deflates its span),
         x_0 = Q b + P^T x_init,   r_0 = b - E x_0,   z_0 = M r_0,   p_0 = P^T z_0,
         alpha_j = <r_j, z_j> / <p_j, E p_j>,
         x_{j+1} = x_j + alpha_j p_j,   r_{j+1} = r_j - alpha_j E p_j,
@@ -95,12 +96,14 @@ def lanczos_tridiagonal(alphas, rhos, m: int):
     return T
 
 
-def ritz_space(T, Z, k: int):
-    """The k smallest Ritz values of T and their Ritz vectors sum_j s_i[j] Z[j]."""
+def ritz_space(T, Z, k: int, largest: bool = False):
+    """The k smallest (largest=True: largest, in descending order) Ritz values
+    of T and their Ritz vectors sum_j s_i[j] Z[j]."""
     theta, S = np.linalg.eigh(T)
     m = T.shape[0]
-    W = [sum(S[j, i] * Z[j] for j in range(m)) for i in range(k)]
-    return theta[:k], W
+    idx = list(range(m - 1, m - 1 - k, -1)) if largest else list(range(k))
+    W = [sum(S[j, i] * Z[j] for j in range(m)) for i in idx]
+    return theta[idx], W
 
 
 def deflated_pcg(apply_E, apply_M, b, W, tol: float = 1e-4, maxit: int = 100, x_init=None):
@@ -112,7 +115,10 @@ def deflated_pcg(apply_E, apply_M, b, W, tol: float = 1e-4, maxit: int = 100, x_
     shape = b.shape
     EW = np.stack([apply_E(w.reshape(shape)).reshape(-1) for w in Wm.T], 1)
     Ec = Wm.conj().T @ EW
-    Eci = np.linalg.inv(Ec)
+    # Moore-Penrose inverse (eigenvalues below 1e-10 of the largest dropped):
+    # the deflation of span(W) when W is (nearly) rank-deficient, the inverse
+    # otherwise
+    Eci = np.linalg.pinv(Ec, rcond=1e-10, hermitian=True)
 
     def Q(v):
         return (Wm @ (Eci @ (Wm.conj().T @ v.reshape(-1)))).reshape(shape)

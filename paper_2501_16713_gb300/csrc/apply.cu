@@ -445,11 +445,13 @@ nrsense_status nrsense_plan_set_tuning(nrsense_plan_t p, const nrsense_tuning* t
   p->spread_image_variant = image_variant_of(t->spread_image_warp);
   p->fft_pruned = t->fft_pruned == 1;
   p->image_fft_pruned = t->image_fft_pruned == 1;
+  p->epoch += 1;
   return NRSENSE_OK;
 }
 
 nrsense_status nrsense_plan_autotune(nrsense_plan_t p, int32_t reps, nrsense_tuning* out,
                                      void* stream) {
+  if (p) p->epoch += 1;  // choices and (re-tiled) buffers change below
   if (p == nullptr || out == nullptr || reps < 1 || reps > 100) return NRSENSE_ERR_ARG;
   std::memset(out, 0, sizeof(*out));
   out->spread_variant = p->spread_variant == kSpreadRegister ? NRSENSE_TUNE_SPREAD_REGISTER
@@ -735,6 +737,7 @@ nrsense_status nrsense_plan_set_reduce(nrsense_plan_t p, nrsense_reduce_fn fn, v
   if (p == nullptr) return NRSENSE_ERR_ARG;
   p->reduce_fn = fn;
   p->reduce_user = user;
+  p->epoch += 1;
   return NRSENSE_OK;
 }
 

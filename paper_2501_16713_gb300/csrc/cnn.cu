@@ -29,6 +29,8 @@
 #include <new>
 #include <vector>
 
+#include <atomic>
+
 #include "plan_internal.h"
 
 namespace nrs {
@@ -561,6 +563,7 @@ using namespace nrs::cnnk;
 
 struct nrsense_cnn_s {
   Vol vol;
+  uint64_t serial = 0;  // creation number: solver graphs key on it, not on the address
   int device = 0;
   int wg_grid = 0;
   bf16* act[kLayers] = {};  // a0 .. a4 (inference uses a0, a1 as ping-pong)
@@ -739,6 +742,8 @@ namespace nrs {
 
 long long cnn_nvox(const nrsense_cnn_s* net) { return net->vol.n; }
 
+uint64_t cnn_serial(const nrsense_cnn_s* net) { return net ? net->serial : 0; }
+
 bool cnn_shape_matches(const nrsense_cnn_s* net, int n0, int n1, int n2) {
   return net->vol.d == n0 && net->vol.h == n1 && net->vol.w == n2;
 }
@@ -763,6 +768,8 @@ nrsense_status nrsense_cnn_create(const int32_t* n_host, uint32_t flags, void* s
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   nrsense_cnn_s* net = new (std::nothrow) nrsense_cnn_s();
   if (!net) return NRSENSE_ERR_OOM;
+  static std::atomic<uint64_t> next_serial{1};
+  net->serial = next_serial.fetch_add(1);
   net->spd = (flags & NRSENSE_CNN_SYMMETRIC) != 0;
   Vol& v = net->vol;
   v.d = n_host[0];

@@ -621,6 +621,7 @@ struct nrsense_fista_ws {
   float g_step = 0.0f, g_tau = 0.0f;
   const void* g_mu = nullptr;
   const void* g_partial = nullptr;
+  uint64_t g_epoch = ~0ull;  // plan epoch (buffers and choices of the operator)
 };
 
 namespace nrs {
@@ -824,7 +825,8 @@ nrsense_status nrsense_solve_fista(nrsense_plan_t p, const nrsense_c64* y, doubl
   int done = 0;
   if (graph && maxit >= kChunk) {
     if (w->gexec == nullptr || w->g_x != x || w->g_J != levels || w->g_step != step ||
-        w->g_tau != tau || w->g_mu != w->mu || w->g_partial != w->partial) {
+        w->g_tau != tau || w->g_mu != w->mu || w->g_partial != w->partial ||
+        w->g_epoch != p->epoch) {
       if (w->gexec) {
         cudaGraphExecDestroy(w->gexec);
         w->gexec = nullptr;
@@ -853,6 +855,7 @@ nrsense_status nrsense_solve_fista(nrsense_plan_t p, const nrsense_c64* y, doubl
       w->g_tau = tau;
       w->g_mu = w->mu;
       w->g_partial = w->partial;
+      w->g_epoch = p->epoch;
     }
     for (; done + kChunk <= maxit; done += kChunk) {
       if (cudaGraphLaunch(w->gexec, s) != cudaSuccess) return NRSENSE_ERR_CUDA;

@@ -836,6 +836,7 @@ void release(nrsense_plan_s* p) {
 namespace nrs {
 
 nrsense_status retile_kspace(nrsense_plan_s* p, int max_item, cudaStream_t s) {
+  p->epoch += 1;  // point-set buffers are rebuilt
   if (max_item < 64 || max_item > (1 << 16)) return NRSENSE_ERR_ARG;
   if (p->C == 0 || max_item == p->spread_max_item) {
     p->spread_max_item = p->C == 0 ? p->spread_max_item : max_item;

@@ -156,12 +156,29 @@ struct nrsense_plan_s {
   nrsense_reduce_fn reduce_fn = nullptr;
   void* reduce_user = nullptr;
   nrsense_cg_ws* cg = nullptr;  // allocated by the first nrsense_solve_cg
+  // bumped whenever a device buffer or launch choice that a captured solver
+  // graph bakes in may have changed (tuning, re-tiling, reduction hook,
+  // deflation space, solver workspace reallocation): graphs are re-captured
+  uint64_t epoch = 0;
   // circulant preconditioner (nrsense_set_circulant, solver.cu)
   float* circ_d = nullptr;          // per frequency (DFT order): 1 / (max(Re hhat, 0) + lambda)
   nrsense_c64* circ_tmp = nullptr;  // image-sized work vector
   cufftHandle fft_circ = 0;
   bool have_fft_circ = false;
   bool circ_on = false;
+  // recycled deflation space (nrsense_set_deflation, solver.cu): W, E0 W and
+  // E W (k image vectors each, E W for defl_lambda), the k x k FP64 Gram
+  // matrices W^H E0 W and W^H W (host), E_c^-1 and the projection
+  // coefficients (device, complex FP64), dot-product partial sums
+  int defl_k = 0;
+  nrsense_c64* defl_w = nullptr;
+  nrsense_c64* defl_e0w = nullptr;
+  nrsense_c64* defl_ew = nullptr;
+  double defl_lambda = -1.0;  // lambda of defl_ew and defl_ecinv (< 0: not formed)
+  std::vector<double> defl_g0, defl_gw;  // k x k complex, row-major, (re, im) pairs
+  double* defl_ecinv = nullptr;          // k x k complex
+  double* defl_coef = nullptr;           // k complex
+  double* defl_partial = nullptr;        // 2 k x kDeflBlocks
   nrsense_fista_ws* fista = nullptr;  // allocated by the first FISTA or power-iteration call
   nrsense_motion_ws* motion = nullptr;  // allocated by the first DCF or weighted-adjoint call
 };
@@ -190,6 +207,7 @@ namespace nrs {
 // ---- preconditioner network (cnn.cu) --------------------------------------
 long long cnn_nvox(const nrsense_cnn_s* net);
 bool cnn_shape_matches(const nrsense_cnn_s* net, int n0, int n1, int n2);
+uint64_t cnn_serial(const nrsense_cnn_s* net);  // unique per created network (0: none)
 // z = M(r) on stream s, no host synchronisation; sumsq_dev (may be null) is an
 // FP64 sum of |r|^2 already on the device.  Returns the kernels launched.
 long long cnn_apply_async(nrsense_cnn_s* net, const float2* r, const double* sumsq_dev, float2* z,

@@ -295,6 +295,121 @@ __global__ void rsub_kernel(const float2* __restrict__ x, float2* __restrict__ e
   }
 }
 
+// ---------------------------------------------------------------------------
+// Deflation (A-DEF2 of Tang, Nabben and Vuik) with a basis W of k vectors.
+
+constexpr int kDeflBlocks = 296;  // fixed grid of the k-vector dot products
+constexpr int kDeflMax = 64;
+
+// partial[(2 i + c) nb + block] = Re (c = 0) / Im (c = 1) of sum conj(V_i) z
+// over the block's fixed grid-stride range, V_i = V + i n (FP64).
+__global__ void __launch_bounds__(kRedThreads) defl_dots_kernel(const float2* __restrict__ V,
+                                                                const float2* __restrict__ z,
+                                                                long long n,
+                                                                double* __restrict__ partial) {
+  const int i = blockIdx.y;
+  const float2* __restrict__ vi = V + (long long)i * n;
+  double re = 0.0, im = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const float2 a = vi[t], b = z[t];
+    re = fma((double)a.x, (double)b.x, fma((double)a.y, (double)b.y, re));
+    im = fma((double)a.x, (double)b.y, fma(-(double)a.y, (double)b.x, im));
+  }
+  re = block_sum(re);
+  im = block_sum(im);
+  if (threadIdx.x == 0) {
+    partial[(2 * i) * gridDim.x + blockIdx.x] = re;
+    partial[(2 * i + 1) * gridDim.x + blockIdx.x] = im;
+  }
+}
+
+// d = the summed partials (W^H v, k complex, each summed in block order);
+// coef = E_c^-1 d (complex FP64, E_c^-1 row-major).
+__global__ void defl_coef_kernel(const double* __restrict__ partial, int nb, int k,
+                                 const double* __restrict__ ecinv, double* __restrict__ coef) {
+  __shared__ double d[2 * kDeflMax];
+  for (int c = threadIdx.x; c < 2 * k; c += blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) acc += partial[c * nb + b];
+    d[c] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double ar = ecinv[2 * (i * k + j)], ai = ecinv[2 * (i * k + j) + 1];
+      re += ar * d[2 * j] - ai * d[2 * j + 1];
+      im += ar * d[2 * j + 1] + ai * d[2 * j];
+    }
+    coef[2 * i] = re;
+    coef[2 * i + 1] = im;
+  }
+}
+
+// out = in - sum_i c_i U_i (in may equal out); with x2: x2 += sum_i c_i U2_i.
+// Terms in increasing i.
+__global__ void __launch_bounds__(kRedThreads) defl_update_kernel(
+    float2* out, const float2* in, const float2* __restrict__ U, const double* __restrict__ coef,
+    int k, long long n, float2* x2, const float2* __restrict__ U2) {
+  __shared__ float2 c[kDeflMax];
+  if (threadIdx.x < k) c[threadIdx.x] = make_float2(float(coef[2 * threadIdx.x]),
+                                                    float(coef[2 * threadIdx.x + 1]));
+  __syncthreads();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    float2 a = in[t];
+    float2 xa = x2 ? x2[t] : make_float2(0.f, 0.f);
+    for (int i = 0; i < k; ++i) {
+      const float2 ci = c[i];
+      const float2 u = U[(long long)i * n + t];
+      a.x = fmaf(-ci.x, u.x, fmaf(ci.y, u.y, a.x));
+      a.y = fmaf(-ci.x, u.y, fmaf(-ci.y, u.x, a.y));
+      if (x2) {
+        const float2 u2 = U2[(long long)i * n + t];
+        xa.x = fmaf(ci.x, u2.x, fmaf(-ci.y, u2.y, xa.x));
+        xa.y = fmaf(ci.x, u2.y, fmaf(ci.y, u2.x, xa.y));
+      }
+    }
+    out[t] = a;
+    if (x2) x2[t] = xa;
+  }
+}
+
+// ew = e0w + lambda w over k n values
+__global__ void defl_form_ew_kernel(float2* __restrict__ ew, const float2* __restrict__ e0w,
+                                    const float2* __restrict__ w, float lambda, long long total) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const float2 a = e0w[t], b = w[t];
+    ew[t] = make_float2(fmaf(lambda, b.x, a.x), fmaf(lambda, b.y, a.y));
+  }
+}
+
+// dst = scale src (dst may equal src)
+__global__ void defl_scale_kernel(float2* dst, const float2* src, float scale, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const float2 a = src[t];
+    dst[t] = make_float2(a.x * scale, a.y * scale);
+  }
+}
+
+// out = sum_j coef[j] Z_j (real coefficients, j < m, in increasing j)
+__global__ void defl_combine_kernel(float2* __restrict__ out, const float2* __restrict__ Z,
+                                    const float* __restrict__ coef, int m, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    float2 a = make_float2(0.f, 0.f);
+    for (int j = 0; j < m; ++j) {
+      const float2 z = Z[(long long)j * n + t];
+      a.x = fmaf(coef[j], z.x, a.x);
+      a.y = fmaf(coef[j], z.y, a.y);
+    }
+    out[t] = a;
+  }
+}
+
 // r = b - E x (r holds b on entry, Ex holds E x)
 __global__ void sub_kernel(float2* __restrict__ r, const float2* __restrict__ ex, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -362,7 +477,8 @@ struct nrsense_cg_ws {
   cudaGraphExec_t gexec = nullptr;
   // what the captured graph baked in
   const void* g_x = nullptr;
-  const void* g_net = nullptr;
+  uint64_t g_net = 0;      // network serial
+  uint64_t g_epoch = ~0ull;  // plan epoch
   int g_mode = -1;
   double g_lambda = 0.0;
   int g_chunk = 0;
@@ -370,7 +486,21 @@ struct nrsense_cg_ws {
 
 namespace nrs {
 
+void defl_release(nrsense_plan_s* p) {
+  void* bufs[] = {p->defl_w, p->defl_e0w, p->defl_ew, p->defl_ecinv, p->defl_coef,
+                  p->defl_partial};
+  for (void* b : bufs) cudaFree(b);
+  p->defl_w = p->defl_e0w = p->defl_ew = nullptr;
+  p->defl_ecinv = p->defl_coef = p->defl_partial = nullptr;
+  p->defl_k = 0;
+  p->defl_lambda = -1.0;
+  p->defl_g0.clear();
+  p->defl_gw.clear();
+  p->epoch += 1;
+}
+
 void cg_release(nrsense_plan_s* p) {
+  defl_release(p);
   if (p->have_fft_circ) cufftDestroy(p->fft_circ);
   p->have_fft_circ = false;
   cudaFree(p->circ_d);
@@ -420,6 +550,7 @@ nrsense_status cg_workspace(nrsense_plan_s* p, int maxit, bool flexible, bool ci
       return NRSENSE_ERR_CUDA;
   }
   nrsense_cg_ws* w = p->cg;
+  if ((flexible && !w->z) || (circ && !w->zc) || w->hist_cap < maxit + 1) p->epoch += 1;
   if (flexible && !w->z && cudaMalloc(&w->z, vb) != cudaSuccess) {
     cudaGetLastError();
     w->z = nullptr;
@@ -460,11 +591,276 @@ nrsense_status circ_apply(nrsense_plan_s* p, const nrsense_c64* r, nrsense_c64* 
   return launched();
 }
 
+// Eigen-decomposition of a real symmetric m x m matrix (row-major) by cyclic
+// Jacobi rotations (each rotation in the (p, q) plane zeroes A[p][q]; sweeps
+// until the off-diagonal mass is below 1e-30 of the total): on return the
+// diagonal of A holds the eigenvalues and column i of V the eigenvector of
+// A[i][i].
+void jacobi_eigen(int m, std::vector<double>& A, std::vector<double>& V) {
+  V.assign(size_t(m) * m, 0.0);
+  for (int i = 0; i < m; ++i) V[size_t(i) * m + i] = 1.0;
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int r = 0; r < m; ++r)
+      for (int c = 0; c < m; ++c) {
+        const double v = A[size_t(r) * m + c] * A[size_t(r) * m + c];
+        tot += v;
+        if (r != c) off += v;
+      }
+    if (off == 0.0 || off <= 1e-30 * tot) break;
+    for (int pp = 0; pp < m - 1; ++pp)
+      for (int q = pp + 1; q < m; ++q) {
+        const double apq = A[size_t(pp) * m + q];
+        if (apq == 0.0) continue;
+        const double tau = (A[size_t(q) * m + q] - A[size_t(pp) * m + pp]) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+        for (int r = 0; r < m; ++r) {  // A J
+          const double arp = A[size_t(r) * m + pp], arq = A[size_t(r) * m + q];
+          A[size_t(r) * m + pp] = c * arp - sn * arq;
+          A[size_t(r) * m + q] = sn * arp + c * arq;
+        }
+        for (int r = 0; r < m; ++r) {  // J^T (A J)
+          const double apr = A[size_t(pp) * m + r], aqr = A[size_t(q) * m + r];
+          A[size_t(pp) * m + r] = c * apr - sn * aqr;
+          A[size_t(q) * m + r] = sn * apr + c * aqr;
+        }
+        for (int r = 0; r < m; ++r) {  // V J
+          const double vrp = V[size_t(r) * m + pp], vrq = V[size_t(r) * m + q];
+          V[size_t(r) * m + pp] = c * vrp - sn * vrq;
+          V[size_t(r) * m + q] = sn * vrp + c * vrq;
+        }
+      }
+  }
+}
+
+// Eigenvalues ascending, eigenvectors as the columns of vecs (row-major).
+void symmetric_eigen_sorted(int m, const double* a, double* vals, double* vecs) {
+  std::vector<double> A(a, a + size_t(m) * m), V;
+  jacobi_eigen(m, A, V);
+  std::vector<int> order(m);
+  for (int i = 0; i < m; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return A[size_t(x) * m + x] < A[size_t(y) * m + y];
+  });
+  for (int i = 0; i < m; ++i) {
+    vals[i] = A[size_t(order[i]) * m + order[i]];
+    for (int r = 0; r < m; ++r) vecs[size_t(r) * m + i] = V[size_t(r) * m + order[i]];
+  }
+}
+
+// Pseudo-inverse of a Hermitian positive-semidefinite k x k complex matrix
+// (row-major (re, im) pairs, FP64), in place: through the real symmetric
+// embedding H = [[Re, -Im], [Im, Re]] (each eigenvalue twice), H^+ = sum over
+// eigenvalues above 1e-10 of the largest of v v^T / theta, whose blocks are
+// Re and Im of the pseudo-inverse.  Directions of nearly dependent basis
+// vectors (repeated Ritz vectors of a long run) are dropped instead of
+// amplified.  Returns the number of kept eigenvalue pairs (0: nothing left).
+int pinv_hermitian(std::vector<double>& a, int k) {
+  const int m = 2 * k;
+  std::vector<double> H(size_t(m) * m), vals(m), vecs(size_t(m) * m);
+  for (int r = 0; r < k; ++r)
+    for (int c = 0; c < k; ++c) {
+      const double re = 0.5 * (a[2 * (r * k + c)] + a[2 * (c * k + r)]);       // Hermitian part
+      const double im = 0.5 * (a[2 * (r * k + c) + 1] - a[2 * (c * k + r) + 1]);
+      H[size_t(r) * m + c] = re;
+      H[size_t(r + k) * m + c + k] = re;
+      H[size_t(r) * m + c + k] = -im;
+      H[size_t(r + k) * m + c] = im;
+    }
+  symmetric_eigen_sorted(m, H.data(), vals.data(), vecs.data());
+  const double top = vals[m - 1];
+  if (!(top > 0.0) || !std::isfinite(top)) return 0;
+  std::vector<double> P(size_t(m) * m, 0.0);
+  int kept = 0;
+  for (int e = 0; e < m; ++e) {
+    if (!(vals[e] > 1e-10 * top)) continue;
+    ++kept;
+    const double inv = 1.0 / vals[e];
+    for (int r = 0; r < m; ++r) {
+      const double vr = vecs[size_t(r) * m + e] * inv;
+      for (int c = 0; c < m; ++c) P[size_t(r) * m + c] += vr * vecs[size_t(c) * m + e];
+    }
+  }
+  for (int r = 0; r < k; ++r)
+    for (int c = 0; c < k; ++c) {
+      a[2 * (r * k + c)] = P[size_t(r) * m + c];
+      a[2 * (r * k + c) + 1] = P[size_t(r + k) * m + c];
+    }
+  return kept / 2;
+}
+
+// V^H z partial sums into p->defl_partial (V: `count` consecutive vectors)
+void defl_dots(nrsense_plan_s* p, const nrsense_c64* V, int count, const nrsense_c64* z,
+               cudaStream_t s) {
+  defl_dots_kernel<<<dim3(kDeflBlocks, count), kRedThreads, 0, s>>>(
+      reinterpret_cast<const float2*>(V), reinterpret_cast<const float2*>(z), p->geo.nvox,
+      p->defl_partial);
+  p->launches += 1;
+}
+
+// V^H z on the host (2 count values, each summed in block order)
+nrsense_status defl_dots_host(nrsense_plan_s* p, const nrsense_c64* V, int count,
+                              const nrsense_c64* z, cudaStream_t s, double* out) {
+  const int k = count;
+  defl_dots(p, V, count, z, s);
+  std::vector<double> h(size_t(2) * k * kDeflBlocks);
+  if (cudaMemcpyAsync(h.data(), p->defl_partial, h.size() * sizeof(double),
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return NRSENSE_ERR_CUDA;
+  for (int c = 0; c < 2 * k; ++c) {
+    double acc = 0.0;
+    for (int b = 0; b < kDeflBlocks; ++b) acc += h[size_t(c) * kDeflBlocks + b];
+    out[c] = acc;
+  }
+  return NRSENSE_OK;
+}
+
+// Buffers for a space of k vectors (W itself is filled by the caller).
+nrsense_status defl_alloc(nrsense_plan_s* p, int k) {
+  defl_release(p);
+  const size_t vb = size_t(p->geo.nvox) * sizeof(nrsense_c64);
+  if (cudaMalloc(&p->defl_w, k * vb) != cudaSuccess ||
+      cudaMalloc(&p->defl_e0w, k * vb) != cudaSuccess ||
+      cudaMalloc(&p->defl_ew, k * vb) != cudaSuccess ||
+      cudaMalloc(&p->defl_ecinv, size_t(2) * k * k * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&p->defl_coef, size_t(2) * k * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&p->defl_partial, size_t(2) * k * kDeflBlocks * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    defl_release(p);
+    return NRSENSE_ERR_OOM;
+  }
+  p->defl_k = k;
+  return NRSENSE_OK;
+}
+
+// W orthonormalised in place by modified Gram-Schmidt (twice per vector,
+// FP64 inner products, FP32 vectors); a vector with less than 1 % of its norm
+// outside the span of the kept ones (a repeated Ritz vector of a long run) is
+// dropped.  The kept vectors move to the front; p->defl_k becomes their count.
+nrsense_status defl_orthonormalize(nrsense_plan_s* p, cudaStream_t s) {
+  const int k = p->defl_k;
+  const long long n = p->geo.nvox;
+  int kept = 0;
+  std::vector<double> c(size_t(2) * k);
+  double nn[2];
+  for (int i = 0; i < k; ++i) {
+    nrsense_c64* wi = p->defl_w + i * n;
+    NRS_TRY(defl_dots_host(p, wi, 1, wi, s, nn));
+    const double n0 = std::sqrt(std::max(nn[0], 0.0));
+    if (!(n0 > 0.0) || !std::isfinite(n0)) continue;
+    for (int pass = 0; pass < 2 && kept > 0; ++pass) {
+      NRS_TRY(defl_dots_host(p, p->defl_w, kept, wi, s, c.data()));
+      if (cudaMemcpyAsync(p->defl_coef, c.data(), size_t(2) * kept * sizeof(double),
+                          cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return NRSENSE_ERR_CUDA;
+      defl_update_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(
+          reinterpret_cast<float2*>(wi), reinterpret_cast<const float2*>(wi),
+          reinterpret_cast<const float2*>(p->defl_w), p->defl_coef, kept, n, nullptr, nullptr);
+      p->launches += 1;
+    }
+    NRS_TRY(defl_dots_host(p, wi, 1, wi, s, nn));
+    const double n1 = std::sqrt(std::max(nn[0], 0.0));
+    if (!(n1 >= 1e-2 * n0)) continue;
+    defl_scale_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(
+        reinterpret_cast<float2*>(p->defl_w + kept * n), reinterpret_cast<const float2*>(wi),
+        float(1.0 / n1), n);
+    p->launches += 1;
+    NRS_TRY(launched());
+    ++kept;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return NRSENSE_ERR_CUDA;
+  p->defl_k = kept;
+  p->epoch += 1;  // the count of basis vectors is a launch parameter
+  return NRSENSE_OK;
+}
+
+// With W in place: W orthonormalised, E0 W (one normal-operator application
+// per kept vector, lambda = 0) and the Gram matrices W^H E0 W, W^H W (host,
+// FP64).  ERR_BREAKDOWN when no vector is kept.
+nrsense_status defl_install(nrsense_plan_s* p, cudaStream_t s) {
+  NRS_TRY(defl_orthonormalize(p, s));
+  if (p->defl_k == 0) return NRSENSE_ERR_BREAKDOWN;
+  const int k = p->defl_k;
+  const long long n = p->geo.nvox;
+  for (int i = 0; i < k; ++i)
+    NRS_TRY(nrsense_apply_normal(p, p->defl_w + i * n, 0.0, p->defl_e0w + i * n, s));
+  p->defl_g0.assign(size_t(2) * k * k, 0.0);
+  p->defl_gw.assign(size_t(2) * k * k, 0.0);
+  std::vector<double> col(size_t(2) * k);
+  for (int j = 0; j < k; ++j) {
+    NRS_TRY(defl_dots_host(p, p->defl_w, k, p->defl_e0w + j * n, s, col.data()));
+    for (int i = 0; i < k; ++i) {
+      p->defl_g0[2 * (i * k + j)] = col[2 * i];
+      p->defl_g0[2 * (i * k + j) + 1] = col[2 * i + 1];
+    }
+    NRS_TRY(defl_dots_host(p, p->defl_w, k, p->defl_w + j * n, s, col.data()));
+    for (int i = 0; i < k; ++i) {
+      p->defl_gw[2 * (i * k + j)] = col[2 * i];
+      p->defl_gw[2 * (i * k + j) + 1] = col[2 * i + 1];
+    }
+  }
+  p->defl_lambda = -1.0;
+  return NRSENSE_OK;
+}
+
+// E W = E0 W + lambda W and E_c^-1 = (W^H E0 W + lambda W^H W)^-1 for this
+// lambda (kept until lambda changes).  Synchronises s.
+nrsense_status defl_prepare(nrsense_plan_s* p, double lambda, cudaStream_t s) {
+  if (p->defl_lambda == lambda) return NRSENSE_OK;
+  const int k = p->defl_k;
+  const long long total = (long long)k * p->geo.nvox;
+  defl_form_ew_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(
+      reinterpret_cast<float2*>(p->defl_ew), reinterpret_cast<const float2*>(p->defl_e0w),
+      reinterpret_cast<const float2*>(p->defl_w), float(lambda), total);
+  p->launches += 1;
+  NRS_TRY(launched());
+  std::vector<double> ec(p->defl_g0);
+  for (size_t i = 0; i < ec.size(); ++i) ec[i] += lambda * p->defl_gw[i];
+  if (pinv_hermitian(ec, k) == 0) return NRSENSE_ERR_BREAKDOWN;
+  if (cudaMemcpyAsync(p->defl_ecinv, ec.data(), ec.size() * sizeof(double),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return NRSENSE_ERR_CUDA;
+  p->defl_lambda = lambda;
+  return NRSENSE_OK;
+}
+
+// out = P^T in = in - W E_c^-1 (E W)^H in (out may equal in)
+nrsense_status defl_project(nrsense_plan_s* p, const nrsense_c64* in, nrsense_c64* out,
+                            cudaStream_t s) {
+  StageMark m(p, NRSENSE_STAGE_SOLVER, s);
+  defl_dots(p, p->defl_ew, p->defl_k, in, s);
+  defl_coef_kernel<<<1, kRedThreads, 0, s>>>(p->defl_partial, kDeflBlocks, p->defl_k,
+                                             p->defl_ecinv, p->defl_coef);
+  defl_update_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(
+      reinterpret_cast<float2*>(out), reinterpret_cast<const float2*>(in),
+      reinterpret_cast<const float2*>(p->defl_w), p->defl_coef, p->defl_k, p->geo.nvox, nullptr,
+      nullptr);
+  p->launches += 2;
+  return launched();
+}
+
+// start: c = E_c^-1 W^H r, x += W c, r -= (E W) c
+nrsense_status defl_start(nrsense_plan_s* p, nrsense_c64* x, nrsense_c64* r, cudaStream_t s) {
+  StageMark m(p, NRSENSE_STAGE_SOLVER, s);
+  defl_dots(p, p->defl_w, p->defl_k, r, s);
+  defl_coef_kernel<<<1, kRedThreads, 0, s>>>(p->defl_partial, kDeflBlocks, p->defl_k,
+                                             p->defl_ecinv, p->defl_coef);
+  defl_update_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(
+      reinterpret_cast<float2*>(r), reinterpret_cast<const float2*>(r),
+      reinterpret_cast<const float2*>(p->defl_ew), p->defl_coef, p->defl_k, p->geo.nvox,
+      reinterpret_cast<float2*>(x), reinterpret_cast<const float2*>(p->defl_w));
+  p->launches += 2;
+  return launched();
+}
+
 // z = M(r) (the network), z = M_c r (circulant), z = M(M_c r) (both) or
-// z = r (neither), then the flexible CG coefficient and direction.  start:
-// first direction.
-nrsense_status fcg_direction(nrsense_plan_s* p, nrsense_cnn_s* net, bool circ, bool start,
-                             cudaStream_t s) {
+// z = r (neither), projected by P^T when deflating, then the flexible CG
+// coefficient and direction.  start: first direction.
+nrsense_status fcg_direction(nrsense_plan_s* p, nrsense_cnn_s* net, bool circ, bool defl,
+                             bool start, cudaStream_t s) {
   nrsense_cg_ws* w = p->cg;
   const long long n = p->geo.nvox;
   const float2* r = reinterpret_cast<const float2*>(w->r);
@@ -480,6 +876,12 @@ nrsense_status fcg_direction(nrsense_plan_s* p, nrsense_cnn_s* net, bool circ, b
     p->launches += cnn_apply_async(net, z, sumsq, reinterpret_cast<float2*>(w->z), s);
     z = reinterpret_cast<const float2*>(w->z);
   }
+  if (defl) {
+    // project in place, or into the network buffer when z is the residual
+    nrsense_c64* dst = z == r ? w->z : reinterpret_cast<nrsense_c64*>(const_cast<float2*>(z));
+    NRS_TRY(defl_project(p, reinterpret_cast<const nrsense_c64*>(z), dst, s));
+    z = reinterpret_cast<const float2*>(dst);
+  }
   StageMark m(p, NRSENSE_STAGE_SOLVER, s);
   dot2_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(
       z, r, start ? nullptr : reinterpret_cast<const float2*>(w->Ep), n, w->partial);
@@ -493,7 +895,7 @@ nrsense_status fcg_direction(nrsense_plan_s* p, nrsense_cnn_s* net, bool circ, b
 // One CG (net == nullptr, flexible == false) or flexible CG iteration on
 // stream s, without host synchronisation.
 nrsense_status cg_iteration(nrsense_plan_s* p, nrsense_c64* x, double lambda, bool flexible,
-                            nrsense_cnn_s* net, bool circ, cudaStream_t s) {
+                            nrsense_cnn_s* net, bool circ, bool defl, cudaStream_t s) {
   nrsense_cg_ws* w = p->cg;
   const long long n = p->geo.nvox;
   NRS_TRY(nrsense_apply_normal(p, w->p, lambda, w->Ep, s));
@@ -517,7 +919,7 @@ nrsense_status cg_iteration(nrsense_plan_s* p, nrsense_c64* x, double lambda, bo
     }
     p->launches += 5;
   }
-  if (flexible) NRS_TRY(fcg_direction(p, net, circ, false, s));
+  if (flexible) NRS_TRY(fcg_direction(p, net, circ, defl, false, s));
   return launched();
 }
 
@@ -547,7 +949,9 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
                           uint32_t flags, nrsense_c64* x, const SolveOut& out, Record* rec,
                           cudaStream_t us) {
   const bool circ = flexible && (flags & NRSENSE_CG_CIRCULANT) != 0;
+  const bool defl = flexible && (flags & NRSENSE_CG_DEFLATE) != 0;
   if (circ && !p->circ_on) return NRSENSE_ERR_STATE;
+  if (defl && p->defl_k == 0) return NRSENSE_ERR_STATE;
   NRS_TRY(cg_workspace(p, maxit, flexible, circ));
   nrsense_cg_ws* w = p->cg;
   const long long n = p->geo.nvox;
@@ -556,6 +960,7 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
   cudaStream_t s = w->cs;
   if (cudaEventRecord(w->ev0, us) != cudaSuccess || cudaStreamWaitEvent(s, w->ev0, 0) != cudaSuccess)
     return NRSENSE_ERR_CUDA;
+  if (defl) NRS_TRY(defl_prepare(p, lambda, s));
 
   // b = sum_j A_j^H y_j;  r = b - E x0 (or b);  p = r (or z = M(r))
   NRS_TRY(nrsense_apply_adjoint(p, y, w->b, s));
@@ -581,12 +986,22 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
   } else {
     if (cudaMemsetAsync(x, 0, vb, s) != cudaSuccess) return NRSENSE_ERR_CUDA;
   }
-  cg_init_kernel<<<1, kRedThreads, 0, s>>>(w->partial, use_x0 ? w->partial + kRedBlocks : nullptr,
-                                           kRedBlocks, tol, maxit, w->st, w->hist);
+  if (defl) {
+    // x += W E_c^-1 W^H r, r -= E W E_c^-1 W^H r; then |r|^2 of the result
+    NRS_TRY(defl_start(p, x, w->r, s));
+    StageMark m(p, NRSENSE_STAGE_SOLVER, s);
+    dot_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(
+        reinterpret_cast<const float2*>(w->r), reinterpret_cast<const float2*>(w->r), n,
+        w->partial + kRedBlocks);
+    p->launches += 1;
+  }
+  cg_init_kernel<<<1, kRedThreads, 0, s>>>(
+      w->partial, (use_x0 || defl) ? w->partial + kRedBlocks : nullptr, kRedBlocks, tol, maxit,
+      w->st, w->hist);
   p->launches += 1;
   NRS_TRY(launched());
   if (flexible) {
-    NRS_TRY(fcg_direction(p, net, circ, true, s));
+    NRS_TRY(fcg_direction(p, net, circ, defl, true, s));
   } else if (cudaMemcpyAsync(w->p, w->r, vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
     return NRSENSE_ERR_CUDA;
   }
@@ -600,9 +1015,11 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
   const int chunk = rec ? 1
                   : graph ? std::max(1, std::min<int>(maxit, tol == 0.0 ? kGraphMax : 2))
                           : 5;
-  const int mode = flexible ? (circ ? 2 : 1) : 0;
+  const int mode = (flexible ? (circ ? 2 : 1) : 0) + (defl ? 4 : 0);
+  const uint64_t gnet = cnn_serial(net);
   if (graph && (w->gexec == nullptr || w->g_x != x || w->g_lambda != lambda ||
-                w->g_chunk != chunk || w->g_mode != mode || w->g_net != net)) {
+                w->g_chunk != chunk || w->g_mode != mode || w->g_net != gnet ||
+                w->g_epoch != p->epoch)) {
     if (w->gexec) {
       cudaGraphExecDestroy(w->gexec);
       w->gexec = nullptr;
@@ -612,7 +1029,7 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
       return NRSENSE_ERR_CUDA;
     nrsense_status cst = NRSENSE_OK;
     for (int k = 0; k < chunk && cst == NRSENSE_OK; ++k)
-      cst = cg_iteration(p, x, lambda, flexible, net, circ, s);
+      cst = cg_iteration(p, x, lambda, flexible, net, circ, defl, s);
     const cudaError_t e = cudaStreamEndCapture(s, &gph);
     if (cst != NRSENSE_OK) {
       if (gph) cudaGraphDestroy(gph);
@@ -629,7 +1046,8 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
     w->g_lambda = lambda;
     w->g_chunk = chunk;
     w->g_mode = mode;
-    w->g_net = net;
+    w->g_net = gnet;
+    w->g_epoch = p->epoch;
   }
   CgState h;
   for (int it = 0; it < maxit; it += chunk) {
@@ -648,7 +1066,7 @@ nrsense_status solve_impl(nrsense_plan_s* p, bool flexible, nrsense_cnn_s* net,
       p->launches += 5LL * chunk;  // approximate: kernels of the captured operator not recounted
     } else {
       for (int k = 0; k < chunk && it + k < maxit; ++k)
-        NRS_TRY(cg_iteration(p, x, lambda, flexible, net, circ, s));
+        NRS_TRY(cg_iteration(p, x, lambda, flexible, net, circ, defl, s));
     }
   }
   if (rec) {
@@ -708,6 +1126,7 @@ nrsense_status nrsense_solve_cg(nrsense_plan_t p, const nrsense_c64* y, double l
                                 int32_t maxit, uint32_t flags, nrsense_c64* x, int32_t* iters,
                                 double* res_hist, double* true_res, void* stream) {
   if (!solve_args_ok(p, y, x, lambda, tol, maxit)) return NRSENSE_ERR_ARG;
+  if (flags & (NRSENSE_CG_CIRCULANT | NRSENSE_CG_DEFLATE)) return NRSENSE_ERR_ARG;
   const SolveOut out{iters, res_hist, true_res, nullptr};
   return solve_impl(p, false, nullptr, y, lambda, tol, maxit, flags, x, out, nullptr,
                     static_cast<cudaStream_t>(stream));
@@ -718,7 +1137,8 @@ nrsense_status nrsense_solve_cg_record(nrsense_plan_t p, const nrsense_c64* y, d
                                        int32_t* iters, double* res_hist, double* true_res,
                                        nrsense_c64* rec_r, nrsense_c64* rec_e, int32_t capacity,
                                        int32_t* rec_count, void* stream) {
-  if (!solve_args_ok(p, y, x, lambda, tol, maxit) || (flags & NRSENSE_CG_GRAPH) || capacity < 0 ||
+  if (!solve_args_ok(p, y, x, lambda, tol, maxit) ||
+      (flags & (NRSENSE_CG_GRAPH | NRSENSE_CG_CIRCULANT | NRSENSE_CG_DEFLATE)) || capacity < 0 ||
       (capacity > 0 && (rec_r == nullptr || rec_e == nullptr)) || rec_count == nullptr)
     return NRSENSE_ERR_ARG;
   Record rec{rec_r, rec_e, capacity, 0};
@@ -805,6 +1225,147 @@ nrsense_status nrsense_apply_circulant(nrsense_plan_t p, const nrsense_c64* r, n
   if (p == nullptr || r == nullptr || z == nullptr) return NRSENSE_ERR_ARG;
   if (!p->circ_on) return NRSENSE_ERR_STATE;
   return circ_apply(p, r, z, static_cast<cudaStream_t>(stream));
+}
+
+nrsense_status nrsense_set_deflation(nrsense_plan_t p, const nrsense_c64* w, int32_t k,
+                                     int32_t* kept, void* stream) {
+  if (kept) *kept = 0;
+  if (p == nullptr || k < 0 || k > kDeflMax || (k > 0 && w == nullptr)) return NRSENSE_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (k == 0) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return NRSENSE_ERR_CUDA;
+    defl_release(p);
+    return NRSENSE_OK;
+  }
+  NRS_TRY(defl_alloc(p, k));
+  const size_t vb = size_t(p->geo.nvox) * sizeof(nrsense_c64);
+  if (cudaMemcpyAsync(p->defl_w, w, k * vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+    defl_release(p);
+    return NRSENSE_ERR_CUDA;
+  }
+  const nrsense_status st = defl_install(p, s);
+  if (st != NRSENSE_OK) {
+    defl_release(p);
+    return st;
+  }
+  if (kept) *kept = p->defl_k;
+  return NRSENSE_OK;
+}
+
+nrsense_status nrsense_deflation_from_solve(nrsense_plan_t p, const nrsense_c64* y, double lambda,
+                                            int32_t steps, int32_t k, uint32_t flags,
+                                            double* ritz, int32_t* kept, void* stream) {
+  if (kept) *kept = 0;
+  if (p == nullptr || y == nullptr || !(lambda >= 0.0) || !std::isfinite(lambda) || steps < 1 ||
+      steps > 256 || k < 1 || k > std::min<int>(steps, kDeflMax) ||
+      (flags & ~(NRSENSE_CG_CIRCULANT | NRSENSE_DEFLATE_LARGEST)) != 0)
+    return NRSENSE_ERR_ARG;
+  const bool largest = (flags & NRSENSE_DEFLATE_LARGEST) != 0;
+  const bool circ = (flags & NRSENSE_CG_CIRCULANT) != 0;
+  if (circ && !p->circ_on) return NRSENSE_ERR_STATE;
+  NRS_TRY(cg_workspace(p, steps + 1, true, circ));
+  nrsense_cg_ws* w = p->cg;
+  const long long n = p->geo.nvox;
+  const size_t vb = size_t(n) * sizeof(nrsense_c64);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // scratch: the iterate, the recorded preconditioned residuals, coefficients
+  struct Scratch {
+    nrsense_c64* x = nullptr;
+    nrsense_c64* Z = nullptr;
+    float* coef = nullptr;
+    ~Scratch() {
+      cudaFree(x);
+      cudaFree(Z);
+      cudaFree(coef);
+    }
+  } sc;
+  if (cudaMalloc(&sc.x, vb) != cudaSuccess || cudaMalloc(&sc.Z, size_t(steps) * vb) != cudaSuccess ||
+      cudaMalloc(&sc.coef, size_t(steps) * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return NRSENSE_ERR_OOM;
+  }
+  // b = sum_j A_j^H y_j, r = b, x = 0; run past `steps` so that rho_steps is formed
+  NRS_TRY(nrsense_apply_adjoint(p, y, w->b, s));
+  dot_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(reinterpret_cast<const float2*>(w->b),
+                                                        reinterpret_cast<const float2*>(w->b), n,
+                                                        w->partial);
+  p->launches += 1;
+  if (cudaMemcpyAsync(w->r, w->b, vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(sc.x, 0, vb, s) != cudaSuccess)
+    return NRSENSE_ERR_CUDA;
+  cg_init_kernel<<<1, kRedThreads, 0, s>>>(w->partial, nullptr, kRedBlocks, 0.0, steps + 1, w->st,
+                                           w->hist);
+  p->launches += 1;
+  NRS_TRY(launched());
+  NRS_TRY(fcg_direction(p, nullptr, circ, false, true, s));
+  CgState h;
+  NRS_TRY(read_state(p, s, &h));
+  std::vector<double> alpha, rho{h.rz};
+  int m = 0;
+  const nrsense_c64* zsrc = circ ? w->zc : w->r;
+  for (int j = 0; j < steps && !h.done; ++j) {
+    if (cudaMemcpyAsync(sc.Z + size_t(j) * n, zsrc, vb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return NRSENSE_ERR_CUDA;
+    NRS_TRY(cg_iteration(p, sc.x, lambda, true, nullptr, circ, false, s));
+    NRS_TRY(read_state(p, s, &h));
+    if (h.status != NRSENSE_OK || h.n_fb != 0) return NRSENSE_ERR_BREAKDOWN;
+    alpha.push_back(h.alpha);
+    if (h.done) break;  // exact convergence: rho_{j+1} is not formed
+    rho.push_back(h.rz);
+    m = j + 1;
+  }
+  if (m < 1) return NRSENSE_ERR_BREAKDOWN;
+  for (int j = 0; j <= m; ++j)
+    if (!(rho[j] > 0.0) || !std::isfinite(rho[j])) return NRSENSE_ERR_BREAKDOWN;
+  // the CG-Lanczos tridiagonal for v_j = z_j / sqrt(rho_j), its eigenpairs
+  std::vector<double> T(size_t(m) * m, 0.0), vals(m), vecs(size_t(m) * m);
+  for (int j = 0; j < m; ++j) {
+    T[size_t(j) * m + j] = 1.0 / alpha[j] + (j > 0 ? (rho[j] / rho[j - 1]) / alpha[j - 1] : 0.0);
+    if (j + 1 < m)
+      T[size_t(j) * m + j + 1] = T[size_t(j + 1) * m + j] =
+          -std::sqrt(rho[j + 1] / rho[j]) / alpha[j];
+  }
+  symmetric_eigen_sorted(m, T.data(), vals.data(), vecs.data());
+  const int kk = std::min<int>(k, m);
+  NRS_TRY(defl_alloc(p, kk));
+  std::vector<float> c(m);
+  // the Ritz pair taken i-th: ascending from the smallest, or descending
+  // from the largest
+  auto pick = [&](int i) { return largest ? m - 1 - i : i; };
+  for (int i = 0; i < kk; ++i) {
+    const int e = pick(i);
+    for (int j = 0; j < m; ++j) c[j] = float(vecs[size_t(j) * m + e] / std::sqrt(rho[j]));
+    if (cudaMemcpyAsync(sc.coef, c.data(), m * sizeof(float), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess) {
+      defl_release(p);
+      return NRSENSE_ERR_CUDA;
+    }
+    defl_combine_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(
+        reinterpret_cast<float2*>(p->defl_w + size_t(i) * n),
+        reinterpret_cast<const float2*>(sc.Z), sc.coef, m, n);
+    p->launches += 1;
+    // c is rewritten for the next vector: wait for this copy to be consumed
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      defl_release(p);
+      return NRSENSE_ERR_CUDA;
+    }
+  }
+  const nrsense_status st = defl_install(p, s);
+  if (st != NRSENSE_OK) {
+    defl_release(p);
+    return st;
+  }
+  if (ritz)
+    for (int i = 0; i < k; ++i) ritz[i] = i < kk ? vals[pick(i)] : std::nan("");
+  if (kept) *kept = p->defl_k;
+  return NRSENSE_OK;
+}
+
+nrsense_status nrsense_symmetric_eigen(int32_t m, const double* a, double* vals, double* vecs) {
+  if (m < 1 || m > 256 || a == nullptr || vals == nullptr || vecs == nullptr)
+    return NRSENSE_ERR_ARG;
+  symmetric_eigen_sorted(m, a, vals, vecs);
+  return NRSENSE_OK;
 }
 
 }  // extern "C"

@@ -140,6 +140,12 @@ _SIGS = {
                             _VP],
     "nrsense_plan_set_reduce": [_VP, _VP, _VP],
     "nrsense_copy_c64": [_VP, _VP, ctypes.c_int64, _VP],
+    "nrsense_set_deflation": [_VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _VP],
+    "nrsense_deflation_from_solve": [_VP, _VP, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_int32), _VP],
+    "nrsense_symmetric_eigen": [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
 }
 # nrsense_reduce_fn: (user, image_dev, n, stream) -> status
 REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -147,6 +153,8 @@ REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, c
 CG_X0 = 1
 CG_GRAPH = 2
 CG_CIRCULANT = 4
+CG_DEFLATE = 8
+DEFLATE_LARGEST = 16
 NUM_STAGES = 16
 _STRING_RESULT = ("nrsense_status_string", "nrsense_stage_name")
 _INT64_RESULT = ("nrsense_cnn_num_params",)
@@ -332,6 +340,20 @@ def kmeans(points, k, max_iter=100):
                               ctypes.byref(inertia), ctypes.byref(iters), ctypes.byref(ref)),
            "nrsense_kmeans")
     return labels, centres, inertia.value, iters.value, ref.value
+
+def symmetric_eigen(a):
+    """Eigenvalues (ascending) and eigenvectors (columns) of a real symmetric
+    matrix by the library's host Jacobi solver (nrsense_symmetric_eigen)."""
+    lib = load()
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    m = a.shape[0]
+    vals = np.zeros(m, dtype=np.float64)
+    vecs = np.zeros((m, m), dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib.nrsense_symmetric_eigen(int(m), a.ctypes.data_as(dp), vals.ctypes.data_as(dp),
+                                       vecs.ctypes.data_as(dp)), "nrsense_symmetric_eigen")
+    return vals, vecs
+
 
 class Plan:
     """Nonrigid SENSE operator A_j = G_j S T_j over P motion states.
@@ -587,11 +609,46 @@ class Plan:
                "nrsense_apply_circulant")
         return out
 
+    def set_deflation(self, w, stream=None):
+        """Deflation basis (nrsense_set_deflation): w a (k,) + shape complex64
+        CUDA tensor, or None to switch deflation off.  Returns the number of
+        basis vectors kept after orthonormalisation."""
+        import torch
+        kept = ctypes.c_int32()
+        if w is None:
+            _check(self.lib.nrsense_set_deflation(self._h, None, 0, ctypes.byref(kept),
+                                                  _stream(stream)), "nrsense_set_deflation")
+            return 0
+        if not isinstance(w, torch.Tensor) or w.dim() != 4 or tuple(w.shape[1:]) != self.shape:
+            raise ValueError(f"w must be (k,) + {self.shape}")
+        _need(w, torch.complex64, tuple(w.shape), "w")
+        _check(self.lib.nrsense_set_deflation(self._h, _ptr(w), int(w.shape[0]),
+                                              ctypes.byref(kept), _stream(stream)),
+               "nrsense_set_deflation")
+        return kept.value
+
+    def deflation_from_solve(self, y, lam, steps=60, k=16, circulant=True, largest=False,
+                             stream=None):
+        """Deflation basis from the k smallest (largest=True: largest) Ritz
+        pairs of `steps` iterations of (circulant-preconditioned) CG on the
+        data y (nrsense_deflation_from_solve).  Returns (Ritz values, number
+        of basis vectors kept)."""
+        import torch
+        _need(y, torch.complex64, self.forward_shape(), "y")
+        ritz = (ctypes.c_double * int(k))()
+        kept = ctypes.c_int32()
+        flags = (CG_CIRCULANT if circulant else 0) | (DEFLATE_LARGEST if largest else 0)
+        _check(self.lib.nrsense_deflation_from_solve(
+            self._h, _ptr(y), float(lam), int(steps), int(k), flags, ritz, ctypes.byref(kept),
+            _stream(stream)), "nrsense_deflation_from_solve")
+        return np.array(ritz[:]), kept.value
+
     def solve_fcg(self, y, lam, net=None, tol=1e-4, maxit=100, x0=None, graph=False, stream=None,
-                  check=True, out=None, circulant=False):
+                  check=True, out=None, circulant=False, deflate=False):
         """Flexible CG preconditioned by the network `net` (a Cnn, or None)
         and, with circulant=True, by the circulant preconditioner first
-        (set_circulant must have been called).
+        (set_circulant must have been called); deflate=True projects out the
+        plan's deflation space (set_deflation / deflation_from_solve).
 
         Returns (x, iterations, residual history, true relative residual,
         status code, fallbacks)."""
@@ -602,7 +659,7 @@ class Plan:
         hist = (ctypes.c_double * (int(maxit) + 1))()
         tres = ctypes.c_double()
         flags = ((CG_X0 if x0 is not None else 0) | (CG_GRAPH if graph else 0)
-                 | (CG_CIRCULANT if circulant else 0))
+                 | (CG_CIRCULANT if circulant else 0) | (CG_DEFLATE if deflate else 0))
         code = self.lib.nrsense_solve_fcg(
             self._h, None if net is None else net._h, _ptr(y), float(lam), float(tol), int(maxit),
             flags, _ptr(x), ctypes.byref(it), hist, ctypes.byref(tres), ctypes.byref(fb),

@@ -113,3 +113,25 @@ def test_every_mirrored_field_matches_header(tmp_path):
         want.append(ctypes.sizeof(cls))
         want += [getattr(cls, f).offset for f, _ in cls._fields_]
     assert got == want
+
+
+def test_host_symmetric_eigen_matches_numpy(lib):
+    """The Jacobi eigen-solver behind nrsense_deflation_from_solve (host only)
+    against numpy's on a CG-Lanczos-shaped tridiagonal and on a dense matrix:
+    eigenvalues, orthonormal eigenvectors, A V = V diag(vals)."""
+    import numpy as np
+    from paper_2501_16713_gb300 import nrsense
+    rng = np.random.default_rng(181)
+    m = 40
+    T = np.diag(rng.uniform(0.5, 3.0, m)) - np.diag(rng.uniform(0.1, 1.0, m - 1), 1)
+    T = T + np.triu(T, 1).T
+    X = rng.standard_normal((12, 12))
+    for A in (T, X + X.T):
+        vals, vecs = nrsense.symmetric_eigen(A)
+        ref = np.linalg.eigvalsh(A)
+        scale = np.abs(ref).max()
+        assert np.allclose(vals, ref, rtol=0, atol=1e-12 * scale)
+        assert np.allclose(vecs.T @ vecs, np.eye(A.shape[0]), atol=1e-12)
+        assert np.allclose(A @ vecs, vecs * vals, atol=1e-11 * scale)
+    with pytest.raises(nrsense.NrsenseError):
+        nrsense.symmetric_eigen(np.zeros((0, 0)))
