@@ -58,7 +58,7 @@ __global__ void crop_deapod_kernel(Geo g, const float* __restrict__ dtab,
 // (Backprojection Core B_j^(i) at the displaced voxel positions of the
 // displacement-field equation).  One thread per voxel, all phases: the
 // phases' taps of one voxel are close, so they share L1/L2 lines.
-template <int W>
+template <int W, bool RAT>
 __global__ void __launch_bounds__(256) interp_image_kernel(Geo g, KernelCoefs kc, int P,
                                                            const float* __restrict__ disp,
                                                            const float2* __restrict__ u,
@@ -70,19 +70,26 @@ __global__ void __launch_bounds__(256) interp_image_kernel(Geo g, KernelCoefs kc
   const int i1 = int(r % g.n1);
   const int i0 = int(r / g.n1);
   const float sg = float(g.osf);
-  // sigma = G / N not an integer (g.osf == 0): sigma n = (G n) div N + r / N
-  // exactly, r = (G n) mod N; the rest in FP64
-  const int ip0 = int((long long)g.g0 * i0 / g.n0), ip1 = int((long long)g.g1 * i1 / g.n1),
-            ip2 = int((long long)g.g2 * i2 / g.n2);
-  const double fr0 = double((long long)g.g0 * i0 - (long long)ip0 * g.n0) / g.n0;
-  const double fr1 = double((long long)g.g1 * i1 - (long long)ip1 * g.n1) / g.n1;
-  const double fr2 = double((long long)g.g2 * i2 - (long long)ip2 * g.n2) / g.n2;
-  const double sr0 = double(g.g0) / g.n0, sr1 = double(g.g1) / g.n1, sr2 = double(g.g2) / g.n2;
+  // RAT (sigma = G / N not an integer, g.osf == 0): sigma n = (G n) div N +
+  // r / N exactly, r = (G n) mod N; the rest of the decomposition in FP64
+  int ip0 = 0, ip1 = 0, ip2 = 0;
+  double fr0 = 0.0, fr1 = 0.0, fr2 = 0.0, sr0 = 0.0, sr1 = 0.0, sr2 = 0.0;
+  if constexpr (RAT) {
+    ip0 = int((long long)g.g0 * i0 / g.n0);
+    ip1 = int((long long)g.g1 * i1 / g.n1);
+    ip2 = int((long long)g.g2 * i2 / g.n2);
+    fr0 = double((long long)g.g0 * i0 - (long long)ip0 * g.n0) / g.n0;
+    fr1 = double((long long)g.g1 * i1 - (long long)ip1 * g.n1) / g.n1;
+    fr2 = double((long long)g.g2 * i2 - (long long)ip2 * g.n2) / g.n2;
+    sr0 = double(g.g0) / g.n0;
+    sr1 = double(g.g1) / g.n1;
+    sr2 = double(g.g2) / g.n2;
+  }
   for (int j = 0; j < P; ++j) {
     const float* dj = disp + (long long)j * 3 * g.nvox;
     float f0, f1, f2;
     int b0, b1, b2;
-    if (g.osf > 0) {
+    if constexpr (!RAT) {
       // exact decomposition of q = sigma*n + sigma*d into first tap and fraction
       const float s0 = sg * __ldg(dj + idx);
       const float s1 = sg * __ldg(dj + g.nvox + idx);
@@ -192,10 +199,19 @@ int launch_interp_image(const Geo& g, int W, const KernelCoefs& kc, int P,
                          cudaStream_t s) {
   const auto* up = reinterpret_cast<const float2*>(u);
   auto* mp = reinterpret_cast<float2*>(m);
-  if (W == 4)
-    interp_image_kernel<4><<<blocks_for(g.nvox, 256), 256, 0, s>>>(g, kc, P, disp, up, mp);
-  else
-    interp_image_kernel<6><<<blocks_for(g.nvox, 256), 256, 0, s>>>(g, kc, P, disp, up, mp);
+  const unsigned nb = blocks_for(g.nvox, 256);
+  const bool rat = g.osf == 0;  // sigma not an integer: its own instantiation
+  if (W == 4) {
+    if (rat)
+      interp_image_kernel<4, true><<<nb, 256, 0, s>>>(g, kc, P, disp, up, mp);
+    else
+      interp_image_kernel<4, false><<<nb, 256, 0, s>>>(g, kc, P, disp, up, mp);
+  } else {
+    if (rat)
+      interp_image_kernel<6, true><<<nb, 256, 0, s>>>(g, kc, P, disp, up, mp);
+    else
+      interp_image_kernel<6, false><<<nb, 256, 0, s>>>(g, kc, P, disp, up, mp);
+  }
   return 1;
 }
 
