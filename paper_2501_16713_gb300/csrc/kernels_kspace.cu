@@ -362,14 +362,12 @@ __global__ void __launch_bounds__(256, CC == 2 ? 6 : CC == 4 ? 4 : 1) interp_tma
       q_next = __ldg(qs + s + stride);
       row_next = __ldg(perm + s + stride);
     }
-    int l0 = 0, l1 = 0, l2 = 0;
-    if (live) {
-      int b0, b1, b2;
-      unpack_base(__float_as_uint(qv.w), b0, b1, b2);
-      l0 = min(max(b0 - o0, 0), T - 1);  // in range for a well-formed plan
-      l1 = min(max(b1 - o1, 0), T - 1);
-      l2 = min(max(b2 - o2, 0), T - 1);
-    }
+    // first tap relative to the tile: a sample belongs to the tile of its first
+    // tap and tiles are 8-aligned, so this is b mod 8 (and stays inside the
+    // halo for any record; dead lanes compute on in-range garbage and do not
+    // store)
+    const uint32_t pk = __float_as_uint(qv.w);
+    const int l0 = int(pk >> 20) & (T - 1), l1 = int(pk >> 10) & (T - 1), l2 = int(pk) & (T - 1);
     // kernel weights of the sample: axis a at tap t
     float w0[W], w1[W], w2t;
     if constexpr (CC >= 4) {
@@ -406,7 +404,7 @@ __global__ void __launch_bounds__(256, CC == 2 ? 6 : CC == 4 ? 4 : 1) interp_tma
       }
     }
     float2 acc = make_float2(0.f, 0.f);
-    if (live) {
+    {
       const GT* base = halo + ((c * H + l0) * H + l1) * XP + l2 + txl;
 #pragma unroll
       for (int t0 = 0; t0 < W; ++t0) {
