@@ -369,7 +369,7 @@ def _timed_solve(fn):
     return res, e0.elapsed_time(e1)
 
 
-CIRC_LAMBDA_FACTOR = 10.0
+CIRC_LAMBDA_FACTOR = 5.0
 # recycled deflation space: Ritz vectors of the k largest Ritz values of a
 # DEFL_STEPS-iteration circulant-CG run on another right-hand side (the low
 # end of the circulant-preconditioned spectrum is a large cluster near
@@ -397,8 +397,8 @@ def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, s
     diff = float((out - x_cg).norm() / x_cg.norm())
     # circulant preconditioner (set up once per lambda: one E application,
     # timed apart), alone and followed by the network; built for
-    # CIRC_LAMBDA_FACTOR x lambda (a sweep on this workload: 1x 28, 3x 21,
-    # 10x 19, 30x 22, 100x 27 iterations)
+    # CIRC_LAMBDA_FACTOR x lambda (the sweep of `--workload cgsweep128`:
+    # 1x 28, 2x 23, 3x 21, 5x 18, 10x 19 iterations)
     t0 = time.perf_counter()
     plan.set_circulant(CIRC_LAMBDA_FACTOR * lam)
     ms_setup = (time.perf_counter() - t0) * 1000.0
@@ -470,6 +470,69 @@ def cg_compare(plan, x, shape, dev, net, tol=1e-4, maxit=500, rel_lambda=1e-3, s
             "circulant_deflated": {str(k): v for k, v in deflated.items()},
             "fcg_trained": trained, "target_speedup": 3.0,
             "speedup": round(ms_cg / best, 3), "speedup_fcg_net": round(ms_cg / ms_f, 3)}
+
+
+def run_cgsweep128(args):
+    """The CG preconditioning knobs on the 128^3 8-coil 4-phase problem at
+    lambda = 1e-3 lambda_max, to 1e-4: the circulant preconditioner's lambda
+    factor, alone and with recycled deflation spaces (Ritz vectors of the
+    largest or smallest Ritz values of a circulant-CG run of `steps` iterations
+    on another right-hand side, k asked / kept).  Solves as CUDA graphs, wall
+    time by CUDA events, each space's setup timed apart."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2501_16713_gb300 import Plan, build
+
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = synth.workload("sense128")
+    shape = w["spec"].shape
+    plan = Plan(shape, disp=torch.from_numpy(np.stack(w["disp"])).to(dev),
+                coords=[torch.from_numpy(c).to(dev) for c in w["coords"]],
+                smaps=torch.from_numpy(w["smaps"]).to(dev))
+    plan.autotune(reps=2)
+    x = torch.from_numpy(w["x"]).to(dev)
+    lam = 1e-3 * _lambda_max(plan, shape, dev)
+    gen = torch.Generator(device=dev).manual_seed(5)
+    y = _noisy(plan, x, gen)
+    out = torch.empty(shape, dtype=torch.complex64, device=dev)
+    tol, maxit = 1e-4, 500
+    (cg, ms_cg) = _timed_solve(lambda: plan.solve_cg(y, lam, tol=tol, maxit=maxit, graph=True,
+                                                     out=out))
+    dgen = torch.Generator(device=dev).manual_seed(205)
+    y_tr = _noisy(plan, torch.randn(shape, dtype=torch.complex64, device=dev, generator=dgen), dgen)
+    rows = []
+    for fac in (1.0, 2.0, 3.0, 5.0, 10.0):
+        plan.set_circulant(fac * lam)
+        (pc, ms_pc) = _timed_solve(lambda: plan.solve_fcg(y, lam, None, tol=tol, maxit=maxit,
+                                                          graph=True, out=out, circulant=True))
+        row = {"factor": fac, "circulant": {"iters": pc[1], "ms": round(ms_pc, 2)}, "deflated": []}
+        for steps, k, largest in ((30, 16, True), (40, 24, True), (40, 32, True), (30, 8, False)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ritz, kept = plan.deflation_from_solve(y_tr, lam, steps=steps, k=k, circulant=True,
+                                                   largest=largest)
+            torch.cuda.synchronize()
+            setup = (time.perf_counter() - t0) * 1000.0
+            (pd, ms) = _timed_solve(lambda: plan.solve_fcg(y, lam, None, tol=tol, maxit=maxit,
+                                                           graph=True, out=out, circulant=True,
+                                                           deflate=True))
+            row["deflated"].append({"steps": steps, "k": k, "end": "largest" if largest else
+                                    "smallest", "kept": kept, "iters": pd[1], "ms": round(ms, 2),
+                                    "true_res": pd[3], "setup_ms": round(setup, 1),
+                                    "ritz_first": float(ritz[0]), "ritz_last": float(ritz[-1]),
+                                    "speedup_vs_plain": round(ms_cg / ms, 3)})
+        plan.set_deflation(None)
+        rows.append(row)
+    plan.close()
+    return {"metric": "CG wall time to 1e-4 relative residual", "value": min(
+        d["ms"] for r in rows for d in r["deflated"]), "unit": "ms", "higher_is_better": False,
+        "data": "synthetic", "config": {"workload": "cgsweep128", "image": list(shape),
+                                        "lambda_rel": 1e-3, "tol": tol},
+        "plain": {"iters": cg[1], "ms": round(ms_cg, 2)}, "sweep": rows}
 
 
 def run_precond(args):
@@ -1218,7 +1281,8 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
-    special = {"precond128": run_precond, "cg192": run_cg192, "sweep256": run_sweep256,
+    special = {"precond128": run_precond, "cgsweep128": run_cgsweep128, "cg192": run_cg192,
+               "sweep256": run_sweep256,
                "fista128": run_fista128, "fista_warp192": run_fista_warp192,
                "motion64": run_motion64}
     if args.workload in special and args.impl == "ours":
@@ -1234,7 +1298,7 @@ def main():
         # the oracle on the host cores; rank 0 only
         if rank != 0:
             return
-        if args.workload in ("precond128", "fista_warp192", "motion64"):
+        if args.workload in ("precond128", "cgsweep128", "fista_warp192", "motion64"):
             print(json.dumps({"impl": "reference", "unavailable":
                               f"the {args.workload} workload has no CPU reference arm"}))
             return
