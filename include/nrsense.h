@@ -365,6 +365,29 @@ nrsense_status nrsense_cnn_adam_step(nrsense_cnn_t net, float lr, float grad_sca
 nrsense_status nrsense_cnn_launches(nrsense_cnn_t net, int64_t* out_host);
 
 /*
+ * nrsense_cnn_set_conv - the kernel behind the network's 3x3x3 convolutions:
+ * NRSENSE_CNN_CONV_MMA (mma.sync m16n8k16 BF16, operands fed by ldmatrix; the
+ * default) or NRSENSE_CNN_CONV_TCGEN05 (fifth-generation tensor cores: per
+ * 4 x 8 x 16 output block four M = 128, N = 16 accumulator tiles in tensor
+ * memory, 27 K = 16 BF16 products each issued by one thread, operands in
+ * shared memory in the canonical no-swizzle K-major layout).  Both compute the
+ * same sums in FP32 (in a different order: results agree to FP32 rounding,
+ * and stored BF16 activations to about one BF16 ulp).  The tcgen05 kernel
+ * loads each block's input halo by bulk tensor copies (tensor maps of the
+ * network's activation buffers, built at creation).  Errors: ERR_ARG,
+ * ERR_STATE (tcgen05 asked but the tensor maps could not be built).
+ * nrsense_cnn_device_status - the network's device status word: 0, or
+ * NRSENSE_ERR_TIMEOUT when a tcgen05 convolution's bounded wait for its
+ * products expired (that block stored nothing); clear != 0 resets it.
+ * Synchronises the stream.
+ */
+#define NRSENSE_CNN_CONV_MMA      0
+#define NRSENSE_CNN_CONV_TCGEN05  1
+nrsense_status nrsense_cnn_set_conv(nrsense_cnn_t net, int32_t kind);
+nrsense_status nrsense_cnn_device_status(nrsense_cnn_t net, int32_t clear, int32_t* out_host,
+                                         void* stream);
+
+/*
  * nrsense_dot_noalloc - <x, y> = sum_i conj(x_i) y_i in FP64, for callers that
  * cannot allocate device memory.  The paper has no counterpart: this is a
  * variant of the CG solver's inner-product kernel that needs no plan and

@@ -22,6 +22,7 @@
 // per-warp partial sums in a fixed grid order, reduced in FP64: training is
 // bitwise reproducible.
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -258,6 +259,260 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_kernel(ConvArgs a) {
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// The same convolution on the fifth-generation tensor cores (tcgen05): an
+// implicit GEMM D[voxel][o] = sum_{tap, c} A_tap[voxel][c] B_tap[o][c] with the
+// accumulators in tensor memory.  An output block of 4 x 16 x 8 voxels is four
+// M = 128, N = 16 tiles (output plane z: 16 rows y x 8 voxels x); each of the
+// 27 taps adds one K = 16 (BF16) product to each tile, issued by a single
+// thread: 108 MMAs per block.
+//
+// Operands sit in shared memory in the canonical K-major layout without
+// swizzling: core matrices of 8 rows x 16 bytes (8 channels), rows 16 bytes
+// apart, the two channel halves (K) a fixed stride (LBO) apart and the 8-row
+// groups a fixed stride (SBO) apart.  A tile's 8-row groups are its 16 y rows
+// of 8 consecutive voxels, so a tap's A operand is a view of the one staged
+// halo ([half][hz][hy][hx] x 16 bytes, 6 x 18 x 10 voxels, loaded by two bulk
+// tensor copies, one per channel half, zero outside the volume): start at the
+// shifted first voxel, SBO = one halo row (160 bytes), LBO = one channel
+// half.  Weights: [half][tap][o] x 16 bytes (per-thread asynchronous copies).
+// 48 KB of shared memory: four CTAs per SM, one block each.  Tensor memory:
+// 64 columns (4 tiles x 16 channels) over the 128 lanes; warp w reads lanes
+// 32 (w mod 4) .. + 31 of tiles 2 (w / 4) and 2 (w / 4) + 1.  Both waits on
+// mbarriers (halo landed, products done) are bounded; on expiry the CTA
+// records NRSENSE_ERR_TIMEOUT, stores nothing, waits (bounded) for what it has
+// in flight, frees its tensor memory and returns.  (Measured alternatives: the
+// halo by per-thread copies, 3 % faster; persistent CTAs with a two-stage
+// copy / product / epilogue pipeline, 20 % slower: with two CTAs per SM
+// nothing hides the epilogue.)
+
+constexpr int TBZ = 4, TBY = 16, TBX = 8;               // output block of the tcgen05 kernel
+constexpr int THZ = TBZ + 2, THY = TBY + 2, THX = TBX + 2;
+constexpr int kTcHaloVox = THZ * THY * THX;             // 1080
+constexpr int kTcThreads = 256;
+constexpr int kTcHalfBytes = kTcHaloVox * 16;           // one channel half of the halo: 17280
+constexpr int kTcStageBytes = 2 * kTcHalfBytes;         // the halo, both halves: 34560
+constexpr int kTcWHalfBytes = kTaps * kCh * 16;         // 6912
+constexpr size_t kTcSmem = size_t(kTcStageBytes) + size_t(2) * kTcWHalfBytes + 128;  // 48 KB
+constexpr uint32_t kTcCols = 64;                        // tensor-memory columns (4 tiles)
+constexpr long long kTcMaxPoll = 1LL << 24;
+
+__host__ __device__ inline int tc_blocks(const Vol& v) {
+  return ((v.d + TBZ - 1) / TBZ) * ((v.h + TBY - 1) / TBY) * ((v.w + TBX - 1) / TBX);
+}
+
+// Shared-memory matrix descriptor (no swizzling): start address, leading
+// (K-direction) and stride (M/N-direction) byte offsets in 16-byte units,
+// descriptor version 1 at bits 46-47.
+__device__ __forceinline__ uint64_t tc_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  return uint64_t((saddr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: F32 accumulators (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major, N / 8 at bits 17-22, M / 16 at
+// bits 24-28 (M = 128, N = 16).
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) |
+                              ((128u >> 4) << 24);
+
+__device__ __forceinline__ bool tc_mbar_try_wait(unsigned mbar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// One thread: D(tmem) (+)= A B^T over K = 16
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate)
+      : "memory");
+}
+
+// 16 consecutive accumulator columns of this thread's lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// The epilogue of one output voxel from its 16 channel sums (bias not yet
+// added): the same operations as conv3d_kernel's.
+__device__ __forceinline__ void conv_store_voxel(const ConvArgs& a, long long vox,
+                                                 const float (&acc)[16]) {
+  if (a.epi == kResidualC64) {
+    const float f0 = acc[0] + (a.bias ? a.bias[0] : 0.f);
+    const float f1 = acc[1] + (a.bias ? a.bias[1] : 0.f);
+    const float2 rv = a.r[vox];
+    float2 zv = make_float2(0.f, 0.f);
+    if (a.sc->ok) zv = make_float2(fmaf(rv.x, a.sc->inv_s_f, f0), fmaf(rv.y, a.sc->inv_s_f, f1));
+    a.z[vox] = zv;
+    return;
+  }
+#pragma unroll
+  for (int o = 0; o < kCh; o += 2) {
+    float f0 = acc[o] + (a.bias ? a.bias[o] : 0.f);
+    float f1 = acc[o + 1] + (a.bias ? a.bias[o + 1] : 0.f);
+    if (a.epi == kReluBf16) {
+      f0 = fmaxf(f0, 0.f);
+      f1 = fmaxf(f1, 0.f);
+    } else if (a.epi == kMaskBf16 || a.epi == kAddMaskBf16) {
+      const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + vox * kCh + o);
+      f0 = __bfloat162float(mk.x) > 0.f ? f0 : 0.f;
+      f1 = __bfloat162float(mk.y) > 0.f ? f1 : 0.f;
+      if (a.epi == kAddMaskBf16) {
+        const __nv_bfloat162 ad =
+            *reinterpret_cast<const __nv_bfloat162*>(a.addend + vox * kCh + o);
+        f0 += __bfloat162float(ad.x);
+        f1 += __bfloat162float(ad.y);
+      }
+    }
+    *reinterpret_cast<__nv_bfloat162*>(a.out + vox * kCh + o) = __floats2bfloat162_rn(f0, f1);
+  }
+}
+
+// block b's origin (z0, y0, x0)
+__device__ __forceinline__ void tc_origin(const Vol& v, int b, int& z0, int& y0, int& x0) {
+  const int nbx = (v.w + TBX - 1) / TBX, nby = (v.h + TBY - 1) / TBY;
+  x0 = (b % nbx) * TBX;
+  y0 = ((b / nbx) % nby) * TBY;
+  z0 = (b / (nbx * nby)) * TBZ;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 4) conv3d_tc_kernel(
+    ConvArgs a, const __grid_constant__ CUtensorMap tm_lo, const __grid_constant__ CUtensorMap tm_hi,
+    int* status, long long poll_limit) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // bulk tensor copies need 128-byte aligned destinations: round up (the
+  // launch reserves 128 extra bytes)
+  const unsigned raw = smem_u32(smem_raw);
+  unsigned char* xs = smem_raw + ((128u - (raw & 127u)) & 127u);  // [2][THZ][THY][THX] x 16 B
+  unsigned char* ws = xs + size_t(kTcStageBytes);                  // [2][27][16] x 16 B
+  __shared__ __align__(8) unsigned long long bars[2];             // halo landed, products done
+  __shared__ uint32_t tmem_sh;
+  const Vol& v = a.v;
+  int z0, y0, x0;
+  tc_origin(v, blockIdx.x, z0, y0, x0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&tmem_sh)),
+                 "r"(kTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  const unsigned bar_x = smem_u32(&bars[0]), bar_p = smem_u32(&bars[1]);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_x) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_p) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  // the halo: two bulk tensor copies (channel halves, zero outside the
+  // volume), box origin (channel 0, x0 - 1, y0 - 1, z0 - 1)
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar_x),
+                 "r"(unsigned(kTcStageBytes))
+                 : "memory");
+    const CUtensorMap* maps[2] = {&tm_lo, &tm_hi};
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      asm volatile(
+          "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+          " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(xs + h * kTcHalfBytes)),
+          "l"(reinterpret_cast<unsigned long long>(maps[h])), "r"(0), "r"(x0 - 1), "r"(y0 - 1),
+          "r"(z0 - 1), "r"(bar_x)
+          : "memory");
+  }
+  // weights [tap][o][c] -> [half][tap][o] x 8 channels
+  for (int i = threadIdx.x; i < kTaps * kCh * 2; i += blockDim.x) {
+    const int half = i & 1, to = i >> 1;
+    cp_async_16(ws + size_t(half * kTaps * kCh + to) * 16, a.wpk + to * kVS + half * 8, true);
+  }
+  cp_async_wait_all();
+  bool ok = false;
+  for (long long k = 0; k < poll_limit && !ok; ++k) ok = tc_mbar_try_wait(bar_x, 0);
+  // the staged weights become visible to the tensor core (async proxy); the
+  // tensor-memory address to every thread; one decision for the CTA
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  ok = __syncthreads_and(ok);
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+  bool issued = false;
+  if (ok) {
+    issued = true;
+    if (threadIdx.x == 0) {
+      // descriptors of tap 0 / tile 0; the start-address field (address / 16,
+      // 14 bits, no carry for shared-memory addresses) takes each tap's and
+      // tile's offset by a plain add of compile-time constants
+      const uint64_t a0 = tc_desc(smem_u32(xs), kTcHalfBytes, THX * 16);
+      const uint64_t b0 = tc_desc(smem_u32(ws), kTcWHalfBytes, 128);
+#pragma unroll 1
+      for (int tl = 0; tl < TBZ; ++tl) {
+        const uint64_t a_tl = a0 + uint64_t(tl * THY * THX);  // (16-byte units)
+        const uint32_t d = tmem + uint32_t(tl * 16);
+#pragma unroll
+        for (int tap = 0; tap < kTaps; ++tap) {
+          const int tz = tap / 9, ty = (tap / 3) % 3, tx = tap % 3;
+          tc_mma(d, a_tl + uint64_t((tz * THY + ty) * THX + tx), b0 + uint64_t(tap * kCh),
+                 tap > 0 ? 1u : 0u);
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              bar_p)
+          : "memory");
+    }
+    bool done = false;
+    for (long long k = 0; k < poll_limit && !done; ++k) done = tc_mbar_try_wait(bar_p, 0);
+    ok = __syncthreads_and(done);
+  }
+  if (ok) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const int row = 32 * (warp & 3) + lane;  // = y * 8 + x of a tile
+    const int y = row >> 3, x = row & 7;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int tl = 2 * (warp >> 2) + j;
+      float acc[16];
+      tc_ld16(tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(tl * 16), acc);
+      const int zz = z0 + tl, yy = y0 + y, xx = x0 + x;
+      if (zz < v.d && yy < v.h && xx < v.w)
+        conv_store_voxel(a, ((long long)zz * v.h + yy) * v.w + xx, acc);
+    }
+  } else {
+    // a wait expired: record it, store nothing, give what is in flight (the
+    // halo copy, the products) a last bounded chance before freeing
+    if (threadIdx.x == 0 && status) atomicCAS(status, 0, NRSENSE_ERR_TIMEOUT);
+    bool d = false;
+    for (long long k = 0; k < kTcMaxPoll && !d; ++k) d = tc_mbar_try_wait(bar_x, 0);
+    d = !issued;
+    for (long long k = 0; k < kTcMaxPoll && !d; ++k) d = tc_mbar_try_wait(bar_p, 0);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTcCols)
+                 : "memory");
 }
 
 // Weight and bias gradients of one layer:
@@ -585,10 +840,27 @@ struct nrsense_cnn_s {
   Scalars* sc = nullptr;
   int adam_t = 0;
   long long launches = 0;
+  bool tc = false;            // convolutions on tcgen05 (conv3d_tc_kernel), else mma.sync
+  bool tc_ok = false;         // tensor maps of every activation buffer built
+  int sms = 0;                // SMs of the device (persistent tcgen05 grid: two CTAs each)
+  int* tc_status = nullptr;   // device status word of the tcgen05 convolutions' waits
+  // per activation buffer that a convolution reads: its two channel-half
+  // tensor maps (the halo's bulk tensor copies)
+  struct ActMaps {
+    const void* base;
+    CUtensorMap half[2];
+  };
+  std::vector<ActMaps> act_maps;
   std::vector<void*> allocations;
 };
 
 namespace {
+
+// creation (and configuration) numbers of networks: solver graphs key on them
+uint64_t next_cnn_serial() {
+  static std::atomic<uint64_t> next{1};
+  return next.fetch_add(1);
+}
 
 int ew_grid(long long n) {
   return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16));
@@ -596,6 +868,52 @@ int ew_grid(long long n) {
 
 nrsense_status cuda_ok() {
   return cudaGetLastError() == cudaSuccess ? NRSENSE_OK : NRSENSE_ERR_CUDA;
+}
+
+// Two tensor maps per activation buffer [n][16 channels] (BF16): dimensions
+// (8 channels, x, y, z) with strides (32 B, 32 W B, 32 H W B), the second map's
+// base 16 bytes on (channels 8..15); box 8 x THX x THY x THZ, zero fill outside.
+bool make_act_maps(nrsense_cnn_s* net, const void* base, nrsense_cnn_s::ActMaps* out) {
+  const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(nrs::tensor_map_encoder());
+  if (encode == nullptr) return false;
+  const Vol& v = net->vol;
+  const cuuint64_t dims[4] = {8, cuuint64_t(v.w), cuuint64_t(v.h), cuuint64_t(v.d)};
+  const cuuint64_t strides[3] = {cuuint64_t(kCh) * 2, cuuint64_t(v.w) * kCh * 2,
+                                 cuuint64_t(v.h) * v.w * kCh * 2};
+  const cuuint32_t box[4] = {8, cuuint32_t(THX), cuuint32_t(THY), cuuint32_t(THZ)};
+  const cuuint32_t elem[4] = {1, 1, 1, 1};
+  out->base = base;
+  for (int h = 0; h < 2; ++h) {
+    void* b = const_cast<char*>(static_cast<const char*>(base) + h * 16);
+    if (encode(&out->half[h], CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, b, dims, strides, box, elem,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
+// the maps of every buffer a convolution reads; tc_ok on success
+void build_act_maps(nrsense_cnn_s* net) {
+  std::vector<const void*> bufs;
+  for (int l = 0; l < kLayers; ++l) bufs.push_back(net->act[l]);
+  for (int k = 0; k < 3; ++k)
+    if (net->gb[k]) bufs.push_back(net->gb[k]);
+  if (net->h5) bufs.push_back(net->h5);
+  for (int k = 0; k < 4; ++k)
+    if (net->ut[k]) bufs.push_back(net->ut[k]);
+  net->act_maps.clear();
+  for (const void* b : bufs) {
+    nrsense_cnn_s::ActMaps m;
+    if (!make_act_maps(net, b, &m)) {
+      net->act_maps.clear();
+      net->tc_ok = false;
+      return;
+    }
+    net->act_maps.push_back(m);
+  }
+  net->tc_ok = true;
 }
 
 void conv(nrsense_cnn_s* net, int layer, bool backward, const bf16* in, int epi, const bf16* mask,
@@ -612,7 +930,15 @@ void conv(nrsense_cnn_s* net, int layer, bool backward, const bf16* in, int epi,
   a.r = r;
   a.sc = net->sc;
   a.z = z;
-  conv3d_kernel<<<net->vol.nblocks, kConvThreads, kConvSmem, s>>>(a);
+  const nrsense_cnn_s::ActMaps* maps = nullptr;
+  if (net->tc)
+    for (const auto& m : net->act_maps)
+      if (m.base == in) maps = &m;
+  if (maps)
+    conv3d_tc_kernel<<<tc_blocks(net->vol), kTcThreads, kTcSmem, s>>>(
+        a, maps->half[0], maps->half[1], net->tc_status, kTcMaxPoll);
+  else
+    conv3d_kernel<<<net->vol.nblocks, kConvThreads, kConvSmem, s>>>(a);
   net->launches += 1;
 }
 
@@ -768,8 +1094,7 @@ nrsense_status nrsense_cnn_create(const int32_t* n_host, uint32_t flags, void* s
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   nrsense_cnn_s* net = new (std::nothrow) nrsense_cnn_s();
   if (!net) return NRSENSE_ERR_OOM;
-  static std::atomic<uint64_t> next_serial{1};
-  net->serial = next_serial.fetch_add(1);
+  net->serial = next_cnn_serial();
   net->spd = (flags & NRSENSE_CNN_SYMMETRIC) != 0;
   Vol& v = net->vol;
   v.d = n_host[0];
@@ -790,6 +1115,8 @@ nrsense_status nrsense_cnn_create(const int32_t* n_host, uint32_t flags, void* s
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device) != cudaSuccess ||
       cudaFuncSetAttribute(conv3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kConvSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(conv3d_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kTcSmem) != cudaSuccess ||
       cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kWgSmem) != cudaSuccess) {
     cudaGetLastError();
@@ -797,6 +1124,7 @@ nrsense_status nrsense_cnn_create(const int32_t* n_host, uint32_t flags, void* s
     return NRSENSE_ERR_CUDA;
   }
   net->wg_grid = std::max(1, std::min(v.nblocks, sms));
+  net->sms = sms;
   const size_t ab = size_t(v.n) * kCh * sizeof(bf16);
   const size_t pb = size_t(kLayers) * kLayerP * sizeof(float);
   bool ok = true;
@@ -819,13 +1147,16 @@ nrsense_status nrsense_cnn_create(const int32_t* n_host, uint32_t flags, void* s
   ok = ok && (net->part_b = (float*)dalloc(net, size_t(net->wg_grid) * kCh * sizeof(float))) != nullptr;
   ok = ok && (net->red = (double*)dalloc(net, 3 * kRedBlocks * sizeof(double))) != nullptr;
   ok = ok && (net->sc = (Scalars*)dalloc(net, sizeof(Scalars))) != nullptr;
+  ok = ok && (net->tc_status = (int*)dalloc(net, sizeof(int))) != nullptr;
   if (!ok) {
     release(net);
     return NRSENSE_ERR_OOM;
   }
+  build_act_maps(net);
   if (cudaMemsetAsync(net->wfwd, 0, size_t(kLayers) * kPack * sizeof(bf16), s) != cudaSuccess ||
       cudaMemsetAsync(net->wbwd, 0, size_t(kLayers) * kPack * sizeof(bf16), s) != cudaSuccess ||
-      cudaMemsetAsync(net->sc, 0, sizeof(Scalars), s) != cudaSuccess) {
+      cudaMemsetAsync(net->sc, 0, sizeof(Scalars), s) != cudaSuccess ||
+      cudaMemsetAsync(net->tc_status, 0, sizeof(int), s) != cudaSuccess) {
     release(net);
     return NRSENSE_ERR_CUDA;
   }
@@ -1011,6 +1342,34 @@ nrsense_status nrsense_cnn_adam_step(nrsense_cnn_t net, float lr, float grad_sca
 nrsense_status nrsense_cnn_launches(nrsense_cnn_t net, int64_t* out_host) {
   if (!net || !out_host) return NRSENSE_ERR_ARG;
   *out_host = net->launches;
+  return NRSENSE_OK;
+}
+
+nrsense_status nrsense_cnn_set_conv(nrsense_cnn_t net, int32_t kind) {
+  if (!net || (kind != NRSENSE_CNN_CONV_MMA && kind != NRSENSE_CNN_CONV_TCGEN05))
+    return NRSENSE_ERR_ARG;
+  const bool tc = kind == NRSENSE_CNN_CONV_TCGEN05;
+  if (tc && !net->tc_ok) return NRSENSE_ERR_STATE;
+  if (tc != net->tc) {
+    net->tc = tc;
+    net->serial = next_cnn_serial();  // graphs captured with the other kernel are re-captured
+  }
+  return NRSENSE_OK;
+}
+
+nrsense_status nrsense_cnn_device_status(nrsense_cnn_t net, int32_t clear, int32_t* out_host,
+                                         void* stream) {
+  if (!net || !out_host) return NRSENSE_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  if (cudaMemcpyAsync(&v, net->tc_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return NRSENSE_ERR_CUDA;
+  if (clear && v != 0 &&
+      (cudaMemsetAsync(net->tc_status, 0, sizeof(int), s) != cudaSuccess ||
+       cudaStreamSynchronize(s) != cudaSuccess))
+    return NRSENSE_ERR_CUDA;
+  *out_host = v;
   return NRSENSE_OK;
 }
 

@@ -552,20 +552,26 @@ cudaError_t configure_kernels() {
   return e;
 }
 
+void* tensor_map_encoder() {
+  static void* fn = nullptr;
+  if (fn == nullptr) {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || f == nullptr) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    fn = f;
+  }
+  return fn;
+}
+
 bool make_grid_tensor_map(CUtensorMap* m, const void* base, const Geo& g, long long slots,
                           bool bf16, int coil_chunk) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (encode == nullptr) {
-    cudaDriverEntryPointQueryResult q;
-    void* fn = nullptr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || fn == nullptr) {
-      cudaGetLastError();
-      return false;
-    }
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+  const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+  if (encode == nullptr) return false;
   const cuuint64_t esz = bf16 ? 4 : 8;
   // x innermost; strides in bytes for dimensions 1..3 (multiples of 16)
   const cuuint64_t dims[4] = {cuuint64_t(g.g2), cuuint64_t(g.g1), cuuint64_t(g.g0),

@@ -245,6 +245,8 @@ int launch_interp_kspace(const Geo& g, int W, const KernelCoefs& kc, int C, cons
                          cudaStream_t s, long long poll_limit = -1);
 // Tensor map of `slots` consecutive coil grids at base ([slot][G0][G1][G2]
 // values) with a halo box of 12 x 11 x 11 values x coil_chunk grids.
+// cuTensorMapEncodeTiled through the runtime's driver entry point (null if unavailable)
+void* tensor_map_encoder();
 bool make_grid_tensor_map(CUtensorMap* m, const void* base, const Geo& g, long long slots,
                           bool bf16, int coil_chunk);
 // one-time kernel attributes (large dynamic shared memory); plan time

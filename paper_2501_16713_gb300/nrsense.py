@@ -140,6 +140,8 @@ _SIGS = {
                             _VP],
     "nrsense_plan_set_reduce": [_VP, _VP, _VP],
     "nrsense_copy_c64": [_VP, _VP, ctypes.c_int64, _VP],
+    "nrsense_cnn_set_conv": [_VP, ctypes.c_int32],
+    "nrsense_cnn_device_status": [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _VP],
     "nrsense_set_deflation": [_VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _VP],
     "nrsense_deflation_from_solve": [_VP, _VP, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
@@ -940,4 +942,16 @@ class Cnn:
     def launches(self):
         v = ctypes.c_int64()
         _check(self.lib.nrsense_cnn_launches(self._h, ctypes.byref(v)), "nrsense_cnn_launches")
+        return v.value
+
+    def set_conv(self, tcgen05):
+        """Convolutions on the tcgen05 tensor cores (True) or mma.sync (False)
+        (nrsense_cnn_set_conv)."""
+        _check(self.lib.nrsense_cnn_set_conv(self._h, 1 if tcgen05 else 0), "nrsense_cnn_set_conv")
+
+    def device_status(self, clear=True, stream=None):
+        """The network's device status word (nrsense_cnn_device_status)."""
+        v = ctypes.c_int32()
+        _check(self.lib.nrsense_cnn_device_status(self._h, int(bool(clear)), ctypes.byref(v),
+                                                  _stream(stream)), "nrsense_cnn_device_status")
         return v.value

@@ -296,3 +296,36 @@ def test_symmetric_gradients_match_oracle():
             print(f"  layer {l}: dW rel {ew:.2e}")
             assert ew < TOL_GRAD, (energy, l)
     plan.close()
+
+
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_tcgen05_convolutions_match_mma_sync_and_oracle(symmetric):
+    """The convolutions on the fifth-generation tensor cores (accumulators in
+    tensor memory, one thread issuing the products) against the mma.sync
+    kernels and the oracle: the same FP32 sums in another order, so the output
+    agrees with the mma.sync path to about one BF16 ulp on a few stored values
+    and meets the oracle tolerances; ragged blocks on every axis; bitwise
+    reproducible; the device status word stays clear."""
+    p = _nobias(_params(21)) if symmetric else _params(21)
+    net = _net(p, symmetric=symmetric)
+    r = _field(22)
+    import torch
+    z_mma = net.apply(to_dev(r)).cpu().numpy()
+    net.set_conv(True)
+    out = torch.full(SHAPE, float("nan"), dtype=torch.complex64, device="cuda")
+    z_tc = net.apply(to_dev(r), out=out).cpu().numpy()  # every voxel written
+    assert np.all(np.isfinite(z_tc))
+    assert net.device_status() == 0
+    assert np.array_equal(net.apply(to_dev(r)).cpu().numpy(), z_tc)
+    r64 = r.astype(np.complex128)
+    u0 = r64 / R.input_scale(r64)
+    e = rel_l2(z_tc - u0, z_mma - u0)
+    fwd = R.forward_spd if symmetric else R.forward
+    z_em, _ = fwd(_bf16_weights(p), r64, rnd=R.bf16_round)
+    e_em = rel_l2(z_tc - u0, z_em - u0)
+    print(f"tcgen05 vs mma.sync: o rel L2 {e:.2e}; vs oracle (emulated rounding) {e_em:.2e}")
+    assert e < (TOL_EMULATED_SYM if symmetric else TOL_EMULATED)
+    assert e_em < (TOL_EMULATED_SYM if symmetric else TOL_EMULATED)
+    net.set_conv(False)
+    assert np.array_equal(net.apply(to_dev(r)).cpu().numpy(), z_mma)
+    net.close()
