@@ -430,9 +430,13 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   return r;
 }
 
+// x = hi + lo: hi = x rounded to TF32; the remainder x - hi is exact in FP32
+// and goes to the tensor core as it is (no second rounding: one instruction
+// less per operand element), which uses its TF32 part, within 2^-10 of it,
+// i.e. within 2^-21 of x.
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
   hi = tf32_rna(x);
-  lo = tf32_rna(x - __uint_as_float(hi));
+  lo = __float_as_uint(x - __uint_as_float(hi));
 }
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
