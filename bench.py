@@ -698,6 +698,82 @@ FISTA_TAU = 1e-3      # lambda / L: threshold at 1e-3 of the unit peak image int
 FISTA_STEP_BYTES = 48  # per voxel: read z, E0 z, b, x_{k-1}; write x_k, z_{k+1} (complex64)
 
 
+def run_cnn128(args):
+    """The learned preconditioner's network at 128^3 (the image of the default
+    workload): one application z = N(r) of the symmetric form (10 convolutions)
+    and of the plain form (5 convolutions), each with the mma.sync and the
+    tcgen05 convolution kernels, timed with CUDA events around `steps`
+    applications after the warm-up; the two kernels must give bitwise the same
+    z.  The roofline is the tensor-core one: algorithmic FLOPs of the real
+    channel counts (2 -> 16 -> 16 -> 16 -> 16 -> 2) over the measured time."""
+    import torch
+
+    from paper_2501_16713_gb300 import Cnn, build
+
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    shape = (128, 128, 128)
+    nvox = shape[0] * shape[1] * shape[2]
+    gen = torch.Generator(device=dev).manual_seed(8)
+    r = torch.randn(shape, dtype=torch.complex64, device=dev, generator=gen)
+    # MACs per voxel of one plain pass: 27 taps x (2x16 + 3 x 16x16 + 16x2)
+    macs_plain = 27 * (2 * 16 + 3 * 16 * 16 + 16 * 2)
+    s = torch.cuda.current_stream()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(vis.split(",")[0] if vis else "0")
+    clocks.start()
+    time.sleep(0.3)
+    res, launches = {}, 0
+    for symmetric in (True, False):
+        net = Cnn(shape, seed=1, symmetric=symmetric)
+        outs = {}
+        for tc in (False, True):
+            net.set_conv(tc)
+            z = torch.empty_like(r)
+            for _ in range(args.warmup):
+                net.apply(r, z)
+            torch.cuda.synchronize()
+            l0 = net.launches()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(args.steps):
+                net.apply(r, z)
+            e1.record(s)
+            torch.cuda.synchronize()
+            launches += net.launches() - l0
+            ms = e0.elapsed_time(e1) / args.steps
+            flops = 2.0 * macs_plain * nvox * (2 if symmetric else 1)
+            res[("symmetric" if symmetric else "plain", "tcgen05" if tc else "mma_sync")] = (
+                ms, flops / (ms * 1e-3) / 1e12)
+            outs[tc] = z.clone()
+        if not torch.equal(outs[False], outs[True]):
+            raise RuntimeError("tcgen05 and mma.sync convolutions differ")
+        if net.device_status() != 0:
+            raise RuntimeError("network kernels reported a device error")
+        net.close()
+    clk = clocks.stop()
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks["bf16_tflops"])
+    best = min(res, key=lambda k: res[k][0] if k[0] == "symmetric" else 1e30)
+    ms, tf = res[best]
+    return {"metric": "network applications/s (symmetric form, 128^3)", "value": 1000.0 / ms,
+            "unit": "applications/s", "higher_is_better": True, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 (fp32 accumulation)", "data": "synthetic",
+            "config": {"workload": "cnn128", "image": list(shape),
+                       "channels": "2-16-16-16-16-2", "kernel": "3x3x3",
+                       "l2": "activations 64 MB per layer at 128^3 (16 BF16 channels); no flush"},
+            "ms": {f"{f}/{k}": round(v[0], 4) for (f, k), v in res.items()},
+            "tflops": {f"{f}/{k}": round(v[1], 1) for (f, k), v in res.items()},
+            "roofline": {"kernel": "conv3d (" + best[1] + ")", "bound": "tensor",
+                         "achieved": round(tf, 1), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(tf / peak, 4),
+                         "peak_source": f"{peak_kind} MEASURED_PEAKS.json bf16_tflops",
+                         "traffic": None},
+            "gpu_launches": int(launches), "clocks": clk}
+
+
 def run_fista128(args):
     """Wavelet-FISTA on the 128^3, 8-coil, 4-phase workload (the default E
     workload): 400 iterations of the fused FISTA step (gradient step, 4-level
@@ -1324,7 +1400,7 @@ def main():
     special = {"precond128": run_precond, "cgsweep128": run_cgsweep128, "cg192": run_cg192,
                "sweep256": run_sweep256,
                "fista128": run_fista128, "fista_warp192": run_fista_warp192,
-               "motion64": run_motion64}
+               "motion64": run_motion64, "cnn128": run_cnn128}
     if args.workload in special and args.impl == "ours":
         if int(os.environ.get("RANK", "0")) == 0:
             print(json.dumps(special[args.workload](args)), flush=True)
@@ -1338,7 +1414,7 @@ def main():
         # the oracle on the host cores; rank 0 only
         if rank != 0:
             return
-        if args.workload in ("precond128", "cgsweep128", "fista_warp192", "motion64"):
+        if args.workload in ("precond128", "cgsweep128", "fista_warp192", "motion64", "cnn128"):
             print(json.dumps({"impl": "reference", "unavailable":
                               f"the {args.workload} workload has no CPU reference arm"}))
             return

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) interp_image_kernel(Geo g, KernelCoefs kc
     int x2[W];
 #pragma unroll
     for (int t = 0; t < W; ++t) x2[t] = wrap_once(b2 + t, g.g2);
-    float ar = 0.f, ai = 0.f;
+    float2 aw = make_float2(0.f, 0.f);
 #pragma unroll
     for (int t0 = 0; t0 < W; ++t0) {
       const long long row0 = (long long)wrap_once(b0 + t0, g.g0) * g.g1;
@@ -128,18 +128,16 @@ __global__ void __launch_bounds__(256) interp_image_kernel(Geo g, KernelCoefs kc
       for (int t1 = 0; t1 < W; ++t1) {
         const float w01 = w0[t0] * w1[t1];
         const float2* rowp = u + (row0 + wrap_once(b1 + t1, g.g1)) * g.g2;
-        float rr = 0.f, ri = 0.f;
+        float2 rw = make_float2(0.f, 0.f);
 #pragma unroll
         for (int t2 = 0; t2 < W; ++t2) {
           const float2 v = __ldg(rowp + x2[t2]);
-          rr = fmaf(w2[t2], v.x, rr);
-          ri = fmaf(w2[t2], v.y, ri);
+          rw = __ffma2_rn(make_float2(w2[t2], w2[t2]), v, rw);  // each part as fmaf
         }
-        ar = fmaf(w01, rr, ar);
-        ai = fmaf(w01, ri, ai);
+        aw = __ffma2_rn(make_float2(w01, w01), rw, aw);
       }
     }
-    m[(long long)j * g.nvox + idx] = make_float2(ar, ai);
+    m[(long long)j * g.nvox + idx] = aw;
   }
 }
 

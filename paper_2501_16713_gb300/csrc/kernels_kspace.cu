@@ -413,17 +413,16 @@ __global__ void __launch_bounds__(256, CC == 2 ? 6 : CC == 4 ? 4 : 1) interp_tma
         for (int t1 = 0; t1 < W; ++t1) {
           const float w = w02 * w1[t1];
           const float2 v = grid_ld_shared(base + (t0 * H + t1) * XP);
-          acc.x = fmaf(w, v.x, acc.x);
-          acc.y = fmaf(w, v.y, acc.y);
+          // real and imaginary part in one paired FMA (each part rounded as fmaf)
+          acc = __ffma2_rn(make_float2(w, w), v, acc);
         }
       }
     }
     // reduce over tap x (lanes CC apart within the group)
 #pragma unroll
-    for (int off = CC; off < LPS; off <<= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-    }
+    for (int off = CC; off < LPS; off <<= 1)
+      acc = __fadd2_rn(acc, make_float2(__shfl_xor_sync(0xffffffffu, acc.x, off),
+                                        __shfl_xor_sync(0xffffffffu, acc.y, off)));
     if (live && txl == 0 && coil0 + c < C) y[(row0 + row) * C + coil0 + c] = acc;
   }
 }

@@ -129,13 +129,13 @@ __global__ void __launch_bounds__(32 * kHWarps, 2)
         const float4 meta = *reinterpret_cast<const float4*>(&d.off);
         const float2 wzp = *reinterpret_cast<const float2*>(&d.wz[2 * tz]);
         const float wyx = d.wy[ty] * d.wx[tx];
-        const float wa = wzp.x * wyx, wb = wzp.y * wyx;
+        const float2 wab = __fmul2_rn(wzp, make_float2(wyx, wyx));
+        const float2 vv = make_float2(meta.y, meta.z);
         float2* a = acc + __float_as_int(meta.x) + lane_off;
         float2 ca = a[0], cb = a[2 * kHA * kHAX];
-        ca.x = fmaf(wa, meta.y, ca.x);
-        ca.y = fmaf(wa, meta.z, ca.y);
-        cb.x = fmaf(wb, meta.y, cb.x);
-        cb.y = fmaf(wb, meta.z, cb.y);
+        // paired FMAs: each part rounded as fmaf
+        ca = __ffma2_rn(make_float2(wab.x, wab.x), vv, ca);
+        cb = __ffma2_rn(make_float2(wab.y, wab.y), vv, cb);
         a[0] = ca;
         a[2 * kHA * kHAX] = cb;
       }
@@ -337,24 +337,22 @@ __global__ void __launch_bounds__(256) interp_home_kernel(Geo g, KernelCoefs kc,
     kernel_weights<4>(q.y, kc, w1);
     kernel_weights<4>(q.z, kc, w2);
     const float2* base = reg + ((b0 - o0) * kHR + (b1 - o1)) * kHR + (b2 - o2);
-    float ar = 0.f, ai = 0.f;
+    float2 aw = make_float2(0.f, 0.f);
 #pragma unroll
     for (int t0 = 0; t0 < 4; ++t0)
 #pragma unroll
       for (int t1 = 0; t1 < 4; ++t1) {
         const float w01 = w0[t0] * w1[t1];
         const float2* rowp = base + (t0 * kHR + t1) * kHR;
-        float rr = 0.f, ri = 0.f;
+        float2 rw = make_float2(0.f, 0.f);
 #pragma unroll
         for (int t2 = 0; t2 < 4; ++t2) {
           const float2 v = rowp[t2];
-          rr = fmaf(w2[t2], v.x, rr);
-          ri = fmaf(w2[t2], v.y, ri);
+          rw = __ffma2_rn(make_float2(w2[t2], w2[t2]), v, rw);  // each part as fmaf
         }
-        ar = fmaf(w01, rr, ar);
-        ai = fmaf(w01, ri, ai);
+        aw = __ffma2_rn(make_float2(w01, w01), rw, aw);
       }
-    m[row] = make_float2(ar, ai);
+    m[row] = aw;
   }
 }
 
