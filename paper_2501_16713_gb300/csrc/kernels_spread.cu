@@ -614,7 +614,7 @@ struct CubeStage {
 static_assert(sizeof(CubeStage) == 144, "staging record");
 
 template <typename GT, int WPC>
-__global__ void __launch_bounds__(32 * WPC, WPC == 4 ? 6 : 16 / WPC) spread_coils_cube_kernel(
+__global__ void __launch_bounds__(32 * WPC, 24 / WPC) spread_coils_cube_kernel(
     Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
     GT* __restrict__ grids, float2* __restrict__ scratch) {
   constexpr int CC = 8, W = 4, T = 8, B = 32;
