@@ -614,14 +614,19 @@ struct CubeStage {
 static_assert(sizeof(CubeStage) == 144, "staging record");
 
 template <typename GT, int WPC>
-__global__ void __launch_bounds__(32 * WPC, 24 / WPC) spread_coils_cube_kernel(
+__global__ void __launch_bounds__(32 * WPC, 28 / WPC) spread_coils_cube_kernel(
     Geo g, KernelCoefs kc, int C, TilePlan tp, PhaseTable pt, const float2* __restrict__ vals,
     GT* __restrict__ grids, float2* __restrict__ scratch) {
   constexpr int CC = 8, W = 4, T = 8, B = 32;
   static_assert(WPC == 1 || WPC == 2 || WPC == 4, "warps per CTA");
   __shared__ __align__(16) CubeStage stg_all[WPC][B];
+  // per warp: starts of runs 1-3 in the sub-block's sequence, and for each
+  // run the list index minus the sequence position (kept in shared memory,
+  // not registers: they are read once per batch)
+  __shared__ int run_all[WPC][8];
   const int warp = int(threadIdx.x >> 5);
   CubeStage* stg = stg_all[warp];
+  int* run = run_all[warp];
   const int block_id = int(blockIdx.x) * WPC + warp;
 
   const ItemRef ir = item_ref(pt, block_id >> 3);
@@ -648,15 +653,24 @@ __global__ void __launch_bounds__(32 * WPC, 24 / WPC) spread_coils_cube_kernel(
     // the four runs (classes 9 cz + 3 cy + {bx, bx + 1}, cz in {bz, bz + 1},
     // cy in {by, by + 1}) and their prefix sums
     const int32_t* cb = pt.cbins[ir.jj] + (long long)ir.local * kCubeBins;
-    int rs[4], pre[5];
-    pre[0] = 0;
+    int total = 0;
+    if (lane < 4) {
+      const int c = 9 * (bz + (lane >> 1)) + 3 * (by + (lane & 1)) + bx;
+      const int rs = __ldg(cb + c), len = __ldg(cb + c + 2) - rs;
+      // inclusive prefix of the four run lengths over lanes 0-3
+      int incl = len;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int c = 9 * (bz + (r >> 1)) + 3 * (by + (r & 1)) + bx;
-      rs[r] = __ldg(cb + c);
-      pre[r + 1] = pre[r] + (__ldg(cb + c + 2) - rs[r]);
+      for (int d = 1; d < 4; d <<= 1) {
+        const int t = __shfl_up_sync(0xfu, incl, d, 4);
+        if (lane >= d) incl += t;
+      }
+      const int start = incl - len;
+      if (lane > 0) run[lane - 1] = start;
+      run[4 + lane] = it.begin + rs - start;
+      total = incl;
     }
-    const int total = pre[4];
+    total = __shfl_sync(0xffffffffu, total, 3);
+    __syncwarp();
     // 16-byte value loads when every staged row segment is 16-byte aligned
     const bool vec_vals = (C & 1) == 0 && coil0 + CC <= C &&
                           (reinterpret_cast<uintptr_t>(vals) & 15) == 0;
@@ -664,10 +678,8 @@ __global__ void __launch_bounds__(32 * WPC, 24 / WPC) spread_coils_cube_kernel(
       const int n = min(B, total - base);
       if (lane < n) {
         const int i = base + lane;
-        const int r = (i >= pre[1]) + (i >= pre[2]) + (i >= pre[3]);
-        const int rsr = r == 0 ? rs[0] : r == 1 ? rs[1] : r == 2 ? rs[2] : rs[3];
-        const int prr = r == 0 ? pre[0] : r == 1 ? pre[1] : r == 2 ? pre[2] : pre[3];
-        const int2 e = __ldg(list + it.begin + rsr + (i - prr));
+        const int r = (i >= run[0]) + (i >= run[1]) + (i >= run[2]);
+        const int2 e = __ldg(list + i + run[4 + r]);
         const float4 qq = __ldg(qs + e.x);
         int b0, b1, b2;
         unpack_base(__float_as_uint(qq.w), b0, b1, b2);
