@@ -720,6 +720,7 @@ __global__ void __launch_bounds__(32 * WPC, 28 / WPC) spread_coils_cube_kernel(
         float pyx[2][2];
         int rz[2];
         const CubeStage* dj[2];
+        unsigned planes = 0;  // m-tiles (z planes) the lane's two points reach
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int k = 8 * ks + q + 4 * j;
@@ -728,6 +729,8 @@ __global__ void __launch_bounds__(32 * WPC, 28 / WPC) spread_coils_cube_kernel(
           dj[j] = &d;
           const int4 rr = *reinterpret_cast<const int4*>(&d.r0);
           rz[j] = rr.x;
+          // z taps rz .. rz + 3 meet planes max(rz, 0) .. min(rz + 3, 3)
+          if (live) planes |= rr.x >= 0 ? (0xFu << min(rr.x, 4)) & 0xFu : 0xFu >> min(-rr.x, 4);
           const int tx = (gq & 3) - rr.z;
           const float wxv = (live && (unsigned)tx < (unsigned)W) ? d.wx[tx & (W - 1)] : 0.f;
           const int ty0 = (gq >> 2) - rr.y, ty1 = ty0 + 2;
@@ -743,8 +746,14 @@ __global__ void __launch_bounds__(32 * WPC, 28 / WPC) spread_coils_cube_kernel(
             const float2 v = k < n ? stg[k].val[4 * nt + (gq >> 1)] : make_float2(0.f, 0.f);
             split_tf32((gq & 1) ? v.y : v.x, bh[nt][j], bl[nt][j]);
           }
+        // an m-tile none of the k-step's eight points reaches has all-zero A
+        // entries and would add exact zeros: skipped (warp-uniform).  The
+        // plan keeps every footprint-class run in first-tap z order, so the
+        // points of a k-step mostly share their planes.
+        planes = __reduce_or_sync(0xffffffffu, planes);
 #pragma unroll
         for (int mt = 0; mt < 4; ++mt) {
+          if (!(planes & (1u << mt))) continue;
           float a[2][2];
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
