@@ -159,7 +159,7 @@ __device__ __forceinline__ void stage_halo(const Vol& v, const bf16* __restrict_
 // A = activations (M = 16 voxels of one row, K = 16 channels), B = weights
 // (K = channels, N = 8 output channels): per tap one K step.  Warp w owns
 // z plane w/2, rows 4(w%2) .. 4(w%2)+3 of the block: 4 m-tiles x 2 n-tiles.
-__global__ void __launch_bounds__(kConvThreads) conv3d_kernel(ConvArgs a) {
+__global__ void __launch_bounds__(kConvThreads, 3) conv3d_kernel(ConvArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   bf16* sx = reinterpret_cast<bf16*>(smem_raw);  // [kHalo][kVS]
   bf16* sw = sx + kHalo * kVS;                    // [27 * 16][kVS]
@@ -1115,6 +1115,9 @@ nrsense_status nrsense_cnn_create(const int32_t* n_host, uint32_t flags, void* s
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device) != cudaSuccess ||
       cudaFuncSetAttribute(conv3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kConvSmem) != cudaSuccess ||
+      // three CTAs of 72.6 KB per SM need the largest shared-memory carveout
+      cudaFuncSetAttribute(conv3d_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           int(cudaSharedmemCarveoutMaxShared)) != cudaSuccess ||
       cudaFuncSetAttribute(conv3d_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kTcSmem) != cudaSuccess ||
       cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
