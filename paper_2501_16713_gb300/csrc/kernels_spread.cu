@@ -605,6 +605,11 @@ __global__ void __launch_bounds__(32 * WPC, WPC == 4 ? 5 : 16 / WPC) spread_coil
 // fall by 29 %.  Rows m = 16 z + 4 y + x of the sub-block (z, y, x in 0..3):
 // lane (g, q) holds x = g % 4 with y = g / 4 (row g) and y + 2 (row g + 8) for
 // every m-tile z.  Columns and the TF32 split are those of the plane kernel.
+// A k-step skips the m-tiles none of its eight points reaches (the runs are in
+// first-tap z order, so neighbouring points mostly share their z planes).  The
+// launch bound of 28 warps per SM holds the kernel at 72 registers; with one
+// warp per CTA (the usual choice) a CTA's slot frees as soon as its sub-block
+// is done, whatever the other sub-blocks' point counts.
 struct CubeStage {
   float wz[4], wy[4], wx[4];
   int r0, r1, r2, pad0;  // first tap relative to the sub-block origin, in [-3, 3]
