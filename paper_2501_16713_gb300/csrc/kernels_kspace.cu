@@ -268,6 +268,8 @@ __global__ void __launch_bounds__(256, CC == 2 ? 6 : CC == 4 ? 4 : 1) interp_tma
   GT* halo = reinterpret_cast<GT*>(reinterpret_cast<unsigned char*>(smem_raw) +
                                    ((128u - (raw & 127u)) & 127u));  // [CC][H][H][XP]
   __shared__ float s_coef[W][kNumCoef];
+  // per warp and sample slot: the sample's tap weights of axes 0, 1, 2 (CC >= 4)
+  __shared__ __align__(16) float4 s_wrec[8][CC >= 4 ? SPW : 1][3];
   __shared__ __align__(8) unsigned long long mbar;
   const int jj = phase_of(pt.item0, pt.nphase, blockIdx.x);
   const SpreadItem it = pt.items[jj][blockIdx.x - pt.item0[jj]];
@@ -371,19 +373,30 @@ __global__ void __launch_bounds__(256, CC == 2 ? 6 : CC == 4 ? 4 : 1) interp_tma
     // kernel weights of the sample: axis a at tap t
     float w0[W], w1[W], w2t;
     if constexpr (CC >= 4) {
-      // lane (txl, c) evaluates axis min(c, 2) at tap txl; the others take
-      // it by shuffle (the same values as evaluating all three here)
+      // lane (txl, c) evaluates axis min(c, 2) at tap txl; lanes c <= 2 put
+      // their value in the sample's weight record in shared memory and every
+      // lane reads the taps it needs (three broadcast loads: shuffles would
+      // take nine passes of the shared-memory data path the tap reads use;
+      // the same values as evaluating all three here)
       const float f = c == 0 ? qv.x : (c == 1 ? qv.y : qv.z);
       const float sf = fmaf(2.f, f, -1.f);
       float a = cf[kNumCoef - 1];
 #pragma unroll
       for (int k = kNumCoef - 2; k >= 0; --k) a = fmaf(a, sf, cf[k]);
-#pragma unroll
-      for (int t = 0; t < W; ++t) {
-        w0[t] = __shfl_sync(0xffffffffu, a, gbase + t * CC);
-        w1[t] = __shfl_sync(0xffffffffu, a, gbase + t * CC + 1);
-      }
-      w2t = __shfl_sync(0xffffffffu, a, gbase + txl * CC + 2);
+      float4* sw = s_wrec[warp][active_lane ? grp : 0];
+      __syncwarp();  // the previous sample's record has been read
+      if (active_lane && c <= 2) reinterpret_cast<float*>(&sw[c])[txl] = a;
+      __syncwarp();
+      const float4 v0 = sw[0], v1 = sw[1];
+      w0[0] = v0.x;
+      w0[1] = v0.y;
+      w0[2] = v0.z;
+      w0[3] = v0.w;
+      w1[0] = v1.x;
+      w1[1] = v1.y;
+      w1[2] = v1.z;
+      w1[3] = v1.w;
+      w2t = reinterpret_cast<const float*>(&sw[2])[txl];
     } else {
       // this lane's tap txl on each axis
       const float s0f = fmaf(2.f, qv.x, -1.f), s1f = fmaf(2.f, qv.y, -1.f),
